@@ -1,0 +1,156 @@
+/*
+ * librtcc3 -- real-time CC3 (RT-CC3) approximate-triples hot path on one GPU.
+ *
+ * The library evaluates, for a closed-shell molecule in a time-dependent
+ * electric field, the right-hand sides of the RT-CC3 equations of motion
+ *
+ *     i dt_mu/dt      = <mu| H + [H,T2] + [H,T3] (+ 1/2[[H,T2],T2]) |0>     (Eqs. 2, A10-A11)
+ *    -i dlambda_mu/dt = dL_CC3/dt_mu                                      (Eqs. 3, A13-A14)
+ *
+ * where H is the T1-transformed Hamiltonian (Eq. 8, Eq. A4), the triples t3
+ * solve their stationarity condition (Eq. 4 / Eq. A12 with dt3/dt = 0) and
+ * L_CC3 is the CC3 Lagrangian of Eq. A6, and propagates (t1, t2, lambda1,
+ * lambda2) with classical fourth-order Runge-Kutta, returning the dipole
+ * moment sum_pq D_pq mu_pq (D the one-electron density, dL/dV) and the
+ * energy <0|H + [H,T2]|0> - E_ref (Eq. A8) at every step.
+ *
+ * Conventions
+ *   - nocc occupied and nvir virtual spatial orbitals, nmo = nocc + nvir,
+ *     occupied first; canonical reference with orbital energies eps (Eq. A2).
+ *   - two-electron integrals are density fitted: (pq|rs) = sum_P L[P][p][q] L[P][r][s]
+ *     (chemists' order; the paper's <pq|rs> is (pr|qs)).
+ *   - the field couples as V = -E(t) . mu (Eq. 10).
+ *   - complex numbers are interleaved (re, im) pairs of double (C99
+ *     "double _Complex" compatible), row-major arrays:
+ *       t1[i][a] = t_i^a, t2[i][j][a][b] = t_ij^ab (= t_ji^ba),
+ *       l1[i][a] = lambda_a^i, l2[i][j][a][b] = lambda_ab^ij,
+ *     with the Lagrangian normalised as L = E + sum l1 R1 + 1/2 sum l2 R2.
+ *
+ * Errors: every call returns RTCC3_OK (0) or a negative status; no exception
+ * or abort crosses the ABI.  rtcc3_last_error() returns a message for the last
+ * failing call on a context.  A context is used by one host thread at a time.
+ * Host buffers passed in are copied; the caller keeps ownership.
+ */
+#ifndef RTCC3_H
+#define RTCC3_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTCC3_OK 0
+#define RTCC3_ERR_ARG (-1)           /* invalid argument or size */
+#define RTCC3_ERR_OOM (-2)           /* device allocation failed */
+#define RTCC3_ERR_CUDA (-3)          /* CUDA runtime error */
+#define RTCC3_ERR_NONFINITE (-4)     /* NaN/Inf appeared in the propagated state */
+#define RTCC3_ERR_TIMEOUT (-5)       /* a bounded device wait gave up */
+#define RTCC3_ERR_NOT_CONVERGED (-6) /* ground-state iterations did not converge */
+#define RTCC3_ERR_STATE (-7)         /* call out of order (e.g. no Hamiltonian set) */
+
+/* Arithmetic of the residual evaluation.  The RK4 state, its update, the
+ * orbital-energy divisions and the dipole/energy reductions are FP64 in every
+ * mode. */
+#define RTCC3_PREC_FP64 0 /* complex128 throughout */
+#define RTCC3_PREC_FP32 1 /* complex64 residual graph on CUDA cores */
+#define RTCC3_PREC_TF32 2 /* complex64 graph, triples contractions on tcgen05 TF32 */
+#define RTCC3_PREC_BF16 3 /* complex64 graph, triples contractions on tcgen05 BF16 */
+
+#define RTCC3_FIELD_NONE 0
+#define RTCC3_FIELD_STATIC 1 /* E(t) = A                                   */
+#define RTCC3_FIELD_COS 2    /* E(t) = A cos(omega t)                (Eq. 14) */
+#define RTCC3_FIELD_GAUSS 3  /* E(t) = A exp(-(t - c)^2 / (2 w^2))   (Eq. 32) */
+
+typedef struct rtcc3_ctx rtcc3_ctx;
+
+typedef struct rtcc3_options {
+  int precision;     /* RTCC3_PREC_*                                          */
+  int triples;       /* 1: CC3 (default); 0: CCSD only                       */
+  int device;        /* CUDA device ordinal                                  */
+  int use_graphs;    /* 1: capture one RK4 step as a CUDA graph and replay   */
+  double field_tol;  /* target relative error of the field-coupled triples
+                        fixed point (0: 1e-14 in FP64, 1e-8 otherwise)       */
+} rtcc3_options;
+
+/* Fill *opt with defaults (FP64, triples on, device 0, graphs on). */
+void rtcc3_default_options(rtcc3_options* opt);
+
+/* Create a context for nbatch independent propagations (field slots).
+ * nocc >= 1, nvir >= 1, 1 <= nbatch <= 64.  *out receives the handle. */
+int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3_ctx** out);
+/* Release all device memory of the context.  NULL is accepted. */
+int rtcc3_destroy(rtcc3_ctx* ctx);
+const char* rtcc3_last_error(const rtcc3_ctx* ctx);
+
+/* Hamiltonian (Eqs. A1-A3): eps[nmo] canonical orbital energies, Lfac[naux][nmo][nmo]
+ * real DF factors symmetric in (p,q), dipole[3][nmo][nmo] real symmetric.  The
+ * core operator is h = diag(eps) - G[D_ref], G_pq = sum_k 2(pq|kk) - (pk|kq),
+ * so the reference is a canonical Hartree-Fock determinant.  Resets all slots
+ * to zero amplitudes and time 0. */
+int rtcc3_set_hamiltonian(rtcc3_ctx* ctx, const double* eps, int naux, const double* Lfac,
+                          const double* dipole);
+
+/* Field of slot b (0 <= b < nbatch): kind RTCC3_FIELD_*, amplitude A (au),
+ * omega, center, width (au) and a Cartesian direction dir[3]. */
+int rtcc3_set_field(rtcc3_ctx* ctx, int b, int kind, double amplitude, double omega,
+                    double center, double width, const double* dir);
+
+/* Amplitudes of slot b (host, interleaved complex; layouts above).  Any of
+ * the pointers may be NULL on get. */
+int rtcc3_set_amplitudes(rtcc3_ctx* ctx, int b, const double* t1, const double* t2,
+                         const double* l1, const double* l2);
+int rtcc3_get_amplitudes(const rtcc3_ctx* ctx, int b, double* t1, double* t2, double* l1,
+                         double* l2);
+/* Simulation time of the context (shared by all slots). */
+int rtcc3_set_time(rtcc3_ctx* ctx, double time);
+int rtcc3_get_time(const rtcc3_ctx* ctx, double* time);
+
+/* One residual evaluation (one RK4 stage) of slot b at the given time:
+ * r_t1, r_t2 = T residuals (Eqs. A10-A11), r_l1, r_l2 = lambda residuals
+ * (Eqs. A13-A14), energy[2] (complex), dipole[6] (3 complex components).
+ * Any output pointer may be NULL. */
+int rtcc3_compute_residuals(rtcc3_ctx* ctx, int b, double time, double* r_t1, double* r_t2,
+                            double* r_l1, double* r_l2, double* energy, double* dipole);
+
+/* Zero-field ground state by Jacobi iterations t <- t - R/D, then lambda,
+ * until max|R| < tol; copies the result to every slot and sets time 0. */
+int rtcc3_solve_ground_state(rtcc3_ctx* ctx, double tol, int maxiter);
+
+/* Advance every slot nsteps RK4 steps of size h (stage times t, t+h/2,
+ * t+h/2, t+h).  dipole: nbatch x (nsteps+1) x 3 complex, energy: nbatch x
+ * (nsteps+1) complex (either may be NULL); entry n is evaluated from the
+ * state at t0 + n h.  Returns RTCC3_ERR_NONFINITE if the state became
+ * non-finite (the state is then left at the failing step). */
+int rtcc3_propagate_rk4(rtcc3_ctx* ctx, double h, int nsteps, double* dipole, double* energy);
+
+/* As above with DEVICE output buffers (double2 layout as above), on the CUDA
+ * stream `stream` (cudaStream_t, may be NULL for the context stream).  The
+ * call returns after the work is enqueued and the stream synchronised. */
+int rtcc3_propagate_rk4_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_dev,
+                            void* energy_dev, void* stream);
+
+/* Triples map of slot b's Hamiltonian at `time` (device buffers, interleaved
+ * complex double): (t1, t2) -> (X1, X2), the triples contributions to the T
+ * residuals (Eqs. A21-A22), and its holomorphic vector-Jacobian product
+ * g = u^T J for cotangents (u1, u2) (the lambda-side triples terms, Eqs. A23-A24
+ * when u = (lambda1, lambda2/2)).  Buffers sized o*v and o*o*v*v. */
+int rtcc3_triples_forward_dev(rtcc3_ctx* ctx, int b, double time, const void* t1,
+                              const void* t2, void* x1, void* x2, void* stream);
+int rtcc3_triples_vjp_dev(rtcc3_ctx* ctx, int b, double time, const void* t1, const void* t2,
+                          const void* u1, const void* u2, void* g1, void* g2, void* stream);
+
+/* Checkpoint: FP64 state of all slots plus time and step counter, as a flat
+ * byte image with a version word and checksum.  Query the size with
+ * buf == NULL.  Restoring checks size, version and checksum. */
+int rtcc3_state_size(const rtcc3_ctx* ctx, long long* bytes);
+int rtcc3_get_state(const rtcc3_ctx* ctx, void* buf, long long bytes);
+int rtcc3_set_state(rtcc3_ctx* ctx, const void* buf, long long bytes);
+
+/* Diagnostics: number of kernel launches issued by the last propagate or
+ * compute call, and bytes of device memory reserved by the context. */
+int rtcc3_stats(const rtcc3_ctx* ctx, long long* launches, long long* device_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTCC3_H */

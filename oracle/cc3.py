@@ -370,38 +370,69 @@ def evaluate(ham, t1, t2, l1, l2, w, triples: bool = True, need_lambda: bool = T
 # --------------------------------------------------------------------------
 # Ground state (zero field) and RK4 propagation
 # --------------------------------------------------------------------------
+class DIIS:
+    """Pulay extrapolation over the last ``size`` Jacobi iterates."""
+
+    def __init__(self, size=8):
+        self.size, self.vecs, self.errs = size, [], []
+
+    def __call__(self, x, e):
+        self.vecs.append(x)
+        self.errs.append(e)
+        if len(self.vecs) > self.size:
+            self.vecs.pop(0)
+            self.errs.pop(0)
+        m = len(self.vecs)
+        if m < 2:
+            return x
+        E = torch.stack(self.errs)
+        B = torch.zeros(m + 1, m + 1, dtype=CD)
+        B[:m, :m] = E.conj() @ E.T
+        B[m, :m] = -1.0
+        B[:m, m] = -1.0
+        rhs = torch.zeros(m + 1, dtype=CD)
+        rhs[m] = -1.0
+        c = torch.linalg.solve(B, rhs)[:m]
+        return sum(ci * vi for ci, vi in zip(c, self.vecs))
+
+
+def _jacobi_diis(step_fn, x1, x2, d1, d2, tol, maxiter, label, verbose):
+    """Iterate ``x <- x - R(x)/D`` with DIIS until ``max|R| < tol``."""
+    diis = DIIS()
+    o_v = x1.numel()
+    for it in range(maxiter):
+        r1, r2 = step_fn(x1, x2)
+        err = max(float(r1.abs().max()), float(r2.abs().max()))
+        if verbose:
+            print(label, it, err)
+        if err < tol:
+            return x1, x2
+        e = torch.cat([(-r1 / d1).flatten(), (-r2 / d2).flatten()])
+        x = torch.cat([x1.flatten(), x2.flatten()]) + e
+        x = diis(x, e)
+        x1, x2 = x[:o_v].reshape(x1.shape), x[o_v:].reshape(x2.shape)
+    raise RuntimeError(f'{label} amplitudes did not converge')
+
+
 def solve_ground_state(ham, triples=True, tol=1e-12, maxiter=400, verbose=False):
-    """Jacobi iterations ``t <- t - R/D`` then ``l <- l - R_l/D`` at zero field."""
+    """Zero-field ground state: Jacobi steps ``t <- t - R/D`` (orbital-energy
+    denominators) accelerated by DIIS, first for T then for lambda."""
     o, v, n = ham.o, ham.v, ham.n
     d1, d2 = ham.denominators()
     d1, d2 = d1.to(CD), d2.to(CD)
     w = torch.zeros(n, n, dtype=CD)
-    t1 = torch.zeros(o, v, dtype=CD)
-    t2 = torch.zeros(o, o, v, v, dtype=CD)
-    for it in range(maxiter):
-        r1, r2, _, _ = forward(ham, t1, t2, w, triples, field_on=False)
-        err = max(float(r1.abs().max()), float(r2.abs().max()))
-        if verbose:
-            print('T', it, err)
-        if err < tol:
-            break
-        t1 = t1 - r1 / d1
-        t2 = t2 - r2 / d2
-    else:
-        raise RuntimeError('T amplitudes did not converge')
-    l1 = torch.zeros(o, v, dtype=CD)
-    l2 = torch.zeros(o, o, v, v, dtype=CD)
-    for it in range(maxiter):
-        res = evaluate(ham, t1, t2, l1, l2, w, triples)
-        err = max(float(res.r_l1.abs().max()), float(res.r_l2.abs().max()))
-        if verbose:
-            print('L', it, err)
-        if err < tol:
-            break
-        l1 = l1 - res.r_l1 / d1
-        l2 = l2 - res.r_l2 / d2
-    else:
-        raise RuntimeError('lambda amplitudes did not converge')
+
+    def tstep(x1, x2):
+        r1, r2, _, _ = forward(ham, x1, x2, w, triples, field_on=False)
+        return r1, r2
+    t1, t2 = _jacobi_diis(tstep, torch.zeros(o, v, dtype=CD), torch.zeros(o, o, v, v, dtype=CD),
+                          d1, d2, tol, maxiter, 'T', verbose)
+
+    def lstep(x1, x2):
+        res = evaluate(ham, t1, t2, x1, x2, w, triples)
+        return res.r_l1, res.r_l2
+    l1, l2 = _jacobi_diis(lstep, torch.zeros(o, v, dtype=CD), torch.zeros(o, o, v, v, dtype=CD),
+                          d1, d2, tol, maxiter, 'L', verbose)
     return t1, t2, l1, l2
 
 

@@ -1,0 +1,162 @@
+"""Thin Python binding over the C ABI of librtcc3 (numpy in, numpy out).
+
+Names follow ``include/rtcc3.h``; complex arrays are numpy complex128 in the
+row-major layouts documented there (t1[i,a], t2[i,j,a,b], l1[i,a], l2[i,j,a,b]).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (FIELD_COS, FIELD_GAUSS, FIELD_NONE, FIELD_STATIC, PREC_BF16, PREC_FP32,  # noqa: F401
+                   PREC_FP64, PREC_TF32, RTCC3Error)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _c128(a, shape):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    if a.shape != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+class RTCC3:
+    """One librtcc3 context: ``nbatch`` field slots sharing a Hamiltonian."""
+
+    def __init__(self, nocc: int, nvir: int, nbatch: int = 1, precision: int = PREC_FP64,
+                 triples: bool = True, device: int = 0, use_graphs: bool = True,
+                 field_tol: float = 0.0):
+        self.lib = _lib.load()
+        self.nocc, self.nvir, self.nbatch = nocc, nvir, nbatch
+        opt = _lib.Options()
+        self.lib.rtcc3_default_options(ctypes.byref(opt))
+        opt.precision = precision
+        opt.triples = 1 if triples else 0
+        opt.device = device
+        opt.use_graphs = 1 if use_graphs else 0
+        opt.field_tol = field_tol
+        h = ctypes.c_void_p()
+        rc = self.lib.rtcc3_create(nocc, nvir, nbatch, ctypes.byref(opt), ctypes.byref(h))
+        if rc != 0:
+            raise RTCC3Error(rc, "rtcc3_create failed")
+        self.h = h
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            msg = self.lib.rtcc3_last_error(self.h)
+            raise RTCC3Error(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rtcc3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def shapes(self):
+        o, v = self.nocc, self.nvir
+        return (o, v), (o, o, v, v)
+
+    # -- API ----------------------------------------------------------------
+    def set_hamiltonian(self, eps, Lfac, dipole):
+        n = self.nocc + self.nvir
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        Lfac = np.ascontiguousarray(Lfac, dtype=np.float64)
+        dipole = np.ascontiguousarray(dipole, dtype=np.float64)
+        if eps.shape != (n,) or Lfac.shape[1:] != (n, n) or dipole.shape != (3, n, n):
+            raise ValueError("Hamiltonian arrays have the wrong shape")
+        self._check(self.lib.rtcc3_set_hamiltonian(self.h, _dp(eps), Lfac.shape[0], _dp(Lfac),
+                                                   _dp(dipole)))
+
+    def set_field(self, b, kind, amplitude=0.0, omega=0.0, center=0.0, width=1.0,
+                  direction=(0.0, 0.0, 1.0)):
+        d = np.ascontiguousarray(direction, dtype=np.float64)
+        self._check(self.lib.rtcc3_set_field(self.h, b, kind, amplitude, omega, center, width, _dp(d)))
+
+    def set_amplitudes(self, b, t1=None, t2=None, l1=None, l2=None):
+        s1, s2 = self.shapes
+        arrs = [None if x is None else _c128(x, s) for x, s in ((t1, s1), (t2, s2), (l1, s1), (l2, s2))]
+        self._check(self.lib.rtcc3_set_amplitudes(self.h, b, *[_dp(a) for a in arrs]))
+
+    def get_amplitudes(self, b):
+        s1, s2 = self.shapes
+        out = [np.zeros(s1, np.complex128), np.zeros(s2, np.complex128),
+               np.zeros(s1, np.complex128), np.zeros(s2, np.complex128)]
+        self._check(self.lib.rtcc3_get_amplitudes(self.h, b, *[_dp(a) for a in out]))
+        return tuple(out)
+
+    def set_time(self, t):
+        self._check(self.lib.rtcc3_set_time(self.h, t))
+
+    def get_time(self):
+        t = ctypes.c_double()
+        self._check(self.lib.rtcc3_get_time(self.h, ctypes.byref(t)))
+        return t.value
+
+    def compute_residuals(self, b, time=0.0, lam=True):
+        s1, s2 = self.shapes
+        r = [np.zeros(s1, np.complex128), np.zeros(s2, np.complex128)]
+        rl = [np.zeros(s1, np.complex128), np.zeros(s2, np.complex128)] if lam else [None, None]
+        e = np.zeros(1, np.complex128)
+        dip = np.zeros(3, np.complex128) if lam else None
+        self._check(self.lib.rtcc3_compute_residuals(self.h, b, time, _dp(r[0]), _dp(r[1]), _dp(rl[0]),
+                                                     _dp(rl[1]), _dp(e), _dp(dip)))
+        return {"r_t1": r[0], "r_t2": r[1], "r_l1": rl[0], "r_l2": rl[1], "energy": complex(e[0]),
+                "dipole": dip}
+
+    def solve_ground_state(self, tol=1e-10, maxiter=500):
+        self._check(self.lib.rtcc3_solve_ground_state(self.h, tol, maxiter))
+
+    def propagate_rk4(self, h, nsteps):
+        dip = np.zeros((self.nbatch, nsteps + 1, 3), np.complex128)
+        en = np.zeros((self.nbatch, nsteps + 1), np.complex128)
+        self._check(self.lib.rtcc3_propagate_rk4(self.h, h, nsteps, _dp(dip), _dp(en)))
+        return dip, en
+
+    def propagate_rk4_dev(self, h, nsteps, dip_ptr, en_ptr, stream_ptr=None):
+        self._check(self.lib.rtcc3_propagate_rk4_dev(self.h, h, nsteps, ctypes.c_void_p(dip_ptr),
+                                                     ctypes.c_void_p(en_ptr),
+                                                     ctypes.c_void_p(stream_ptr or 0)))
+
+    def triples_forward_dev(self, b, time, t1_ptr, t2_ptr, x1_ptr, x2_ptr, stream_ptr=None):
+        P = ctypes.c_void_p
+        self._check(self.lib.rtcc3_triples_forward_dev(self.h, b, time, P(t1_ptr), P(t2_ptr), P(x1_ptr),
+                                                       P(x2_ptr), P(stream_ptr or 0)))
+
+    def triples_vjp_dev(self, b, time, t1_ptr, t2_ptr, u1_ptr, u2_ptr, g1_ptr, g2_ptr, stream_ptr=None):
+        P = ctypes.c_void_p
+        self._check(self.lib.rtcc3_triples_vjp_dev(self.h, b, time, P(t1_ptr), P(t2_ptr), P(u1_ptr),
+                                                   P(u2_ptr), P(g1_ptr), P(g2_ptr), P(stream_ptr or 0)))
+
+    def get_state(self) -> bytes:
+        n = ctypes.c_longlong()
+        self._check(self.lib.rtcc3_state_size(self.h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self.lib.rtcc3_get_state(self.h, buf, n.value))
+        return buf.raw
+
+    def set_state(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        self._check(self.lib.rtcc3_set_state(self.h, buf, len(data)))
+
+    def stats(self):
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self.lib.rtcc3_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return {"launches": a.value, "device_bytes": b.value}

@@ -1,0 +1,883 @@
+// C ABI of librtcc3 (include/rtcc3.h): context, Hamiltonian, fields, state,
+// residual evaluation, ground state, RK4 propagation and checkpoints.
+#include "../../include/rtcc3.h"
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "engine.h"
+#include "model.h"
+#include "stage_graph.h"
+
+using namespace rtcc3;
+
+namespace {
+
+struct Base {
+  virtual ~Base() {}
+};
+
+// Everything that depends on the compute precision R.
+template <typename R>
+struct Runner : Base {
+  int o, v, n;
+  cudaStream_t stream;
+  Engine<R> E;
+  Hamil<R> H;
+  Cx<R>* l1s = nullptr;  // stage lambda values (seeds)
+  Cx<R>* l2s = nullptr;
+  std::vector<void*> owned;
+  Runner(int o_, int v_, cudaStream_t s) : o(o_), v(v_), n(o_ + v_), stream(s), E(s) {
+    const size_t n1 = size_t(o) * v;
+    l1s = alloc<Cx<R>>(n1);
+    l2s = alloc<Cx<R>>(n1 * n1);
+  }
+  ~Runner() override {
+    for (void* p : owned) cudaFree(p);
+  }
+  template <typename T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    RTCC3_CUDA(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)));
+    owned.push_back(p);
+    return static_cast<T*>(p);
+  }
+};
+
+}  // namespace
+
+struct rtcc3_ctx {
+  int o = 0, v = 0, n = 0, nb = 0, naux = 0;
+  rtcc3_options opt{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool have_ham = false;
+  std::unique_ptr<Base> runner;
+  // FP64 constants
+  double* eps = nullptr;
+  double* mu = nullptr;
+  std::vector<double> eps_h, mu_h;
+  double e_ref = 0.0;
+  // state: nb slots of [t1, t2, l1, l2] (complex128)
+  size_t n1 = 0, n2 = 0, ny = 0;
+  double2* y = nullptr;
+  double2* acc = nullptr;
+  double2* kbuf = nullptr;
+  double2* res = nullptr;  // FP64 residual export (ny)
+  FieldDev* fdev = nullptr;
+  FieldDev* fnone = nullptr;
+  std::vector<FieldDev> fhost;
+  double* tdev = nullptr;
+  double* teval = nullptr;
+  int* stepdev = nullptr;
+  int* baddev = nullptr;
+  double* maxr = nullptr;
+  double2* dip_traj = nullptr;
+  double2* en_traj = nullptr;
+  size_t traj_cap = 0;
+  double time = 0.0;
+  long long step_total = 0;
+  long long last_launches = 0;
+  std::vector<void*> owned;
+
+  template <typename T>
+  T* dalloc(size_t count) {
+    void* p = nullptr;
+    RTCC3_CUDA(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)));
+    owned.push_back(p);
+    return static_cast<T*>(p);
+  }
+  bool fp64() const { return opt.precision == RTCC3_PREC_FP64; }
+  template <typename R>
+  Runner<R>& run() { return *static_cast<Runner<R>*>(runner.get()); }
+  ~rtcc3_ctx() {
+    runner.reset();
+    if (dip_traj) cudaFree(dip_traj);
+    if (en_traj) cudaFree(en_traj);
+    for (void* p : owned) cudaFree(p);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+int fail(rtcc3_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(rtcc3_ctx* ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->err.clear();
+    return RTCC3_OK;
+  } catch (const Error& e) {
+    return fail(ctx, e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, RTCC3_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(ctx, RTCC3_ERR_CUDA, e.what());
+  }
+}
+
+double frob_block(const std::vector<double>& mu, const double* dir, int n, int r0, int r1, int c0,
+                  int c1) {
+  double s = 0.0;
+  const size_t nn = size_t(n) * n;
+  for (int p = r0; p < r1; ++p)
+    for (int q = c0; q < c1; ++q) {
+      const double m = dir[0] * mu[p * n + q] + dir[1] * mu[nn + p * n + q] + dir[2] * mu[2 * nn + p * n + q];
+      s += m * m;
+    }
+  return std::sqrt(s);
+}
+
+// Fixed-point sweeps of the field-coupled triples equation needed for a
+// relative error below tol: contraction factor rho bounded with Frobenius
+// norms of the field blocks (|t1| <= 1 assumed for the dressing terms).
+int field_sweeps(const rtcc3_ctx* ctx, int b) {
+  const FieldDev& f = ctx->fhost[b];
+  if (f.kind == RTCC3_FIELD_NONE || f.amp == 0.0) return 1;
+  const int o = ctx->o, n = ctx->n;
+  const double A = std::fabs(f.amp);
+  const double wvv = A * frob_block(ctx->mu_h, f.dir, n, o, n, o, n);
+  const double woo = A * frob_block(ctx->mu_h, f.dir, n, 0, o, 0, o);
+  const double wov = A * frob_block(ctx->mu_h, f.dir, n, 0, o, o, n);
+  double emax_o = -1e300, emin_v = 1e300;
+  for (int p = 0; p < o; ++p) emax_o = std::max(emax_o, ctx->eps_h[p]);
+  for (int p = o; p < n; ++p) emin_v = std::min(emin_v, ctx->eps_h[p]);
+  const double e3 = 3.0 * (emin_v - emax_o);
+  const double rho = 3.0 * (wvv + woo + 2.0 * wov) / e3;
+  RTCC3_CHECK(rho < 0.9, RTCC3_ERR_ARG, "field too strong for the triples fixed point (rho >= 0.9)");
+  double tol = ctx->opt.field_tol;
+  if (tol <= 0.0) tol = ctx->fp64() ? 1e-14 : 1e-8;
+  if (rho <= 0.0) return 1;
+  const int k = int(std::ceil(std::log(tol) / std::log(rho))) + 1;
+  return std::max(1, std::min(k, 200));
+}
+
+// One stage evaluation for slot b: records the graph with inputs
+// y_b + ch * kprev at time *tsrc + dt and, if need_grad, runs the backward
+// pass with the Lagrangian seeds.
+template <typename R>
+StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2* kprev, double ch,
+                      const double* tsrc, double dt, bool need_grad, const FieldDev* f,
+                      bool field_terms, int sweeps, bool ccsd_terms = true) {
+  Runner<R>& Rn = ctx->run<R>();
+  Engine<R>& E = Rn.E;
+  E.begin();
+  StageOptions so;
+  so.triples = ctx->opt.triples != 0;
+  so.need_grad = need_grad;
+  so.field_terms = field_terms;
+  so.field_iters = sweeps;
+  (void)ccsd_terms;
+  StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
+    launch_stage_inputs<R>(ybase, kprev, ch, E.data(s.t1), E.data(s.t2), Rn.l1s, Rn.l2s,
+                           E.data(s.w), ctx->mu, f, tsrc, dt, ctx->o, ctx->v, ctx->n, ctx->stream);
+  });
+  if (need_grad) {
+    E.prepare_backward();
+    launch_seeds<R>(E.grad(S.e), E.grad(S.r1), E.grad(S.r2), Rn.l1s, Rn.l2s, ctx->o, ctx->v,
+                    ctx->stream);
+    E.backward();
+  }
+  return S;
+}
+
+template <typename R>
+void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
+  auto rn = std::make_unique<Runner<R>>(ctx->o, ctx->v, ctx->stream);
+  const int n = ctx->n, na = ctx->naux;
+  Hamil<R>& H = rn->H;
+  H.o = ctx->o; H.v = ctx->v; H.n = n; H.naux = na;
+  H.eps = ctx->eps;
+  H.mu = ctx->mu;
+  H.e_ref = ctx->e_ref;
+  // h = diag(eps) - (2J - K) with J, K from the DF factors (FP64 on host:
+  // set-up only, O(naux n^2 o))
+  std::vector<double> h(size_t(n) * n, 0.0);
+  for (int p = 0; p < n; ++p) h[p * n + p] = ctx->eps_h[p];
+  const int o = ctx->o;
+  std::vector<double> dk(na, 0.0);
+  for (int P = 0; P < na; ++P)
+    for (int k = 0; k < o; ++k) dk[P] += Lfac[(size_t(P) * n + k) * n + k];
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      double J = 0.0, K = 0.0;
+      for (int P = 0; P < na; ++P) {
+        const double* LP = Lfac + size_t(P) * n * n;
+        J += LP[p * n + q] * dk[P];
+        for (int k = 0; k < o; ++k) K += LP[p * n + k] * LP[k * n + q];
+      }
+      h[p * n + q] -= 2.0 * J - K;
+    }
+  double eref = 0.0;
+  for (int i = 0; i < o; ++i) eref += h[i * n + i] + ctx->eps_h[i];
+  ctx->e_ref = eref;
+  H.e_ref = eref;
+  std::vector<Cx<R>> hc(size_t(n) * n), Lc(size_t(na) * n * n), ones(n);
+  for (size_t t = 0; t < hc.size(); ++t) hc[t] = cmake<R>(R(h[t]), R(0));
+  for (size_t t = 0; t < Lc.size(); ++t) Lc[t] = cmake<R>(R(Lfac[t]), R(0));
+  for (int t = 0; t < n; ++t) ones[t] = cmake<R>(R(1), R(0));
+  H.h = rn->template alloc<Cx<R>>(hc.size());
+  H.L = rn->template alloc<Cx<R>>(Lc.size());
+  H.ones = rn->template alloc<Cx<R>>(n);
+  RTCC3_CUDA(cudaMemcpy(H.h, hc.data(), hc.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
+  RTCC3_CUDA(cudaMemcpy(H.L, Lc.data(), Lc.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
+  RTCC3_CUDA(cudaMemcpy(H.ones, ones.data(), ones.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
+  ctx->runner = std::move(rn);
+}
+
+void ensure_traj(rtcc3_ctx* ctx, size_t entries) {
+  if (entries <= ctx->traj_cap) return;
+  if (ctx->dip_traj) cudaFree(ctx->dip_traj);
+  if (ctx->en_traj) cudaFree(ctx->en_traj);
+  ctx->dip_traj = nullptr;
+  ctx->en_traj = nullptr;
+  RTCC3_CUDA(cudaMalloc(&ctx->dip_traj, entries * 3 * sizeof(double2)));
+  RTCC3_CUDA(cudaMalloc(&ctx->en_traj, entries * sizeof(double2)));
+  ctx->traj_cap = entries;
+}
+
+// One RK4 step for every slot; observables of the step-start state go to
+// trajectory entry *stepdev of slot b (arrays strided by `stride`).
+template <typename R>
+void rk4_step(rtcc3_ctx* ctx, double h, double2* dip, double2* en, size_t stride,
+              const std::vector<int>& sweeps) {
+  Runner<R>& Rn = ctx->run<R>();
+  Engine<R>& E = Rn.E;
+  const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+  const double ws[4] = {1.0, 2.0, 2.0, 1.0};
+  for (int b = 0; b < ctx->nb; ++b) {
+    double2* yb = ctx->y + size_t(b) * ctx->ny;
+    launch_stage_prep_acc(ctx->acc, yb, ctx->ny, ctx->stream);
+    for (int s = 0; s < 4; ++s) {
+      StageNodes S = eval_stage<R>(ctx, b, yb, s == 0 ? nullptr : ctx->kbuf, cs[s] * h, ctx->tdev,
+                                   cs[s] * h, true, ctx->fdev + b, true, sweeps[b]);
+      if (s == 0)
+        launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n,
+                              dip ? dip + size_t(b) * stride * 3 : nullptr,
+                              en ? en + size_t(b) * stride : nullptr, ctx->stepdev, 0, ctx->stream);
+      launch_stage_output<R>(E.data(S.r1), E.data(S.r2), E.grad(S.t1), E.grad(S.t2),
+                             s < 3 ? ctx->kbuf : nullptr, ctx->acc, h * ws[s] / 6.0, ctx->o, ctx->v,
+                             ctx->stream);
+    }
+    launch_step_finish(yb, ctx->acc, ctx->ny, ctx->stepdev, ctx->baddev, ctx->stream);
+  }
+  launch_step_advance(ctx->tdev, h, ctx->stepdev, ctx->stream);
+}
+
+template <typename R>
+void final_observables(rtcc3_ctx* ctx, double2* dip, double2* en, size_t stride,
+                       const std::vector<int>& sweeps) {
+  Runner<R>& Rn = ctx->run<R>();
+  Engine<R>& E = Rn.E;
+  for (int b = 0; b < ctx->nb; ++b) {
+    double2* yb = ctx->y + size_t(b) * ctx->ny;
+    StageNodes S = eval_stage<R>(ctx, b, yb, nullptr, 0.0, ctx->tdev, 0.0, true, ctx->fdev + b,
+                                 true, sweeps[b]);
+    launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n,
+                          dip ? dip + size_t(b) * stride * 3 : nullptr,
+                          en ? en + size_t(b) * stride : nullptr, ctx->stepdev, 0, ctx->stream);
+  }
+}
+
+template <typename R>
+void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2* en, size_t stride) {
+  Engine<R>& E = ctx->run<R>().E;
+  std::vector<int> sweeps(ctx->nb);
+  for (int b = 0; b < ctx->nb; ++b) sweeps[b] = field_sweeps(ctx, b);
+  RTCC3_CUDA(cudaMemsetAsync(ctx->stepdev, 0, sizeof(int), ctx->stream));
+  const int minus1 = -1;
+  RTCC3_CUDA(cudaMemcpyAsync(ctx->baddev, &minus1, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  E.reset_launch_count();
+  int done = 0;
+  if (nsteps > 0) {
+    rk4_step<R>(ctx, h, dip, en, stride, sweeps);  // eager: builds plans and arena
+    done = 1;
+  }
+  if (nsteps > 1 && ctx->opt.use_graphs) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    E.freeze_plans(true);
+    const int launches_before = E.launches();
+    try {
+      RTCC3_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      try {
+        rk4_step<R>(ctx, h, dip, en, stride, sweeps);
+      } catch (...) {
+        cudaStreamEndCapture(ctx->stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      RTCC3_CUDA(cudaStreamEndCapture(ctx->stream, &graph));
+      RTCC3_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    } catch (...) {
+      E.freeze_plans(false);
+      throw;
+    }
+    E.freeze_plans(false);
+    const int per_step = E.launches() - launches_before;
+    for (; done < nsteps; ++done) RTCC3_CUDA(cudaGraphLaunch(exec, ctx->stream));
+    ctx->last_launches = (long long)E.launches() + (long long)per_step * (nsteps - 2);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+  } else {
+    for (; done < nsteps; ++done) rk4_step<R>(ctx, h, dip, en, stride, sweeps);
+    ctx->last_launches = E.launches();
+  }
+  final_observables<R>(ctx, dip, en, stride, sweeps);
+  RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->time += h * nsteps;
+  ctx->step_total += nsteps;
+  int bad = -1;
+  RTCC3_CUDA(cudaMemcpy(&bad, ctx->baddev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (bad >= 0)
+    throw Error(RTCC3_ERR_NONFINITE, "non-finite amplitudes after RK4 step " + std::to_string(bad));
+}
+
+void check_slot(const rtcc3_ctx* ctx, int b) {
+  RTCC3_CHECK(b >= 0 && b < ctx->nb, RTCC3_ERR_ARG, "slot index out of range");
+}
+
+void require_ham(const rtcc3_ctx* ctx) {
+  RTCC3_CHECK(ctx->have_ham, RTCC3_ERR_STATE, "rtcc3_set_hamiltonian has not been called");
+}
+
+template <typename R>
+void residuals_impl(rtcc3_ctx* ctx, int b, double time, double* r_t1, double* r_t2, double* r_l1,
+                    double* r_l2, double* energy, double* dipole) {
+  Engine<R>& E = ctx->run<R>().E;
+  RTCC3_CUDA(cudaMemcpyAsync(ctx->teval, &time, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  const bool need_grad = r_l1 || r_l2 || dipole;
+  E.reset_launch_count();
+  StageNodes S = eval_stage<R>(ctx, b, ctx->y + size_t(b) * ctx->ny, nullptr, 0.0, ctx->teval, 0.0,
+                               need_grad, ctx->fdev + b, need_grad || ctx->fhost[b].kind != 0,
+                               field_sweeps(ctx, b));
+  launch_residual_export<R>(E.data(S.r1), E.data(S.r2), need_grad ? E.grad(S.t1) : nullptr,
+                            need_grad ? E.grad(S.t2) : nullptr, ctx->res, ctx->o, ctx->v, need_grad,
+                            ctx->stream);
+  ensure_traj(ctx, 1);
+  launch_observables<R>(need_grad ? E.grad(S.w) : E.data(S.w), E.data(S.e), ctx->mu, ctx->e_ref,
+                        ctx->n, ctx->dip_traj, ctx->en_traj, nullptr, 0, ctx->stream);
+  RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->last_launches = E.launches();
+  const size_t n1 = ctx->n1, n2 = ctx->n2;
+  auto get = [&](double* dst, size_t off, size_t cnt) {
+    if (dst)
+      RTCC3_CUDA(cudaMemcpy(dst, ctx->res + off, cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+  };
+  get(r_t1, 0, n1);
+  get(r_t2, n1, n2);
+  get(r_l1, n1 + n2, n1);
+  get(r_l2, 2 * n1 + n2, n2);
+  if (energy) RTCC3_CUDA(cudaMemcpy(energy, ctx->en_traj, sizeof(double2), cudaMemcpyDeviceToHost));
+  if (dipole) RTCC3_CUDA(cudaMemcpy(dipole, ctx->dip_traj, 3 * sizeof(double2), cudaMemcpyDeviceToHost));
+}
+
+// Solve the (m+1)x(m+1) complex DIIS system by Gaussian elimination with
+// partial pivoting (host; m <= 8).
+std::vector<double2> diis_coefficients(const std::vector<double2>& Bm, int m) {
+  const int N = m + 1;
+  std::vector<double> ar(size_t(N) * N), ai(size_t(N) * N), br(N, 0.0), bi(N, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) { ar[i * N + j] = Bm[i * m + j].x; ai[i * N + j] = Bm[i * m + j].y; }
+  for (int i = 0; i < m; ++i) { ar[i * N + m] = -1.0; ar[m * N + i] = -1.0; }
+  br[m] = -1.0;
+  for (int c = 0; c < N; ++c) {
+    int piv = c;
+    double best = -1.0;
+    for (int r = c; r < N; ++r) {
+      const double mag = std::hypot(ar[r * N + c], ai[r * N + c]);
+      if (mag > best) { best = mag; piv = r; }
+    }
+    RTCC3_CHECK(best > 0.0, RTCC3_ERR_NOT_CONVERGED, "singular DIIS matrix");
+    if (piv != c) {
+      for (int k = 0; k < N; ++k) { std::swap(ar[c * N + k], ar[piv * N + k]); std::swap(ai[c * N + k], ai[piv * N + k]); }
+      std::swap(br[c], br[piv]); std::swap(bi[c], bi[piv]);
+    }
+    const double pr = ar[c * N + c], pi = ai[c * N + c], pd = pr * pr + pi * pi;
+    for (int r = c + 1; r < N; ++r) {
+      const double xr = ar[r * N + c], xi = ai[r * N + c];
+      const double fr = (xr * pr + xi * pi) / pd, fi = (xi * pr - xr * pi) / pd;
+      for (int k = c; k < N; ++k) {
+        const double yr = ar[c * N + k], yi = ai[c * N + k];
+        ar[r * N + k] -= fr * yr - fi * yi;
+        ai[r * N + k] -= fr * yi + fi * yr;
+      }
+      br[r] -= fr * br[c] - fi * bi[c];
+      bi[r] -= fr * bi[c] + fi * br[c];
+    }
+  }
+  std::vector<double> xr(N), xi(N);
+  for (int r = N - 1; r >= 0; --r) {
+    double sr = br[r], si = bi[r];
+    for (int k = r + 1; k < N; ++k) {
+      sr -= ar[r * N + k] * xr[k] - ai[r * N + k] * xi[k];
+      si -= ar[r * N + k] * xi[k] + ai[r * N + k] * xr[k];
+    }
+    const double pr = ar[r * N + r], pi = ai[r * N + r], pd = pr * pr + pi * pi;
+    xr[r] = (sr * pr + si * pi) / pd;
+    xi[r] = (si * pr - sr * pi) / pd;
+  }
+  std::vector<double2> c(m);
+  for (int k = 0; k < m; ++k) c[k] = make_double2(xr[k], xi[k]);
+  return c;
+}
+
+template <typename R>
+void ground_state_impl(rtcc3_ctx* ctx, double tol, int maxiter) {
+  Engine<R>& E = ctx->run<R>().E;
+  double2* y0 = ctx->y;
+  RTCC3_CUDA(cudaMemsetAsync(y0, 0, ctx->ny * sizeof(double2), ctx->stream));
+  const double zero = 0.0;
+  RTCC3_CUDA(cudaMemcpyAsync(ctx->teval, &zero, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  const size_t n1 = ctx->n1, n2 = ctx->n2, len = n1 + n2;
+  const int kDiis = 8;
+  double2* X = ctx->dalloc<double2>(len * kDiis);
+  double2* Ev = ctx->dalloc<double2>(len * kDiis);
+  double2* dots = ctx->dalloc<double2>(kDiis);
+  double2* coef = ctx->dalloc<double2>(kDiis);
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool lam = pass == 1;
+    const size_t off = lam ? len : 0;
+    bool conv = false;
+    int m = 0, head = 0;  // ring buffer of DIIS vectors
+    std::vector<double2> B(kDiis * kDiis, make_double2(0.0, 0.0));
+    for (int it = 0; it < maxiter; ++it) {
+      StageNodes S = eval_stage<R>(ctx, 0, y0, nullptr, 0.0, ctx->teval, 0.0, lam, ctx->fnone, false, 1);
+      launch_residual_export<R>(E.data(S.r1), E.data(S.r2), lam ? E.grad(S.t1) : nullptr,
+                                lam ? E.grad(S.t2) : nullptr, ctx->res, ctx->o, ctx->v, lam,
+                                ctx->stream);
+      RTCC3_CUDA(cudaMemsetAsync(ctx->maxr, 0, sizeof(double), ctx->stream));
+      const int slot = head;
+      launch_diis_step(y0 + off, ctx->res + off, ctx->eps, ctx->o, ctx->v, X + slot * len,
+                       Ev + slot * len, ctx->maxr, ctx->stream);
+      const int mm = std::min(m + 1, kDiis);
+      launch_dots(Ev, Ev + slot * len, mm, len, dots, ctx->stream);
+      double mx = 0.0;
+      std::vector<double2> d(mm);
+      RTCC3_CUDA(cudaMemcpyAsync(&mx, ctx->maxr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      RTCC3_CUDA(cudaMemcpyAsync(d.data(), dots, mm * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+      RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
+      RTCC3_CHECK(std::isfinite(mx), RTCC3_ERR_NONFINITE, "non-finite residual in the ground-state solve");
+      if (mx < tol) { conv = true; break; }
+      m = mm;
+      head = (head + 1) % kDiis;
+      // B[k][slot] = <E_k|E_slot>, B[slot][k] = conj
+      for (int k = 0; k < m; ++k) {
+        B[k * kDiis + slot] = d[k];
+        B[slot * kDiis + k] = make_double2(d[k].x, -d[k].y);
+      }
+      std::vector<double2> Bm(size_t(m) * m);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Bm[i * m + j] = B[i * kDiis + j];
+      std::vector<double2> c = m >= 2 ? diis_coefficients(Bm, m) : std::vector<double2>();
+      if (m < 2) {
+        c.assign(m, make_double2(0.0, 0.0));
+        c[slot] = make_double2(1.0, 0.0);
+      }
+      RTCC3_CUDA(cudaMemcpyAsync(coef, c.data(), m * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+      launch_lincomb(X, coef, m, len, y0 + off, ctx->stream);
+    }
+    if (!conv)
+      throw Error(RTCC3_ERR_NOT_CONVERGED,
+                  std::string(lam ? "lambda" : "T") + " equations did not converge");
+  }
+  for (int b = 1; b < ctx->nb; ++b)
+    RTCC3_CUDA(cudaMemcpyAsync(ctx->y + size_t(b) * ctx->ny, y0, ctx->ny * sizeof(double2),
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+  RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->time = 0.0;
+  ctx->step_total = 0;
+  RTCC3_CUDA(cudaMemcpy(ctx->tdev, &ctx->time, sizeof(double), cudaMemcpyHostToDevice));
+}
+
+// Triples-only map (t1, t2) -> (X1, X2) and its vector-Jacobian product.
+template <typename R>
+void triples_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1, const double2* t2,
+                  const double2* u1, const double2* u2, double2* x1, double2* x2, double2* g1,
+                  double2* g2, cudaStream_t st) {
+  Runner<R>& Rn = ctx->run<R>();
+  Engine<R>& E = Rn.E;
+  const bool vjp = (g1 || g2);
+  RTCC3_CUDA(cudaMemcpyAsync(ctx->teval, &time, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  E.begin();
+  StageOptions so;
+  so.ccsd = false;  // R1, R2 = X1, X2 only
+  so.triples = true;
+  so.need_grad = vjp;
+  so.field_terms = true;
+  so.field_iters = field_sweeps(ctx, b);
+  auto fill = [&](const StageNodes& s) {
+    launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, ctx->stream);
+    launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, ctx->teval, 0.0, ctx->n, ctx->stream);
+  };
+  (void)st;
+  const size_t n1 = ctx->n1, n2 = ctx->n2;
+  StageNodes S = record_stage<R>(E, Rn.H, so, fill);
+  if (vjp) {
+    E.prepare_backward();  // grad(e) stays zero: only u . X is differentiated
+    launch_load_amplitudes<R>(u1, u2, E.grad(S.r1), E.grad(S.r2), ctx->o, ctx->v, ctx->stream);
+    E.backward();
+    launch_export<R>(E.grad(S.t1), g1, n1, ctx->stream);
+    launch_export<R>(E.grad(S.t2), g2, n2, ctx->stream);
+  } else {
+    launch_export<R>(E.data(S.r1), x1, n1, ctx->stream);
+    launch_export<R>(E.data(S.r2), x2, n2, ctx->stream);
+  }
+  RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+  uint64_t h = 1469598103934665603ULL;
+  for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ULL; }
+  return h;
+}
+
+struct StateHeader {
+  char magic[8];
+  int version, o, v, nb;
+  long long ny;
+  double time;
+  long long step;
+};
+
+}  // namespace
+
+extern "C" {
+
+void rtcc3_default_options(rtcc3_options* opt) {
+  if (!opt) return;
+  opt->precision = RTCC3_PREC_FP64;
+  opt->triples = 1;
+  opt->device = 0;
+  opt->use_graphs = 1;
+  opt->field_tol = 0.0;
+}
+
+int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3_ctx** out) {
+  if (!out) return RTCC3_ERR_ARG;
+  *out = nullptr;
+  if (nocc < 1 || nvir < 1 || nbatch < 1 || nbatch > 64) return RTCC3_ERR_ARG;
+  auto ctx = std::make_unique<rtcc3_ctx>();
+  if (opt) ctx->opt = *opt; else rtcc3_default_options(&ctx->opt);
+  if (ctx->opt.precision < RTCC3_PREC_FP64 || ctx->opt.precision > RTCC3_PREC_BF16)
+    return RTCC3_ERR_ARG;
+  ctx->o = nocc; ctx->v = nvir; ctx->n = nocc + nvir; ctx->nb = nbatch;
+  ctx->n1 = size_t(nocc) * nvir;
+  ctx->n2 = ctx->n1 * ctx->n1;
+  ctx->ny = 2 * (ctx->n1 + ctx->n2);
+  rtcc3_ctx* raw = ctx.get();
+  const int rc = guarded(raw, [&] {
+    RTCC3_CUDA(cudaSetDevice(raw->opt.device));
+    RTCC3_CUDA(cudaStreamCreateWithFlags(&raw->stream, cudaStreamNonBlocking));
+    raw->y = raw->dalloc<double2>(raw->ny * nbatch);
+    raw->acc = raw->dalloc<double2>(raw->ny);
+    raw->kbuf = raw->dalloc<double2>(raw->ny);
+    raw->res = raw->dalloc<double2>(raw->ny);
+    raw->fdev = raw->dalloc<FieldDev>(nbatch);
+    raw->fnone = raw->dalloc<FieldDev>(1);
+    raw->tdev = raw->dalloc<double>(1);
+    raw->teval = raw->dalloc<double>(1);
+    raw->stepdev = raw->dalloc<int>(1);
+    raw->baddev = raw->dalloc<int>(1);
+    raw->maxr = raw->dalloc<double>(1);
+    raw->fhost.assign(nbatch, FieldDev{0, 0.0, 0.0, 0.0, 1.0, {0.0, 0.0, 1.0}});
+    RTCC3_CUDA(cudaMemcpy(raw->fdev, raw->fhost.data(), nbatch * sizeof(FieldDev), cudaMemcpyHostToDevice));
+    RTCC3_CUDA(cudaMemcpy(raw->fnone, raw->fhost.data(), sizeof(FieldDev), cudaMemcpyHostToDevice));
+    RTCC3_CUDA(cudaMemset(raw->y, 0, raw->ny * nbatch * sizeof(double2)));
+    RTCC3_CUDA(cudaMemset(raw->tdev, 0, sizeof(double)));
+  });
+  if (rc != RTCC3_OK) return rc;
+  *out = ctx.release();
+  return RTCC3_OK;
+}
+
+int rtcc3_destroy(rtcc3_ctx* ctx) {
+  delete ctx;
+  return RTCC3_OK;
+}
+
+const char* rtcc3_last_error(const rtcc3_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int rtcc3_set_hamiltonian(rtcc3_ctx* ctx, const double* eps, int naux, const double* Lfac,
+                          const double* dipole) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  if (!eps || !Lfac || !dipole || naux < 1) return fail(ctx, RTCC3_ERR_ARG, "null input or naux < 1");
+  return guarded(ctx, [&] {
+    RTCC3_CUDA(cudaSetDevice(ctx->opt.device));
+    const int n = ctx->n;
+    for (int p = 0; p < n; ++p) RTCC3_CHECK(std::isfinite(eps[p]), RTCC3_ERR_ARG, "non-finite eps");
+    double emax_o = -1e300, emin_v = 1e300;
+    for (int p = 0; p < ctx->o; ++p) emax_o = std::max(emax_o, eps[p]);
+    for (int p = ctx->o; p < n; ++p) emin_v = std::min(emin_v, eps[p]);
+    RTCC3_CHECK(emax_o < emin_v, RTCC3_ERR_ARG,
+                "highest occupied orbital energy must lie below the lowest virtual");
+    ctx->naux = naux;
+    ctx->eps_h.assign(eps, eps + n);
+    ctx->mu_h.assign(dipole, dipole + size_t(3) * n * n);
+    if (!ctx->eps) ctx->eps = ctx->dalloc<double>(n);
+    if (!ctx->mu) ctx->mu = ctx->dalloc<double>(size_t(3) * n * n);
+    RTCC3_CUDA(cudaMemcpy(ctx->eps, eps, n * sizeof(double), cudaMemcpyHostToDevice));
+    RTCC3_CUDA(cudaMemcpy(ctx->mu, dipole, size_t(3) * n * n * sizeof(double), cudaMemcpyHostToDevice));
+    ctx->runner.reset();
+    if (ctx->fp64()) setup_runner<double>(ctx, Lfac);
+    else setup_runner<float>(ctx, Lfac);
+    RTCC3_CUDA(cudaMemset(ctx->y, 0, ctx->ny * ctx->nb * sizeof(double2)));
+    ctx->time = 0.0;
+    ctx->step_total = 0;
+    RTCC3_CUDA(cudaMemcpy(ctx->tdev, &ctx->time, sizeof(double), cudaMemcpyHostToDevice));
+    ctx->have_ham = true;
+  });
+}
+
+int rtcc3_set_field(rtcc3_ctx* ctx, int b, int kind, double amplitude, double omega, double center,
+                    double width, const double* dir) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    check_slot(ctx, b);
+    RTCC3_CHECK(kind >= RTCC3_FIELD_NONE && kind <= RTCC3_FIELD_GAUSS, RTCC3_ERR_ARG, "unknown field kind");
+    RTCC3_CHECK(std::isfinite(amplitude) && std::isfinite(omega) && std::isfinite(center) &&
+                    std::isfinite(width), RTCC3_ERR_ARG, "non-finite field parameter");
+    RTCC3_CHECK(kind != RTCC3_FIELD_GAUSS || width > 0.0, RTCC3_ERR_ARG, "Gaussian width must be > 0");
+    FieldDev f{kind, amplitude, omega, center, width, {0.0, 0.0, 1.0}};
+    if (dir) { f.dir[0] = dir[0]; f.dir[1] = dir[1]; f.dir[2] = dir[2]; }
+    ctx->fhost[b] = f;
+    RTCC3_CUDA(cudaMemcpy(ctx->fdev + b, &f, sizeof(FieldDev), cudaMemcpyHostToDevice));
+  });
+}
+
+int rtcc3_set_amplitudes(rtcc3_ctx* ctx, int b, const double* t1, const double* t2,
+                         const double* l1, const double* l2) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    check_slot(ctx, b);
+    double2* yb = ctx->y + size_t(b) * ctx->ny;
+    const size_t n1 = ctx->n1, n2 = ctx->n2;
+    const double* src[4] = {t1, t2, l1, l2};
+    const size_t off[4] = {0, n1, n1 + n2, 2 * n1 + n2};
+    const size_t cnt[4] = {n1, n2, n1, n2};
+    for (int k = 0; k < 4; ++k) {
+      if (!src[k]) continue;
+      for (size_t t = 0; t < 2 * cnt[k]; ++t)
+        RTCC3_CHECK(std::isfinite(src[k][t]), RTCC3_ERR_ARG, "non-finite amplitude");
+      RTCC3_CUDA(cudaMemcpy(yb + off[k], src[k], cnt[k] * sizeof(double2), cudaMemcpyHostToDevice));
+    }
+  });
+}
+
+int rtcc3_get_amplitudes(const rtcc3_ctx* cctx, int b, double* t1, double* t2, double* l1,
+                         double* l2) {
+  rtcc3_ctx* ctx = const_cast<rtcc3_ctx*>(cctx);
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    check_slot(ctx, b);
+    RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
+    const double2* yb = ctx->y + size_t(b) * ctx->ny;
+    const size_t n1 = ctx->n1, n2 = ctx->n2;
+    double* dst[4] = {t1, t2, l1, l2};
+    const size_t off[4] = {0, n1, n1 + n2, 2 * n1 + n2};
+    const size_t cnt[4] = {n1, n2, n1, n2};
+    for (int k = 0; k < 4; ++k)
+      if (dst[k]) RTCC3_CUDA(cudaMemcpy(dst[k], yb + off[k], cnt[k] * sizeof(double2), cudaMemcpyDeviceToHost));
+  });
+}
+
+int rtcc3_set_time(rtcc3_ctx* ctx, double time) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    RTCC3_CHECK(std::isfinite(time), RTCC3_ERR_ARG, "non-finite time");
+    ctx->time = time;
+    RTCC3_CUDA(cudaMemcpy(ctx->tdev, &time, sizeof(double), cudaMemcpyHostToDevice));
+  });
+}
+
+int rtcc3_get_time(const rtcc3_ctx* ctx, double* time) {
+  if (!ctx || !time) return RTCC3_ERR_ARG;
+  *time = ctx->time;
+  return RTCC3_OK;
+}
+
+int rtcc3_compute_residuals(rtcc3_ctx* ctx, int b, double time, double* r_t1, double* r_t2,
+                            double* r_l1, double* r_l2, double* energy, double* dipole) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    require_ham(ctx);
+    check_slot(ctx, b);
+    RTCC3_CHECK(std::isfinite(time), RTCC3_ERR_ARG, "non-finite time");
+    if (ctx->fp64()) residuals_impl<double>(ctx, b, time, r_t1, r_t2, r_l1, r_l2, energy, dipole);
+    else residuals_impl<float>(ctx, b, time, r_t1, r_t2, r_l1, r_l2, energy, dipole);
+  });
+}
+
+int rtcc3_solve_ground_state(rtcc3_ctx* ctx, double tol, int maxiter) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    require_ham(ctx);
+    RTCC3_CHECK(tol > 0.0 && maxiter > 0, RTCC3_ERR_ARG, "tol must be > 0 and maxiter > 0");
+    if (ctx->fp64()) ground_state_impl<double>(ctx, tol, maxiter);
+    else ground_state_impl<float>(ctx, tol, maxiter);
+  });
+}
+
+static int propagate_common(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2* en,
+                            bool host, double* dip_h, double* en_h) {
+  return guarded(ctx, [&] {
+    require_ham(ctx);
+    RTCC3_CHECK(nsteps >= 0 && std::isfinite(h) && h != 0.0, RTCC3_ERR_ARG, "bad step size or count");
+    const size_t entries = size_t(nsteps) + 1;
+    double2* d = dip;
+    double2* e = en;
+    if (host) {
+      ensure_traj(ctx, entries * ctx->nb);
+      d = ctx->dip_traj;
+      e = ctx->en_traj;
+    }
+    if (ctx->fp64()) propagate_impl<double>(ctx, h, nsteps, d, e, entries);
+    else propagate_impl<float>(ctx, h, nsteps, d, e, entries);
+    if (host) {
+      if (dip_h)
+        RTCC3_CUDA(cudaMemcpy(dip_h, d, entries * ctx->nb * 3 * sizeof(double2), cudaMemcpyDeviceToHost));
+      if (en_h)
+        RTCC3_CUDA(cudaMemcpy(en_h, e, entries * ctx->nb * sizeof(double2), cudaMemcpyDeviceToHost));
+    }
+  });
+}
+
+int rtcc3_propagate_rk4(rtcc3_ctx* ctx, double h, int nsteps, double* dipole, double* energy) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return propagate_common(ctx, h, nsteps, nullptr, nullptr, true, dipole, energy);
+}
+
+int rtcc3_propagate_rk4_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_dev,
+                            void* energy_dev, void* stream) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  // the work runs on the context stream; an external stream is ordered
+  // before and after it with events
+  cudaStream_t ext = static_cast<cudaStream_t>(stream);
+  return guarded(ctx, [&] {
+    if (ext) {
+      cudaEvent_t ev;
+      RTCC3_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      RTCC3_CUDA(cudaEventRecord(ev, ext));
+      RTCC3_CUDA(cudaStreamWaitEvent(ctx->stream, ev, 0));
+      cudaEventDestroy(ev);
+    }
+    const int rc = propagate_common(ctx, h, nsteps, static_cast<double2*>(dipole_dev),
+                                    static_cast<double2*>(energy_dev), false, nullptr, nullptr);
+    if (rc != RTCC3_OK) throw Error(rc, ctx->err);
+  });
+}
+
+int rtcc3_triples_forward_dev(rtcc3_ctx* ctx, int b, double time, const void* t1, const void* t2,
+                              void* x1, void* x2, void* stream) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    require_ham(ctx);
+    check_slot(ctx, b);
+    RTCC3_CHECK(t1 && t2 && x1 && x2, RTCC3_ERR_ARG, "null device buffer");
+    RTCC3_CHECK(ctx->opt.triples, RTCC3_ERR_STATE, "context created without triples");
+    if (stream) RTCC3_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    auto f = [&](auto tag) {
+      using R = decltype(tag);
+      triples_impl<R>(ctx, b, time, static_cast<const double2*>(t1), static_cast<const double2*>(t2),
+                      nullptr, nullptr, static_cast<double2*>(x1), static_cast<double2*>(x2),
+                      nullptr, nullptr, static_cast<cudaStream_t>(stream));
+    };
+    if (ctx->fp64()) f(double()); else f(float());
+  });
+}
+
+int rtcc3_triples_vjp_dev(rtcc3_ctx* ctx, int b, double time, const void* t1, const void* t2,
+                          const void* u1, const void* u2, void* g1, void* g2, void* stream) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    require_ham(ctx);
+    check_slot(ctx, b);
+    RTCC3_CHECK(t1 && t2 && u1 && u2 && g1 && g2, RTCC3_ERR_ARG, "null device buffer");
+    RTCC3_CHECK(ctx->opt.triples, RTCC3_ERR_STATE, "context created without triples");
+    if (stream) RTCC3_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    auto f = [&](auto tag) {
+      using R = decltype(tag);
+      triples_impl<R>(ctx, b, time, static_cast<const double2*>(t1), static_cast<const double2*>(t2),
+                      static_cast<const double2*>(u1), static_cast<const double2*>(u2), nullptr,
+                      nullptr, static_cast<double2*>(g1), static_cast<double2*>(g2),
+                      static_cast<cudaStream_t>(stream));
+    };
+    if (ctx->fp64()) f(double()); else f(float());
+  });
+}
+
+int rtcc3_state_size(const rtcc3_ctx* ctx, long long* bytes) {
+  if (!ctx || !bytes) return RTCC3_ERR_ARG;
+  *bytes = (long long)(sizeof(StateHeader) + ctx->ny * ctx->nb * sizeof(double2) + sizeof(uint64_t));
+  return RTCC3_OK;
+}
+
+int rtcc3_get_state(const rtcc3_ctx* cctx, void* buf, long long bytes) {
+  rtcc3_ctx* ctx = const_cast<rtcc3_ctx*>(cctx);
+  if (!ctx || !buf) return RTCC3_ERR_ARG;
+  long long need = 0;
+  rtcc3_state_size(ctx, &need);
+  if (bytes < need) return fail(ctx, RTCC3_ERR_ARG, "state buffer too small");
+  return guarded(ctx, [&] {
+    RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
+    unsigned char* p = static_cast<unsigned char*>(buf);
+    StateHeader hd{};
+    std::memcpy(hd.magic, "RTCC3ST1", 8);
+    hd.version = 1; hd.o = ctx->o; hd.v = ctx->v; hd.nb = ctx->nb;
+    hd.ny = (long long)ctx->ny; hd.time = ctx->time; hd.step = ctx->step_total;
+    std::memcpy(p, &hd, sizeof(hd));
+    const size_t body = ctx->ny * ctx->nb * sizeof(double2);
+    RTCC3_CUDA(cudaMemcpy(p + sizeof(hd), ctx->y, body, cudaMemcpyDeviceToHost));
+    const uint64_t h = fnv1a(p, sizeof(hd) + body);
+    std::memcpy(p + sizeof(hd) + body, &h, sizeof(h));
+  });
+}
+
+int rtcc3_set_state(rtcc3_ctx* ctx, const void* buf, long long bytes) {
+  if (!ctx || !buf) return RTCC3_ERR_ARG;
+  long long need = 0;
+  rtcc3_state_size(ctx, &need);
+  if (bytes != need) return fail(ctx, RTCC3_ERR_ARG, "state image has the wrong size");
+  return guarded(ctx, [&] {
+    const unsigned char* p = static_cast<const unsigned char*>(buf);
+    StateHeader hd{};
+    std::memcpy(&hd, p, sizeof(hd));
+    RTCC3_CHECK(std::memcmp(hd.magic, "RTCC3ST1", 8) == 0 && hd.version == 1, RTCC3_ERR_ARG,
+                "not an rtcc3 state image (magic/version)");
+    RTCC3_CHECK(hd.o == ctx->o && hd.v == ctx->v && hd.nb == ctx->nb && hd.ny == (long long)ctx->ny,
+                RTCC3_ERR_ARG, "state image was written for different sizes");
+    const size_t body = ctx->ny * ctx->nb * sizeof(double2);
+    uint64_t h = 0;
+    std::memcpy(&h, p + sizeof(hd) + body, sizeof(h));
+    RTCC3_CHECK(h == fnv1a(p, sizeof(hd) + body), RTCC3_ERR_ARG, "state image checksum mismatch");
+    RTCC3_CUDA(cudaMemcpy(ctx->y, p + sizeof(hd), body, cudaMemcpyHostToDevice));
+    ctx->time = hd.time;
+    ctx->step_total = hd.step;
+    RTCC3_CUDA(cudaMemcpy(ctx->tdev, &ctx->time, sizeof(double), cudaMemcpyHostToDevice));
+  });
+}
+
+int rtcc3_stats(const rtcc3_ctx* ctx, long long* launches, long long* device_bytes) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  if (launches) *launches = ctx->last_launches;
+  if (device_bytes) {
+    long long s = 0;
+    if (ctx->runner) {
+      if (ctx->fp64()) s += (long long)static_cast<Runner<double>*>(ctx->runner.get())->E.arena().reserved();
+      else s += (long long)static_cast<Runner<float>*>(ctx->runner.get())->E.arena().reserved();
+    }
+    *device_bytes = s;
+  }
+  return RTCC3_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Shared helpers for the RT-CC3 CUDA library: complex storage types, error
+// propagation and the device arena.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace rtcc3 {
+
+// Complex numbers are interleaved (re, im) pairs: double2 / float2.
+template <typename R> struct CxT;
+template <> struct CxT<double> { using type = double2; };
+template <> struct CxT<float> { using type = float2; };
+template <typename R> using Cx = typename CxT<R>::type;
+
+template <typename R> __host__ __device__ inline Cx<R> cmake(R re, R im) {
+  Cx<R> z; z.x = re; z.y = im; return z;
+}
+
+// Error carried across the C ABI as a status code plus message.
+struct Error : public std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+enum Status {
+  kOk = 0, kErrArg = -1, kErrOom = -2, kErrCuda = -3, kErrNonfinite = -4,
+  kErrTimeout = -5, kErrNotConverged = -6, kErrState = -7
+};
+
+#define RTCC3_CUDA(expr)                                                          \
+  do {                                                                            \
+    cudaError_t e__ = (expr);                                                     \
+    if (e__ != cudaSuccess) {                                                     \
+      throw ::rtcc3::Error(e__ == cudaErrorMemoryAllocation ? ::rtcc3::kErrOom    \
+                                                            : ::rtcc3::kErrCuda,  \
+                           std::string(#expr) + ": " + cudaGetErrorString(e__));  \
+    }                                                                             \
+  } while (0)
+
+#define RTCC3_CHECK(cond, code, msg)                                              \
+  do { if (!(cond)) throw ::rtcc3::Error((code), (msg)); } while (0)
+
+// Bump allocator over device blocks.  Every evaluation of a residual graph
+// requests the same sequence of sizes, so after reset() the same addresses are
+// handed out again: buffers are stable across evaluations, which lets a whole
+// RK4 step be captured once as a CUDA graph and replayed.
+class Arena {
+ public:
+  ~Arena() { release(); }
+  void* alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    while (true) {
+      if (cur_ < blocks_.size()) {
+        Block& b = blocks_[cur_];
+        if (off_ + bytes <= b.size) {
+          void* p = static_cast<char*>(b.ptr) + off_;
+          off_ += bytes;
+          used_ = std::max(used_, total_before(cur_) + off_);
+          return p;
+        }
+        ++cur_;
+        off_ = 0;
+        continue;
+      }
+      size_t sz = std::max(bytes, size_t(256) << 20);
+      void* p = nullptr;
+      RTCC3_CUDA(cudaMalloc(&p, sz));
+      blocks_.push_back({p, sz});
+    }
+  }
+  void reset() { cur_ = 0; off_ = 0; }
+  void release() {
+    for (auto& b : blocks_) cudaFree(b.ptr);
+    blocks_.clear();
+    cur_ = 0; off_ = 0;
+  }
+  size_t reserved() const { size_t s = 0; for (auto& b : blocks_) s += b.size; return s; }
+  size_t high_water() const { return used_; }
+
+ private:
+  struct Block { void* ptr; size_t size; };
+  size_t total_before(size_t k) const { size_t s = 0; for (size_t i = 0; i < k; ++i) s += blocks_[i].size; return s; }
+  std::vector<Block> blocks_;
+  size_t cur_ = 0, off_ = 0, used_ = 0;
+};
+
+}  // namespace rtcc3

@@ -1,0 +1,657 @@
+// Kernels and host logic of the reverse-mode tensor engine (see engine.h).
+#include "engine.h"
+
+#include <algorithm>
+#include <cstring>
+#include <sstream>
+
+namespace rtcc3 {
+
+namespace {
+
+constexpr int kBM = 64, kBN = 64, kBK = 16, kThreads = 256;
+
+struct EpsArgs {
+  int sign[kMaxDim];
+  int base[kMaxDim];
+};
+
+struct StridedDesc {
+  int nd;
+  int shape[kMaxDim];
+  long long s0[kMaxDim];
+  long long s1[kMaxDim];
+  long long s2[kMaxDim];
+  long long off0, off1, off2;
+};
+
+template <typename R>
+__device__ __forceinline__ void cfma(R& ar, R& ai, Cx<R> a, Cx<R> b) {
+  ar = fma(a.x, b.x, ar);
+  ar = fma(-a.y, b.y, ar);
+  ai = fma(a.x, b.y, ai);
+  ai = fma(a.y, b.x, ai);
+}
+
+// Generic strided complex contraction as a gather-GEMM: C[b,m,n] (+)= alpha *
+// sum_k A[b,m,k] B[b,n,k] with every (b,m,n,k) -> address mapping given by
+// offset tables.  64x64 output tile per CTA, 16-deep K slices in shared
+// memory, 4x4 complex micro-tile per thread.  With nsplit > 1 each CTA sums a
+// K chunk into a partial buffer and k_split_reduce adds the chunks in fixed
+// order (deterministic results).
+template <typename R, bool A_KC, bool B_KC>
+__global__ void __launch_bounds__(kThreads)
+k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __restrict__ Cp,
+           const long long* __restrict__ aM, const long long* __restrict__ aK,
+           const long long* __restrict__ bN, const long long* __restrict__ bK,
+           const long long* __restrict__ cM, const long long* __restrict__ cN,
+           const long long* __restrict__ aB, const long long* __restrict__ bB,
+           const long long* __restrict__ cB, int M, int N, int K, int nsplit, int kchunk,
+           R alpha, int accumulate, Cx<R>* __restrict__ part) {
+  __shared__ Cx<R> As[kBK][kBM];
+  __shared__ Cx<R> Bs[kBK][kBN];
+  const int bz = blockIdx.z;
+  const int b = bz / nsplit, split = bz % nsplit;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int kbeg = split * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const Cx<R>* Ab = A + aB[b];
+  const Cx<R>* Bb = B + bB[b];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  R accr[4][4], acci[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { accr[i][j] = R(0); acci[i][j] = R(0); }
+  const Cx<R> zero = cmake<R>(R(0), R(0));
+  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+#pragma unroll
+    for (int e0 = 0; e0 < kBM * kBK; e0 += kThreads) {
+      const int e = e0 + tid;
+      int mm, kk;
+      if (A_KC) { kk = e % kBK; mm = e / kBK; } else { mm = e % kBM; kk = e / kBM; }
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < kend) ? Ab[aM[m] + aK[k]] : zero;
+    }
+#pragma unroll
+    for (int e0 = 0; e0 < kBN * kBK; e0 += kThreads) {
+      const int e = e0 + tid;
+      int nn, kk;
+      if (B_KC) { kk = e % kBK; nn = e / kBK; } else { nn = e % kBN; kk = e / kBN; }
+      const int n = n0 + nn, k = k0 + kk;
+      Bs[kk][nn] = (n < N && k < kend) ? Bb[bN[n] + bK[k]] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      Cx<R> a[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma<R>(accr[i][j], acci[i][j], a[i], bv[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      if (nsplit == 1) {
+        const long long idx = cB[b] + cM[m] + cN[n];
+        Cx<R> val = cmake<R>(alpha * accr[i][j], alpha * acci[i][j]);
+        if (accumulate) { val.x += Cp[idx].x; val.y += Cp[idx].y; }
+        Cp[idx] = val;
+      } else {
+        part[((size_t)bz * M + m) * N + n] = cmake<R>(accr[i][j], acci[i][j]);
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_split_reduce(const Cx<R>* __restrict__ part, Cx<R>* __restrict__ Cp,
+                               const long long* __restrict__ cM, const long long* __restrict__ cN,
+                               const long long* __restrict__ cB, int M, int N, int nb, int nsplit,
+                               R alpha, int accumulate) {
+  const size_t total = (size_t)nb * M * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int n = int(t % N);
+    const int m = int((t / N) % M);
+    const int b = int(t / ((size_t)M * N));
+    R sr = 0, si = 0;
+    for (int s = 0; s < nsplit; ++s) {
+      const Cx<R> p = part[(((size_t)b * nsplit + s) * M + m) * N + n];
+      sr += p.x;
+      si += p.y;
+    }
+    const long long idx = cB[b] + cM[m] + cN[n];
+    Cx<R> val = cmake<R>(alpha * sr, alpha * si);
+    if (accumulate) { val.x += Cp[idx].x; val.y += Cp[idx].y; }
+    Cp[idx] = val;
+  }
+}
+
+__device__ __forceinline__ void decode(const StridedDesc& d, size_t t, long long& o0, long long& o1,
+                                       long long& o2) {
+  o0 = d.off0; o1 = d.off1; o2 = d.off2;
+  for (int k = d.nd - 1; k >= 0; --k) {
+    const long long i = (long long)(t % (size_t)d.shape[k]);
+    t /= (size_t)d.shape[k];
+    o0 += i * d.s0[k];
+    o1 += i * d.s1[k];
+    o2 += i * d.s2[k];
+  }
+}
+
+// Y[.] += alpha X[.] over Y's shape (desc slots: 0 = X, 1 = Y).
+template <typename R>
+__global__ void k_axpy(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, StridedDesc d, R alpha,
+                       size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    long long ox, oy, oz;
+    decode(d, t, ox, oy, oz);
+    const Cx<R> x = X[ox];
+    Cx<R> y = Y[oy];
+    y.x += alpha * x.x;
+    y.y += alpha * x.y;
+    Y[oy] = y;
+  }
+}
+
+// Y[.] += X[.] * c[.] (complex product; slots 0 = X, 1 = Y, 2 = c).
+template <typename R>
+__global__ void k_mulc(const Cx<R>* __restrict__ X, const Cx<R>* __restrict__ Cst,
+                       Cx<R>* __restrict__ Y, StridedDesc d, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    long long ox, oy, oc;
+    decode(d, t, ox, oy, oc);
+    const Cx<R> x = X[ox], c = Cst[oc];
+    Cx<R> y = Y[oy];
+    y.x += x.x * c.x - x.y * c.y;
+    y.y += x.x * c.y + x.y * c.x;
+    Y[oy] = y;
+  }
+}
+
+// Y[.] += X[.] / eps(index) in FP64 (slot 0 = X, 1 = Y).
+template <typename R>
+__global__ void k_div_eps(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, StridedDesc d,
+                          const double* __restrict__ eps, EpsArgs ea, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    long long ox = d.off0, oy = d.off1;
+    double den = 0.0;
+    size_t rem = t;
+    for (int k = d.nd - 1; k >= 0; --k) {
+      const long long i = (long long)(rem % (size_t)d.shape[k]);
+      rem /= (size_t)d.shape[k];
+      ox += i * d.s0[k];
+      oy += i * d.s1[k];
+      if (ea.sign[k]) den += ea.sign[k] * eps[ea.base[k] + i];
+    }
+    const Cx<R> x = X[ox];
+    Cx<R> y = Y[oy];
+    y.x += R(double(x.x) / den);
+    y.y += R(double(x.y) / den);
+    Y[oy] = y;
+  }
+}
+
+template <typename R>
+__global__ void k_fill(Cx<R>* p, size_t n, R re, R im) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x)
+    p[t] = cmake<R>(re, im);
+}
+
+template <typename R>
+__global__ void k_identity(Cx<R>* p, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n * n) p[t] = cmake<R>((t / n) == (t % n) ? R(1) : R(0), R(0));
+}
+
+int grid_for(size_t n) {
+  size_t g = (n + 255) / 256;
+  return int(std::max<size_t>(1, std::min<size_t>(g, 152 * 16)));
+}
+
+struct Spec {
+  std::string a, b, c;
+};
+
+Spec parse(const std::string& s) {
+  Spec r;
+  const size_t comma = s.find(','), arrow = s.find("->");
+  if (comma == std::string::npos || arrow == std::string::npos || comma > arrow)
+    throw Error(kErrArg, "bad contraction spec " + s);
+  r.a = s.substr(0, comma);
+  r.b = s.substr(comma + 1, arrow - comma - 1);
+  r.c = s.substr(arrow + 2);
+  return r;
+}
+
+std::string view_key(const View& v) {
+  std::ostringstream o;
+  o << v.off << ':';
+  for (int d = 0; d < v.nd; ++d) o << v.shape[d] << '/' << v.stride[d] << ',';
+  return o.str();
+}
+
+}  // namespace
+
+template <typename R>
+void launch_fill(Cx<R>* p, size_t n, double re, double im, cudaStream_t s) {
+  if (n == 0) return;
+  k_fill<R><<<grid_for(n), 256, 0, s>>>(p, n, R(re), R(im));
+}
+
+template <typename R>
+Engine<R>::~Engine() {
+  for (auto& kv : plans_)
+    if (kv.second->dev) cudaFree(kv.second->dev);
+  if (scratch_) cudaFree(scratch_);
+}
+
+template <typename R>
+void Engine<R>::begin() {
+  arena_.reset();
+  nodes_.clear();
+  tape_.clear();
+}
+
+template <typename R>
+int Engine<R>::node(const std::vector<int>& shape, bool needs_grad) {
+  Node nd;
+  nd.shape = shape;
+  nd.numel = 1;
+  for (int s : shape) nd.numel *= size_t(s);
+  RTCC3_CHECK((int)shape.size() <= kMaxDim, kErrArg, "tensor rank too large");
+  nd.data = static_cast<C*>(arena_.alloc(nd.numel * sizeof(C)));
+  RTCC3_CUDA(cudaMemsetAsync(nd.data, 0, nd.numel * sizeof(C), stream_));
+  nd.needs_grad = needs_grad;
+  nodes_.push_back(nd);
+  return int(nodes_.size()) - 1;
+}
+
+template <typename R>
+int Engine<R>::external(C* data, const std::vector<int>& shape) {
+  Node nd;
+  nd.shape = shape;
+  nd.numel = 1;
+  for (int s : shape) nd.numel *= size_t(s);
+  nd.data = data;
+  nd.needs_grad = false;
+  nodes_.push_back(nd);
+  return int(nodes_.size()) - 1;
+}
+
+template <typename R>
+View Engine<R>::v(int n) const {
+  const Node& nd = nodes_[n];
+  View r;
+  r.node = n;
+  r.off = 0;
+  r.nd = int(nd.shape.size());
+  long long st = 1;
+  for (int d = r.nd - 1; d >= 0; --d) {
+    r.shape[d] = nd.shape[d];
+    r.stride[d] = st;
+    st *= nd.shape[d];
+  }
+  return r;
+}
+
+template <typename R>
+View Engine<R>::ev(const char* spec_c, const View& x) const {
+  const std::string spec(spec_c);
+  const size_t arrow = spec.find("->");
+  RTCC3_CHECK(arrow != std::string::npos, kErrArg, "bad view spec");
+  const std::string in = spec.substr(0, arrow), out = spec.substr(arrow + 2);
+  RTCC3_CHECK((int)in.size() == x.nd, kErrArg, "view spec rank mismatch: " + spec);
+  View r;
+  r.node = x.node;
+  r.off = x.off;
+  r.nd = int(out.size());
+  for (int d = 0; d < r.nd; ++d) {
+    long long st = 0;
+    int ext = -1;
+    for (int k = 0; k < x.nd; ++k)
+      if (in[k] == out[d]) {
+        st += x.stride[k];
+        RTCC3_CHECK(ext < 0 || ext == x.shape[k], kErrArg, "diagonal extents differ: " + spec);
+        ext = x.shape[k];
+      }
+    RTCC3_CHECK(ext >= 0, kErrArg, "view output letter missing: " + spec);
+    r.shape[d] = ext;
+    r.stride[d] = st;
+  }
+  for (size_t k = 0; k < in.size(); ++k)
+    RTCC3_CHECK(out.find(in[k]) != std::string::npos, kErrArg, "view drops a letter: " + spec);
+  return r;
+}
+
+template <typename R>
+void* Engine<R>::scratch(size_t bytes) {
+  if (bytes > scratch_bytes_) {
+    RTCC3_CHECK(!frozen_, kErrState, "scratch growth during graph capture");
+    if (scratch_) cudaFree(scratch_);
+    scratch_ = nullptr;
+    RTCC3_CUDA(cudaMalloc(&scratch_, bytes));
+    scratch_bytes_ = bytes;
+  }
+  return scratch_;
+}
+
+template <typename R>
+ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View& B, const View& Cv) {
+  const std::string key = spec + "|" + view_key(A) + "|" + view_key(B) + "|" + view_key(Cv);
+  auto it = plans_.find(key);
+  if (it != plans_.end()) return *it->second;
+  RTCC3_CHECK(!frozen_, kErrState, "new contraction plan during graph capture: " + spec);
+  const Spec s = parse(spec);
+  RTCC3_CHECK((int)s.a.size() == A.nd && (int)s.b.size() == B.nd && (int)s.c.size() == Cv.nd,
+              kErrArg, "contraction rank mismatch: " + spec);
+  struct Letter { char ch; int ext; long long sa, sb, sc; bool ia, ib, ic; };
+  std::vector<Letter> letters;
+  auto find = [&](char ch) -> Letter& {
+    for (auto& l : letters) if (l.ch == ch) return l;
+    letters.push_back({ch, -1, 0, 0, 0, false, false, false});
+    return letters.back();
+  };
+  auto add = [&](const std::string& str, const View& vw, int which) {
+    for (int d = 0; d < (int)str.size(); ++d) {
+      Letter& l = find(str[d]);
+      bool& seen = which == 0 ? l.ia : (which == 1 ? l.ib : l.ic);
+      RTCC3_CHECK(!seen, kErrArg, "repeated index in one operand (use a diagonal view): " + spec);
+      seen = true;
+      RTCC3_CHECK(l.ext < 0 || l.ext == vw.shape[d], kErrArg, "extent mismatch in " + spec);
+      l.ext = vw.shape[d];
+      (which == 0 ? l.sa : (which == 1 ? l.sb : l.sc)) = vw.stride[d];
+    }
+  };
+  add(s.a, A, 0);
+  add(s.b, B, 1);
+  add(s.c, Cv, 2);
+  std::vector<Letter> gb, gm, gn, gk;
+  for (char ch : s.c) {
+    Letter& l = find(ch);
+    if (l.ia && l.ib) gb.push_back(l);
+    else if (l.ia) gm.push_back(l);
+    else if (l.ib) gn.push_back(l);
+    else throw Error(kErrArg, "output index in no operand: " + spec);
+  }
+  for (auto& l : letters) {
+    if (l.ic) continue;
+    RTCC3_CHECK(l.ia && l.ib, kErrArg, "index summed in one operand only: " + spec);
+    gk.push_back(l);
+  }
+  // K order: smallest |stride in A| fastest (last)
+  std::stable_sort(gk.begin(), gk.end(), [](const Letter& x, const Letter& y) {
+    return std::llabs(x.sa) > std::llabs(y.sa);
+  });
+  auto P = std::make_unique<ContractPlan>();
+  auto count = [](const std::vector<Letter>& g) {
+    long long n = 1;
+    for (auto& l : g) n *= l.ext;
+    return n;
+  };
+  const long long M = count(gm), N = count(gn), K = count(gk), NB = count(gb);
+  RTCC3_CHECK(M < (1LL << 31) && N < (1LL << 31) && K < (1LL << 31) && NB < (1LL << 31), kErrArg,
+              "contraction too large: " + spec);
+  P->M = int(M); P->N = int(N); P->K = int(K); P->nb = int(NB);
+  // tables (row-major decode over each group, last letter fastest)
+  auto table = [](const std::vector<Letter>& g, int which, std::vector<long long>& out) {
+    long long n = 1;
+    for (auto& l : g) n *= l.ext;
+    const size_t base = out.size();
+    out.resize(base + size_t(n));
+    for (long long t = 0; t < n; ++t) {
+      long long rem = t, off = 0;
+      for (int k = int(g.size()) - 1; k >= 0; --k) {
+        const long long i = rem % g[k].ext;
+        rem /= g[k].ext;
+        off += i * (which == 0 ? g[k].sa : (which == 1 ? g[k].sb : g[k].sc));
+      }
+      out[base + size_t(t)] = off;
+    }
+    return base;
+  };
+  std::vector<long long>& h = P->host;
+  const size_t iaM = table(gm, 0, h), iaK = table(gk, 0, h), ibN = table(gn, 1, h),
+               ibK = table(gk, 1, h), icM = table(gm, 2, h), icN = table(gn, 2, h);
+  const size_t iaB = table(gb, 0, h), ibB = table(gb, 1, h), icB = table(gb, 2, h);
+  for (size_t t = iaB; t < iaB + size_t(NB); ++t) h[t] += A.off;
+  for (size_t t = ibB; t < ibB + size_t(NB); ++t) h[t] += B.off;
+  for (size_t t = icB; t < icB + size_t(NB); ++t) h[t] += Cv.off;
+  P->a_kcontig = !gk.empty() && std::llabs(gk.back().sa) == 1;
+  P->b_kcontig = !gk.empty() && std::llabs(gk.back().sb) == 1;
+  RTCC3_CUDA(cudaMalloc(&P->dev, h.size() * sizeof(long long)));
+  RTCC3_CUDA(cudaMemcpy(P->dev, h.data(), h.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  long long* d = static_cast<long long*>(P->dev);
+  P->aM = d + iaM; P->aK = d + iaK; P->bN = d + ibN; P->bK = d + ibK;
+  P->cM = d + icM; P->cN = d + icN; P->aB = d + iaB; P->bB = d + ibB; P->cB = d + icB;
+  // split-K when the output tiles alone do not fill the GPU
+  const long long tiles = ((M + kBM - 1) / kBM) * ((N + kBN - 1) / kBN) * NB;
+  int nsplit = 1;
+  if (tiles < 2 * 152 && K > 4 * kBK) {
+    const long long want = (2 * 152 + tiles - 1) / tiles;
+    const long long maxs = (K + 4 * kBK - 1) / (4 * kBK);
+    nsplit = int(std::max<long long>(1, std::min(want, maxs)));
+  }
+  int kchunk = int((K + nsplit - 1) / nsplit);
+  kchunk = ((kchunk + kBK - 1) / kBK) * kBK;
+  nsplit = int((K + kchunk - 1) / kchunk);
+  P->nsplit = nsplit;
+  P->kchunk = kchunk;
+  ContractPlan& ref = *P;
+  plans_[key] = std::move(P);
+  return ref;
+}
+
+template <typename R>
+void Engine<R>::run_contract(const std::string& spec, double alpha, const View& A, bool a_grad,
+                             const View& B, bool b_grad, const View& Cv, bool c_grad,
+                             bool accumulate) {
+  ContractPlan& P = plan(spec, A, B, Cv);
+  const C* pa = (a_grad ? nodes_[A.node].grad : nodes_[A.node].data);
+  const C* pb = (b_grad ? nodes_[B.node].grad : nodes_[B.node].data);
+  C* pc = (c_grad ? nodes_[Cv.node].grad : nodes_[Cv.node].data);
+  RTCC3_CHECK(pa && pb && pc, kErrState, "contraction on an unallocated buffer: " + spec);
+  C* part = nullptr;
+  if (P.nsplit > 1)
+    part = static_cast<C*>(scratch(size_t(P.nb) * P.nsplit * P.M * P.N * sizeof(C)));
+  dim3 grid((P.N + kBN - 1) / kBN, (P.M + kBM - 1) / kBM, P.nb * P.nsplit);
+  RTCC3_CHECK(grid.y < 65536 && grid.z < 65536, kErrArg, "contraction grid too large: " + spec);
+#define RTCC3_LAUNCH(AK, BK)                                                                   \
+  k_contract<R, AK, BK><<<grid, kThreads, 0, stream_>>>(                                       \
+      pa, pb, pc, P.aM, P.aK, P.bN, P.bK, P.cM, P.cN, P.aB, P.bB, P.cB, P.M, P.N, P.K, P.nsplit, \
+      P.kchunk, R(alpha), accumulate ? 1 : 0, part)
+  if (P.a_kcontig && P.b_kcontig) RTCC3_LAUNCH(true, true);
+  else if (P.a_kcontig) RTCC3_LAUNCH(true, false);
+  else if (P.b_kcontig) RTCC3_LAUNCH(false, true);
+  else RTCC3_LAUNCH(false, false);
+#undef RTCC3_LAUNCH
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
+  if (P.nsplit > 1) {
+    const size_t n = size_t(P.nb) * P.M * P.N;
+    k_split_reduce<R><<<grid_for(n), 256, 0, stream_>>>(part, pc, P.cM, P.cN, P.cB, P.M, P.N, P.nb,
+                                                        P.nsplit, R(alpha), accumulate ? 1 : 0);
+    ++launches_;
+    RTCC3_CUDA(cudaGetLastError());
+  }
+}
+
+template <typename R>
+void Engine<R>::contract(const char* spec, double alpha, const View& A, const View& B,
+                         const View& Cv, bool accumulate) {
+  RTCC3_CHECK(Cv.node != A.node && Cv.node != B.node, kErrArg, "contraction output aliases input");
+  run_contract(spec, alpha, A, false, B, false, Cv, false, accumulate);
+  if (nodes_[A.node].needs_grad || nodes_[B.node].needs_grad) nodes_[Cv.node].needs_grad = true;
+  Op op{kContract, spec, alpha, A, B, Cv, EpsSpec()};
+  tape_.push_back(op);
+}
+
+template <typename R>
+void Engine<R>::run_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg) {
+  RTCC3_CHECK(X.nd == Y.nd, kErrArg, "axpy rank mismatch");
+  StridedDesc d{};
+  d.nd = Y.nd;
+  for (int k = 0; k < Y.nd; ++k) {
+    RTCC3_CHECK(X.shape[k] == Y.shape[k], kErrArg, "axpy shape mismatch");
+    d.shape[k] = Y.shape[k];
+    d.s0[k] = X.stride[k];
+    d.s1[k] = Y.stride[k];
+  }
+  d.off0 = X.off;
+  d.off1 = Y.off;
+  const size_t n = Y.numel();
+  if (n == 0) return;
+  const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
+  C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+  k_axpy<R><<<grid_for(n), 256, 0, stream_>>>(px, py, d, R(alpha), n);
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+template <typename R>
+void Engine<R>::axpy(double alpha, const View& X, const View& Y) {
+  RTCC3_CHECK(X.node != Y.node, kErrArg, "axpy output aliases input");
+  run_axpy(alpha, X, false, Y, false);
+  if (nodes_[X.node].needs_grad) nodes_[Y.node].needs_grad = true;
+  Op op{kAxpy, "", alpha, X, View(), Y, EpsSpec()};
+  tape_.push_back(op);
+}
+
+template <typename R>
+void Engine<R>::run_mulc(const View& X, bool xg, const View& Cst, const View& Y, bool yg) {
+  RTCC3_CHECK(X.nd == Y.nd && Cst.nd == Y.nd, kErrArg, "mulc rank mismatch");
+  StridedDesc d{};
+  d.nd = Y.nd;
+  for (int k = 0; k < Y.nd; ++k) {
+    RTCC3_CHECK(X.shape[k] == Y.shape[k] && Cst.shape[k] == Y.shape[k], kErrArg, "mulc shape mismatch");
+    d.shape[k] = Y.shape[k];
+    d.s0[k] = X.stride[k];
+    d.s1[k] = Y.stride[k];
+    d.s2[k] = Cst.stride[k];
+  }
+  d.off0 = X.off; d.off1 = Y.off; d.off2 = Cst.off;
+  const size_t n = Y.numel();
+  if (n == 0) return;
+  const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
+  C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+  k_mulc<R><<<grid_for(n), 256, 0, stream_>>>(px, nodes_[Cst.node].data, py, d, n);
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+template <typename R>
+void Engine<R>::mulc(const View& X, const View& Cst, const View& Y) {
+  RTCC3_CHECK(X.node != Y.node, kErrArg, "mulc output aliases input");
+  RTCC3_CHECK(!nodes_[Cst.node].needs_grad, kErrArg, "mulc constant must not need gradients");
+  run_mulc(X, false, Cst, Y, false);
+  if (nodes_[X.node].needs_grad) nodes_[Y.node].needs_grad = true;
+  Op op{kMulc, "", 1.0, X, Cst, Y, EpsSpec()};
+  tape_.push_back(op);
+}
+
+template <typename R>
+void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg) {
+  RTCC3_CHECK(X.nd == Y.nd, kErrArg, "div_eps rank mismatch");
+  StridedDesc d{};
+  EpsArgs ea{};
+  d.nd = Y.nd;
+  for (int k = 0; k < Y.nd; ++k) {
+    RTCC3_CHECK(X.shape[k] == Y.shape[k], kErrArg, "div_eps shape mismatch");
+    d.shape[k] = Y.shape[k];
+    d.s0[k] = X.stride[k];
+    d.s1[k] = Y.stride[k];
+    ea.sign[k] = es.sign[k];
+    ea.base[k] = es.base[k];
+  }
+  d.off0 = X.off;
+  d.off1 = Y.off;
+  const size_t n = Y.numel();
+  if (n == 0) return;
+  const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
+  C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+  k_div_eps<R><<<grid_for(n), 256, 0, stream_>>>(px, py, d, es.eps, ea, n);
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+template <typename R>
+void Engine<R>::div_eps(const View& X, const EpsSpec& es, const View& Y) {
+  RTCC3_CHECK(X.node != Y.node, kErrArg, "div_eps output aliases input");
+  run_div(X, false, es, Y, false);
+  if (nodes_[X.node].needs_grad) nodes_[Y.node].needs_grad = true;
+  Op op{kDiv, "", 1.0, X, View(), Y, es};
+  tape_.push_back(op);
+}
+
+template <typename R>
+void Engine<R>::fill_identity(int n) {
+  const Node& nd = nodes_[n];
+  RTCC3_CHECK(nd.shape.size() == 2 && nd.shape[0] == nd.shape[1], kErrArg, "identity needs a square node");
+  const int m = nd.shape[0];
+  k_identity<R><<<(m * m + 255) / 256, 256, 0, stream_>>>(nd.data, m);
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+template <typename R>
+void Engine<R>::fill_ones(int n) {
+  launch_fill<R>(nodes_[n].data, nodes_[n].numel, 1.0, 0.0, stream_);
+  ++launches_;
+}
+
+template <typename R>
+void Engine<R>::prepare_backward() {
+  for (auto& nd : nodes_) {
+    if (!nd.needs_grad) continue;
+    nd.grad = static_cast<C*>(arena_.alloc(nd.numel * sizeof(C)));
+    RTCC3_CUDA(cudaMemsetAsync(nd.grad, 0, nd.numel * sizeof(C), stream_));
+  }
+}
+
+template <typename R>
+void Engine<R>::backward() {
+  for (auto it = tape_.rbegin(); it != tape_.rend(); ++it) {
+    const Op& op = *it;
+    if (op.kind == kContract) {
+      if (!nodes_[op.c.node].needs_grad) continue;
+      const Spec s = parse(op.spec);
+      if (nodes_[op.a.node].needs_grad)
+        run_contract(s.c + "," + s.b + "->" + s.a, op.alpha, op.c, true, op.b, false, op.a, true, true);
+      if (nodes_[op.b.node].needs_grad)
+        run_contract(s.a + "," + s.c + "->" + s.b, op.alpha, op.a, false, op.c, true, op.b, true, true);
+    } else if (op.kind == kAxpy) {
+      if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
+      run_axpy(op.alpha, op.c, true, op.a, true);
+    } else if (op.kind == kMulc) {
+      if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
+      run_mulc(op.c, true, op.b, op.a, true);
+    } else {
+      if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
+      run_div(op.c, true, op.es, op.a, true);
+    }
+  }
+}
+
+template class Engine<double>;
+template class Engine<float>;
+template void launch_fill<double>(Cx<double>*, size_t, double, double, cudaStream_t);
+template void launch_fill<float>(Cx<float>*, size_t, double, double, cudaStream_t);
+
+}  // namespace rtcc3

@@ -1,0 +1,149 @@
+// Reverse-mode tensor engine for the RT-CC3 residual graph.
+//
+// A residual evaluation is recorded as a list of operations on dense complex
+// tensors ("nodes") living in a device arena:
+//   * contract:  C (+)= alpha * sum_K A[..] B[..]   (einsum with two operands)
+//   * axpy:      Y += alpha * X                      (X, Y arbitrary strided views)
+//   * mulc:      Y += X .* c                         (c a constant tensor)
+// Views carry an element offset and strides, so slices of the dressed
+// integral tensor, index permutations and diagonals cost nothing.
+// backward() replays the list in reverse and accumulates holomorphic
+// vector-Jacobian products (plain transposes, no conjugation): for a
+// contraction "a,b->c", grad(A) += alpha einsum("c,b->a", grad(C), B) and
+// grad(B) += alpha einsum("a,c->b", A, grad(C)).
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+namespace rtcc3 {
+
+constexpr int kMaxDim = 8;
+
+struct View {
+  int node = -1;
+  long long off = 0;
+  int nd = 0;
+  int shape[kMaxDim] = {0};
+  long long stride[kMaxDim] = {0};
+  size_t numel() const {
+    size_t n = 1;
+    for (int d = 0; d < nd; ++d) n *= size_t(shape[d]);
+    return n;
+  }
+  // Slice [start, start+len) of dimension dim.
+  View sub(int dim, int start, int len) const {
+    View r = *this;
+    r.off += (long long)start * stride[dim];
+    r.shape[dim] = len;
+    return r;
+  }
+};
+
+// Offset tables of a planned contraction (device memory, cached per shape).
+struct ContractPlan {
+  int M = 1, N = 1, K = 1, nb = 1;
+  int nsplit = 1, kchunk = 1;
+  bool a_kcontig = false, b_kcontig = false;
+  long long *aM = nullptr, *aK = nullptr, *bN = nullptr, *bK = nullptr;
+  long long *cM = nullptr, *cN = nullptr, *aB = nullptr, *bB = nullptr, *cB = nullptr;
+  std::vector<long long> host;  // backing store for the uploaded tables
+  void* dev = nullptr;
+};
+
+template <typename R>
+class Engine {
+ public:
+  using C = Cx<R>;
+  struct Node {
+    C* data = nullptr;
+    C* grad = nullptr;
+    size_t numel = 0;
+    std::vector<int> shape;
+    bool needs_grad = false;
+  };
+
+  explicit Engine(cudaStream_t s) : stream_(s) {}
+  ~Engine();
+  void set_stream(cudaStream_t s) { stream_ = s; }
+  cudaStream_t stream() const { return stream_; }
+
+  // Start a new graph: resets the arena cursor and the tape.
+  void begin();
+  // New tensor (zero-filled on the stream); a leaf may require gradients.
+  int node(const std::vector<int>& shape, bool needs_grad = false);
+  // Register persistent device memory (a constant of the graph, no gradient).
+  int external(C* data, const std::vector<int>& shape);
+  View v(int node) const;
+  // Permuted / diagonal view: spec like "jikbac->ijkabc" or "pqkk->pqk".
+  View ev(const char* spec, const View& x) const;
+
+  void contract(const char* spec, double alpha, const View& A, const View& B, const View& Cv,
+                bool accumulate);
+  void axpy(double alpha, const View& X, const View& Y);
+  void mulc(const View& X, const View& Cst, const View& Y);
+  // Y += X / eps(index) with eps(index) = sum_d sign[d] * eps_dev[base[d] + index_d],
+  // the orbital-energy denominators; the division is carried out in FP64.
+  struct EpsSpec {
+    const double* eps = nullptr;
+    int sign[kMaxDim] = {0};
+    int base[kMaxDim] = {0};
+  };
+  void div_eps(const View& X, const EpsSpec& es, const View& Y);
+  // Non-differentiable initialisation.
+  void fill_identity(int node);
+  void fill_ones(int node);
+
+  // Allocate and zero gradient buffers of every node that needs one; after
+  // writing the seeds into grad(), call backward().
+  void prepare_backward();
+  void backward();
+
+  C* data(int n) const { return nodes_[n].data; }
+  C* grad(int n) const { return nodes_[n].grad; }
+  const Node& info(int n) const { return nodes_[n]; }
+  Arena& arena() { return arena_; }
+  size_t num_plans() const { return plans_.size(); }
+  int launches() const { return launches_; }
+  void reset_launch_count() { launches_ = 0; }
+  // When true, creating a new contraction plan raises (used while a CUDA
+  // graph is being captured: plans upload tables synchronously).
+  void freeze_plans(bool f) { frozen_ = f; }
+  void* scratch(size_t bytes);
+
+ private:
+  enum OpKind { kContract, kAxpy, kMulc, kDiv };
+  struct Op {
+    OpKind kind;
+    std::string spec;
+    double alpha;
+    View a, b, c;
+    EpsSpec es;
+  };
+  void run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg);
+  void run_contract(const std::string& spec, double alpha, const View& A, bool a_grad, const View& B,
+                    bool b_grad, const View& Cv, bool c_grad, bool accumulate);
+  void run_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg);
+  void run_mulc(const View& X, bool xg, const View& Cst, const View& Y, bool yg);
+  ContractPlan& plan(const std::string& spec, const View& A, const View& B, const View& Cv);
+
+  cudaStream_t stream_;
+  Arena arena_;
+  std::vector<Node> nodes_;
+  std::vector<Op> tape_;
+  std::map<std::string, std::unique_ptr<ContractPlan>> plans_;
+  void* scratch_ = nullptr;
+  size_t scratch_bytes_ = 0;
+  int launches_ = 0;
+  bool frozen_ = false;
+};
+
+// Small elementwise kernels used by the model and the integrator.
+template <typename R>
+void launch_fill(Cx<R>* p, size_t n, double re, double im, cudaStream_t s);
+
+}  // namespace rtcc3

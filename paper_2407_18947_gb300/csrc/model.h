@@ -1,0 +1,108 @@
+// The RT-CC3 residual graph (one RK4 stage for one field) and the small
+// device kernels of the integrator around it.
+#pragma once
+
+#include "common.h"
+#include "engine.h"
+
+namespace rtcc3 {
+
+// Field profile (Eq. 14 cosine, Eq. 32 Gaussian, static), one per batch slot.
+struct FieldDev {
+  int kind;  // 0 none, 1 static, 2 cos, 3 gauss
+  double amp, omega, center, width;
+  double dir[3];
+};
+
+// Hamiltonian constants on the device in the compute precision R, plus the
+// FP64 copies used by denominators and reductions.
+template <typename R>
+struct Hamil {
+  int o = 0, v = 0, n = 0, naux = 0;
+  Cx<R>* L = nullptr;     // naux x n x n, DF factors (real, stored complex)
+  Cx<R>* h = nullptr;     // n x n core Hamiltonian h = f - G[D_ref]
+  Cx<R>* ones = nullptr;  // n ones (for traces)
+  double* eps = nullptr;  // n orbital energies (FP64)
+  double* mu = nullptr;   // 3 x n x n dipole matrices (FP64)
+  double e_ref = 0.0;     // sum_i (h_ii + eps_i)
+};
+
+// Node ids of one recorded stage.
+struct StageNodes {
+  int t1 = -1, t2 = -1, w = -1;  // leaves
+  int r1 = -1, r2 = -1, e = -1;  // T residuals and the (reference-less) energy
+  int t3 = -1;                   // final triples amplitudes (for diagnostics)
+};
+
+struct StageOptions {
+  bool ccsd = true;  // false: R1, R2 hold only the triples terms X1, X2
+  bool triples = true;
+  bool need_grad = true;
+  bool field_terms = true;  // include the V-coupling of the triples equation
+  int field_iters = 1;      // fixed-point sweeps of the triples equation
+};
+
+// Records dressing, the CCSD residual, the triples and the energy (the same
+// equations as the paper's Appendix A: Eqs. A4, A8, A10-A12, A21, A22, A25,
+// A30) onto the engine's tape.  `fill` is called right after the leaves are
+// created so the caller can write t1, t2 and w before any operation reads them.
+template <typename R, typename Fill>
+StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt, Fill&& fill);
+
+// ---- integrator kernels (model.cu) --------------------------------------
+// Write the stage inputs: t = y + ch * kprev (FP64 -> R), lambda stage values
+// (kept for the seeds) and w = -E(t_s) dir . mu.
+template <typename R>
+void launch_stage_inputs(const double2* y, const double2* kprev, double ch, Cx<R>* t1, Cx<R>* t2,
+                         Cx<R>* l1s, Cx<R>* l2s, Cx<R>* w, const double* mu, const FieldDev* f,
+                         const double* tdev, double dt, int o, int v, int n, cudaStream_t s);
+// grad(e) = 1, grad(r1) = l1s, grad(r2) = l2s / 2 (Lagrangian E + l1.R1 + 1/2 l2.R2).
+template <typename R>
+void launch_seeds(Cx<R>* ge, Cx<R>* gr1, Cx<R>* gr2, const Cx<R>* l1s, const Cx<R>* l2s, int o,
+                  int v, cudaStream_t s);
+// k = (-i R1, -i R2, +i g1, +i (g2 + g2^T)); acc += hw * k; optional k copy.
+template <typename R>
+void launch_stage_output(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, const Cx<R>* g2,
+                         double2* kout, double2* acc, double hw, int o, int v, cudaStream_t s);
+// dipole[3] = sum_pq D_pq mu^x_pq (FP64) and energy = e - e_ref, written at
+// index *step of the trajectory arrays of slot b.
+template <typename R>
+void launch_observables(const Cx<R>* D, const Cx<R>* e, const double* mu, double e_ref, int n,
+                        double2* dip_traj, double2* en_traj, const int* step, int stride_steps,
+                        cudaStream_t s);
+// Host-readable FP64 copy of the residuals: out = [r1, r2, g1, g2 + g2^T].
+template <typename R>
+void launch_residual_export(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, const Cx<R>* g2,
+                            double2* out, int o, int v, bool have_grad, cudaStream_t s);
+// Jacobi update of one amplitude pair: x1 -= r1 / D1, x2 -= r2 / D2 (orbital-
+// energy denominators, FP64) and max |r| into *maxr.
+void launch_jacobi(double2* x1, double2* x2, const double2* r1, const double2* r2,
+                   const double* eps, int o, int v, double* maxr, cudaStream_t s);
+// DIIS support (ground state): e = -r / D, xs = x + e over one contiguous
+// amplitude block [x1 | x2]; max |r| into *maxr.
+void launch_diis_step(const double2* x, const double2* r, const double* eps, int o, int v,
+                      double2* xs, double2* es, double* maxr, cudaStream_t s);
+// out[k] = sum conj(E_k) . e for k < m (vectors of length len, stride len).
+void launch_dots(const double2* E, const double2* e, int m, size_t len, double2* out, cudaStream_t s);
+// x = sum_k c_k X_k.
+void launch_lincomb(const double2* X, const double2* c, int m, size_t len, double2* x, cudaStream_t s);
+// y = acc and flag non-finite entries (first bad step index kept in *bad_step).
+void launch_step_finish(double2* y, const double2* acc, size_t ny, const int* step, int* bad_step,
+                        cudaStream_t s);
+// *t += h; ++*step.
+void launch_step_advance(double* tdev, double h, int* step, cudaStream_t s);
+// Load t1, t2 (complex128 device arrays) into compute-precision leaves.
+template <typename R>
+void launch_load_amplitudes(const double2* t1, const double2* t2, Cx<R>* d1, Cx<R>* d2, int o,
+                            int v, cudaStream_t s);
+// out (complex128) = in (compute precision), n elements.
+template <typename R>
+void launch_export(const Cx<R>* in, double2* out, size_t n, cudaStream_t s);
+// w = -E(t) dir . mu for the field of one slot at time *tdev + dt.
+template <typename R>
+void launch_field_operator(Cx<R>* w, const double* mu, const FieldDev* f, const double* tdev,
+                           double dt, int n, cudaStream_t s);
+void launch_copy_c128(double2* dst, const double2* src, size_t n, cudaStream_t s);
+void launch_stage_prep_acc(double2* acc, const double2* y, size_t ny, cudaStream_t s);
+
+}  // namespace rtcc3

@@ -1,0 +1,198 @@
+// Recording of one RT-CC3 residual evaluation on the engine tape.
+//
+// Conventions (closed shell, occupied orbitals first, n = o + v):
+//   g[p,q,r,s] = (pq|rs)~  dressed chemists' integrals; the paper's <pq|rs> is (pr|qs)
+//   t1[i,a] = t_i^a, t2[i,j,a,b] = t_ij^ab, t3[i,j,k,a,b,c] = t_ijk^abc  (Eqs. A17-A19)
+//   w = beta V = -E(t) . mu (Eq. 1, Eq. 10)
+// The T residuals are R1 = <mu1|H + [H,T2] + [H,T3]|0>, R2 = <mu2|... + 1/2[[H,T2],T2]|0>
+// (Eqs. A10-A11) with H the T1-transformed Hamiltonian (Eq. 8, Eq. A4) and t3 the
+// solution of the triples equation Eq. 4 / Eq. A12 with dt3/dt = 0.
+#pragma once
+
+#include "model.h"
+
+namespace rtcc3 {
+
+template <typename R, typename Fill>
+StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt, Fill&& fill) {
+  const int o = H.o, v = H.v, n = H.n, na = H.naux;
+  StageNodes S;
+  S.t1 = E.node({o, v}, opt.need_grad);
+  S.t2 = E.node({o, o, v, v}, opt.need_grad);
+  S.w = E.node({n, n}, opt.need_grad);
+  fill(S);
+
+  const int Lc = E.external(H.L, {na, n, n});
+  const int hc = E.external(H.h, {n, n});
+  const int on = E.external(H.ones, {n});
+  const View ones_o = E.v(on).sub(0, 0, o);
+  const View T = E.v(S.t2);
+
+  // ---- T1 dressing: X = 1 - tau, Y = 1 + tau, tau[a,i] = t_i^a ----------------
+  const int X = E.node({n, n}), Y = E.node({n, n});
+  E.fill_identity(X);
+  E.fill_identity(Y);
+  const View t1T = E.ev("ia->ai", E.v(S.t1));
+  E.axpy(-1.0, t1T, E.v(X).sub(0, o, v).sub(1, 0, o));
+  E.axpy(1.0, t1T, E.v(Y).sub(0, o, v).sub(1, 0, o));
+  const int LX = E.node({na, n, n}), Lt = E.node({na, n, n});
+  E.contract("pr,Prs->Pps", 1.0, E.v(X), E.v(Lc), E.v(LX), true);
+  E.contract("Pps,sq->Ppq", 1.0, E.v(LX), E.v(Y), E.v(Lt), true);
+  const int hw = E.node({n, n}), hX = E.node({n, n}), ht = E.node({n, n});
+  E.axpy(1.0, E.v(hc), E.v(hw));
+  E.axpy(1.0, E.v(S.w), E.v(hw));
+  E.contract("pr,rs->ps", 1.0, E.v(X), E.v(hw), E.v(hX), true);
+  E.contract("ps,sq->pq", 1.0, E.v(hX), E.v(Y), E.v(ht), true);
+  const int wX = E.node({n, n}), wt = E.node({n, n});
+  E.contract("pr,rs->ps", 1.0, E.v(X), E.v(S.w), E.v(wX), true);
+  E.contract("ps,sq->pq", 1.0, E.v(wX), E.v(Y), E.v(wt), true);
+  const int g = E.node({n, n, n, n});
+  E.contract("Ppq,Prs->pqrs", 1.0, E.v(Lt), E.v(Lt), E.v(g), true);
+  // f~ = h~ + sum_k 2 g~_pqkk - g~_pkkq
+  const int ft = E.node({n, n});
+  E.axpy(1.0, E.v(ht), E.v(ft));
+  E.contract("pqk,k->pq", 2.0, E.ev("pqkk->pqk", E.v(g).sub(2, 0, o).sub(3, 0, o)), ones_o,
+             E.v(ft), true);
+  E.contract("pkq,k->pq", -1.0, E.ev("pkkq->pkq", E.v(g).sub(1, 0, o).sub(2, 0, o)), ones_o,
+             E.v(ft), true);
+
+  // block views: 'o' -> [0,o), 'v' -> [o,n)
+  auto blk = [&](int node, const char* b) {
+    View r = E.v(node);
+    for (int d = 0; b[d]; ++d) r = (b[d] == 'o') ? r.sub(d, 0, o) : r.sub(d, o, v);
+    return r;
+  };
+  auto G = [&](const char* b) { return blk(g, b); };
+  auto F = [&](const char* b) { return blk(ft, b); };
+
+  // ---- CCSD residual (T1-transformed, spin adapted) ---------------------------
+  const int u = E.node({o, o, v, v});
+  E.axpy(2.0, T, E.v(u));
+  E.axpy(-1.0, E.ev("ijba->ijab", T), E.v(u));
+  const View U = E.v(u);
+  S.r1 = E.node({o, v});
+  const View R1 = E.v(S.r1);
+  S.r2 = E.node({o, o, v, v});
+  const View R2 = E.v(S.r2);
+  const int Sd = E.node({o, o, v, v});
+  const View SD = E.v(Sd);
+  const int Lov = E.node({o, v, o, v});
+  E.axpy(2.0, G("ovov"), E.v(Lov));
+  E.axpy(-1.0, E.ev("lckd->ldkc", G("ovov")), E.v(Lov));
+  if (opt.ccsd) {
+  E.contract("kicd,adkc->ia", 1.0, U, G("vvov"), R1, true);
+  E.contract("klac,kilc->ia", -1.0, U, G("ooov"), R1, true);
+  E.contract("ikac,kc->ia", 1.0, U, F("ov"), R1, true);
+  E.axpy(1.0, E.ev("ai->ia", F("vo")), R1);
+
+  E.axpy(1.0, E.ev("aibj->ijab", G("vovo")), R2);
+  E.contract("ijcd,acbd->ijab", 1.0, T, G("vvvv"), R2, true);
+  const int Wk = E.node({o, o, o, o});
+  E.axpy(1.0, G("oooo"), E.v(Wk));
+  E.contract("ijcd,kcld->kilj", 1.0, T, G("ovov"), E.v(Wk), true);
+  E.contract("klab,kilj->ijab", 1.0, T, E.v(Wk), R2, true);
+  const int Xc = E.node({o, o, v, v});
+  E.axpy(1.0, G("oovv"), E.v(Xc));
+  E.contract("liad,kdlc->kiac", -0.5, T, G("ovov"), E.v(Xc), true);
+  E.contract("kjbc,kiac->ijab", -0.5, T, E.v(Xc), SD, true);
+  E.contract("kibc,kjac->ijab", -1.0, T, E.v(Xc), SD, true);
+  const int Ltv = E.node({v, o, o, v});
+  E.axpy(2.0, G("voov"), E.v(Ltv));
+  E.axpy(-1.0, E.ev("acki->aikc", G("vvoo")), E.v(Ltv));
+  const int Xd = E.node({o, v, o, v});
+  E.axpy(1.0, E.ev("aikc->iakc", E.v(Ltv)), E.v(Xd));
+  E.contract("ilad,ldkc->iakc", 0.5, U, E.v(Lov), E.v(Xd), true);
+  E.contract("jkbc,iakc->ijab", 0.5, U, E.v(Xd), SD, true);
+  const int Fvv = E.node({v, v}), Foo = E.node({o, o});
+  E.axpy(1.0, F("vv"), E.v(Fvv));
+  E.contract("klbd,ldkc->bc", -1.0, U, G("ovov"), E.v(Fvv), true);
+  E.axpy(1.0, F("oo"), E.v(Foo));
+  E.contract("ljcd,kdlc->kj", 1.0, U, G("ovov"), E.v(Foo), true);
+  E.contract("ijac,bc->ijab", 1.0, T, E.v(Fvv), SD, true);
+  E.contract("ikab,kj->ijab", -1.0, T, E.v(Foo), SD, true);
+  }  // opt.ccsd
+
+  // ---- triples ---------------------------------------------------------------
+  if (opt.triples) {
+    const std::vector<int> s6 = {o, o, o, v, v, v};
+    static const char* perms[6] = {"ijkabc->ijkabc", "jikbac->ijkabc", "ikjacb->ijkabc",
+                                   "kjicba->ijkabc", "kijcab->ijkabc", "jkibca->ijkabc"};
+    // Z = sum_e t_ij^ae <cb|ke>~ - sum_m t_im^ab <mc|jk>~ ; W = P_ijk^abc Z (Eqs. A25, A30)
+    const int Z = E.node(s6);
+    E.contract("ijae,ckbe->ijkabc", 1.0, T, G("vovv"), E.v(Z), true);
+    E.contract("imab,mjck->ijkabc", -1.0, T, G("oovo"), E.v(Z), true);
+    // rhs = -(W + <mu3|1/2[[V~,T2],T2]|0>), the latter = -P sum_ld v~_ld t_ij^ad t_kl^cb
+    const int rhs = E.node(s6);
+    for (auto p : perms) E.axpy(-1.0, E.ev(p, E.v(Z)), E.v(rhs));
+    const bool field = opt.field_terms;
+    if (field) {
+      const int Yl = E.node({o, o, o, v});
+      E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), true);
+      const int Z2 = E.node(s6);
+      E.contract("lija,klcb->ijkabc", 1.0, E.v(Yl), T, E.v(Z2), true);
+      for (auto p : perms) E.axpy(1.0, E.ev(p, E.v(Z2)), E.v(rhs));
+    }
+    typename Engine<R>::EpsSpec es;
+    es.eps = H.eps;
+    for (int d = 0; d < 3; ++d) { es.sign[d] = -1; es.base[d] = 0; }
+    for (int d = 3; d < 6; ++d) { es.sign[d] = 1; es.base[d] = o; }
+    int t3 = E.node(s6);
+    E.div_eps(E.v(rhs), es, E.v(t3));
+    // eps3 t3 + [V~,T3] = rhs: +v~_ad on virtual slots, -v~_li on occupied slots
+    const int iters = field ? std::max(1, opt.field_iters) : 0;
+    const View wvv = blk(wt, "vv"), woo = blk(wt, "oo");
+    for (int it = 0; it < iters; ++it) {
+      const int sx = E.node(s6);
+      const View SX = E.v(sx), T3 = E.v(t3);
+      E.axpy(1.0, E.v(rhs), SX);
+      E.contract("ad,ijkdbc->ijkabc", -1.0, wvv, T3, SX, true);
+      E.contract("bd,ijkadc->ijkabc", -1.0, wvv, T3, SX, true);
+      E.contract("cd,ijkabd->ijkabc", -1.0, wvv, T3, SX, true);
+      E.contract("li,ljkabc->ijkabc", 1.0, woo, T3, SX, true);
+      E.contract("lj,ilkabc->ijkabc", 1.0, woo, T3, SX, true);
+      E.contract("lk,ijlabc->ijkabc", 1.0, woo, T3, SX, true);
+      const int tn = E.node(s6);
+      E.div_eps(SX, es, E.v(tn));
+      t3 = tn;
+    }
+    S.t3 = t3;
+    const View T3 = E.v(t3);
+    // X1 (Eq. A21) and X2 (Eq. A22)
+    const int dd = E.node(s6);
+    E.axpy(1.0, T3, E.v(dd));
+    E.axpy(-1.0, E.ev("ijkcba->ijkabc", T3), E.v(dd));
+    const int Ljk = E.node({o, o, v, v});
+    E.axpy(2.0, E.ev("jbkc->jkbc", G("ovov")), E.v(Ljk));
+    E.axpy(-1.0, E.ev("jckb->jkbc", G("ovov")), E.v(Ljk));
+    E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), E.v(Ljk), R1, true);
+    const int S3 = E.node({o, o, v, v});
+    E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), F("ov"), E.v(S3), true);
+    const int Ub = E.node(s6);
+    E.axpy(2.0, T3, E.v(Ub));
+    E.axpy(-1.0, E.ev("ijkxzy->ijkxyz", T3), E.v(Ub));
+    E.axpy(-1.0, E.ev("ijkzyx->ijkxyz", T3), E.v(Ub));
+    E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), G("vvov"), E.v(S3), true);
+    const int Uc = E.node(s6);
+    E.axpy(2.0, T3, E.v(Uc));
+    E.axpy(-1.0, E.ev("mjkyxz->mjkxyz", T3), E.v(Uc));
+    E.axpy(-1.0, E.ev("mjkzyx->mjkxyz", T3), E.v(Uc));
+    E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), G("ooov"), E.v(S3), true);
+    E.axpy(1.0, E.v(S3), SD);
+  }
+  // P_ij^ab on the symmetrised part
+  E.axpy(1.0, SD, R2);
+  E.axpy(1.0, E.ev("jiba->ijab", SD), R2);
+
+  // ---- energy <0|H + [H,T2]|0> - E_ref (Eq. A8); E_ref is subtracted in FP64 ----
+  S.e = E.node({});
+  const View Ev = E.v(S.e);
+  const int oo = E.node({o, o});
+  E.fill_ones(oo);
+  E.contract("i,i->", 2.0, E.ev("ii->i", blk(ht, "oo")), ones_o, Ev, true);
+  E.contract("ij,ij->", 2.0, E.ev("iijj->ij", G("oooo")), E.v(oo), Ev, true);
+  E.contract("ij,ij->", -1.0, E.ev("ijji->ij", G("oooo")), E.v(oo), Ev, true);
+  E.contract("ijab,iajb->", 1.0, T, E.v(Lov), Ev, true);
+  return S;
+}
+
+}  // namespace rtcc3
