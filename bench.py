@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""RT-CC3 hot-path benchmark: RK4 steps/s on the (H2O)2-sized synthetic workload.
+
+One timed step is one full RK4 step (four residual evaluations, each the
+T1 dressing, CCSD residual, connected triples with field coupling, X1/X2,
+energy, and the reverse pass giving the lambda residuals and the density)
+plus the FP64 RK4 update, for every field slot, through librtcc3's C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|tf32|bf16]
+                    [--impl gpu|reference] [--workload 1..5]
+
+Under torchrun each rank propagates its own field (weak scaling, no data-path
+collective); rank 0 prints one JSON line.  ``--impl reference`` times the CPU
+oracle on the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RT-CC3 RK4 steps/s at (H2O)n-sized o,v; triples TFLOP/s vs GB300 peak"
+UNIT = "RK4 steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# field per workload (amplitude au, omega au, kind); kind 1 static, 2 cos
+WORKLOADS = {
+    1: dict(n=1, kind=1, amp=0.002, omega=0.0, h=0.01),
+    2: dict(n=2, kind=2, amp=0.001, omega=0.0656, h=0.01),
+    3: dict(n=3, kind=1, amp=0.002, omega=0.0, h=0.01),
+    4: dict(n=4, kind=1, amp=0.002, omega=0.0, h=0.01),
+    5: dict(n=5, kind=1, amp=0.002, omega=0.0, h=0.01),
+}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+DTYPES = {"fp64": "c128 (f64)", "fp32": "c64 (f32)", "tf32": "c64 (tf32 triples, f32 acc)",
+          "bf16": "c64 (bf16 triples, f32 acc)"}
+
+
+def nominal_flops(o, v):
+    """8 (93 o^3 v^4 + 134 o^4 v^3) real flops per RK4 step per field: the
+    paper's factorised triples work (t3 and lambda3 once per stage, density
+    once per step), counted at 8 flops per complex multiply-add."""
+    return 8.0 * (93.0 * o ** 3 * v ** 4 + 134.0 * o ** 4 * v ** 3)
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def roofline_of(stats, peaks, peak_kind, precision):
+    """Dominant kernel (largest device time) against its own roofline."""
+    if not stats:
+        return None, None
+    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    sec = st["ms"] / 1e3
+    per_launch = sec / max(st["launches"], 1)
+    tflops = st["flops"] / sec / 1e12 if sec > 0 else 0.0
+    gbs = st["bytes"] / sec / 1e9 if sec > 0 else 0.0
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    if name.startswith("contract_simt"):
+        # CUDA-core complex FMA: 152 SMs x 128 FP32 lanes x 2 flop/cycle (FP32),
+        # FP64 at the GB300 nominal 1.25 TFLOP/s
+        if "c128" in name:
+            peak, note = 1.25, "nominal FP64 (recipe table)"
+        else:
+            peak, note = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "152 SM x 128 FP32 lanes x 2 x max SM clock"
+        rl = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+              "frac": round(tflops / peak, 4), "traffic": None, "kernel": name, "peak_source": note}
+    elif name.startswith("contract_tc"):
+        ratio = 1.1 / 2.25 if "tf32" in name else 1.0
+        peak = peaks["bf16_tflops_sustained"] * ratio
+        rl = {"bound": "tensor", "achieved": round(tflops, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+              "frac": round(tflops / peak, 4), "traffic": None, "kernel": name,
+              "peak_source": f"{peak_kind} bf16 sustained x nominal dtype ratio"}
+    else:
+        peak = peaks["hbm_gbs"]
+        rl = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+              "frac": round(gbs / peak, 4), "traffic": None, "kernel": name,
+              "peak_source": f"{peak_kind} hbm_gbs"}
+    rl["launches"] = st["launches"]
+    rl["avg_launch_us"] = round(per_launch * 1e6, 3)
+    rl["share_of_step"] = round(st["ms"] / sum(s["ms"] for s in stats.values()), 4)
+    return rl, name
+
+
+def oracle_stage_seconds(wl, threads=None):
+    """One oracle residual evaluation (1 of the 4 RK4 stages) on the workload."""
+    import torch
+
+    from oracle import cc3
+    from paper_2407_18947_gb300.synth import random_amplitudes, water_system
+    if threads:
+        torch.set_num_threads(threads)
+    s = water_system(wl["n"])
+    ham = cc3.Hamiltonian.from_system(s)
+    t1, t2, l1, l2 = random_amplitudes(s.nocc, s.nvir, seed=1)
+    w = ham.field_operator([0.0, 0.0, wl["amp"]])
+    t0 = time.perf_counter()
+    cc3.evaluate(ham, t1, t2, l1, l2, w)
+    return time.perf_counter() - t0, torch.get_num_threads()
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    o, v = 5 * wl["n"], 19 * wl["n"]
+    secs, cores = oracle_stage_seconds(wl)
+    value = 1.0 / (4.0 * secs)
+    sample = (f"one residual evaluation (1 of 4 RK4 stages: forward + Lagrangian derivatives) of the "
+              f"nocc={o} nvir={v} workload, extrapolated x4 per RK4 step; the --steps/--warmup loop is "
+              f"not repeated because one stage takes ~{secs:.0f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 4e3 * secs, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64, CPU)", "data": "synthetic",
+            "config": workload_config(wl, "fp64", 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(wl, precision, nbatch):
+    o, v = 5 * wl["n"], 19 * wl["n"]
+    field = ("static" if wl["kind"] == 1 else f"cos omega={wl['omega']} au") + f" A={wl['amp']} au along z"
+    return {"workload": f"(H2O){wl['n']}-sized RT-CC3: nocc={o} nvir={v} naux={3 * (o + v)}, {field}, "
+                        f"h={wl['h']} au, T and lambda propagated",
+            "nocc": o, "nvir": v, "precision": precision, "fields_per_gpu": nbatch,
+            "l2": "working set larger than L2 (o^3 v^3 triples tensors)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", type=int, default=2, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2407_18947_gb300.api import RTCC3
+    from paper_2407_18947_gb300.synth import water_system
+
+    s = water_system(wl["n"])
+    o, v = s.nocc, s.nvir
+    prec = PRECISIONS[args.precision]
+    eng = RTCC3(o, v, nbatch=1, precision=prec, device=local)
+    eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+    # each rank propagates its own field strength (independent problems)
+    amp = wl["amp"] * (1.0 + 0.25 * rank)
+    eng.set_field(0, wl["kind"], amp, omega=wl["omega"], direction=(0.0, 0.0, 1.0))
+    t0 = time.perf_counter()
+    eng.solve_ground_state(tol=1e-10 if prec == 0 else 1e-5, maxiter=400)
+    t_gs = time.perf_counter() - t0
+    y0 = eng.get_amplitudes(0)
+    h = wl["h"]
+    K, W = args.steps, args.warmup
+    dev = torch.device("cuda", local)
+    dip = torch.zeros((1, max(K, W) + 1, 3, 2), dtype=torch.float64, device=dev)
+    en = torch.zeros((1, max(K, W) + 1, 2), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # warm-up (captures the step graph)
+    eng.propagate_rk4_dev(h, W, dip.data_ptr(), en.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    eng.propagate_rk4_dev(h, K, dip.data_ptr(), en.data_ptr(), stream.cuda_stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = eng.stats()["launches"]
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * K / (ms_max / 1e3)
+    dip_h = dip.cpu().numpy()
+    assert np.all(np.isfinite(dip_h[0, :K + 1])), "non-finite dipole trajectory"
+
+    # end to end through the host API: every step uploads the state from
+    # pinned host memory, runs one RK4 step and reads back dipole and energy
+    e2e = None
+    if not args.no_e2e:
+        ke = max(1, min(K, 5))
+        pinned = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy() for x in y0]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            eng.set_amplitudes(0, *pinned)
+            d_h, e_h = eng.propagate_rk4(h, 1)
+        t_e2e = time.perf_counter() - t0
+        h2d = sum(x.nbytes for x in pinned)
+        d2h = d_h.nbytes + e_h.nbytes
+        e2e = {"value": world * ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # per-kernel device times (CUDA events on the library stream, eager launches)
+    eng.set_amplitudes(0, *y0)
+    eng.set_profiling(True)
+    eng.propagate_rk4(h, 1)
+    kstats = eng.kernel_stats()
+    eng.set_profiling(False)
+    peaks, peak_kind = load_peaks()
+    roofline, dom = roofline_of(kstats, peaks, peak_kind, args.precision)
+    flops = nominal_flops(o, v)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, cores = oracle_stage_seconds(wl)
+        cpu = {"value": 1.0 / (4.0 * secs), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one residual evaluation (1 of 4 RK4 stages) of the same workload on the host, "
+                         f"{secs:.1f} s, extrapolated x4 per RK4 step"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPES[args.precision], "data": "synthetic",
+                "config": workload_config(wl, args.precision, 1),
+                "triples_tflops_nominal": round(flops * world * K / (ms_max / 1e3) / 1e12, 3),
+                "nominal_flops_per_step": flops,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk, "ground_state_s": round(t_gs, 2),
+                "kernels": {k: {"launches": v_["launches"], "ms": round(v_["ms"], 4)}
+                            for k, v_ in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])}}
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

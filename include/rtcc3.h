@@ -149,6 +149,21 @@ int rtcc3_set_state(rtcc3_ctx* ctx, const void* buf, long long bytes);
  * compute call, and bytes of device memory reserved by the context. */
 int rtcc3_stats(const rtcc3_ctx* ctx, long long* launches, long long* device_bytes);
 
+/* Per-kernel timing.  While enabled, every launch of the library is
+ * bracketed by CUDA events on its stream and CUDA graphs are not used;
+ * rtcc3_kernel_stats returns, per kernel name, the launch count, total
+ * device milliseconds and the algorithmic flops and bytes of those launches
+ * (operands read once, results written once).  Enabling resets the tallies. */
+typedef struct rtcc3_kernel_stat {
+  char name[48];
+  long long launches;
+  double ms;
+  double flops;
+  double bytes;
+} rtcc3_kernel_stat;
+int rtcc3_set_profiling(rtcc3_ctx* ctx, int enable);
+int rtcc3_kernel_stats(rtcc3_ctx* ctx, rtcc3_kernel_stat* out, int max_entries, int* count);
+
 #ifdef __cplusplus
 }
 #endif

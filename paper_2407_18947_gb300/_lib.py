@@ -28,6 +28,11 @@ class Options(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("field_tol", ctypes.c_double)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 #: Every exported symbol with (restype, argtypes); mirrors include/rtcc3.h.
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -55,6 +60,8 @@ SIGNATURES = {
     "rtcc3_get_state": (_I, [_P, _P, ctypes.c_longlong]),
     "rtcc3_set_state": (_I, [_P, _P, ctypes.c_longlong]),
     "rtcc3_stats": (_I, [_P, _LLP, _LLP]),
+    "rtcc3_set_profiling": (_I, [_P, _I]),
+    "rtcc3_kernel_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
 }
 
 _lib = None

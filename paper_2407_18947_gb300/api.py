@@ -160,3 +160,16 @@ class RTCC3:
         a, b = ctypes.c_longlong(), ctypes.c_longlong()
         self._check(self.lib.rtcc3_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return {"launches": a.value, "device_bytes": b.value}
+
+    def set_profiling(self, enable: bool):
+        self._check(self.lib.rtcc3_set_profiling(self.h, 1 if enable else 0))
+
+    def kernel_stats(self):
+        """Per-kernel {name: dict(launches, ms, flops, bytes)} since profiling was enabled."""
+        cnt = ctypes.c_int()
+        self._check(self.lib.rtcc3_kernel_stats(self.h, None, 0, ctypes.byref(cnt)))
+        arr = (_lib.KernelStat * max(cnt.value, 1))()
+        self._check(self.lib.rtcc3_kernel_stats(self.h, arr, cnt.value, ctypes.byref(cnt)))
+        return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms,
+                                        "flops": arr[i].flops, "bytes": arr[i].bytes}
+                for i in range(cnt.value)}

@@ -82,6 +82,14 @@ struct rtcc3_ctx {
   double time = 0.0;
   long long step_total = 0;
   long long last_launches = 0;
+  Profiler prof;
+  TrajDesc* tdesc = nullptr;
+  // cached CUDA graph of one RK4 step (all slots)
+  cudaGraphExec_t gexec = nullptr;
+  double gh = 0.0;
+  std::vector<int> gsweeps;
+  int ggen = -1;
+  long long gsteplaunches = 0;
   std::vector<void*> owned;
 
   template <typename T>
@@ -95,6 +103,7 @@ struct rtcc3_ctx {
   template <typename R>
   Runner<R>& run() { return *static_cast<Runner<R>*>(runner.get()); }
   ~rtcc3_ctx() {
+    if (gexec) cudaGraphExecDestroy(gexec);
     runner.reset();
     if (dip_traj) cudaFree(dip_traj);
     if (en_traj) cudaFree(en_traj);
@@ -104,6 +113,18 @@ struct rtcc3_ctx {
 };
 
 namespace {
+
+// Times the launches issued inside its scope when profiling is enabled.
+struct PScope {
+  Profiler& p;
+  cudaStream_t s;
+  const char* name;
+  double flops, bytes;
+  int k;
+  PScope(Profiler& p_, cudaStream_t s_, const char* n, double f, double b)
+      : p(p_), s(s_), name(n), flops(f), bytes(b), k(p_.begin(s_)) {}
+  ~PScope() { p.end(k, s, name, flops, bytes); }
+};
 
 int fail(rtcc3_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -178,13 +199,18 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
   so.field_iters = sweeps;
   (void)ccsd_terms;
   StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
+    PScope ps(ctx->prof, ctx->stream, "stage_inputs", 0.0,
+              double(ctx->ny) * (kprev ? 32.0 : 16.0) + double(ctx->ny) * sizeof(Cx<R>));
     launch_stage_inputs<R>(ybase, kprev, ch, E.data(s.t1), E.data(s.t2), Rn.l1s, Rn.l2s,
                            E.data(s.w), ctx->mu, f, tsrc, dt, ctx->o, ctx->v, ctx->n, ctx->stream);
   });
   if (need_grad) {
     E.prepare_backward();
-    launch_seeds<R>(E.grad(S.e), E.grad(S.r1), E.grad(S.r2), Rn.l1s, Rn.l2s, ctx->o, ctx->v,
-                    ctx->stream);
+    {
+      PScope ps(ctx->prof, ctx->stream, "seeds", 0.0, double(ctx->ny) * sizeof(Cx<R>));
+      launch_seeds<R>(E.grad(S.e), E.grad(S.r1), E.grad(S.r2), Rn.l1s, Rn.l2s, ctx->o, ctx->v,
+                      ctx->stream);
+    }
     E.backward();
   }
   return S;
@@ -231,6 +257,7 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
   RTCC3_CUDA(cudaMemcpy(H.h, hc.data(), hc.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
   RTCC3_CUDA(cudaMemcpy(H.L, Lc.data(), Lc.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
   RTCC3_CUDA(cudaMemcpy(H.ones, ones.data(), ones.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
+  rn->E.set_profiler(&ctx->prof);
   ctx->runner = std::move(rn);
 }
 
@@ -248,44 +275,58 @@ void ensure_traj(rtcc3_ctx* ctx, size_t entries) {
 // One RK4 step for every slot; observables of the step-start state go to
 // trajectory entry *stepdev of slot b (arrays strided by `stride`).
 template <typename R>
-void rk4_step(rtcc3_ctx* ctx, double h, double2* dip, double2* en, size_t stride,
-              const std::vector<int>& sweeps) {
+void rk4_step(rtcc3_ctx* ctx, double h, const std::vector<int>& sweeps) {
   Runner<R>& Rn = ctx->run<R>();
   Engine<R>& E = Rn.E;
   const double cs[4] = {0.0, 0.5, 0.5, 1.0};
   const double ws[4] = {1.0, 2.0, 2.0, 1.0};
   for (int b = 0; b < ctx->nb; ++b) {
     double2* yb = ctx->y + size_t(b) * ctx->ny;
-    launch_stage_prep_acc(ctx->acc, yb, ctx->ny, ctx->stream);
+    const double ybytes = double(ctx->ny) * 16.0;
+    {
+      PScope ps(ctx->prof, ctx->stream, "rk4_update", 0.0, 2.0 * ybytes);
+      launch_stage_prep_acc(ctx->acc, yb, ctx->ny, ctx->stream);
+    }
     for (int s = 0; s < 4; ++s) {
       StageNodes S = eval_stage<R>(ctx, b, yb, s == 0 ? nullptr : ctx->kbuf, cs[s] * h, ctx->tdev,
                                    cs[s] * h, true, ctx->fdev + b, true, sweeps[b]);
-      if (s == 0)
-        launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n,
-                              dip ? dip + size_t(b) * stride * 3 : nullptr,
-                              en ? en + size_t(b) * stride : nullptr, ctx->stepdev, 0, ctx->stream);
+      if (s == 0) {
+        PScope ps(ctx->prof, ctx->stream, "observables", 8.0 * ctx->n * ctx->n,
+                  double(ctx->n) * ctx->n * (sizeof(Cx<R>) + 24.0));
+        launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->tdesc,
+                              b, ctx->stepdev, ctx->stream);
+      }
+      PScope ps(ctx->prof, ctx->stream, "rk4_update", 4.0 * ctx->ny,
+                double(ctx->ny) * sizeof(Cx<R>) + (s < 3 ? 3.0 : 2.0) * ybytes);
       launch_stage_output<R>(E.data(S.r1), E.data(S.r2), E.grad(S.t1), E.grad(S.t2),
                              s < 3 ? ctx->kbuf : nullptr, ctx->acc, h * ws[s] / 6.0, ctx->o, ctx->v,
                              ctx->stream);
     }
+    PScope ps(ctx->prof, ctx->stream, "rk4_update", 0.0, 2.0 * ybytes);
     launch_step_finish(yb, ctx->acc, ctx->ny, ctx->stepdev, ctx->baddev, ctx->stream);
   }
   launch_step_advance(ctx->tdev, h, ctx->stepdev, ctx->stream);
 }
 
 template <typename R>
-void final_observables(rtcc3_ctx* ctx, double2* dip, double2* en, size_t stride,
-                       const std::vector<int>& sweeps) {
+void final_observables(rtcc3_ctx* ctx, const std::vector<int>& sweeps) {
   Runner<R>& Rn = ctx->run<R>();
   Engine<R>& E = Rn.E;
   for (int b = 0; b < ctx->nb; ++b) {
     double2* yb = ctx->y + size_t(b) * ctx->ny;
     StageNodes S = eval_stage<R>(ctx, b, yb, nullptr, 0.0, ctx->tdev, 0.0, true, ctx->fdev + b,
                                  true, sweeps[b]);
-    launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n,
-                          dip ? dip + size_t(b) * stride * 3 : nullptr,
-                          en ? en + size_t(b) * stride : nullptr, ctx->stepdev, 0, ctx->stream);
+    PScope ps(ctx->prof, ctx->stream, "observables", 8.0 * ctx->n * ctx->n,
+              double(ctx->n) * ctx->n * (sizeof(Cx<R>) + 24.0));
+    launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->tdesc, b,
+                          ctx->stepdev, ctx->stream);
   }
+}
+
+void drop_graph(rtcc3_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  ctx->gsweeps.clear();
 }
 
 template <typename R>
@@ -293,46 +334,66 @@ void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2*
   Engine<R>& E = ctx->run<R>().E;
   std::vector<int> sweeps(ctx->nb);
   for (int b = 0; b < ctx->nb; ++b) sweeps[b] = field_sweeps(ctx, b);
+  const TrajDesc td{dip, en, (long long)stride};
+  RTCC3_CUDA(cudaMemcpyAsync(ctx->tdesc, &td, sizeof(td), cudaMemcpyHostToDevice, ctx->stream));
   RTCC3_CUDA(cudaMemsetAsync(ctx->stepdev, 0, sizeof(int), ctx->stream));
   const int minus1 = -1;
   RTCC3_CUDA(cudaMemcpyAsync(ctx->baddev, &minus1, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  // stage-local buffers must not be overwritten before the copies above land
+  RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   E.reset_launch_count();
+  const bool graphs = ctx->opt.use_graphs && !ctx->prof.enabled;
+  // the captured step depends on h, the sweep counts and the engine's
+  // persistent buffers; anything else is read from device memory
+  if (ctx->gexec && (!graphs || ctx->gh != h || ctx->gsweeps != sweeps || ctx->ggen != E.generation()))
+    drop_graph(ctx);
   int done = 0;
-  if (nsteps > 0) {
-    rk4_step<R>(ctx, h, dip, en, stride, sweeps);  // eager: builds plans and arena
+  long long launches = 0;
+  if (graphs && !ctx->gexec && nsteps > 0) {
+    rk4_step<R>(ctx, h, sweeps);  // eager first step: builds plans, arena and scratch
     done = 1;
-  }
-  if (nsteps > 1 && ctx->opt.use_graphs) {
+    launches += E.launches();
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     E.freeze_plans(true);
-    const int launches_before = E.launches();
+    const int before = E.launches();
     try {
       RTCC3_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
       try {
-        rk4_step<R>(ctx, h, dip, en, stride, sweeps);
+        rk4_step<R>(ctx, h, sweeps);
       } catch (...) {
         cudaStreamEndCapture(ctx->stream, &graph);
         if (graph) cudaGraphDestroy(graph);
         throw;
       }
       RTCC3_CUDA(cudaStreamEndCapture(ctx->stream, &graph));
-      RTCC3_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      RTCC3_CUDA(ie);
+      ctx->gexec = exec;
     } catch (...) {
       E.freeze_plans(false);
       throw;
     }
     E.freeze_plans(false);
-    const int per_step = E.launches() - launches_before;
-    for (; done < nsteps; ++done) RTCC3_CUDA(cudaGraphLaunch(exec, ctx->stream));
-    ctx->last_launches = (long long)E.launches() + (long long)per_step * (nsteps - 2);
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-  } else {
-    for (; done < nsteps; ++done) rk4_step<R>(ctx, h, dip, en, stride, sweeps);
-    ctx->last_launches = E.launches();
+    ctx->gsteplaunches = E.launches() - before;
+    ctx->gh = h;
+    ctx->gsweeps = sweeps;
+    ctx->ggen = E.generation();
   }
-  final_observables<R>(ctx, dip, en, stride, sweeps);
+  if (graphs && ctx->gexec) {
+    for (; done < nsteps; ++done) {
+      RTCC3_CUDA(cudaGraphLaunch(ctx->gexec, ctx->stream));
+      launches += ctx->gsteplaunches;
+    }
+  } else {
+    E.reset_launch_count();
+    for (; done < nsteps; ++done) rk4_step<R>(ctx, h, sweeps);
+    launches += E.launches();
+  }
+  E.reset_launch_count();
+  final_observables<R>(ctx, sweeps);
+  ctx->last_launches = launches + E.launches();
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->time += h * nsteps;
   ctx->step_total += nsteps;
@@ -364,8 +425,10 @@ void residuals_impl(rtcc3_ctx* ctx, int b, double time, double* r_t1, double* r_
                             need_grad ? E.grad(S.t2) : nullptr, ctx->res, ctx->o, ctx->v, need_grad,
                             ctx->stream);
   ensure_traj(ctx, 1);
+  const TrajDesc td{ctx->dip_traj, ctx->en_traj, 0};
+  RTCC3_CUDA(cudaMemcpyAsync(ctx->tdesc, &td, sizeof(td), cudaMemcpyHostToDevice, ctx->stream));
   launch_observables<R>(need_grad ? E.grad(S.w) : E.data(S.w), E.data(S.e), ctx->mu, ctx->e_ref,
-                        ctx->n, ctx->dip_traj, ctx->en_traj, nullptr, 0, ctx->stream);
+                        ctx->n, ctx->tdesc, 0, nullptr, ctx->stream);
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->last_launches = E.launches();
   const size_t n1 = ctx->n1, n2 = ctx->n2;
@@ -589,6 +652,7 @@ int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3
     raw->stepdev = raw->dalloc<int>(1);
     raw->baddev = raw->dalloc<int>(1);
     raw->maxr = raw->dalloc<double>(1);
+    raw->tdesc = raw->dalloc<TrajDesc>(1);
     raw->fhost.assign(nbatch, FieldDev{0, 0.0, 0.0, 0.0, 1.0, {0.0, 0.0, 1.0}});
     RTCC3_CUDA(cudaMemcpy(raw->fdev, raw->fhost.data(), nbatch * sizeof(FieldDev), cudaMemcpyHostToDevice));
     RTCC3_CUDA(cudaMemcpy(raw->fnone, raw->fhost.data(), sizeof(FieldDev), cudaMemcpyHostToDevice));
@@ -627,6 +691,7 @@ int rtcc3_set_hamiltonian(rtcc3_ctx* ctx, const double* eps, int naux, const dou
     if (!ctx->mu) ctx->mu = ctx->dalloc<double>(size_t(3) * n * n);
     RTCC3_CUDA(cudaMemcpy(ctx->eps, eps, n * sizeof(double), cudaMemcpyHostToDevice));
     RTCC3_CUDA(cudaMemcpy(ctx->mu, dipole, size_t(3) * n * n * sizeof(double), cudaMemcpyHostToDevice));
+    drop_graph(ctx);
     ctx->runner.reset();
     if (ctx->fp64()) setup_runner<double>(ctx, Lfac);
     else setup_runner<float>(ctx, Lfac);
@@ -650,6 +715,7 @@ int rtcc3_set_field(rtcc3_ctx* ctx, int b, int kind, double amplitude, double om
     FieldDev f{kind, amplitude, omega, center, width, {0.0, 0.0, 1.0}};
     if (dir) { f.dir[0] = dir[0]; f.dir[1] = dir[1]; f.dir[2] = dir[2]; }
     ctx->fhost[b] = f;
+    drop_graph(ctx);  // field parameters live on the device, sweep counts do not
     RTCC3_CUDA(cudaMemcpy(ctx->fdev + b, &f, sizeof(FieldDev), cudaMemcpyHostToDevice));
   });
 }
@@ -773,6 +839,13 @@ int rtcc3_propagate_rk4_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_d
     const int rc = propagate_common(ctx, h, nsteps, static_cast<double2*>(dipole_dev),
                                     static_cast<double2*>(energy_dev), false, nullptr, nullptr);
     if (rc != RTCC3_OK) throw Error(rc, ctx->err);
+    if (ext) {
+      cudaEvent_t ev;
+      RTCC3_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      RTCC3_CUDA(cudaEventRecord(ev, ctx->stream));
+      RTCC3_CUDA(cudaStreamWaitEvent(ext, ev, 0));
+      cudaEventDestroy(ev);
+    }
   });
 }
 
@@ -863,6 +936,32 @@ int rtcc3_set_state(rtcc3_ctx* ctx, const void* buf, long long bytes) {
     ctx->time = hd.time;
     ctx->step_total = hd.step;
     RTCC3_CUDA(cudaMemcpy(ctx->tdev, &ctx->time, sizeof(double), cudaMemcpyHostToDevice));
+  });
+}
+
+int rtcc3_set_profiling(rtcc3_ctx* ctx, int enable) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    ctx->prof.reset();
+    ctx->prof.enabled = enable != 0;
+    drop_graph(ctx);
+  });
+}
+
+int rtcc3_kernel_stats(rtcc3_ctx* ctx, rtcc3_kernel_stat* out, int max_entries, int* count) {
+  if (!ctx || !count) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    ctx->prof.collect();
+    const auto& st = ctx->prof.stats();
+    *count = int(st.size());
+    for (int i = 0; i < int(st.size()) && i < max_entries && out; ++i) {
+      std::memset(&out[i], 0, sizeof(rtcc3_kernel_stat));
+      std::strncpy(out[i].name, st[i].name.c_str(), sizeof(out[i].name) - 1);
+      out[i].launches = st[i].launches;
+      out[i].ms = st[i].ms;
+      out[i].flops = st[i].flops;
+      out[i].bytes = st[i].bytes;
+    }
   });
 }
 

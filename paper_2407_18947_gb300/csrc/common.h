@@ -46,6 +46,67 @@ enum Status {
 #define RTCC3_CHECK(cond, code, msg)                                              \
   do { if (!(cond)) throw ::rtcc3::Error((code), (msg)); } while (0)
 
+// Optional per-kernel timing with CUDA events (eager launches only: CUDA
+// graphs are not used while it is enabled).  Each launch is bracketed by an
+// event pair on the launching stream; collect() synchronises and adds the
+// elapsed times, the algorithmic flops and bytes per kernel name.
+class Profiler {
+ public:
+  struct Stat { std::string name; long long launches = 0; double ms = 0.0, flops = 0.0, bytes = 0.0; };
+  ~Profiler() { for (auto e : pool_) cudaEventDestroy(e); }
+  bool enabled = false;
+  int begin(cudaStream_t s) {
+    if (!enabled) return -1;
+    const int k = next_event();
+    cudaEventRecord(pool_[k], s);
+    return k;
+  }
+  void end(int k0, cudaStream_t s, const char* name, double flops, double bytes) {
+    if (k0 < 0) return;
+    const int k1 = next_event();
+    cudaEventRecord(pool_[k1], s);
+    pending_.push_back({k0, k1, find(name), flops, bytes});
+  }
+  void collect() {
+    if (pending_.empty()) return;
+    for (auto& p : pending_) cudaEventSynchronize(pool_[p.e1]);
+    for (auto& p : pending_) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, pool_[p.e0], pool_[p.e1]);
+      Stat& s = stats_[p.stat];
+      s.launches += 1;
+      s.ms += ms;
+      s.flops += p.flops;
+      s.bytes += p.bytes;
+    }
+    pending_.clear();
+    used_ = 0;
+  }
+  void reset() { collect(); stats_.clear(); }
+  const std::vector<Stat>& stats() const { return stats_; }
+
+ private:
+  struct Pending { int e0, e1, stat; double flops, bytes; };
+  int next_event() {
+    if (used_ == pool_.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool_.push_back(e);
+    }
+    return int(used_++);
+  }
+  int find(const char* name) {
+    for (size_t i = 0; i < stats_.size(); ++i) if (stats_[i].name == name) return int(i);
+    stats_.push_back(Stat());
+    stats_.back().name = name;
+    return int(stats_.size()) - 1;
+  }
+  std::vector<cudaEvent_t> pool_;
+  size_t used_ = 0;
+  std::vector<Pending> pending_;
+  std::vector<Stat> stats_;
+};
+
 // Bump allocator over device blocks.  Every evaluation of a residual graph
 // requests the same sequence of sizes, so after reset() the same addresses are
 // handed out again: buffers are stable across evaluations, which lets a whole

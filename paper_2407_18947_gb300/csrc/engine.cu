@@ -349,6 +349,7 @@ void* Engine<R>::scratch(size_t bytes) {
     scratch_ = nullptr;
     RTCC3_CUDA(cudaMalloc(&scratch_, bytes));
     scratch_bytes_ = bytes;
+    ++generation_;
   }
   return scratch_;
 }
@@ -473,6 +474,7 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
     part = static_cast<C*>(scratch(size_t(P.nb) * P.nsplit * P.M * P.N * sizeof(C)));
   dim3 grid((P.N + kBN - 1) / kBN, (P.M + kBM - 1) / kBM, P.nb * P.nsplit);
   RTCC3_CHECK(grid.y < 65536 && grid.z < 65536, kErrArg, "contraction grid too large: " + spec);
+  const int pk = pbegin();
 #define RTCC3_LAUNCH(AK, BK)                                                                   \
   k_contract<R, AK, BK><<<grid, kThreads, 0, stream_>>>(                                       \
       pa, pb, pc, P.aM, P.aK, P.bN, P.bK, P.cM, P.cN, P.aB, P.bB, P.cB, P.M, P.N, P.K, P.nsplit, \
@@ -484,12 +486,20 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
 #undef RTCC3_LAUNCH
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
+  {
+    const double mnk = double(P.M) * P.N * P.K * P.nb;
+    const double bytes = (double(P.M) * P.K + double(P.N) * P.K +
+                          double(P.M) * P.N * (accumulate ? 2.0 : 1.0)) * P.nb * sizeof(C);
+    pend(pk, sizeof(R) == 8 ? "contract_simt_c128" : "contract_simt_c64", 8.0 * mnk, bytes);
+  }
   if (P.nsplit > 1) {
     const size_t n = size_t(P.nb) * P.M * P.N;
+    const int pr = pbegin();
     k_split_reduce<R><<<grid_for(n), 256, 0, stream_>>>(part, pc, P.cM, P.cN, P.cB, P.M, P.N, P.nb,
                                                         P.nsplit, R(alpha), accumulate ? 1 : 0);
     ++launches_;
     RTCC3_CUDA(cudaGetLastError());
+    pend(pr, "split_reduce", 2.0 * n * P.nsplit, double(n) * (P.nsplit + 2) * sizeof(C));
   }
 }
 
@@ -520,7 +530,9 @@ void Engine<R>::run_axpy(double alpha, const View& X, bool xg, const View& Y, bo
   if (n == 0) return;
   const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+  const int pk = pbegin();
   k_axpy<R><<<grid_for(n), 256, 0, stream_>>>(px, py, d, R(alpha), n);
+  pend(pk, "axpy_strided", 4.0 * n, 3.0 * n * sizeof(C));
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
 }
@@ -551,7 +563,9 @@ void Engine<R>::run_mulc(const View& X, bool xg, const View& Cst, const View& Y,
   if (n == 0) return;
   const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+  const int pk = pbegin();
   k_mulc<R><<<grid_for(n), 256, 0, stream_>>>(px, nodes_[Cst.node].data, py, d, n);
+  pend(pk, "mulc_strided", 8.0 * n, 4.0 * n * sizeof(C));
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
 }
@@ -586,7 +600,9 @@ void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y
   if (n == 0) return;
   const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+  const int pk = pbegin();
   k_div_eps<R><<<grid_for(n), 256, 0, stream_>>>(px, py, d, es.eps, ea, n);
+  pend(pk, "div_eps", 4.0 * n, 3.0 * n * sizeof(C));
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
 }

@@ -114,8 +114,17 @@ class Engine {
   // graph is being captured: plans upload tables synchronously).
   void freeze_plans(bool f) { frozen_ = f; }
   void* scratch(size_t bytes);
+  // Incremented whenever a persistent buffer (the split-K scratch) moves:
+  // a captured CUDA graph recorded under an older generation is stale.
+  int generation() const { return generation_; }
+  void set_profiler(Profiler* p) { prof_ = p; }
 
  private:
+  Profiler* prof_ = nullptr;
+  int pbegin() { return prof_ ? prof_->begin(stream_) : -1; }
+  void pend(int k, const char* name, double flops, double bytes) {
+    if (prof_) prof_->end(k, stream_, name, flops, bytes);
+  }
   enum OpKind { kContract, kAxpy, kMulc, kDiv };
   struct Op {
     OpKind kind;
@@ -139,6 +148,7 @@ class Engine {
   void* scratch_ = nullptr;
   size_t scratch_bytes_ = 0;
   int launches_ = 0;
+  int generation_ = 0;
   bool frozen_ = false;
 };
 

@@ -100,8 +100,7 @@ __global__ void k_stage_output(const Cx<R>* __restrict__ r1, const Cx<R>* __rest
 template <typename R>
 __global__ void k_observables(const Cx<R>* __restrict__ D, const Cx<R>* __restrict__ e,
                               const double* __restrict__ mu, double e_ref, int n,
-                              double2* dip_traj, double2* en_traj, const int* step,
-                              int stride_steps) {
+                              const TrajDesc* __restrict__ td, int slot, const int* step) {
   // one block per Cartesian component; FP64 reduction in fixed order
   __shared__ double sr[256], si[256];
   const int x = blockIdx.x;
@@ -119,12 +118,11 @@ __global__ void k_observables(const Cx<R>* __restrict__ D, const Cx<R>* __restri
     if (threadIdx.x < s) { sr[threadIdx.x] += sr[threadIdx.x + s]; si[threadIdx.x] += si[threadIdx.x + s]; }
     __syncthreads();
   }
-  const int st = step ? *step : 0;
   if (threadIdx.x == 0) {
-    if (dip_traj) dip_traj[size_t(st) * 3 + x] = make_double2(sr[0], si[0]);
-    if (x == 0 && en_traj) en_traj[st] = make_double2(double(e[0].x) - e_ref, double(e[0].y));
+    const long long ent = (long long)slot * td->stride + (step ? *step : 0);
+    if (td->dip) td->dip[size_t(ent) * 3 + x] = make_double2(sr[0], si[0]);
+    if (x == 0 && td->en) td->en[ent] = make_double2(double(e[0].x) - e_ref, double(e[0].y));
   }
-  (void)stride_steps;
 }
 
 template <typename R>
@@ -326,9 +324,8 @@ void launch_stage_output(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, cons
 
 template <typename R>
 void launch_observables(const Cx<R>* D, const Cx<R>* e, const double* mu, double e_ref, int n,
-                        double2* dip_traj, double2* en_traj, const int* step, int stride_steps,
-                        cudaStream_t s) {
-  k_observables<R><<<3, 256, 0, s>>>(D, e, mu, e_ref, n, dip_traj, en_traj, step, stride_steps);
+                        const TrajDesc* td, int slot, const int* step, cudaStream_t s) {
+  k_observables<R><<<3, 256, 0, s>>>(D, e, mu, e_ref, n, td, slot, step);
   RTCC3_CUDA(cudaGetLastError());
 }
 
@@ -416,7 +413,7 @@ void launch_stage_prep_acc(double2* acc, const double2* y, size_t ny, cudaStream
   template void launch_stage_output<R>(const Cx<R>*, const Cx<R>*, const Cx<R>*, const Cx<R>*,    \
                                        double2*, double2*, double, int, int, cudaStream_t);       \
   template void launch_observables<R>(const Cx<R>*, const Cx<R>*, const double*, double, int,     \
-                                      double2*, double2*, const int*, int, cudaStream_t);         \
+                                      const TrajDesc*, int, const int*, cudaStream_t);            \
   template void launch_residual_export<R>(const Cx<R>*, const Cx<R>*, const Cx<R>*, const Cx<R>*, \
                                           double2*, int, int, bool, cudaStream_t);                \
   template void launch_load_amplitudes<R>(const double2*, const double2*, Cx<R>*, Cx<R>*, int,  \

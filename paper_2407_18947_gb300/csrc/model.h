@@ -64,12 +64,19 @@ void launch_seeds(Cx<R>* ge, Cx<R>* gr1, Cx<R>* gr2, const Cx<R>* l1s, const Cx<
 template <typename R>
 void launch_stage_output(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, const Cx<R>* g2,
                          double2* kout, double2* acc, double hw, int o, int v, cudaStream_t s);
+// Where a propagation writes its observables (device struct, so a captured
+// step graph does not depend on the output buffers of one call): entry
+// (slot * stride + step) of dip (x3) and en.
+struct TrajDesc {
+  double2* dip;
+  double2* en;
+  long long stride;
+};
 // dipole[3] = sum_pq D_pq mu^x_pq (FP64) and energy = e - e_ref, written at
-// index *step of the trajectory arrays of slot b.
+// entry (slot * td->stride + *step) (step may be NULL: entry slot * stride).
 template <typename R>
 void launch_observables(const Cx<R>* D, const Cx<R>* e, const double* mu, double e_ref, int n,
-                        double2* dip_traj, double2* en_traj, const int* step, int stride_steps,
-                        cudaStream_t s);
+                        const TrajDesc* td, int slot, const int* step, cudaStream_t s);
 // Host-readable FP64 copy of the residuals: out = [r1, r2, g1, g2 + g2^T].
 template <typename R>
 void launch_residual_export(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, const Cx<R>* g2,
