@@ -250,10 +250,12 @@ def main():
         dist.barrier()
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("rtcc3_timed")
     ev0.record(stream)
     eng.propagate_rk4_dev(h, K, dip.data_ptr(), en.data_ptr(), stream.cuda_stream)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_pop()
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
