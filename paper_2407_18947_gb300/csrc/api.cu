@@ -258,6 +258,8 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
   RTCC3_CUDA(cudaMemcpy(H.L, Lc.data(), Lc.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
   RTCC3_CUDA(cudaMemcpy(H.ones, ones.data(), ones.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
   rn->E.set_profiler(&ctx->prof);
+  if (ctx->opt.precision == RTCC3_PREC_TF32) rn->E.set_tensor_cores(4);
+  if (ctx->opt.precision == RTCC3_PREC_BF16) rn->E.set_tensor_cores(2);
   ctx->runner = std::move(rn);
 }
 
@@ -320,6 +322,19 @@ void final_observables(rtcc3_ctx* ctx, const std::vector<int>& sweeps) {
               double(ctx->n) * ctx->n * (sizeof(Cx<R>) + 24.0));
     launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->tdesc, b,
                           ctx->stepdev, ctx->stream);
+  }
+}
+
+// A bounded device wait that gave up leaves a flag; report it and clear it.
+template <typename R>
+void check_device_timeout(rtcc3_ctx* ctx) {
+  Engine<R>& E = ctx->run<R>().E;
+  if (E.tensor_cores() == 0) return;
+  int flag = 0;
+  RTCC3_CUDA(cudaMemcpy(&flag, E.error_flag(), sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    RTCC3_CUDA(cudaMemset(E.error_flag(), 0, sizeof(int)));
+    throw Error(RTCC3_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on its pipeline");
   }
 }
 
@@ -397,6 +412,7 @@ void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2*
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->time += h * nsteps;
   ctx->step_total += nsteps;
+  check_device_timeout<R>(ctx);
   int bad = -1;
   RTCC3_CUDA(cudaMemcpy(&bad, ctx->baddev, sizeof(int), cudaMemcpyDeviceToHost));
   if (bad >= 0)
@@ -431,6 +447,7 @@ void residuals_impl(rtcc3_ctx* ctx, int b, double time, double* r_t1, double* r_
                         ctx->n, ctx->tdesc, 0, nullptr, ctx->stream);
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->last_launches = E.launches();
+  check_device_timeout<R>(ctx);
   const size_t n1 = ctx->n1, n2 = ctx->n2;
   auto get = [&](double* dst, size_t off, size_t cnt) {
     if (dst)

@@ -2,6 +2,9 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <type_traits>
+
+#include "tc_gemm.h"
 #include <cstring>
 #include <sstream>
 
@@ -260,11 +263,23 @@ template <typename R>
 Engine<R>::~Engine() {
   for (auto& kv : plans_)
     if (kv.second->dev) cudaFree(kv.second->dev);
-  if (scratch_) cudaFree(scratch_);
+  for (int s = 0; s < kScratchSlots; ++s)
+    if (scratch_[s]) cudaFree(scratch_[s]);
+  if (err_) cudaFree(err_);
+}
+
+template <typename R>
+int* Engine<R>::error_flag() {
+  if (!err_) {
+    RTCC3_CUDA(cudaMalloc(&err_, sizeof(int)));
+    RTCC3_CUDA(cudaMemset(err_, 0, sizeof(int)));
+  }
+  return err_;
 }
 
 template <typename R>
 void Engine<R>::begin() {
+  tc_region_ = false;
   arena_.reset();
   nodes_.clear();
   tape_.clear();
@@ -342,21 +357,23 @@ View Engine<R>::ev(const char* spec_c, const View& x) const {
 }
 
 template <typename R>
-void* Engine<R>::scratch(size_t bytes) {
-  if (bytes > scratch_bytes_) {
+void* Engine<R>::scratch(int slot, size_t bytes) {
+  if (bytes > scratch_bytes_[slot]) {
     RTCC3_CHECK(!frozen_, kErrState, "scratch growth during graph capture");
-    if (scratch_) cudaFree(scratch_);
-    scratch_ = nullptr;
-    RTCC3_CUDA(cudaMalloc(&scratch_, bytes));
-    scratch_bytes_ = bytes;
+    if (scratch_[slot]) cudaFree(scratch_[slot]);
+    scratch_[slot] = nullptr;
+    RTCC3_CUDA(cudaMalloc(&scratch_[slot], bytes));
+    scratch_bytes_[slot] = bytes;
     ++generation_;
   }
-  return scratch_;
+  return scratch_[slot];
 }
 
 template <typename R>
 ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View& B, const View& Cv) {
-  const std::string key = spec + "|" + view_key(A) + "|" + view_key(B) + "|" + view_key(Cv);
+  const bool tc_ok = cur_tc_ && tc_eb_ > 0;
+  const std::string key = spec + "|" + view_key(A) + "|" + view_key(B) + "|" + view_key(Cv) +
+                          (tc_ok ? "|tc" : "");
   auto it = plans_.find(key);
   if (it != plans_.end()) return *it->second;
   RTCC3_CHECK(!frozen_, kErrState, "new contraction plan during graph capture: " + spec);
@@ -455,6 +472,24 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   nsplit = int((K + kchunk - 1) / kchunk);
   P->nsplit = nsplit;
   P->kchunk = kchunk;
+  P->a_off0 = h[iaB];
+  P->b_off0 = h[ibB];
+  P->c_off0 = h[icB];
+  // tensor-core route: one batch, a large output side and enough work
+  if (std::is_same<R, float>::value && tc_ok && NB == 1 && std::max(M, N) >= 128 &&
+      std::min(M, N) >= 4 && M * N * K >= (1LL << 21)) {
+    P->use_tc = true;
+    P->tc_swap = N > M;  // the expanded (2x2 real) operand is the smaller one
+    const long long Mg = std::max(M, N), Ng = std::min(M, N);
+    P->tc_kp = tc_packed_k(int(K), tc_eb_);
+    const int nkb = P->tc_kp / (128 / tc_eb_);
+    const long long nr = 2 * Ng;
+    const long long bn = nr >= 192 ? 256 : (nr >= 96 ? 128 : 64);
+    const long long tcs = ((nr + bn - 1) / bn) * ((Mg + 127) / 128);
+    int ts = 1;
+    if (tcs < 152 && nkb >= 8) ts = int(std::max<long long>(1, std::min<long long>((304 + tcs - 1) / tcs, nkb / 4)));
+    P->tc_nsplit = ts;
+  }
   ContractPlan& ref = *P;
   plans_[key] = std::move(P);
   return ref;
@@ -469,9 +504,13 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
   const C* pb = (b_grad ? nodes_[B.node].grad : nodes_[B.node].data);
   C* pc = (c_grad ? nodes_[Cv.node].grad : nodes_[Cv.node].data);
   RTCC3_CHECK(pa && pb && pc, kErrState, "contraction on an unallocated buffer: " + spec);
+  if (P.use_tc) {
+    run_contract_tc(P, alpha, pa, pb, pc, accumulate);
+    return;
+  }
   C* part = nullptr;
   if (P.nsplit > 1)
-    part = static_cast<C*>(scratch(size_t(P.nb) * P.nsplit * P.M * P.N * sizeof(C)));
+    part = static_cast<C*>(scratch(0, size_t(P.nb) * P.nsplit * P.M * P.N * sizeof(C)));
   dim3 grid((P.N + kBN - 1) / kBN, (P.M + kBM - 1) / kBM, P.nb * P.nsplit);
   RTCC3_CHECK(grid.y < 65536 && grid.z < 65536, kErrArg, "contraction grid too large: " + spec);
   const int pk = pbegin();
@@ -504,12 +543,70 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
 }
 
 template <typename R>
+void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, const C* pb, C* pc,
+                                bool accumulate) {
+  if constexpr (std::is_same<R, float>::value) {
+    const bool sw = P.tc_swap;
+    TcOperands op;
+    op.M = sw ? P.N : P.M;
+    op.N = sw ? P.M : P.N;
+    op.K = P.K;
+    op.Kp = P.tc_kp;
+    op.elem_bytes = tc_eb_;
+    const float2* ga = sw ? pb : pa;
+    const float2* gb = sw ? pa : pb;
+    const long long* gaM = sw ? P.bN : P.aM;
+    const long long* gaK = sw ? P.bK : P.aK;
+    const long long* gbN = sw ? P.aM : P.bN;
+    const long long* gbK = sw ? P.aK : P.bK;
+    const long long* gcM = sw ? P.cN : P.cM;
+    const long long* gcN = sw ? P.cM : P.cN;
+    const long long goa = sw ? P.b_off0 : P.a_off0;
+    const long long gob = sw ? P.a_off0 : P.b_off0;
+    void* apk = scratch(1, size_t(op.M) * op.Kp * tc_eb_);
+    void* bpk = scratch(2, size_t(2 * op.N) * op.Kp * tc_eb_);
+    float* part = nullptr;
+    if (P.tc_nsplit > 1)
+      part = static_cast<float*>(scratch(3, size_t(P.tc_nsplit) * op.M * 2 * op.N * sizeof(float)));
+    int* err = error_flag();
+    const double pbytes = double(op.M + 2.0 * op.N) * op.K * 2.0 * sizeof(float);
+    int pk = pbegin();
+    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, tc_eb_, apk, stream_);
+    tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, tc_eb_, bpk, stream_);
+    pend(pk, "tc_pack", 0.0, pbytes + double(op.M + 2.0 * op.N) * op.Kp * tc_eb_);
+    launches_ += 2;
+    pk = pbegin();
+    const bool ok = tc_gemm(apk, bpk, op, pc, gcM, gcN, P.c_off0, float(alpha), accumulate,
+                            P.tc_nsplit, part, err, stream_);
+    RTCC3_CHECK(ok, kErrCuda, "tensor-core GEMM set-up failed (tensor map encoding)");
+    const double mnk = double(op.M) * op.N * op.K;
+    const double bytes = (double(op.M) * op.Kp + 2.0 * op.N * op.Kp) * tc_eb_ +
+                         double(op.M) * op.N * sizeof(C) * (accumulate ? 2.0 : 1.0);
+    pend(pk, tc_eb_ == 4 ? "contract_tc_tf32" : "contract_tc_bf16", 8.0 * mnk, bytes);
+    ++launches_;
+    if (P.tc_nsplit > 1) {
+      pk = pbegin();
+      tc_split_finish(part, P.tc_nsplit, op.M, op.N, pc, gcM, gcN, P.c_off0, float(alpha),
+                      accumulate, stream_);
+      pend(pk, "tc_split_finish", 0.0,
+           double(P.tc_nsplit) * op.M * 2 * op.N * 4.0 + double(op.M) * op.N * sizeof(C) * 2.0);
+      ++launches_;
+    }
+  } else {
+    (void)P; (void)alpha; (void)pa; (void)pb; (void)pc; (void)accumulate;
+    throw Error(kErrState, "tensor-core route requires a complex64 graph");
+  }
+}
+
+template <typename R>
 void Engine<R>::contract(const char* spec, double alpha, const View& A, const View& B,
                          const View& Cv, bool accumulate) {
   RTCC3_CHECK(Cv.node != A.node && Cv.node != B.node, kErrArg, "contraction output aliases input");
+  cur_tc_ = tc_region_;
   run_contract(spec, alpha, A, false, B, false, Cv, false, accumulate);
   if (nodes_[A.node].needs_grad || nodes_[B.node].needs_grad) nodes_[Cv.node].needs_grad = true;
   Op op{kContract, spec, alpha, A, B, Cv, EpsSpec()};
+  op.tc = tc_region_;
   tape_.push_back(op);
 }
 
@@ -648,6 +745,7 @@ void Engine<R>::backward() {
     if (op.kind == kContract) {
       if (!nodes_[op.c.node].needs_grad) continue;
       const Spec s = parse(op.spec);
+      cur_tc_ = op.tc;
       if (nodes_[op.a.node].needs_grad)
         run_contract(s.c + "," + s.b + "->" + s.a, op.alpha, op.c, true, op.b, false, op.a, true, true);
       if (nodes_[op.b.node].needs_grad)

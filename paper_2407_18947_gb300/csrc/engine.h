@@ -49,6 +49,10 @@ struct ContractPlan {
   int M = 1, N = 1, K = 1, nb = 1;
   int nsplit = 1, kchunk = 1;
   bool a_kcontig = false, b_kcontig = false;
+  // tensor-core route (complex64 graphs with TF32/BF16 operands)
+  bool use_tc = false, tc_swap = false;
+  int tc_nsplit = 1, tc_kp = 0;
+  long long a_off0 = 0, b_off0 = 0, c_off0 = 0;  // batch-0 offsets (host copies)
   long long *aM = nullptr, *aK = nullptr, *bN = nullptr, *bK = nullptr;
   long long *cM = nullptr, *cN = nullptr, *aB = nullptr, *bB = nullptr, *cB = nullptr;
   std::vector<long long> host;  // backing store for the uploaded tables
@@ -113,7 +117,18 @@ class Engine {
   // When true, creating a new contraction plan raises (used while a CUDA
   // graph is being captured: plans upload tables synchronously).
   void freeze_plans(bool f) { frozen_ = f; }
-  void* scratch(size_t bytes);
+  // Persistent scratch buffers by slot: 0 split-K partials, 1/2 packed
+  // tensor-core operands, 3 tensor-core split-K partials.
+  void* scratch(int slot, size_t bytes);
+  // Route large contractions of a complex64 graph to the tcgen05 GEMM with
+  // TF32 (elem_bytes 4) or BF16 (2) operands; 0 keeps the CUDA-core kernel.
+  void set_tensor_cores(int elem_bytes) { tc_eb_ = elem_bytes; }
+  int tensor_cores() const { return tc_eb_; }
+  // Contractions recorded while the region is open (and their adjoints) may
+  // take the tensor-core route; everything else stays on CUDA cores in FP32.
+  void set_tc_region(bool open) { tc_region_ = open; }
+  // Device word raised by a bounded wait that gave up (tensor-core kernel).
+  int* error_flag();
   // Incremented whenever a persistent buffer (the split-K scratch) moves:
   // a captured CUDA graph recorded under an older generation is stale.
   int generation() const { return generation_; }
@@ -132,7 +147,9 @@ class Engine {
     double alpha;
     View a, b, c;
     EpsSpec es;
+    bool tc = false;  // recorded inside the tensor-core region
   };
+  bool cur_tc_ = false;  // tensor-core permission of the contraction being run
   void run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg);
   void run_contract(const std::string& spec, double alpha, const View& A, bool a_grad, const View& B,
                     bool b_grad, const View& Cv, bool c_grad, bool accumulate);
@@ -145,8 +162,14 @@ class Engine {
   std::vector<Node> nodes_;
   std::vector<Op> tape_;
   std::map<std::string, std::unique_ptr<ContractPlan>> plans_;
-  void* scratch_ = nullptr;
-  size_t scratch_bytes_ = 0;
+  static constexpr int kScratchSlots = 4;
+  void* scratch_[kScratchSlots] = {nullptr, nullptr, nullptr, nullptr};
+  size_t scratch_bytes_[kScratchSlots] = {0, 0, 0, 0};
+  int tc_eb_ = 0;
+  bool tc_region_ = false;
+  int* err_ = nullptr;
+  void run_contract_tc(ContractPlan& P, double alpha, const C* pa, const C* pb, C* pc,
+                       bool accumulate);
   int launches_ = 0;
   int generation_ = 0;
   bool frozen_ = false;

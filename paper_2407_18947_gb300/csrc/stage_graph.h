@@ -114,6 +114,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
 
   // ---- triples ---------------------------------------------------------------
   if (opt.triples) {
+    E.set_tc_region(true);  // the dense triples contractions may use tensor cores
     const std::vector<int> s6 = {o, o, o, v, v, v};
     static const char* perms[6] = {"ijkabc->ijkabc", "jikbac->ijkabc", "ikjacb->ijkabc",
                                    "kjicba->ijkabc", "kijcab->ijkabc", "jkibca->ijkabc"};
@@ -178,6 +179,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     E.axpy(-1.0, E.ev("mjkzyx->mjkxyz", T3), E.v(Uc));
     E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), G("ooov"), E.v(S3), true);
     E.axpy(1.0, E.v(S3), SD);
+    E.set_tc_region(false);
   }
   // P_ij^ab on the symmetrised part
   E.axpy(1.0, SD, R2);

@@ -1,0 +1,446 @@
+// tcgen05 GEMM for the complex contractions (see tc_gemm.h).
+//
+// One CTA computes a 128 x BN tile of the real product Apack (M x Kp) times
+// Bpack^T (Nr x Kp), both K-major, staged by TMA (128-byte swizzle) through a
+// 4-deep shared-memory ring.  Warp 0 issues the TMA loads, warp 1 allocates
+// tensor memory and issues tcgen05.mma (one elected thread), warps 2-5 read
+// the FP32 accumulator back with tcgen05.ld and write the complex result
+// (coalesced through a per-warp shared-memory transpose) or FP32 split-K
+// partials.  Every mbarrier wait is bounded by a clock budget; on expiry the
+// kernel raises *err and winds down, releasing its tensor memory.
+#include "tc_gemm.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
+namespace rtcc3 {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kStages = 4;
+constexpr int kThreads = 192;
+constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= uint64_t((addr >> 4) & 0x3FFF);
+  d |= uint64_t(1) << 16;                    // leading byte offset (unused for this layout)
+  d |= uint64_t((1024 >> 4) & 0x3FFF) << 32;  // stride byte offset
+  d |= uint64_t(1) << 46;                    // version
+  d |= uint64_t(2) << 61;                    // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D = F32, A/B format (2 = TF32 for kind::tf32,
+// 1 = BF16 for kind::f16), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+template <bool BF16>
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (uint32_t(BF16 ? 1 : 2) << 7) | (uint32_t(BF16 ? 1 : 2) << 10) |
+         (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if (BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN>
+struct TcSmem {
+  static constexpr int kABytes = kBM * 128;
+  static constexpr int kBBytes = BN * 128;
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kBarOff = kStages * kStageBytes;
+  static constexpr int kStageOutOff = kBarOff + 256;
+  static constexpr int kStageOutBytes = 4 * 32 * 33 * 4;
+  static constexpr int kTotal = kStageOutOff + kStageOutBytes + 1024;  // + alignment slack
+};
+
+template <int BN, bool BF16>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          int M, int Nr, int nkb_total, int kb_per_split, float2* __restrict__ C,
+          const long long* __restrict__ cM, const long long* __restrict__ cN, long long coff,
+          float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err) {
+  using L = TcSmem<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* done = bars + 2 * kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  float* stage_out = reinterpret_cast<float*>(smem + L::kStageOutOff);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+  const int split = blockIdx.z;
+  const int kb0 = split * kb_per_split;
+  const int nkb = max(0, min(nkb_total, kb0 + kb_per_split) - kb0);
+  constexpr int kElemPerK = BF16 ? 64 : 32;  // elements per 128-byte K tile
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int s = i % kStages;
+        if (i >= kStages) ok = mbar_wait(smem_u32(&empty[s]), ((i / kStages) - 1) & 1);
+        if (!ok) break;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, L::kStageBytes);
+        uint8_t* sa = smem + s * L::kStageBytes;
+        const int kx = (kb0 + i) * kElemPerK;
+        tma_load_2d(smem_u32(sa), &tmA, kx, m0, fb);
+        tma_load_2d(smem_u32(sa + L::kABytes), &tmB, kx, n0, fb);
+      }
+      // drain: wait until the MMAs that read the last stages are done so no
+      // copy into this CTA's shared memory is outstanding at exit
+      for (int i = max(0, nkb - kStages); i < nkb && ok; ++i)
+        ok = mbar_wait(smem_u32(&empty[i % kStages]), (i / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = instr_desc<BF16>(kBM, BN);
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int s = i % kStages;
+        ok = mbar_wait(smem_u32(&full[s]), (i / kStages) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(smem + s * L::kStageBytes);
+        const uint32_t sb = sa + L::kABytes;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma<BF16>(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc,
+                    (i > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&empty[s]));
+      }
+      mma_commit(smem_u32(done));
+    }
+  } else {
+    // epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+    const int q = warp & 3;
+    ok = (nkb == 0) ? true : mbar_wait(smem_u32(done), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float* st = stage_out + (warp - 2) * 32 * 33;
+    const int row = q * 32 + lane;
+    const int m = m0 + row;
+    for (int c0 = 0; c0 < BN && ok; c0 += 32) {
+      uint32_t r[32];
+      if (nkb > 0) {
+        tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c0), r);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) r[j] = 0u;
+      }
+      if (partial) {
+        if (m < M) {
+          float* dst = partial + (size_t(split) * M + m) * size_t(Nr) + n0 + c0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (n0 + c0 + j < Nr) dst[j] = __uint_as_float(r[j]);
+        }
+        continue;
+      }
+      // transpose through shared memory so a warp stores runs of the output row
+#pragma unroll
+      for (int j = 0; j < 32; ++j) st[lane * 33 + j] = __uint_as_float(r[j]);
+      __syncwarp();
+      const int jc = lane & 15;   // complex column within the 16-column chunk
+      const int rh = lane >> 4;   // row parity handled by this half-warp
+      const int n = (n0 + c0) / 2 + jc;
+      const bool ncol = (2 * n) < Nr;
+      const long long cn = ncol ? cN[n] : 0;
+      for (int rr = rh; rr < 32; rr += 2) {
+        const int mm = m0 + q * 32 + rr;
+        if (mm < M && ncol) {
+          float2 val = make_float2(alpha * st[rr * 33 + 2 * jc], alpha * st[rr * 33 + 2 * jc + 1]);
+          const long long idx = coff + cM[mm] + cn;
+          if (accumulate) {
+            const float2 old = C[idx];
+            val.x += old.x;
+            val.y += old.y;
+          }
+          C[idx] = val;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (!ok && err) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                 : "memory");
+  }
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void put(void* out, size_t idx, float v, int elem_bytes) {
+  if (elem_bytes == 4) {
+    static_cast<uint32_t*>(out)[idx] = to_tf32(v);
+  } else {
+    const uint32_t u = __float_as_uint(v);
+    // round to nearest even on the upper 16 bits (finite inputs)
+    const uint32_t rounded = u + 0x7FFFu + ((u >> 16) & 1u);
+    static_cast<unsigned short*>(out)[idx] = static_cast<unsigned short>(rounded >> 16);
+  }
+}
+
+__global__ void k_pack_a(const float2* __restrict__ A, const long long* __restrict__ aM,
+                         const long long* __restrict__ aK, long long aoff, int M, int K, int Kp,
+                         int elem_bytes, void* out) {
+  const size_t total = size_t(M) * Kp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int kp = int(t % Kp);
+    const int m = int(t / Kp);
+    const int k = kp >> 1;
+    float v = 0.f;
+    if (k < K) {
+      const float2 a = A[aoff + aM[m] + aK[k]];
+      v = (kp & 1) ? a.y : a.x;
+    }
+    put(out, t, v, elem_bytes);
+  }
+}
+
+__global__ void k_pack_b(const float2* __restrict__ B, const long long* __restrict__ bN,
+                         const long long* __restrict__ bK, long long boff, int N, int K, int Kp,
+                         int elem_bytes, void* out) {
+  const size_t total = size_t(2 * N) * Kp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int kp = int(t % Kp);
+    const int r = int(t / Kp);
+    const int n = r >> 1, k = kp >> 1;
+    float v = 0.f;
+    if (k < K) {
+      const float2 b = B[boff + bN[n] + bK[k]];
+      // row 2n: (Br, -Bi); row 2n+1: (Bi, Br) along (re, im) of K
+      if ((r & 1) == 0) v = (kp & 1) ? -b.y : b.x;
+      else v = (kp & 1) ? b.x : b.y;
+    }
+    put(out, t, v, elem_bytes);
+  }
+}
+
+__global__ void k_split_finish(const float* __restrict__ partial, int nsplit, int M, int N,
+                               float2* __restrict__ C, const long long* __restrict__ cM,
+                               const long long* __restrict__ cN, long long coff, float alpha,
+                               int accumulate) {
+  const size_t total = size_t(M) * N;
+  const size_t plane = size_t(M) * 2 * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int n = int(t % N), m = int(t / N);
+    float re = 0.f, im = 0.f;
+    for (int s = 0; s < nsplit; ++s) {
+      const float* p = partial + s * plane + size_t(m) * 2 * N + 2 * n;
+      re += p[0];
+      im += p[1];
+    }
+    const long long idx = coff + cM[m] + cN[n];
+    float2 v = make_float2(alpha * re, alpha * im);
+    if (accumulate) { v.x += C[idx].x; v.y += C[idx].y; }
+    C[idx] = v;
+  }
+}
+
+int grid_for(size_t n) {
+  size_t g = (n + 255) / 256;
+  return int(std::max<size_t>(1, std::min<size_t>(g, 152 * 8)));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* base, int elem_bytes, int Kp, int rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(Kp), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(Kp) * elem_bytes};
+  const cuuint32_t box[2] = {cuuint32_t(128 / elem_bytes), cuuint32_t(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, bool BF16>
+void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, float2* C,
+            const long long* cM, const long long* cN, long long coff, float alpha, bool accumulate,
+            int nsplit, float* partial, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    RTCC3_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TcSmem<BN>::kTotal));
+    attr = true;
+  }
+  const int Nr = 2 * op.N;
+  const int nkb = op.Kp / (128 / op.elem_bytes);
+  const int per = (nkb + nsplit - 1) / nsplit;
+  dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, nsplit);
+  k_tc_gemm<BN, BF16><<<grid, kThreads, TcSmem<BN>::kTotal, s>>>(
+      ma, mb, op.M, Nr, nkb, per, C, cM, cN, coff, alpha, accumulate ? 1 : 0,
+      nsplit > 1 ? partial : nullptr, err);
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
+               int K, int Kp, int elem_bytes, void* out, cudaStream_t s) {
+  k_pack_a<<<grid_for(size_t(M) * Kp), 256, 0, s>>>(A, aM, aK, aoff, M, K, Kp, elem_bytes, out);
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
+               int K, int Kp, int elem_bytes, void* out, cudaStream_t s) {
+  k_pack_b<<<grid_for(size_t(2 * N) * Kp), 256, 0, s>>>(B, bN, bK, boff, N, K, Kp, elem_bytes, out);
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2* C,
+             const long long* cM, const long long* cN, long long coff, float alpha, bool accumulate,
+             int nsplit, float* partial, int* err_flag, cudaStream_t s) {
+  const int Nr = 2 * op.N;
+  if (op.M <= 0 || op.N <= 0 || op.Kp <= 0) return false;
+  if (op.Kp % (128 / op.elem_bytes) != 0) return false;
+  const int BN = Nr >= 192 ? 256 : (Nr >= 96 ? 128 : 64);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, Apack, op.elem_bytes, op.Kp, op.M, kBM)) return false;
+  if (!make_map(&mb, Bpack, op.elem_bytes, op.Kp, Nr, BN)) return false;
+  const bool bf16 = op.elem_bytes == 2;
+#define RTCC3_TC(BNV)                                                                             \
+  (bf16 ? launch<BNV, true>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s) \
+        : launch<BNV, false>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s))
+  if (BN == 256) RTCC3_TC(256);
+  else if (BN == 128) RTCC3_TC(128);
+  else RTCC3_TC(64);
+#undef RTCC3_TC
+  return true;
+}
+
+void tc_split_finish(const float* partial, int nsplit, int M, int N, float2* C, const long long* cM,
+                     const long long* cN, long long coff, float alpha, bool accumulate,
+                     cudaStream_t s) {
+  k_split_finish<<<grid_for(size_t(M) * N), 256, 0, s>>>(partial, nsplit, M, N, C, cM, cN, coff,
+                                                          alpha, accumulate ? 1 : 0);
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+}  // namespace rtcc3

@@ -1,0 +1,47 @@
+// Tensor-core (tcgen05, sm_103a) path for the large complex contractions.
+//
+// A complex contraction C[m,n] (+)= alpha sum_k A[m,k] B[n,k] is run as one
+// real GEMM: A is packed K-major with (re, im) interleaved along K (M x 2K
+// real), B is packed as its real 2x2 embedding ([Br -Bi; Bi Br] per
+// element, 2N x 2K real), and the real product M x 2N is the interleaved
+// complex result.  Operands are rounded to TF32 (or converted to BF16) by the
+// packing kernels; accumulation is FP32 in tensor memory.  The epilogue
+// scatters into any strided output view through the contraction's offset
+// tables (or writes FP32 partials for split-K).
+#pragma once
+
+#include "common.h"
+
+namespace rtcc3 {
+
+struct TcOperands {
+  int M = 0, N = 0, K = 0;  // complex extents
+  int Kp = 0;               // packed real K (multiple of the K tile)
+  int elem_bytes = 4;       // 4: TF32 operands, 2: BF16 operands
+};
+
+// Pack A (complex, addressed by tables) into a K-major real buffer.
+void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
+               int K, int Kp, int elem_bytes, void* out, cudaStream_t s);
+// Pack B as its 2x2 real embedding: rows 2n (real part) and 2n+1 (imaginary part).
+void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
+               int K, int Kp, int elem_bytes, void* out, cudaStream_t s);
+
+// C[cB + cM[m] + cN[n]] (+)= alpha * (Apack Bpack^T)[m, 2n..2n+1] as complex.
+// nsplit > 1: K is split over CTAs; partial sums (M x 2N FP32 per split) go
+// to `partial` and tc_split_finish reduces them into C.  Returns false if the
+// shape is not supported by the tensor-core path.
+bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2* C,
+             const long long* cM, const long long* cN, long long coff, float alpha, bool accumulate,
+             int nsplit, float* partial, int* err_flag, cudaStream_t s);
+void tc_split_finish(const float* partial, int nsplit, int M, int N, float2* C, const long long* cM,
+                     const long long* cN, long long coff, float alpha, bool accumulate,
+                     cudaStream_t s);
+
+// Packed K for a complex K at the given element size (K tile = 128 bytes).
+inline int tc_packed_k(int K, int elem_bytes) {
+  const int tile = 128 / elem_bytes;
+  return ((2 * K + tile - 1) / tile) * tile;
+}
+
+}  // namespace rtcc3

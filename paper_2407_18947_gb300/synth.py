@@ -11,8 +11,12 @@ Section 3 and Table 1, whose integrals and geometries are not available):
 * Orbital energies: occupied ``U[-1.5, -0.3]`` Ha, virtual ``U[0.2, 3.0]`` Ha,
   each sorted ascending.
 * Density-fitted electron-repulsion factors ``L[P, p, q]`` drawn
-  ``N(0, 0.05^2)`` for ``p <= q`` and mirrored, ``naux = 3 nmo`` by default,
-  so that ``(pq|rs) = sum_P L[P,p,q] L[P,r,s]``.
+  ``N(0, sigma^2)`` for ``p <= q`` and mirrored, ``naux = 3 nmo`` by default,
+  so that ``(pq|rs) = sum_P L[P,p,q] L[P,r,s]``.  ``sigma = 0.05 sqrt(72 /
+  naux)``: 0.05 at the (H2O)1 size (naux = 72) and scaled so that the
+  diagonal and exchange-type integrals ``(pq|pq) ~ naux sigma^2 ~ 0.18`` Ha
+  keep that magnitude at every size (with a fixed sigma they would grow with
+  naux and the coupled-cluster iterations stop converging beyond (H2O)1).
 * Dipole matrices ``mu[x|y|z, p, q]``: real symmetric ``N(0, 0.1^2)``.
 * numpy ``PCG64`` with draw order eps_occ, eps_vir, L, mu_x, mu_y, mu_z.
 
@@ -53,13 +57,15 @@ class System:
 
 def make_system(nocc: int, nvir: int, naux: int | None = None, seed: int = BASE_SEED,
                 eps_occ_range=(-1.5, -0.3), eps_vir_range=(0.2, 3.0),
-                l_sigma: float = 0.05, mu_sigma: float = 0.1) -> System:
+                l_sigma: float | None = None, mu_sigma: float = 0.1) -> System:
     """Draw one synthetic closed-shell system (recipe in the module docstring)."""
     if nocc < 1 or nvir < 1:
         raise ValueError("nocc and nvir must be positive")
     nmo = nocc + nvir
     if naux is None:
         naux = 3 * nmo
+    if l_sigma is None:
+        l_sigma = 0.05 * np.sqrt(72.0 / naux)
     rng = np.random.Generator(np.random.PCG64(seed))
     eps_o = np.sort(rng.uniform(eps_occ_range[0], eps_occ_range[1], nocc))
     eps_v = np.sort(rng.uniform(eps_vir_range[0], eps_vir_range[1], nvir))
