@@ -214,6 +214,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     // epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
     const int q = warp & 3;
     ok = (nkb == 0) ? true : mbar_wait(smem_u32(done), 0);
+    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float* st = stage_out + (warp - 2) * 32 * 33;
     const int row = q * 32 + lane;
@@ -264,6 +265,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
+    __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
                  : "memory");
