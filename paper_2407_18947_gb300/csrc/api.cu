@@ -3,6 +3,7 @@
 #include "../../include/rtcc3.h"
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -961,6 +962,8 @@ int rtcc3_set_profiling(rtcc3_ctx* ctx, int enable) {
   return guarded(ctx, [&] {
     ctx->prof.reset();
     ctx->prof.enabled = enable != 0;
+    const char* det = std::getenv("RTCC3_PROFILE_DETAIL");
+    ctx->prof.set_detail(det && det[0] == '1');
     drop_graph(ctx);
   });
 }

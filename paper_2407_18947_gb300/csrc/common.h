@@ -61,12 +61,20 @@ class Profiler {
     cudaEventRecord(pool_[k], s);
     return k;
   }
-  void end(int k0, cudaStream_t s, const char* name, double flops, double bytes) {
+  void end(int k0, cudaStream_t s, const char* name, double flops, double bytes,
+           const std::string& detail = std::string()) {
     if (k0 < 0) return;
     const int k1 = next_event();
     cudaEventRecord(pool_[k1], s);
-    pending_.push_back({k0, k1, find(name), flops, bytes});
+    if (detail_ && !detail.empty())
+      pending_.push_back({k0, k1, find((std::string(name) + "|" + detail).c_str()), flops, bytes});
+    else
+      pending_.push_back({k0, k1, find(name), flops, bytes});
   }
+  // Per-operation names (kernel|spec) when the environment sets
+  // RTCC3_PROFILE_DETAIL=1; used for tuning, not by the benchmark.
+  void set_detail(bool d) { detail_ = d; }
+  bool detail() const { return detail_; }
   void collect() {
     if (pending_.empty()) return;
     for (auto& p : pending_) cudaEventSynchronize(pool_[p.e1]);
@@ -103,6 +111,7 @@ class Profiler {
   }
   std::vector<cudaEvent_t> pool_;
   size_t used_ = 0;
+  bool detail_ = false;
   std::vector<Pending> pending_;
   std::vector<Stat> stats_;
 };

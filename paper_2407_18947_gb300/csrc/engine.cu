@@ -205,8 +205,12 @@ __global__ void k_div_eps(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, St
     }
     const Cx<R> x = X[ox];
     Cx<R> y = Y[oy];
-    y.x += R(double(x.x) / den);
-    y.y += R(double(x.y) / den);
+    // the orbital-energy sum is formed in FP64; the division runs in the
+    // graph's precision (R = float: one FP32 reciprocal instead of two FP64
+    // divisions, which GB300's reduced FP64 rate makes the costliest step)
+    const R inv = R(1) / R(den);
+    y.x += x.x * inv;
+    y.y += x.y * inv;
     Y[oy] = y;
   }
 }
@@ -481,7 +485,11 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
     P->use_tc = true;
     P->tc_swap = N > M;  // the expanded (2x2 real) operand is the smaller one
     const long long Mg = std::max(M, N), Ng = std::min(M, N);
-    P->tc_kp = tc_packed_k(int(K), tc_eb_);
+    // TF32 operands are split into hi + lo TF32 parts and the three leading
+    // products (hi.hi + hi.lo + lo.hi) are summed by one GEMM over a tripled
+    // K: FP32-level accuracy at three times the tensor work
+    const int segs = tc_eb_ == 4 ? 3 : 1;
+    P->tc_kp = segs * tc_packed_k(int(K), tc_eb_);
     const int nkb = P->tc_kp / (128 / tc_eb_);
     const long long nr = 2 * Ng;
     const long long bn = nr >= 192 ? 256 : (nr >= 96 ? 128 : 64);
@@ -500,6 +508,9 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
                              const View& B, bool b_grad, const View& Cv, bool c_grad,
                              bool accumulate) {
   ContractPlan& P = plan(spec, A, B, Cv);
+  if (prof_ && prof_->detail())
+    cur_detail_ = spec + " M=" + std::to_string(P.M) + " N=" + std::to_string(P.N) +
+                  " K=" + std::to_string(P.K) + (P.use_tc ? (P.tc_swap ? " tc-swap" : " tc") : "");
   const C* pa = (a_grad ? nodes_[A.node].grad : nodes_[A.node].data);
   const C* pb = (b_grad ? nodes_[B.node].grad : nodes_[B.node].data);
   C* pc = (c_grad ? nodes_[Cv.node].grad : nodes_[Cv.node].data);
@@ -529,7 +540,8 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
     const double mnk = double(P.M) * P.N * P.K * P.nb;
     const double bytes = (double(P.M) * P.K + double(P.N) * P.K +
                           double(P.M) * P.N * (accumulate ? 2.0 : 1.0)) * P.nb * sizeof(C);
-    pend(pk, sizeof(R) == 8 ? "contract_simt_c128" : "contract_simt_c64", 8.0 * mnk, bytes);
+    pend(pk, sizeof(R) == 8 ? "contract_simt_c128" : "contract_simt_c64", 8.0 * mnk, bytes,
+         cur_detail_);
   }
   if (P.nsplit > 1) {
     const size_t n = size_t(P.nb) * P.M * P.N;
@@ -571,9 +583,10 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     int* err = error_flag();
     const double pbytes = double(op.M + 2.0 * op.N) * op.K * 2.0 * sizeof(float);
     int pk = pbegin();
-    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, tc_eb_, apk, stream_);
-    tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, tc_eb_, bpk, stream_);
-    pend(pk, "tc_pack", 0.0, pbytes + double(op.M + 2.0 * op.N) * op.Kp * tc_eb_);
+    const int segs = tc_eb_ == 4 ? 3 : 1;
+    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, segs, tc_eb_, apk, stream_);
+    tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, segs, tc_eb_, bpk, stream_);
+    pend(pk, "tc_pack", 0.0, pbytes + double(op.M + 2.0 * op.N) * op.Kp * tc_eb_, cur_detail_);
     launches_ += 2;
     pk = pbegin();
     const bool ok = tc_gemm(apk, bpk, op, pc, gcM, gcN, P.c_off0, float(alpha), accumulate,
@@ -582,7 +595,7 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     const double mnk = double(op.M) * op.N * op.K;
     const double bytes = (double(op.M) * op.Kp + 2.0 * op.N * op.Kp) * tc_eb_ +
                          double(op.M) * op.N * sizeof(C) * (accumulate ? 2.0 : 1.0);
-    pend(pk, tc_eb_ == 4 ? "contract_tc_tf32" : "contract_tc_bf16", 8.0 * mnk, bytes);
+    pend(pk, tc_eb_ == 4 ? "contract_tc_tf32" : "contract_tc_bf16", 8.0 * mnk, bytes, cur_detail_);
     ++launches_;
     if (P.tc_nsplit > 1) {
       pk = pbegin();
@@ -629,7 +642,10 @@ void Engine<R>::run_axpy(double alpha, const View& X, bool xg, const View& Y, bo
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
   const int pk = pbegin();
   k_axpy<R><<<grid_for(n), 256, 0, stream_>>>(px, py, d, R(alpha), n);
-  pend(pk, "axpy_strided", 4.0 * n, 3.0 * n * sizeof(C));
+  pend(pk, "axpy_strided", 4.0 * n, 3.0 * n * sizeof(C),
+       prof_ && prof_->detail() ? "n=" + std::to_string(n) + " xs=" + std::to_string(X.stride[X.nd - 1]) +
+                                      " ys=" + std::to_string(Y.stride[Y.nd - 1])
+                                : std::string());
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
 }

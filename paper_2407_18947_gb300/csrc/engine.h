@@ -137,9 +137,11 @@ class Engine {
  private:
   Profiler* prof_ = nullptr;
   int pbegin() { return prof_ ? prof_->begin(stream_) : -1; }
-  void pend(int k, const char* name, double flops, double bytes) {
-    if (prof_) prof_->end(k, stream_, name, flops, bytes);
+  void pend(int k, const char* name, double flops, double bytes,
+            const std::string& detail = std::string()) {
+    if (prof_) prof_->end(k, stream_, name, flops, bytes, detail);
   }
+  std::string cur_detail_;  // spec and extents of the operation being run (profiling)
   enum OpKind { kContract, kAxpy, kMulc, kDiv };
   struct Op {
     OpKind kind;

@@ -289,19 +289,29 @@ __device__ __forceinline__ void put(void* out, size_t idx, float v, int elem_byt
   }
 }
 
+// hi/lo TF32 split of v for segment seg: A takes (hi, hi, lo), B (hi, lo, hi)
+__device__ __forceinline__ float split_part(float v, int seg, bool is_a) {
+  const float hi = __uint_as_float(to_tf32(v));
+  const bool lo = is_a ? (seg == 2) : (seg == 1);
+  return lo ? v - hi : hi;
+}
+
 __global__ void k_pack_a(const float2* __restrict__ A, const long long* __restrict__ aM,
                          const long long* __restrict__ aK, long long aoff, int M, int K, int Kp,
-                         int elem_bytes, void* out) {
+                         int segs, int elem_bytes, void* out) {
   const size_t total = size_t(M) * Kp;
+  const int seg_w = Kp / segs;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
-    const int kp = int(t % Kp);
+    const int kq = int(t % Kp);
     const int m = int(t / Kp);
+    const int seg = kq / seg_w, kp = kq - seg * seg_w;
     const int k = kp >> 1;
     float v = 0.f;
     if (k < K) {
       const float2 a = A[aoff + aM[m] + aK[k]];
       v = (kp & 1) ? a.y : a.x;
+      if (segs == 3) v = split_part(v, seg, true);
     }
     put(out, t, v, elem_bytes);
   }
@@ -309,12 +319,14 @@ __global__ void k_pack_a(const float2* __restrict__ A, const long long* __restri
 
 __global__ void k_pack_b(const float2* __restrict__ B, const long long* __restrict__ bN,
                          const long long* __restrict__ bK, long long boff, int N, int K, int Kp,
-                         int elem_bytes, void* out) {
+                         int segs, int elem_bytes, void* out) {
   const size_t total = size_t(2 * N) * Kp;
+  const int seg_w = Kp / segs;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
-    const int kp = int(t % Kp);
+    const int kq = int(t % Kp);
     const int r = int(t / Kp);
+    const int seg = kq / seg_w, kp = kq - seg * seg_w;
     const int n = r >> 1, k = kp >> 1;
     float v = 0.f;
     if (k < K) {
@@ -322,6 +334,7 @@ __global__ void k_pack_b(const float2* __restrict__ B, const long long* __restri
       // row 2n: (Br, -Bi); row 2n+1: (Bi, Br) along (re, im) of K
       if ((r & 1) == 0) v = (kp & 1) ? -b.y : b.x;
       else v = (kp & 1) ? b.x : b.y;
+      if (segs == 3) v = split_part(v, seg, false);
     }
     put(out, t, v, elem_bytes);
   }
@@ -405,14 +418,16 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
 }  // namespace
 
 void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
-               int K, int Kp, int elem_bytes, void* out, cudaStream_t s) {
-  k_pack_a<<<grid_for(size_t(M) * Kp), 256, 0, s>>>(A, aM, aK, aoff, M, K, Kp, elem_bytes, out);
+               int K, int Kp, int segs, int elem_bytes, void* out, cudaStream_t s) {
+  k_pack_a<<<grid_for(size_t(M) * Kp), 256, 0, s>>>(A, aM, aK, aoff, M, K, Kp, segs, elem_bytes,
+                                                     out);
   RTCC3_CUDA(cudaGetLastError());
 }
 
 void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
-               int K, int Kp, int elem_bytes, void* out, cudaStream_t s) {
-  k_pack_b<<<grid_for(size_t(2 * N) * Kp), 256, 0, s>>>(B, bN, bK, boff, N, K, Kp, elem_bytes, out);
+               int K, int Kp, int segs, int elem_bytes, void* out, cudaStream_t s) {
+  k_pack_b<<<grid_for(size_t(2 * N) * Kp), 256, 0, s>>>(B, bN, bK, boff, N, K, Kp, segs,
+                                                         elem_bytes, out);
   RTCC3_CUDA(cudaGetLastError());
 }
 
