@@ -13,6 +13,7 @@ namespace rtcc3 {
 namespace {
 
 constexpr int kBM = 64, kBN = 64, kBK = 16, kThreads = 256;
+constexpr int kSBM = 16, kSBK = 64;  // small-tile variant
 
 struct EpsArgs {
   int sign[kMaxDim];
@@ -42,7 +43,7 @@ __device__ __forceinline__ void cfma(R& ar, R& ai, Cx<R> a, Cx<R> b) {
 // memory, 4x4 complex micro-tile per thread.  With nsplit > 1 each CTA sums a
 // K chunk into a partial buffer and k_split_reduce adds the chunks in fixed
 // order (deterministic results).
-template <typename R, bool A_KC, bool B_KC>
+template <typename R, bool A_KC, bool B_KC, int BM, int BN, int BK>
 __global__ void __launch_bounds__(kThreads)
 k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __restrict__ Cp,
            const long long* __restrict__ aM, const long long* __restrict__ aK,
@@ -51,60 +52,61 @@ k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __re
            const long long* __restrict__ aB, const long long* __restrict__ bB,
            const long long* __restrict__ cB, int M, int N, int K, int nsplit, int kchunk,
            R alpha, int accumulate, Cx<R>* __restrict__ part) {
-  __shared__ Cx<R> As[kBK][kBM];
-  __shared__ Cx<R> Bs[kBK][kBN];
+  constexpr int TM = BM / 16, TN = BN / 16;  // 16 x 16 threads, TM x TN outputs each
+  __shared__ Cx<R> As[BK][BM];
+  __shared__ Cx<R> Bs[BK][BN];
   const int bz = blockIdx.z;
   const int b = bz / nsplit, split = bz % nsplit;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kbeg = split * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const Cx<R>* Ab = A + aB[b];
   const Cx<R>* Bb = B + bB[b];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  R accr[4][4], acci[4][4];
+  R accr[TM][TN], acci[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { accr[i][j] = R(0); acci[i][j] = R(0); }
+    for (int j = 0; j < TN; ++j) { accr[i][j] = R(0); acci[i][j] = R(0); }
   const Cx<R> zero = cmake<R>(R(0), R(0));
-  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-    for (int e0 = 0; e0 < kBM * kBK; e0 += kThreads) {
+    for (int e0 = 0; e0 < BM * BK; e0 += kThreads) {
       const int e = e0 + tid;
       int mm, kk;
-      if (A_KC) { kk = e % kBK; mm = e / kBK; } else { mm = e % kBM; kk = e / kBM; }
+      if (A_KC) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
       const int m = m0 + mm, k = k0 + kk;
       As[kk][mm] = (m < M && k < kend) ? Ab[aM[m] + aK[k]] : zero;
     }
 #pragma unroll
-    for (int e0 = 0; e0 < kBN * kBK; e0 += kThreads) {
+    for (int e0 = 0; e0 < BN * BK; e0 += kThreads) {
       const int e = e0 + tid;
       int nn, kk;
-      if (B_KC) { kk = e % kBK; nn = e / kBK; } else { nn = e % kBN; kk = e / kBN; }
+      if (B_KC) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
       const int n = n0 + nn, k = k0 + kk;
       Bs[kk][nn] = (n < N && k < kend) ? Bb[bN[n] + bK[k]] : zero;
     }
     __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < BK; ++kk) {
+      Cx<R> a[TM], bv[TN];
 #pragma unroll
-    for (int kk = 0; kk < kBK; ++kk) {
-      Cx<R> a[4], bv[4];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cfma<R>(accr[i][j], acci[i][j], a[i], bv[j]);
+        for (int j = 0; j < TN; ++j) cfma<R>(accr[i][j], acci[i][j], a[i], bv[j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int m = m0 + ty + 16 * i;
     if (m >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= N) continue;
       if (nsplit == 1) {
@@ -463,16 +465,19 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   long long* d = static_cast<long long*>(P->dev);
   P->aM = d + iaM; P->aK = d + iaK; P->bN = d + ibN; P->bK = d + ibK;
   P->cM = d + icM; P->cN = d + icN; P->aB = d + iaB; P->bB = d + ibB; P->cB = d + icB;
+  // skinny outputs with long sums use 16 x 16 tiles and 64-deep K slices
+  P->small_tile = std::max(M, N) <= 48 && K >= 1024;
+  const int bm = P->small_tile ? kSBM : kBM, bk = P->small_tile ? kSBK : kBK;
   // split-K when the output tiles alone do not fill the GPU
-  const long long tiles = ((M + kBM - 1) / kBM) * ((N + kBN - 1) / kBN) * NB;
+  const long long tiles = ((M + bm - 1) / bm) * ((N + bm - 1) / bm) * NB;
   int nsplit = 1;
-  if (tiles < 2 * 152 && K > 4 * kBK) {
-    const long long want = (2 * 152 + tiles - 1) / tiles;
-    const long long maxs = (K + 4 * kBK - 1) / (4 * kBK);
+  if (tiles < 2 * 152 && K > 4 * bk) {
+    const long long want = (4 * 152 + tiles - 1) / tiles;
+    const long long maxs = (K + 4 * bk - 1) / (4 * bk);
     nsplit = int(std::max<long long>(1, std::min(want, maxs)));
   }
   int kchunk = int((K + nsplit - 1) / nsplit);
-  kchunk = ((kchunk + kBK - 1) / kBK) * kBK;
+  kchunk = ((kchunk + bk - 1) / bk) * bk;
   nsplit = int((K + kchunk - 1) / kchunk);
   P->nsplit = nsplit;
   P->kchunk = kchunk;
@@ -522,17 +527,25 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
   C* part = nullptr;
   if (P.nsplit > 1)
     part = static_cast<C*>(scratch(0, size_t(P.nb) * P.nsplit * P.M * P.N * sizeof(C)));
-  dim3 grid((P.N + kBN - 1) / kBN, (P.M + kBM - 1) / kBM, P.nb * P.nsplit);
+  const int bm = P.small_tile ? kSBM : kBM;
+  dim3 grid((P.N + bm - 1) / bm, (P.M + bm - 1) / bm, P.nb * P.nsplit);
   RTCC3_CHECK(grid.y < 65536 && grid.z < 65536, kErrArg, "contraction grid too large: " + spec);
   const int pk = pbegin();
-#define RTCC3_LAUNCH(AK, BK)                                                                   \
-  k_contract<R, AK, BK><<<grid, kThreads, 0, stream_>>>(                                       \
+#define RTCC3_LAUNCH(AK, BK, TBM, TBK)                                                           \
+  k_contract<R, AK, BK, TBM, TBM, TBK><<<grid, kThreads, 0, stream_>>>(                          \
       pa, pb, pc, P.aM, P.aK, P.bN, P.bK, P.cM, P.cN, P.aB, P.bB, P.cB, P.M, P.N, P.K, P.nsplit, \
       P.kchunk, R(alpha), accumulate ? 1 : 0, part)
-  if (P.a_kcontig && P.b_kcontig) RTCC3_LAUNCH(true, true);
-  else if (P.a_kcontig) RTCC3_LAUNCH(true, false);
-  else if (P.b_kcontig) RTCC3_LAUNCH(false, true);
-  else RTCC3_LAUNCH(false, false);
+#define RTCC3_LAUNCH4(TBM, TBK)                                                  \
+  if (P.a_kcontig && P.b_kcontig) RTCC3_LAUNCH(true, true, TBM, TBK);             \
+  else if (P.a_kcontig) RTCC3_LAUNCH(true, false, TBM, TBK);                     \
+  else if (P.b_kcontig) RTCC3_LAUNCH(false, true, TBM, TBK);                     \
+  else RTCC3_LAUNCH(false, false, TBM, TBK)
+  if (P.small_tile) {
+    RTCC3_LAUNCH4(kSBM, kSBK);
+  } else {
+    RTCC3_LAUNCH4(kBM, kBK);
+  }
+#undef RTCC3_LAUNCH4
 #undef RTCC3_LAUNCH
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
@@ -772,9 +785,14 @@ void Engine<R>::backward() {
     } else if (op.kind == kMulc) {
       if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
       run_mulc(op.c, true, op.b, op.a, true);
-    } else {
+    } else if (op.kind == kDiv) {
       if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
       run_div(op.c, true, op.es, op.a, true);
+    } else {
+      const bool saved = tc_region_;
+      tc_region_ = op.tc;
+      op.fn();
+      tc_region_ = saved;
     }
   }
 }

@@ -13,6 +13,7 @@
 // grad(B) += alpha einsum("a,c->b", A, grad(C)).
 #pragma once
 
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -49,6 +50,7 @@ struct ContractPlan {
   int M = 1, N = 1, K = 1, nb = 1;
   int nsplit = 1, kchunk = 1;
   bool a_kcontig = false, b_kcontig = false;
+  bool small_tile = false;  // 16x16 output tiles with 64-deep K slices (skinny shapes)
   // tensor-core route (complex64 graphs with TF32/BF16 operands)
   bool use_tc = false, tc_swap = false;
   int tc_nsplit = 1, tc_kp = 0;
@@ -107,6 +109,34 @@ class Engine {
   void prepare_backward();
   void backward();
 
+  // Untaped execution on data (g = false) or gradient (g = true) buffers,
+  // for custom operations whose adjoint is written by hand.
+  void exec_contract(const char* spec, double alpha, const View& A, bool ag, const View& B,
+                     bool bg, const View& Cv, bool cg) {
+    cur_tc_ = tc_region_;
+    run_contract(spec, alpha, A, ag, B, bg, Cv, cg, true);
+  }
+  void exec_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg) {
+    run_axpy(alpha, X, xg, Y, yg);
+  }
+  void exec_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg) {
+    run_div(X, xg, es, Y, yg);
+  }
+  // Record a custom operation: `bwd` runs at its place in the reverse sweep
+  // (all gradients of tensors it produced are complete by then).
+  void custom(std::function<void()> bwd, bool tc) {
+    Op op{kCustom, "", 0.0, View(), View(), View(), EpsSpec()};
+    op.tc = tc;
+    op.fn = std::move(bwd);
+    tape_.push_back(std::move(op));
+  }
+  void zero(int node, bool grad = false) {
+    RTCC3_CUDA(cudaMemsetAsync(grad ? nodes_[node].grad : nodes_[node].data, 0,
+                               nodes_[node].numel * sizeof(C), stream_));
+  }
+  void set_needs_grad(int node, bool g) { nodes_[node].needs_grad = g; }
+  bool needs_grad(int node) const { return nodes_[node].needs_grad; }
+
   C* data(int n) const { return nodes_[n].data; }
   C* grad(int n) const { return nodes_[n].grad; }
   const Node& info(int n) const { return nodes_[n]; }
@@ -142,7 +172,7 @@ class Engine {
     if (prof_) prof_->end(k, stream_, name, flops, bytes, detail);
   }
   std::string cur_detail_;  // spec and extents of the operation being run (profiling)
-  enum OpKind { kContract, kAxpy, kMulc, kDiv };
+  enum OpKind { kContract, kAxpy, kMulc, kDiv, kCustom };
   struct Op {
     OpKind kind;
     std::string spec;
@@ -150,6 +180,7 @@ class Engine {
     View a, b, c;
     EpsSpec es;
     bool tc = false;  // recorded inside the tensor-core region
+    std::function<void()> fn;  // kCustom backward
   };
   bool cur_tc_ = false;  // tensor-core permission of the contraction being run
   void run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg);

@@ -13,6 +13,77 @@
 
 namespace rtcc3 {
 
+// A t3 = rhs with A = eps3 + [V~, .] (Eq. 4 / Eq. A12 with dt3/dt = 0): +v~_ad on
+// each virtual slot, -v~_li on each occupied slot.  Forward: `sweeps`
+// fixed-point corrections t3 <- (rhs - S t3) / eps3 after t3 = rhs / eps3
+// (the paper's iterative scheme on the stored tensor, Section 2.1).  Adjoint
+// (implicit, no unrolled sweeps): y = A^-T grad(t3) by the same fixed point
+// with S^T, then grad(rhs) += y, grad(v~_vv)[a,d] -= sum_slots y[..a..] t3[..d..]
+// and grad(v~_oo)[l,i] += sum_slots y[i..] t3[l..] -- the triples terms of
+// the one-electron density (the paper's D_ab and D_ij, Eqs. A31-A32).
+template <typename R>
+int field_coupled_solve(Engine<R>& E, int rhs, const View& wvv, const View& woo, int wt,
+                        const typename Engine<R>::EpsSpec& es, const std::vector<int>& s6,
+                        int sweeps) {
+  const int t3 = E.node(s6);
+  const int sx = E.node(s6);
+  const View T3 = E.v(t3), SX = E.v(sx), RHS = E.v(rhs);
+  // captures by value: the closure also runs later, in the reverse sweep
+  auto apply = [&E, sx, wvv, woo](const View& src, bool src_grad, const View& x, bool transpose) {
+    // SX = src - S x (S^T when transpose), on data buffers
+    const View SX = E.v(sx);
+    E.zero(sx);
+    E.exec_axpy(1.0, src, src_grad, SX, false);
+    if (!transpose) {
+      E.exec_contract("ad,ijkdbc->ijkabc", -1.0, wvv, false, x, false, SX, false);
+      E.exec_contract("bd,ijkadc->ijkabc", -1.0, wvv, false, x, false, SX, false);
+      E.exec_contract("cd,ijkabd->ijkabc", -1.0, wvv, false, x, false, SX, false);
+      E.exec_contract("li,ljkabc->ijkabc", 1.0, woo, false, x, false, SX, false);
+      E.exec_contract("lj,ilkabc->ijkabc", 1.0, woo, false, x, false, SX, false);
+      E.exec_contract("lk,ijlabc->ijkabc", 1.0, woo, false, x, false, SX, false);
+    } else {
+      E.exec_contract("ad,ijkabc->ijkdbc", -1.0, wvv, false, x, false, SX, false);
+      E.exec_contract("bd,ijkabc->ijkadc", -1.0, wvv, false, x, false, SX, false);
+      E.exec_contract("cd,ijkabc->ijkabd", -1.0, wvv, false, x, false, SX, false);
+      E.exec_contract("li,ijkabc->ljkabc", 1.0, woo, false, x, false, SX, false);
+      E.exec_contract("lj,ijkabc->ilkabc", 1.0, woo, false, x, false, SX, false);
+      E.exec_contract("lk,ijkabc->ijlabc", 1.0, woo, false, x, false, SX, false);
+    }
+  };
+  E.exec_div(RHS, false, es, T3, false);
+  for (int it = 0; it < sweeps; ++it) {
+    apply(RHS, false, T3, false);
+    E.zero(t3);
+    E.exec_div(SX, false, es, T3, false);
+  }
+  const bool g = E.needs_grad(rhs) || E.needs_grad(wt);
+  E.set_needs_grad(t3, g);
+  if (g) {
+    E.custom([&E, rhs, wt, t3, sx, wvv, woo, es, s6, sweeps, apply]() mutable {
+      if (!E.needs_grad(t3)) return;
+      const View T3 = E.v(t3), SX = E.v(sx);
+      const int y = E.node(s6);
+      const View Y = E.v(y);
+      E.exec_div(T3, true, es, Y, false);  // y = grad(t3) / eps3
+      for (int it = 0; it < sweeps; ++it) {
+        apply(T3, true, Y, true);
+        E.zero(y);
+        E.exec_div(SX, false, es, Y, false);
+      }
+      if (E.needs_grad(rhs)) E.exec_axpy(1.0, Y, false, E.v(rhs), true);
+      if (E.needs_grad(wt)) {
+        E.exec_contract("ijkabc,ijkdbc->ad", -1.0, Y, false, T3, false, wvv, true);
+        E.exec_contract("ijkabc,ijkadc->bd", -1.0, Y, false, T3, false, wvv, true);
+        E.exec_contract("ijkabc,ijkabd->cd", -1.0, Y, false, T3, false, wvv, true);
+        E.exec_contract("ijkabc,ljkabc->li", 1.0, Y, false, T3, false, woo, true);
+        E.exec_contract("ijkabc,ilkabc->lj", 1.0, Y, false, T3, false, woo, true);
+        E.exec_contract("ijkabc,ijlabc->lk", 1.0, Y, false, T3, false, woo, true);
+      }
+    }, true);
+  }
+  return t3;
+}
+
 template <typename R, typename Fill>
 StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt, Fill&& fill) {
   const int o = H.o, v = H.v, n = H.n, na = H.naux;
@@ -137,24 +208,13 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     es.eps = H.eps;
     for (int d = 0; d < 3; ++d) { es.sign[d] = -1; es.base[d] = 0; }
     for (int d = 3; d < 6; ++d) { es.sign[d] = 1; es.base[d] = o; }
-    int t3 = E.node(s6);
-    E.div_eps(E.v(rhs), es, E.v(t3));
-    // eps3 t3 + [V~,T3] = rhs: +v~_ad on virtual slots, -v~_li on occupied slots
-    const int iters = field ? std::max(1, opt.field_iters) : 0;
-    const View wvv = blk(wt, "vv"), woo = blk(wt, "oo");
-    for (int it = 0; it < iters; ++it) {
-      const int sx = E.node(s6);
-      const View SX = E.v(sx), T3 = E.v(t3);
-      E.axpy(1.0, E.v(rhs), SX);
-      E.contract("ad,ijkdbc->ijkabc", -1.0, wvv, T3, SX, true);
-      E.contract("bd,ijkadc->ijkabc", -1.0, wvv, T3, SX, true);
-      E.contract("cd,ijkabd->ijkabc", -1.0, wvv, T3, SX, true);
-      E.contract("li,ljkabc->ijkabc", 1.0, woo, T3, SX, true);
-      E.contract("lj,ilkabc->ijkabc", 1.0, woo, T3, SX, true);
-      E.contract("lk,ijlabc->ijkabc", 1.0, woo, T3, SX, true);
-      const int tn = E.node(s6);
-      E.div_eps(SX, es, E.v(tn));
-      t3 = tn;
+    int t3;
+    if (!field) {
+      t3 = E.node(s6);
+      E.div_eps(E.v(rhs), es, E.v(t3));
+    } else {
+      t3 = field_coupled_solve(E, rhs, blk(wt, "vv"), blk(wt, "oo"), wt, es, s6,
+                               std::max(1, opt.field_iters));
     }
     S.t3 = t3;
     const View T3 = E.v(t3);
