@@ -190,23 +190,23 @@ __global__ void k_mulc(const Cx<R>* __restrict__ X, const Cx<R>* __restrict__ Cs
 }
 
 // Y[.] += X[.] / eps(index) in FP64 (slot 0 = X, 1 = Y).
-template <typename R>
+template <typename R, typename I>
 __global__ void k_div_eps(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, StridedDesc d,
-                          const double* __restrict__ eps, EpsArgs ea, size_t n) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
-       t += (size_t)gridDim.x * blockDim.x) {
+                          const double* __restrict__ eps, EpsArgs ea, I n, int overwrite) {
+  for (I t = I(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += I(gridDim.x) * blockDim.x) {
     long long ox = d.off0, oy = d.off1;
     double den = 0.0;
-    size_t rem = t;
+    I rem = t;
     for (int k = d.nd - 1; k >= 0; --k) {
-      const long long i = (long long)(rem % (size_t)d.shape[k]);
-      rem /= (size_t)d.shape[k];
+      const I sh = I(d.shape[k]);
+      const long long i = (long long)(rem % sh);
+      rem /= sh;
       ox += i * d.s0[k];
       oy += i * d.s1[k];
       if (ea.sign[k]) den += ea.sign[k] * eps[ea.base[k] + i];
     }
     const Cx<R> x = X[ox];
-    Cx<R> y = Y[oy];
+    Cx<R> y = overwrite ? cmake<R>(R(0), R(0)) : Y[oy];
     // the orbital-energy sum is formed in FP64; the division runs in the
     // graph's precision (R = float: one FP32 reciprocal instead of two FP64
     // divisions, which GB300's reduced FP64 rate makes the costliest step)
@@ -214,6 +214,55 @@ __global__ void k_div_eps(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, St
     y.x += x.x * inv;
     y.y += x.y * inv;
     Y[oy] = y;
+  }
+}
+
+// Y[.] (+)= sum_s alpha_s X_s[.] over Y's shape: up to kMaxSrc strided
+// sources, one pass, coalesced on Y (threads walk Y's last index fastest).
+constexpr int kMaxSrc = 6;
+template <typename R>
+struct CombDesc {
+  int nd, nsrc, overwrite;
+  int shape[kMaxDim];
+  long long sy[kMaxDim];
+  long long sx[kMaxSrc][kMaxDim];
+  long long offy;
+  long long offx[kMaxSrc];
+  R alpha[kMaxSrc];
+  const Cx<R>* src[kMaxSrc];
+};
+
+template <typename R, typename I>
+__global__ void k_combine(Cx<R>* __restrict__ Y, const CombDesc<R> d, I n) {
+  for (I t = I(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += I(gridDim.x) * blockDim.x) {
+    I rem = t;
+    long long oy = d.offy;
+    long long ox[kMaxSrc];
+#pragma unroll
+    for (int s = 0; s < kMaxSrc; ++s) ox[s] = d.offx[s];
+    for (int k = d.nd - 1; k >= 0; --k) {
+      const I sh = I(d.shape[k]);
+      const I i = rem % sh;
+      rem /= sh;
+      oy += (long long)i * d.sy[k];
+#pragma unroll
+      for (int s = 0; s < kMaxSrc; ++s)
+        if (s < d.nsrc) ox[s] += (long long)i * d.sx[s][k];
+    }
+    R re = R(0), im = R(0);
+#pragma unroll
+    for (int s = 0; s < kMaxSrc; ++s)
+      if (s < d.nsrc) {
+        const Cx<R> x = d.src[s][ox[s]];
+        re += d.alpha[s] * x.x;
+        im += d.alpha[s] * x.y;
+      }
+    if (!d.overwrite) {
+      const Cx<R> y = Y[oy];
+      re += y.x;
+      im += y.y;
+    }
+    Y[oy] = cmake<R>(re, im);
   }
 }
 
@@ -292,14 +341,14 @@ void Engine<R>::begin() {
 }
 
 template <typename R>
-int Engine<R>::node(const std::vector<int>& shape, bool needs_grad) {
+int Engine<R>::node(const std::vector<int>& shape, bool needs_grad, bool zero) {
   Node nd;
   nd.shape = shape;
   nd.numel = 1;
   for (int s : shape) nd.numel *= size_t(s);
   RTCC3_CHECK((int)shape.size() <= kMaxDim, kErrArg, "tensor rank too large");
   nd.data = static_cast<C*>(arena_.alloc(nd.numel * sizeof(C)));
-  RTCC3_CUDA(cudaMemsetAsync(nd.data, 0, nd.numel * sizeof(C), stream_));
+  if (zero) RTCC3_CUDA(cudaMemsetAsync(nd.data, 0, nd.numel * sizeof(C), stream_));
   nd.needs_grad = needs_grad;
   nodes_.push_back(nd);
   return int(nodes_.size()) - 1;
@@ -638,29 +687,122 @@ void Engine<R>::contract(const char* spec, double alpha, const View& A, const Vi
 
 template <typename R>
 void Engine<R>::run_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg) {
-  RTCC3_CHECK(X.nd == Y.nd, kErrArg, "axpy rank mismatch");
-  StridedDesc d{};
-  d.nd = Y.nd;
-  for (int k = 0; k < Y.nd; ++k) {
-    RTCC3_CHECK(X.shape[k] == Y.shape[k], kErrArg, "axpy shape mismatch");
-    d.shape[k] = Y.shape[k];
-    d.s0[k] = X.stride[k];
-    d.s1[k] = Y.stride[k];
+  run_combine(&X, &xg, &alpha, 1, Y, yg, false, "axpy_strided");
+}
+
+template <typename R>
+void Engine<R>::run_combine(const View* xs, const bool* xg, const double* alphas, int ns,
+                            const View& Y, bool yg, bool overwrite, const char* name) {
+  RTCC3_CHECK(ns >= 1 && ns <= kMaxSrc, kErrArg, "combine takes 1..6 sources");
+  CombDesc<R> d{};
+  d.nsrc = ns;
+  d.overwrite = overwrite ? 1 : 0;
+  d.offy = Y.off;
+  // copy dims, then merge neighbours that are contiguous in every operand
+  int nd = Y.nd;
+  int shape[kMaxDim];
+  long long sy[kMaxDim], sx[kMaxSrc][kMaxDim];
+  for (int k = 0; k < nd; ++k) {
+    shape[k] = Y.shape[k];
+    sy[k] = Y.stride[k];
   }
-  d.off0 = X.off;
-  d.off1 = Y.off;
+  for (int s = 0; s < ns; ++s) {
+    RTCC3_CHECK(xs[s].nd == Y.nd, kErrArg, "combine rank mismatch");
+    for (int k = 0; k < nd; ++k) {
+      RTCC3_CHECK(xs[s].shape[k] == Y.shape[k], kErrArg, "combine shape mismatch");
+      sx[s][k] = xs[s].stride[k];
+    }
+    d.offx[s] = xs[s].off;
+    d.alpha[s] = R(alphas[s]);
+    d.src[s] = xg[s] ? nodes_[xs[s].node].grad : nodes_[xs[s].node].data;
+  }
+  int w = 0;
+  for (int k = 0; k < nd; ++k) {
+    if (w > 0) {
+      bool merge = sy[w - 1] == sy[k] * shape[k];
+      for (int s = 0; s < ns && merge; ++s) merge = sx[s][w - 1] == sx[s][k] * shape[k];
+      if (merge) {
+        shape[w - 1] *= shape[k];
+        sy[w - 1] = sy[k];
+        for (int s = 0; s < ns; ++s) sx[s][w - 1] = sx[s][k];
+        continue;
+      }
+    }
+    shape[w] = shape[k];
+    sy[w] = sy[k];
+    for (int s = 0; s < ns; ++s) sx[s][w] = sx[s][k];
+    ++w;
+  }
+  d.nd = w;
+  for (int k = 0; k < w; ++k) {
+    d.shape[k] = shape[k];
+    d.sy[k] = sy[k];
+    for (int s = 0; s < ns; ++s) d.sx[s][k] = sx[s][k];
+  }
   const size_t n = Y.numel();
   if (n == 0) return;
-  const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
   const int pk = pbegin();
-  k_axpy<R><<<grid_for(n), 256, 0, stream_>>>(px, py, d, R(alpha), n);
-  pend(pk, "axpy_strided", 4.0 * n, 3.0 * n * sizeof(C),
-       prof_ && prof_->detail() ? "n=" + std::to_string(n) + " xs=" + std::to_string(X.stride[X.nd - 1]) +
-                                      " ys=" + std::to_string(Y.stride[Y.nd - 1])
+  if (n < (size_t(1) << 31))
+    k_combine<R, unsigned><<<grid_for(n), 256, 0, stream_>>>(py, d, unsigned(n));
+  else
+    k_combine<R, size_t><<<grid_for(n), 256, 0, stream_>>>(py, d, n);
+  pend(pk, name, 2.0 * ns * n, double(n) * sizeof(C) * (ns + (overwrite ? 1 : 2)),
+       prof_ && prof_->detail() ? "n=" + std::to_string(n) + " nsrc=" + std::to_string(ns) +
+                                      " nd=" + std::to_string(w)
                                 : std::string());
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
+}
+
+template <typename R>
+void Engine<R>::combine(std::initializer_list<std::pair<double, View>> srcs, const View& Y,
+                        bool overwrite) {
+  View xs[kMaxSrc];
+  bool xg[kMaxSrc] = {false, false, false, false, false, false};
+  double al[kMaxSrc];
+  int ns = 0;
+  bool g = false;
+  for (auto& s : srcs) {
+    RTCC3_CHECK(ns < kMaxSrc, kErrArg, "combine takes at most 6 sources");
+    RTCC3_CHECK(s.second.node != Y.node, kErrArg, "combine output aliases an input");
+    xs[ns] = s.second;
+    al[ns] = s.first;
+    g = g || nodes_[s.second.node].needs_grad;
+    ++ns;
+  }
+  run_combine(xs, xg, al, ns, Y, false, overwrite, "combine");
+  if (g) nodes_[Y.node].needs_grad = true;
+  for (int s = 0; s < ns; ++s) {
+    Op op{kAxpy, "", al[s], xs[s], View(), Y, EpsSpec()};
+    tape_.push_back(op);  // adjoint: grad(X_s) += alpha_s grad(Y)
+  }
+}
+
+template <typename R>
+void Engine<R>::sym6(double alpha, const View& X, const View& Y, bool overwrite) {
+  RTCC3_CHECK(X.node != Y.node, kErrArg, "sym6 output aliases input");
+  run_sym6(alpha, X, false, Y, false, overwrite);
+  if (nodes_[X.node].needs_grad) nodes_[Y.node].needs_grad = true;
+  Op op{kSym6, "", alpha, X, View(), Y, EpsSpec()};
+  tape_.push_back(op);
+}
+
+template <typename R>
+void Engine<R>::run_sym6(double alpha, const View& X, bool xg, const View& Y, bool yg,
+                         bool overwrite) {
+  // P_ijk^abc (Eq. A30): the six simultaneous permutations of (ijk, abc)
+  static const char* perms[6] = {"ijkabc->ijkabc", "jikbac->ijkabc", "ikjacb->ijkabc",
+                                 "kjicba->ijkabc", "kijcab->ijkabc", "jkibca->ijkabc"};
+  View xs[6];
+  bool xgs[6];
+  double al[6];
+  for (int s = 0; s < 6; ++s) {
+    xs[s] = ev(perms[s], X);
+    xgs[s] = xg;
+    al[s] = alpha;
+  }
+  run_combine(xs, xgs, al, 6, Y, yg, overwrite, "sym6");
 }
 
 template <typename R>
@@ -707,7 +849,8 @@ void Engine<R>::mulc(const View& X, const View& Cst, const View& Y) {
 }
 
 template <typename R>
-void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg) {
+void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
+                        bool overwrite) {
   RTCC3_CHECK(X.nd == Y.nd, kErrArg, "div_eps rank mismatch");
   StridedDesc d{};
   EpsArgs ea{};
@@ -727,16 +870,20 @@ void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y
   const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
   const int pk = pbegin();
-  k_div_eps<R><<<grid_for(n), 256, 0, stream_>>>(px, py, d, es.eps, ea, n);
-  pend(pk, "div_eps", 4.0 * n, 3.0 * n * sizeof(C));
+  if (n < (size_t(1) << 31))
+    k_div_eps<R, unsigned><<<grid_for(n), 256, 0, stream_>>>(px, py, d, es.eps, ea, unsigned(n),
+                                                              overwrite ? 1 : 0);
+  else
+    k_div_eps<R, size_t><<<grid_for(n), 256, 0, stream_>>>(px, py, d, es.eps, ea, n, overwrite ? 1 : 0);
+  pend(pk, "div_eps", 4.0 * n, (overwrite ? 2.0 : 3.0) * n * sizeof(C));
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
 }
 
 template <typename R>
-void Engine<R>::div_eps(const View& X, const EpsSpec& es, const View& Y) {
+void Engine<R>::div_eps(const View& X, const EpsSpec& es, const View& Y, bool overwrite) {
   RTCC3_CHECK(X.node != Y.node, kErrArg, "div_eps output aliases input");
-  run_div(X, false, es, Y, false);
+  run_div(X, false, es, Y, false, overwrite);
   if (nodes_[X.node].needs_grad) nodes_[Y.node].needs_grad = true;
   Op op{kDiv, "", 1.0, X, View(), Y, es};
   tape_.push_back(op);
@@ -788,6 +935,9 @@ void Engine<R>::backward() {
     } else if (op.kind == kDiv) {
       if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
       run_div(op.c, true, op.es, op.a, true);
+    } else if (op.kind == kSym6) {
+      if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
+      run_sym6(op.alpha, op.c, true, op.a, true, false);
     } else {
       const bool saved = tc_region_;
       tc_region_ = op.tc;

@@ -81,7 +81,8 @@ class Engine {
   // Start a new graph: resets the arena cursor and the tape.
   void begin();
   // New tensor (zero-filled on the stream); a leaf may require gradients.
-  int node(const std::vector<int>& shape, bool needs_grad = false);
+  // zero = false skips the fill when the first writer overwrites every element.
+  int node(const std::vector<int>& shape, bool needs_grad = false, bool zero = true);
   // Register persistent device memory (a constant of the graph, no gradient).
   int external(C* data, const std::vector<int>& shape);
   View v(int node) const;
@@ -91,6 +92,10 @@ class Engine {
   void contract(const char* spec, double alpha, const View& A, const View& B, const View& Cv,
                 bool accumulate);
   void axpy(double alpha, const View& X, const View& Y);
+  // Y (+)= sum_s alpha_s X_s in one pass (up to six strided sources).
+  void combine(std::initializer_list<std::pair<double, View>> srcs, const View& Y, bool overwrite);
+  // Y (+)= alpha P_ijk^abc X for 6-index tensors (o,o,o,v,v,v); self-adjoint.
+  void sym6(double alpha, const View& X, const View& Y, bool overwrite);
   void mulc(const View& X, const View& Cst, const View& Y);
   // Y += X / eps(index) with eps(index) = sum_d sign[d] * eps_dev[base[d] + index_d],
   // the orbital-energy denominators; the division is carried out in FP64.
@@ -99,7 +104,7 @@ class Engine {
     int sign[kMaxDim] = {0};
     int base[kMaxDim] = {0};
   };
-  void div_eps(const View& X, const EpsSpec& es, const View& Y);
+  void div_eps(const View& X, const EpsSpec& es, const View& Y, bool overwrite = false);
   // Non-differentiable initialisation.
   void fill_identity(int node);
   void fill_ones(int node);
@@ -172,7 +177,7 @@ class Engine {
     if (prof_) prof_->end(k, stream_, name, flops, bytes, detail);
   }
   std::string cur_detail_;  // spec and extents of the operation being run (profiling)
-  enum OpKind { kContract, kAxpy, kMulc, kDiv, kCustom };
+  enum OpKind { kContract, kAxpy, kMulc, kDiv, kCustom, kSym6 };
   struct Op {
     OpKind kind;
     std::string spec;
@@ -183,7 +188,11 @@ class Engine {
     std::function<void()> fn;  // kCustom backward
   };
   bool cur_tc_ = false;  // tensor-core permission of the contraction being run
-  void run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg);
+  void run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
+               bool overwrite = false);
+  void run_combine(const View* xs, const bool* xg, const double* alphas, int ns, const View& Y,
+                   bool yg, bool overwrite, const char* name);
+  void run_sym6(double alpha, const View& X, bool xg, const View& Y, bool yg, bool overwrite);
   void run_contract(const std::string& spec, double alpha, const View& A, bool a_grad, const View& B,
                     bool b_grad, const View& Cv, bool c_grad, bool accumulate);
   void run_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg);

@@ -137,9 +137,8 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   auto F = [&](const char* b) { return blk(ft, b); };
 
   // ---- CCSD residual (T1-transformed, spin adapted) ---------------------------
-  const int u = E.node({o, o, v, v});
-  E.axpy(2.0, T, E.v(u));
-  E.axpy(-1.0, E.ev("ijba->ijab", T), E.v(u));
+  const int u = E.node({o, o, v, v}, false, false);
+  E.combine({{2.0, T}, {-1.0, E.ev("ijba->ijab", T)}}, E.v(u), true);
   const View U = E.v(u);
   S.r1 = E.node({o, v});
   const View R1 = E.v(S.r1);
@@ -147,9 +146,8 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   const View R2 = E.v(S.r2);
   const int Sd = E.node({o, o, v, v});
   const View SD = E.v(Sd);
-  const int Lov = E.node({o, v, o, v});
-  E.axpy(2.0, G("ovov"), E.v(Lov));
-  E.axpy(-1.0, E.ev("lckd->ldkc", G("ovov")), E.v(Lov));
+  const int Lov = E.node({o, v, o, v}, false, false);
+  E.combine({{2.0, G("ovov")}, {-1.0, E.ev("lckd->ldkc", G("ovov"))}}, E.v(Lov), true);
   if (opt.ccsd) {
   E.contract("kicd,adkc->ia", 1.0, U, G("vvov"), R1, true);
   E.contract("klac,kilc->ia", -1.0, U, G("ooov"), R1, true);
@@ -187,22 +185,20 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   if (opt.triples) {
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores
     const std::vector<int> s6 = {o, o, o, v, v, v};
-    static const char* perms[6] = {"ijkabc->ijkabc", "jikbac->ijkabc", "ikjacb->ijkabc",
-                                   "kjicba->ijkabc", "kijcab->ijkabc", "jkibca->ijkabc"};
     // Z = sum_e t_ij^ae <cb|ke>~ - sum_m t_im^ab <mc|jk>~ ; W = P_ijk^abc Z (Eqs. A25, A30)
     const int Z = E.node(s6);
     E.contract("ijae,ckbe->ijkabc", 1.0, T, G("vovv"), E.v(Z), true);
     E.contract("imab,mjck->ijkabc", -1.0, T, G("oovo"), E.v(Z), true);
     // rhs = -(W + <mu3|1/2[[V~,T2],T2]|0>), the latter = -P sum_ld v~_ld t_ij^ad t_kl^cb
-    const int rhs = E.node(s6);
-    for (auto p : perms) E.axpy(-1.0, E.ev(p, E.v(Z)), E.v(rhs));
+    const int rhs = E.node(s6, false, false);
+    E.sym6(-1.0, E.v(Z), E.v(rhs), true);
     const bool field = opt.field_terms;
     if (field) {
       const int Yl = E.node({o, o, o, v});
       E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), true);
       const int Z2 = E.node(s6);
       E.contract("lija,klcb->ijkabc", 1.0, E.v(Yl), T, E.v(Z2), true);
-      for (auto p : perms) E.axpy(1.0, E.ev(p, E.v(Z2)), E.v(rhs));
+      E.sym6(1.0, E.v(Z2), E.v(rhs), false);
     }
     typename Engine<R>::EpsSpec es;
     es.eps = H.eps;
@@ -210,8 +206,8 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     for (int d = 3; d < 6; ++d) { es.sign[d] = 1; es.base[d] = o; }
     int t3;
     if (!field) {
-      t3 = E.node(s6);
-      E.div_eps(E.v(rhs), es, E.v(t3));
+      t3 = E.node(s6, false, false);
+      E.div_eps(E.v(rhs), es, E.v(t3), true);
     } else {
       t3 = field_coupled_solve(E, rhs, blk(wt, "vv"), blk(wt, "oo"), wt, es, s6,
                                std::max(1, opt.field_iters));
@@ -219,31 +215,27 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     S.t3 = t3;
     const View T3 = E.v(t3);
     // X1 (Eq. A21) and X2 (Eq. A22)
-    const int dd = E.node(s6);
-    E.axpy(1.0, T3, E.v(dd));
-    E.axpy(-1.0, E.ev("ijkcba->ijkabc", T3), E.v(dd));
-    const int Ljk = E.node({o, o, v, v});
-    E.axpy(2.0, E.ev("jbkc->jkbc", G("ovov")), E.v(Ljk));
-    E.axpy(-1.0, E.ev("jckb->jkbc", G("ovov")), E.v(Ljk));
+    const int dd = E.node(s6, false, false);  // t_ijk^abc - t_ijk^cba
+    E.combine({{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}}, E.v(dd), true);
+    const int Ljk = E.node({o, o, v, v}, false, false);
+    E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
+              E.v(Ljk), true);
     E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), E.v(Ljk), R1, true);
     const int S3 = E.node({o, o, v, v});
     E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), F("ov"), E.v(S3), true);
-    const int Ub = E.node(s6);
-    E.axpy(2.0, T3, E.v(Ub));
-    E.axpy(-1.0, E.ev("ijkxzy->ijkxyz", T3), E.v(Ub));
-    E.axpy(-1.0, E.ev("ijkzyx->ijkxyz", T3), E.v(Ub));
+    const int Ub = E.node(s6, false, false);  // 2 t^cbe - t^ceb - t^ebc  as [ijk cbe]
+    E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
+              E.v(Ub), true);
     E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), G("vvov"), E.v(S3), true);
-    const int Uc = E.node(s6);
-    E.axpy(2.0, T3, E.v(Uc));
-    E.axpy(-1.0, E.ev("mjkyxz->mjkxyz", T3), E.v(Uc));
-    E.axpy(-1.0, E.ev("mjkzyx->mjkxyz", T3), E.v(Uc));
+    const int Uc = E.node(s6, false, false);  // 2 t_mjk^cba - t_mjk^bca - t_mjk^abc
+    E.combine({{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}},
+              E.v(Uc), true);
     E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), G("ooov"), E.v(S3), true);
     E.axpy(1.0, E.v(S3), SD);
     E.set_tc_region(false);
   }
   // P_ij^ab on the symmetrised part
-  E.axpy(1.0, SD, R2);
-  E.axpy(1.0, E.ev("jiba->ijab", SD), R2);
+  E.combine({{1.0, SD}, {1.0, E.ev("jiba->ijab", SD)}}, R2, false);
 
   // ---- energy <0|H + [H,T2]|0> - E_ref (Eq. A8); E_ref is subtracted in FP64 ----
   S.e = E.node({});
