@@ -252,6 +252,24 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
   for (size_t t = 0; t < hc.size(); ++t) hc[t] = cmake<R>(R(h[t]), R(0));
   for (size_t t = 0; t < Lc.size(); ++t) Lc[t] = cmake<R>(R(Lfac[t]), R(0));
   for (int t = 0; t < n; ++t) ones[t] = cmake<R>(R(1), R(0));
+  {
+    // FP64 sums of three occupied / three virtual orbital energies (Eq. A16)
+    const int v = ctx->v;
+    std::vector<double> os(size_t(o) * o * o), vs(size_t(v) * v * v);
+    for (int i = 0; i < o; ++i)
+      for (int j = 0; j < o; ++j)
+        for (int k = 0; k < o; ++k)
+          os[(size_t(i) * o + j) * o + k] = ctx->eps_h[i] + ctx->eps_h[j] + ctx->eps_h[k];
+    for (int a = 0; a < v; ++a)
+      for (int b = 0; b < v; ++b)
+        for (int c = 0; c < v; ++c)
+          vs[(size_t(a) * v + b) * v + c] =
+              ctx->eps_h[o + a] + ctx->eps_h[o + b] + ctx->eps_h[o + c];
+    H.osum = rn->template alloc<double>(os.size());
+    H.vsum = rn->template alloc<double>(vs.size());
+    RTCC3_CUDA(cudaMemcpy(H.osum, os.data(), os.size() * sizeof(double), cudaMemcpyHostToDevice));
+    RTCC3_CUDA(cudaMemcpy(H.vsum, vs.data(), vs.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   H.h = rn->template alloc<Cx<R>>(hc.size());
   H.L = rn->template alloc<Cx<R>>(Lc.size());
   H.ones = rn->template alloc<Cx<R>>(n);

@@ -18,7 +18,29 @@ constexpr int kSBM = 16, kSBK = 64;  // small-tile variant
 struct EpsArgs {
   int sign[kMaxDim];
   int base[kMaxDim];
+  const double* osum;
+  const double* vsum;
+  int o, v;
 };
+
+// Triples denominators from the precomputed FP64 occupied / virtual sums, for
+// X and Y both in the dense (o,o,o,v,v,v) layout: one FP64 subtraction per
+// element instead of six FP64 additions (GB300's FP64 rate is low).
+template <typename R, typename I>
+__global__ void k_div_eps_dense6(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx,
+                                 long long offy, const double* __restrict__ osum,
+                                 const double* __restrict__ vsum, I v3, I n, int overwrite) {
+  for (I t = I(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += I(gridDim.x) * blockDim.x) {
+    const I ijk = t / v3;
+    const I abc = t - ijk * v3;
+    const R inv = R(1) / R(vsum[abc] - osum[ijk]);
+    const Cx<R> x = X[offx + t];
+    Cx<R> y = overwrite ? cmake<R>(R(0), R(0)) : Y[offy + t];
+    y.x += x.x * inv;
+    y.y += x.y * inv;
+    Y[offy + t] = y;
+  }
+}
 
 struct StridedDesc {
   int nd;
@@ -534,8 +556,10 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   P->b_off0 = h[ibB];
   P->c_off0 = h[icB];
   // tensor-core route: one batch, a large output side and enough work
+  // (a short K would make the packed operands cost more traffic than the
+  // product saves: those stay on CUDA cores)
   if (std::is_same<R, float>::value && tc_ok && NB == 1 && std::max(M, N) >= 128 &&
-      std::min(M, N) >= 4 && M * N * K >= (1LL << 21)) {
+      std::min(M, N) >= 4 && K >= 64 && M * N * K >= (1LL << 21)) {
     P->use_tc = true;
     P->tc_swap = N > M;  // the expanded (2x2 real) operand is the smaller one
     const long long Mg = std::max(M, N), Ng = std::min(M, N);
@@ -852,6 +876,34 @@ template <typename R>
 void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
                         bool overwrite) {
   RTCC3_CHECK(X.nd == Y.nd, kErrArg, "div_eps rank mismatch");
+  if (es.osum && es.vsum && Y.nd == 6) {
+    auto dense6 = [&](const View& w) {
+      const int dims[6] = {es.o, es.o, es.o, es.v, es.v, es.v};
+      long long st = 1;
+      for (int k = 5; k >= 0; --k) {
+        if (w.shape[k] != dims[k] || w.stride[k] != st) return false;
+        st *= dims[k];
+      }
+      return true;
+    };
+    if (dense6(X) && dense6(Y)) {
+      const size_t n = Y.numel();
+      const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
+      C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+      const long long v3 = (long long)es.v * es.v * es.v;
+      const int pk = pbegin();
+      if (n < (size_t(1) << 31))
+        k_div_eps_dense6<R, unsigned><<<grid_for(n), 256, 0, stream_>>>(
+            px, py, X.off, Y.off, es.osum, es.vsum, unsigned(v3), unsigned(n), overwrite ? 1 : 0);
+      else
+        k_div_eps_dense6<R, size_t><<<grid_for(n), 256, 0, stream_>>>(
+            px, py, X.off, Y.off, es.osum, es.vsum, size_t(v3), n, overwrite ? 1 : 0);
+      pend(pk, "div_eps", 4.0 * n, (overwrite ? 2.0 : 3.0) * n * sizeof(C));
+      ++launches_;
+      RTCC3_CUDA(cudaGetLastError());
+      return;
+    }
+  }
   StridedDesc d{};
   EpsArgs ea{};
   d.nd = Y.nd;

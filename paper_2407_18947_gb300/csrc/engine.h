@@ -103,6 +103,11 @@ class Engine {
     const double* eps = nullptr;
     int sign[kMaxDim] = {0};
     int base[kMaxDim] = {0};
+    // Triples shortcut (o,o,o,v,v,v): precomputed FP64 sums
+    // osum[(i o + j) o + k] = e_i + e_j + e_k, vsum[(a v + b) v + c] = e_a + e_b + e_c.
+    const double* osum = nullptr;
+    const double* vsum = nullptr;
+    int o = 0, v = 0;
   };
   void div_eps(const View& X, const EpsSpec& es, const View& Y, bool overwrite = false);
   // Non-differentiable initialisation.
@@ -124,8 +129,28 @@ class Engine {
   void exec_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg) {
     run_axpy(alpha, X, xg, Y, yg);
   }
-  void exec_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg) {
-    run_div(X, xg, es, Y, yg);
+  void exec_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
+                bool overwrite = false) {
+    run_div(X, xg, es, Y, yg, overwrite);
+  }
+  // Y = X (X on its data or gradient buffer; untaped).
+  void exec_copy(const View& X, bool xg, const View& Y) {
+    const double one = 1.0;
+    run_combine(&X, &xg, &one, 1, Y, false, true, "copy");
+  }
+  // Y (+)= sum_s alpha_s X_s over data buffers (untaped).
+  void exec_combine(std::initializer_list<std::pair<double, View>> srcs, const View& Y,
+                    bool overwrite) {
+    View xs[6];
+    bool xg[6] = {false, false, false, false, false, false};
+    double al[6];
+    int ns = 0;
+    for (auto& s : srcs) {
+      xs[ns] = s.second;
+      al[ns] = s.first;
+      ++ns;
+    }
+    run_combine(xs, xg, al, ns, Y, false, overwrite, "combine");
   }
   // Record a custom operation: `bwd` runs at its place in the reverse sweep
   // (all gradients of tensors it produced are complete by then).

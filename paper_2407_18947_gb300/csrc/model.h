@@ -24,6 +24,8 @@ struct Hamil {
   Cx<R>* ones = nullptr;  // n ones (for traces)
   double* eps = nullptr;  // n orbital energies (FP64)
   double* mu = nullptr;   // 3 x n x n dipole matrices (FP64)
+  double* osum = nullptr;  // o^3 sums e_i + e_j + e_k (FP64)
+  double* vsum = nullptr;  // v^3 sums e_a + e_b + e_c (FP64)
   double e_ref = 0.0;     // sum_i (h_ii + eps_i)
 };
 

@@ -25,15 +25,14 @@ template <typename R>
 int field_coupled_solve(Engine<R>& E, int rhs, const View& wvv, const View& woo, int wt,
                         const typename Engine<R>::EpsSpec& es, const std::vector<int>& s6,
                         int sweeps) {
-  const int t3 = E.node(s6);
-  const int sx = E.node(s6);
+  const int t3 = E.node(s6, false, false);
+  const int sx = E.node(s6, false, false);
   const View T3 = E.v(t3), SX = E.v(sx), RHS = E.v(rhs);
   // captures by value: the closure also runs later, in the reverse sweep
   auto apply = [&E, sx, wvv, woo](const View& src, bool src_grad, const View& x, bool transpose) {
     // SX = src - S x (S^T when transpose), on data buffers
     const View SX = E.v(sx);
-    E.zero(sx);
-    E.exec_axpy(1.0, src, src_grad, SX, false);
+    E.exec_copy(src, src_grad, SX);
     if (!transpose) {
       E.exec_contract("ad,ijkdbc->ijkabc", -1.0, wvv, false, x, false, SX, false);
       E.exec_contract("bd,ijkadc->ijkabc", -1.0, wvv, false, x, false, SX, false);
@@ -50,11 +49,10 @@ int field_coupled_solve(Engine<R>& E, int rhs, const View& wvv, const View& woo,
       E.exec_contract("lk,ijkabc->ijlabc", 1.0, woo, false, x, false, SX, false);
     }
   };
-  E.exec_div(RHS, false, es, T3, false);
+  E.exec_div(RHS, false, es, T3, false, true);
   for (int it = 0; it < sweeps; ++it) {
     apply(RHS, false, T3, false);
-    E.zero(t3);
-    E.exec_div(SX, false, es, T3, false);
+    E.exec_div(SX, false, es, T3, false, true);
   }
   const bool g = E.needs_grad(rhs) || E.needs_grad(wt);
   E.set_needs_grad(t3, g);
@@ -62,22 +60,24 @@ int field_coupled_solve(Engine<R>& E, int rhs, const View& wvv, const View& woo,
     E.custom([&E, rhs, wt, t3, sx, wvv, woo, es, s6, sweeps, apply]() mutable {
       if (!E.needs_grad(t3)) return;
       const View T3 = E.v(t3), SX = E.v(sx);
-      const int y = E.node(s6);
+      const int y = E.node(s6, false, false);
       const View Y = E.v(y);
-      E.exec_div(T3, true, es, Y, false);  // y = grad(t3) / eps3
+      E.exec_div(T3, true, es, Y, false, true);  // y = grad(t3) / eps3
       for (int it = 0; it < sweeps; ++it) {
         apply(T3, true, Y, true);
-        E.zero(y);
-        E.exec_div(SX, false, es, Y, false);
+        E.exec_div(SX, false, es, Y, false, true);
       }
       if (E.needs_grad(rhs)) E.exec_axpy(1.0, Y, false, E.v(rhs), true);
       if (E.needs_grad(wt)) {
-        E.exec_contract("ijkabc,ijkdbc->ad", -1.0, Y, false, T3, false, wvv, true);
-        E.exec_contract("ijkabc,ijkadc->bd", -1.0, Y, false, T3, false, wvv, true);
-        E.exec_contract("ijkabc,ijkabd->cd", -1.0, Y, false, T3, false, wvv, true);
-        E.exec_contract("ijkabc,ljkabc->li", 1.0, Y, false, T3, false, woo, true);
-        E.exec_contract("ijkabc,ilkabc->lj", 1.0, Y, false, T3, false, woo, true);
-        E.exec_contract("ijkabc,ijlabc->lk", 1.0, Y, false, T3, false, woo, true);
+        // t3 is invariant under the simultaneous permutations, so the slot-2
+        // and slot-3 densities of y equal the slot-1 densities of the
+        // permuted y: fold them into ys = y + y(jik,bac) + y(kji,cba)
+        const int ys = E.node(s6, false, false);
+        E.exec_combine({{1.0, Y}, {1.0, E.ev("jikbac->ijkabc", Y)}, {1.0, E.ev("kjicba->ijkabc", Y)}},
+                       E.v(ys), true);
+        const View YS = E.v(ys);
+        E.exec_contract("ijkabc,ijkdbc->ad", -1.0, YS, false, T3, false, wvv, true);
+        E.exec_contract("ijkabc,ljkabc->li", 1.0, YS, false, T3, false, woo, true);
       }
     }, true);
   }
@@ -204,6 +204,10 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     es.eps = H.eps;
     for (int d = 0; d < 3; ++d) { es.sign[d] = -1; es.base[d] = 0; }
     for (int d = 3; d < 6; ++d) { es.sign[d] = 1; es.base[d] = o; }
+    es.osum = H.osum;
+    es.vsum = H.vsum;
+    es.o = o;
+    es.v = v;
     int t3;
     if (!field) {
       t3 = E.node(s6, false, false);
