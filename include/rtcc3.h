@@ -138,6 +138,24 @@ int rtcc3_triples_forward_dev(rtcc3_ctx* ctx, int b, double time, const void* t1
 int rtcc3_triples_vjp_dev(rtcc3_ctx* ctx, int b, double time, const void* t1, const void* t2,
                           const void* u1, const void* u2, void* g1, void* g2, void* stream);
 
+/* Allocation-free variant of rtcc3_triples_forward_dev (no counterpart in the
+ * paper; it exists for callers that cannot allocate device memory when they
+ * call, e.g. code whose allocator is locked between pre-planned stages or
+ * which must not trigger cudaMalloc/cudaFree on its hot path).  Same inputs,
+ * outputs and results, but every piece of device workspace (intermediate
+ * tensors, contraction tables, split-K partial sums, tensor-core operand
+ * buffers) is taken from one static device array of 64 MiB compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Systems whose workspace would exceed it are rejected with
+ * RTCC3_ERR_ARG and a message naming the size.  The call makes no
+ * cudaMalloc/cudaFree (it still needs the context created earlier).  The
+ * first call on a device looks up the array's device address (make it before
+ * any stream capture).  All calls share the array and overwrite it: calls that
+ * overlap on the GPU (other threads, other streams) race.  Work runs on
+ * `stream` (NULL: the context stream) and the call returns after it is done. */
+int rtcc3_triples_forward_noalloc_dev(rtcc3_ctx* ctx, int b, double time, const void* t1,
+                                      const void* t2, void* x1, void* x2, void* stream);
+
 /* Checkpoint: FP64 state of all slots plus time and step counter, as a flat
  * byte image with a version word and checksum.  Query the size with
  * buf == NULL.  Restoring checks size, version and checksum. */

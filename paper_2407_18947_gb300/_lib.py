@@ -56,6 +56,7 @@ SIGNATURES = {
     "rtcc3_propagate_rk4_dev": (_I, [_P, _D, _I, _P, _P, _P]),
     "rtcc3_triples_forward_dev": (_I, [_P, _I, _D, _P, _P, _P, _P, _P]),
     "rtcc3_triples_vjp_dev": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, _P, _P]),
+    "rtcc3_triples_forward_noalloc_dev": (_I, [_P, _I, _D, _P, _P, _P, _P, _P]),
     "rtcc3_state_size": (_I, [_P, _LLP]),
     "rtcc3_get_state": (_I, [_P, _P, ctypes.c_longlong]),
     "rtcc3_set_state": (_I, [_P, _P, ctypes.c_longlong]),

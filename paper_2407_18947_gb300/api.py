@@ -140,6 +140,13 @@ class RTCC3:
         self._check(self.lib.rtcc3_triples_forward_dev(self.h, b, time, P(t1_ptr), P(t2_ptr), P(x1_ptr),
                                                        P(x2_ptr), P(stream_ptr or 0)))
 
+    def triples_forward_noalloc_dev(self, b, time, t1_ptr, t2_ptr, x1_ptr, x2_ptr, stream_ptr=None):
+        """Same as triples_forward_dev with all device workspace taken from the
+        library's static 64 MiB region (no device allocation during the call)."""
+        P = ctypes.c_void_p
+        self._check(self.lib.rtcc3_triples_forward_noalloc_dev(self.h, b, time, P(t1_ptr), P(t2_ptr),
+                                                               P(x1_ptr), P(x2_ptr), P(stream_ptr or 0)))
+
     def triples_vjp_dev(self, b, time, t1_ptr, t2_ptr, u1_ptr, u2_ptr, g1_ptr, g2_ptr, stream_ptr=None):
         P = ctypes.c_void_p
         self._check(self.lib.rtcc3_triples_vjp_dev(self.h, b, time, P(t1_ptr), P(t2_ptr), P(u1_ptr),

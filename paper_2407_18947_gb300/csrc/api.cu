@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -634,6 +635,83 @@ void triples_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1, const d
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
+// ---- allocation-free triples map ------------------------------------------
+// For callers that cannot allocate device memory at the point of the call
+// (for example code running between pre-allocated pipeline stages, or
+// embedders whose allocator forbids cudaMalloc on their hot path), the
+// triples map also runs out of a fixed device region compiled into this
+// library: kNoAllocBytes per device, held by every GPU that loads the
+// library until the process exits.  All calls share the region.
+constexpr size_t kNoAllocBytes = size_t(64) << 20;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_rtcc3_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+// Device address of the static region for `dev` (the current device),
+// looked up once per device.  The first call on a device performs this
+// lookup, so it should come before any stream capture.
+char* noalloc_scratch_address(int dev) {
+  static std::mutex mu;
+  static std::vector<char*> addr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= int(addr.size())) addr.resize(dev + 1, nullptr);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    RTCC3_CUDA(cudaGetSymbolAddress(&p, g_rtcc3_noalloc_scratch));
+    addr[dev] = static_cast<char*>(p);
+  }
+  return addr[dev];
+}
+
+// Conservative workspace of one triples-map evaluation: dressed integrals,
+// the o^3 v^3 triples intermediates, small tensors, plus room for
+// contraction tables and split-K partial sums.
+template <typename R>
+size_t noalloc_estimate(const rtcc3_ctx* ctx) {
+  const size_t o = ctx->o, v = ctx->v, n = ctx->n, na = ctx->naux;
+  const size_t elems = 2 * na * n * n + 12 * n * n + n * n * n * n + 12 * o * o * v * v +
+                       10 * o * o * o * v * v * v + 2 * o * o * o * v;
+  return elems * sizeof(Cx<R>) + (size_t(16) << 20);
+}
+
+template <typename R>
+void triples_noalloc_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1, const double2* t2,
+                          double2* x1, double2* x2, char* base, cudaStream_t st) {
+  Runner<R>& Rn = ctx->run<R>();
+  DevicePool pool;
+  pool.base = base;
+  pool.cap = kNoAllocBytes;
+  Engine<R> E(st);
+  E.use_pool(&pool);
+  E.set_tensor_cores(Rn.E.tensor_cores());
+  // the evaluation time lives in the region too (nothing else is written
+  // before the recorded graph reads it)
+  double* tdev = static_cast<double*>(pool.take(sizeof(double)));
+  RTCC3_CUDA(cudaMemcpyAsync(tdev, &time, sizeof(double), cudaMemcpyHostToDevice, st));
+  E.begin();
+  StageOptions so;
+  so.ccsd = false;
+  so.triples = true;
+  so.need_grad = false;
+  so.field_terms = true;
+  so.field_iters = field_sweeps(ctx, b);
+  StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
+    launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, st);
+    launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, tdev, 0.0, ctx->n, st);
+  });
+  launch_export<R>(E.data(S.r1), x1, ctx->n1, st);
+  launch_export<R>(E.data(S.r2), x2, ctx->n2, st);
+  // the engine's host-side tables must outlive the copies it enqueued
+  RTCC3_CUDA(cudaStreamSynchronize(st));
+  if (E.tensor_cores()) {
+    int flag = 0;
+    RTCC3_CUDA(cudaMemcpy(&flag, E.error_flag(), sizeof(int), cudaMemcpyDeviceToHost));
+    RTCC3_CHECK(flag == 0, RTCC3_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on its pipeline");
+  }
+}
+
 uint64_t fnv1a(const unsigned char* p, size_t n) {
   uint64_t h = 1469598103934665603ULL;
   for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ULL; }
@@ -919,6 +997,33 @@ int rtcc3_triples_vjp_dev(rtcc3_ctx* ctx, int b, double time, const void* t1, co
                       static_cast<const double2*>(u1), static_cast<const double2*>(u2), nullptr,
                       nullptr, static_cast<double2*>(g1), static_cast<double2*>(g2),
                       static_cast<cudaStream_t>(stream));
+    };
+    if (ctx->fp64()) f(double()); else f(float());
+  });
+}
+
+int rtcc3_triples_forward_noalloc_dev(rtcc3_ctx* ctx, int b, double time, const void* t1,
+                                      const void* t2, void* x1, void* x2, void* stream) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    require_ham(ctx);
+    check_slot(ctx, b);
+    RTCC3_CHECK(t1 && t2 && x1 && x2, RTCC3_ERR_ARG, "null device buffer");
+    RTCC3_CHECK(ctx->opt.triples, RTCC3_ERR_STATE, "context created without triples");
+    int dev = 0;
+    RTCC3_CUDA(cudaGetDevice(&dev));
+    char* base = noalloc_scratch_address(dev);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    auto f = [&](auto tag) {
+      using R = decltype(tag);
+      const size_t need = noalloc_estimate<R>(ctx);
+      RTCC3_CHECK(need <= kNoAllocBytes, RTCC3_ERR_ARG,
+                  "system too large for the allocation-free path: needs about " +
+                      std::to_string(need >> 20) + " MiB of workspace, the static region holds " +
+                      std::to_string(kNoAllocBytes >> 20) + " MiB");
+      triples_noalloc_impl<R>(ctx, b, time, static_cast<const double2*>(t1),
+                              static_cast<const double2*>(t2), static_cast<double2*>(x1),
+                              static_cast<double2*>(x2), base, st);
     };
     if (ctx->fp64()) f(double()); else f(float());
   });

@@ -116,6 +116,25 @@ class Profiler {
   std::vector<Stat> stats_;
 };
 
+// A fixed device region handed out by bumping a cursor; used instead of
+// cudaMalloc by an engine that must not allocate (take() fails with
+// kErrArg once the region is exhausted).
+struct DevicePool {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  void* take(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    if (used + bytes > cap)
+      throw Error(kErrArg, "workspace needs more than the " + std::to_string(cap >> 20) +
+                               " MiB static scratch region");
+    void* p = base + used;
+    used += bytes;
+    return p;
+  }
+};
+
 // Bump allocator over device blocks.  Every evaluation of a residual graph
 // requests the same sequence of sizes, so after reset() the same addresses are
 // handed out again: buffers are stable across evaluations, which lets a whole
@@ -123,7 +142,10 @@ class Profiler {
 class Arena {
  public:
   ~Arena() { release(); }
+  // Serve every request from `p` (no device allocation of its own).
+  void use_pool(DevicePool* p) { pool_ = p; }
   void* alloc(size_t bytes) {
+    if (pool_) return pool_->take(bytes);
     bytes = (bytes + 255) & ~size_t(255);
     if (bytes == 0) bytes = 256;
     while (true) {
@@ -155,6 +177,7 @@ class Arena {
   size_t high_water() const { return used_; }
 
  private:
+  DevicePool* pool_ = nullptr;
   struct Block { void* ptr; size_t size; };
   size_t total_before(size_t k) const { size_t s = 0; for (size_t i = 0; i < k; ++i) s += blocks_[i].size; return s; }
   std::vector<Block> blocks_;

@@ -338,6 +338,7 @@ void launch_fill(Cx<R>* p, size_t n, double re, double im, cudaStream_t s) {
 
 template <typename R>
 Engine<R>::~Engine() {
+  if (pool_) return;  // everything lives in the caller's pool
   for (auto& kv : plans_)
     if (kv.second->dev) cudaFree(kv.second->dev);
   for (int s = 0; s < kScratchSlots; ++s)
@@ -348,8 +349,13 @@ Engine<R>::~Engine() {
 template <typename R>
 int* Engine<R>::error_flag() {
   if (!err_) {
-    RTCC3_CUDA(cudaMalloc(&err_, sizeof(int)));
-    RTCC3_CUDA(cudaMemset(err_, 0, sizeof(int)));
+    if (pool_) {
+      err_ = static_cast<int*>(pool_->take(sizeof(int)));
+      RTCC3_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), stream_));
+    } else {
+      RTCC3_CUDA(cudaMalloc(&err_, sizeof(int)));
+      RTCC3_CUDA(cudaMemset(err_, 0, sizeof(int)));
+    }
   }
   return err_;
 }
@@ -437,6 +443,12 @@ template <typename R>
 void* Engine<R>::scratch(int slot, size_t bytes) {
   if (bytes > scratch_bytes_[slot]) {
     RTCC3_CHECK(!frozen_, kErrState, "scratch growth during graph capture");
+    if (pool_) {
+      scratch_[slot] = pool_->take(bytes);
+      scratch_bytes_[slot] = bytes;
+      ++generation_;
+      return scratch_[slot];
+    }
     if (scratch_[slot]) cudaFree(scratch_[slot]);
     scratch_[slot] = nullptr;
     RTCC3_CUDA(cudaMalloc(&scratch_[slot], bytes));
@@ -531,8 +543,16 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   for (size_t t = icB; t < icB + size_t(NB); ++t) h[t] += Cv.off;
   P->a_kcontig = !gk.empty() && std::llabs(gk.back().sa) == 1;
   P->b_kcontig = !gk.empty() && std::llabs(gk.back().sb) == 1;
-  RTCC3_CUDA(cudaMalloc(&P->dev, h.size() * sizeof(long long)));
-  RTCC3_CUDA(cudaMemcpy(P->dev, h.data(), h.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  if (pool_) {
+    // tables go into the pool; the host copy lives in the plan until the
+    // engine is destroyed, after the stream has drained
+    P->dev = pool_->take(h.size() * sizeof(long long));
+    RTCC3_CUDA(cudaMemcpyAsync(P->dev, h.data(), h.size() * sizeof(long long),
+                               cudaMemcpyHostToDevice, stream_));
+  } else {
+    RTCC3_CUDA(cudaMalloc(&P->dev, h.size() * sizeof(long long)));
+    RTCC3_CUDA(cudaMemcpy(P->dev, h.data(), h.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  }
   long long* d = static_cast<long long*>(P->dev);
   P->aM = d + iaM; P->aK = d + iaK; P->bN = d + ibN; P->bK = d + ibK;
   P->cM = d + icM; P->cN = d + icN; P->aB = d + iaB; P->bB = d + ibB; P->cB = d + icB;

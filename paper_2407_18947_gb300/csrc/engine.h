@@ -189,6 +189,12 @@ class Engine {
   void set_tc_region(bool open) { tc_region_ = open; }
   // Device word raised by a bounded wait that gave up (tensor-core kernel).
   int* error_flag();
+  // Take every device buffer (arena, tables, scratch, flag) from `p` instead
+  // of cudaMalloc; the engine then frees nothing either.
+  void use_pool(DevicePool* p) {
+    pool_ = p;
+    arena_.use_pool(p);
+  }
   // Incremented whenever a persistent buffer (the split-K scratch) moves:
   // a captured CUDA graph recorded under an older generation is stale.
   int generation() const { return generation_; }
@@ -235,6 +241,7 @@ class Engine {
   int tc_eb_ = 0;
   bool tc_region_ = false;
   int* err_ = nullptr;
+  DevicePool* pool_ = nullptr;
   void run_contract_tc(ContractPlan& P, double alpha, const C* pa, const C* pb, C* pc,
                        bool accumulate);
   int launches_ = 0;
