@@ -69,6 +69,9 @@ typedef struct rtcc3_options {
   int use_graphs;    /* 1: capture one RK4 step as a CUDA graph and replay   */
   double field_tol;  /* target relative error of the field-coupled triples
                         fixed point (0: 1e-14 in FP64, 1e-8 otherwise)       */
+  int field_solver;  /* field-coupled triples: 0 = field-dressed eigenbasis
+                        (exact, default), 1 = fixed-point sweeps on the
+                        stored triples (the paper's scheme)                   */
 } rtcc3_options;
 
 /* Fill *opt with defaults (FP64, triples on, device 0, graphs on). */

@@ -199,6 +199,7 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
   so.need_grad = need_grad;
   so.field_terms = field_terms;
   so.field_iters = sweeps;
+  so.rotation = ctx->opt.field_solver == 0;
   (void)ccsd_terms;
   StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
     PScope ps(ctx->prof, ctx->stream, "stage_inputs", 0.0,
@@ -349,12 +350,19 @@ void final_observables(rtcc3_ctx* ctx, const std::vector<int>& sweeps) {
 template <typename R>
 void check_device_timeout(rtcc3_ctx* ctx) {
   Engine<R>& E = ctx->run<R>().E;
-  if (E.tensor_cores() == 0) return;
   int flag = 0;
   RTCC3_CUDA(cudaMemcpy(&flag, E.error_flag(), sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     RTCC3_CUDA(cudaMemset(E.error_flag(), 0, sizeof(int)));
-    throw Error(RTCC3_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on its pipeline");
+    if (flag & kEigStatusBase) {
+      const int reason = (flag >> 20) & 0xf, n = (flag >> 10) & 0x3ff, row = flag & 0x3ff;
+      throw Error(reason == kEigNonFinite ? RTCC3_ERR_NONFINITE : RTCC3_ERR_TIMEOUT,
+                  std::string("field eigensolver (order ") + std::to_string(n) + "): " +
+                      (reason == kEigNonFinite ? "non-finite dressed field matrix"
+                                               : "QR sweeps did not converge at row " +
+                                                     std::to_string(row)));
+    }
+    throw Error(RTCC3_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
   }
 }
 
@@ -615,6 +623,7 @@ void triples_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1, const d
   so.need_grad = vjp;
   so.field_terms = true;
   so.field_iters = field_sweeps(ctx, b);
+  so.rotation = ctx->opt.field_solver == 0;
   auto fill = [&](const StageNodes& s) {
     launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, ctx->stream);
     launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, ctx->teval, 0.0, ctx->n, ctx->stream);
@@ -697,6 +706,7 @@ void triples_noalloc_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1,
   so.need_grad = false;
   so.field_terms = true;
   so.field_iters = field_sweeps(ctx, b);
+  so.rotation = ctx->opt.field_solver == 0;
   StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
     launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, st);
     launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, tdev, 0.0, ctx->n, st);
@@ -737,6 +747,7 @@ void rtcc3_default_options(rtcc3_options* opt) {
   opt->device = 0;
   opt->use_graphs = 1;
   opt->field_tol = 0.0;
+  opt->field_solver = 0;
 }
 
 int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3_ctx** out) {

@@ -26,6 +26,28 @@ struct EpsArgs {
 // Triples denominators from the precomputed FP64 occupied / virtual sums, for
 // X and Y both in the dense (o,o,o,v,v,v) layout: one FP64 subtraction per
 // element instead of six FP64 additions (GB300's FP64 rate is low).
+// Complex denominators (field-dressed eigenvalue sums), dense layout:
+// y (+)= x / (vsum[abc] - osum[ijk]); the sums are FP64, the division in R.
+template <typename R, typename I>
+__global__ void k_div_lambda_dense6(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y,
+                                    long long offx, long long offy,
+                                    const double2* __restrict__ osum,
+                                    const double2* __restrict__ vsum, I v3, I n, int overwrite) {
+  for (I t = I(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += I(gridDim.x) * blockDim.x) {
+    const I ijk = t / v3;
+    const I abc = t - ijk * v3;
+    const double2 vs = vsum[abc], os = osum[ijk];
+    const R dr = R(vs.x - os.x), di = R(vs.y - os.y);
+    const R m = R(1) / (dr * dr + di * di);
+    const R ir = dr * m, ii = -di * m;  // 1 / (dr + i di)
+    const Cx<R> x = X[offx + t];
+    Cx<R> y = overwrite ? cmake<R>(R(0), R(0)) : Y[offy + t];
+    y.x += x.x * ir - x.y * ii;
+    y.y += x.x * ii + x.y * ir;
+    Y[offy + t] = y;
+  }
+}
+
 template <typename R, typename I>
 __global__ void k_div_eps_dense6(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx,
                                  long long offy, const double* __restrict__ osum,
@@ -896,6 +918,34 @@ template <typename R>
 void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
                         bool overwrite) {
   RTCC3_CHECK(X.nd == Y.nd, kErrArg, "div_eps rank mismatch");
+  if (es.osum_c && es.vsum_c) {
+    auto dense6 = [&](const View& w) {
+      if (w.nd != 6) return false;
+      const int dims[6] = {es.o, es.o, es.o, es.v, es.v, es.v};
+      long long st = 1;
+      for (int k = 5; k >= 0; --k) {
+        if (w.shape[k] != dims[k] || w.stride[k] != st) return false;
+        st *= dims[k];
+      }
+      return true;
+    };
+    RTCC3_CHECK(dense6(X) && dense6(Y), kErrArg, "complex denominators need dense triples views");
+    const size_t n = Y.numel();
+    const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
+    C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+    const long long v3 = (long long)es.v * es.v * es.v;
+    const int pk = pbegin();
+    if (n < (size_t(1) << 31))
+      k_div_lambda_dense6<R, unsigned><<<grid_for(n), 256, 0, stream_>>>(
+          px, py, X.off, Y.off, es.osum_c, es.vsum_c, unsigned(v3), unsigned(n), overwrite ? 1 : 0);
+    else
+      k_div_lambda_dense6<R, size_t><<<grid_for(n), 256, 0, stream_>>>(
+          px, py, X.off, Y.off, es.osum_c, es.vsum_c, size_t(v3), n, overwrite ? 1 : 0);
+    pend(pk, "div_eps", 8.0 * n, (overwrite ? 2.0 : 3.0) * n * sizeof(C));
+    ++launches_;
+    RTCC3_CUDA(cudaGetLastError());
+    return;
+  }
   if (es.osum && es.vsum && Y.nd == 6) {
     auto dense6 = [&](const View& w) {
       const int dims[6] = {es.o, es.o, es.o, es.v, es.v, es.v};

@@ -108,6 +108,9 @@ class Engine {
     const double* osum = nullptr;
     const double* vsum = nullptr;
     int o = 0, v = 0;
+    // Complex sums of eigenvalues in the field-dressed basis (take precedence).
+    const double2* osum_c = nullptr;
+    const double2* vsum_c = nullptr;
   };
   void div_eps(const View& X, const EpsSpec& es, const View& Y, bool overwrite = false);
   // Non-differentiable initialisation.

@@ -41,6 +41,7 @@ struct StageOptions {
   bool triples = true;
   bool need_grad = true;
   bool field_terms = true;  // include the V-coupling of the triples equation
+  bool rotation = true;     // field-dressed eigenbasis (else fixed-point sweeps)
   int field_iters = 1;      // fixed-point sweeps of the triples equation
 };
 

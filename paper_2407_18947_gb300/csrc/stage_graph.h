@@ -10,8 +10,161 @@
 #pragma once
 
 #include "model.h"
+#include "rotation.h"
 
 namespace rtcc3 {
+
+// Triples with the field coupling in the field-dressed eigenbasis (see
+// rotation.h).  Forward: decompose O and V of this stage, rotate the inputs
+// of W and of the source 1/2[[V~,T2],T2], divide by the complex denominators,
+// form X1 and X2 in the rotated basis and rotate them back.  The rotations
+// are constants of the tape (A^-1 does not depend on the choice of
+// eigenbasis); the dependence of A on v~ is added by a custom adjoint: with
+// y' = grad(t3') / D', grad(v~_vv) -= S_v^-T D'_vv S_v^T and
+// grad(v~_oo) += S_o D'_oo S_o^-1, the slot densities D' of y' and t3'
+// (the triples density terms of Eqs. A31-A32 in the rotated basis).
+// Returns the node of t3' and accumulates into R1 and SD.
+template <typename R, typename BlkFn>
+int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, int g, int ft,
+                    const View& R1, const View& SD, BlkFn&& blk) {
+  const int o = H.o, v = H.v;
+  const cudaStream_t st = E.stream();
+  // ---- eigendecomposition of O and V (FP64) ------------------------------------
+  Arena& A = E.arena();
+  double2* Mo = static_cast<double2*>(A.alloc(sizeof(double2) * o * o));
+  double2* Mv = static_cast<double2*>(A.alloc(sizeof(double2) * v * v));
+  double2* So64 = static_cast<double2*>(A.alloc(sizeof(double2) * o * o));
+  double2* Sio64 = static_cast<double2*>(A.alloc(sizeof(double2) * o * o));
+  double2* Sv64 = static_cast<double2*>(A.alloc(sizeof(double2) * v * v));
+  double2* Siv64 = static_cast<double2*>(A.alloc(sizeof(double2) * v * v));
+  double2* lo = static_cast<double2*>(A.alloc(sizeof(double2) * o));
+  double2* lv = static_cast<double2*>(A.alloc(sizeof(double2) * v));
+  double2* wso = static_cast<double2*>(A.alloc(sizeof(double2) * 3 * o * o));
+  double2* wsv = static_cast<double2*>(A.alloc(sizeof(double2) * 3 * v * v));
+  double2* osum = static_cast<double2*>(A.alloc(sizeof(double2) * o * o * o));
+  double2* vsum = static_cast<double2*>(A.alloc(sizeof(double2) * v * v * v));
+  launch_field_matrices<R>(E.data(wt), H.eps, o, v, Mo, Mv, st);
+  launch_eig(Mo, o, 1, So64, Sio64, lo, wso, E.error_flag(), st);
+  launch_eig(Mv, v, 1, Sv64, Siv64, lv, wsv, E.error_flag(), st);
+  launch_lambda_sums(lo, lv, o, v, osum, vsum, st);
+  const int So = E.node({o, o}, false, false), Sio = E.node({o, o}, false, false);
+  const int Sv = E.node({v, v}, false, false), Siv = E.node({v, v}, false, false);
+  launch_to_precision<R>(So64, E.data(So), size_t(o) * o, st);
+  launch_to_precision<R>(Sio64, E.data(Sio), size_t(o) * o, st);
+  launch_to_precision<R>(Sv64, E.data(Sv), size_t(v) * v, st);
+  launch_to_precision<R>(Siv64, E.data(Siv), size_t(v) * v, st);
+  const View SO = E.v(So), SIO = E.v(Sio), SV = E.v(Sv), SIV = E.v(Siv);
+  auto G = [&](const char* b) { return blk(g, b); };
+  // rotate one index of a 4-index tensor: spec like "Ii,ijae->Ijae"
+  auto rot = [&](const char* spec, const View& S, const View& X, const std::vector<int>& shape) {
+    const int out = E.node(shape);
+    E.contract(spec, 1.0, S, X, E.v(out), true);
+    return E.v(out);
+  };
+  const std::vector<int> s6 = {o, o, o, v, v, v};
+  // ---- rotated inputs of W: indices that become indices of t3 take S^-1 --------
+  View T1p = rot("Ii,ijae->Ijae", SIO, T, {o, o, v, v});
+  T1p = rot("Jj,Ijae->IJae", SIO, T1p, {o, o, v, v});
+  T1p = rot("Aa,IJae->IJAe", SIV, T1p, {o, o, v, v});
+  View G1p = rot("Cc,ckbe->Ckbe", SIV, G("vovv"), {v, o, v, v});
+  G1p = rot("Kk,Ckbe->CKbe", SIO, G1p, {v, o, v, v});
+  G1p = rot("Bb,CKbe->CKBe", SIV, G1p, {v, o, v, v});
+  View T2p = rot("Ii,imab->Imab", SIO, T, {o, o, v, v});
+  T2p = rot("Aa,Imab->ImAb", SIV, T2p, {o, o, v, v});
+  T2p = rot("Bb,ImAb->ImAB", SIV, T2p, {o, o, v, v});
+  View G2p = rot("Jj,mjck->mJck", SIO, G("oovo"), {o, o, v, o});
+  G2p = rot("Cc,mJck->mJCk", SIV, G2p, {o, o, v, o});
+  G2p = rot("Kk,mJCk->mJCK", SIO, G2p, {o, o, v, o});
+  const int Z = E.node(s6);
+  E.contract("ijae,ckbe->ijkabc", 1.0, T1p, G1p, E.v(Z), true);
+  E.contract("imab,mjck->ijkabc", -1.0, T2p, G2p, E.v(Z), true);
+  const int rhs = E.node(s6, false, false);
+  E.sym6(-1.0, E.v(Z), E.v(rhs), true);
+  // source -P sum_ld v~_ld t_ij^ad t_kl^cb, rotated the same way
+  const int Yl = E.node({o, o, o, v});
+  E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), true);
+  View Ylp = rot("Ii,lija->lIja", SIO, E.v(Yl), {o, o, o, v});
+  Ylp = rot("Jj,lIja->lIJa", SIO, Ylp, {o, o, o, v});
+  Ylp = rot("Aa,lIJa->lIJA", SIV, Ylp, {o, o, o, v});
+  View T3p_ = rot("Kk,klcb->Klcb", SIO, T, {o, o, v, v});
+  T3p_ = rot("Cc,Klcb->KlCb", SIV, T3p_, {o, o, v, v});
+  T3p_ = rot("Bb,KlCb->KlCB", SIV, T3p_, {o, o, v, v});
+  const int Z2 = E.node(s6);
+  E.contract("lija,klcb->ijkabc", 1.0, Ylp, T3p_, E.v(Z2), true);
+  E.sym6(1.0, E.v(Z2), E.v(rhs), false);
+  // ---- complex denominators ---------------------------------------------------
+  typename Engine<R>::EpsSpec es;
+  es.o = o;
+  es.v = v;
+  es.osum_c = osum;
+  es.vsum_c = vsum;
+  const int t3p = E.node(s6, false, false);
+  E.div_eps(E.v(rhs), es, E.v(t3p), true);
+  const int wtn = wt;
+  if (E.needs_grad(t3p) && E.needs_grad(wtn)) {
+    const View wvv = blk(wt, "vv"), woo = blk(wt, "oo");
+    E.custom([&E, t3p, wtn, es, s6, SO, SIO, SV, SIV, wvv, woo, o, v]() {
+      if (!E.needs_grad(t3p) || !E.needs_grad(wtn)) return;
+      const View T3 = E.v(t3p);
+      const int yp = E.node(s6, false, false);
+      const View Y = E.v(yp);
+      E.exec_div(T3, true, es, Y, false, true);  // y' = grad(t3') / D'
+      const int ys = E.node(s6, false, false);
+      E.exec_combine({{1.0, Y}, {1.0, E.ev("jikbac->ijkabc", Y)}, {1.0, E.ev("kjicba->ijkabc", Y)}},
+                     E.v(ys), true);
+      const int Dv = E.node({v, v}), Do = E.node({o, o});
+      E.exec_contract("ijkabc,ijkdbc->ad", 1.0, E.v(ys), false, T3, false, E.v(Dv), false);
+      E.exec_contract("ijkabc,ljkabc->li", 1.0, E.v(ys), false, T3, false, E.v(Do), false);
+      const int tv = E.node({v, v}), to = E.node({o, o});
+      E.exec_contract("Aa,AD->aD", 1.0, SIV, false, E.v(Dv), false, E.v(tv), false);
+      E.exec_contract("aD,dD->ad", -1.0, E.v(tv), false, SV, false, wvv, true);
+      E.exec_contract("lL,LI->lI", 1.0, SO, false, E.v(Do), false, E.v(to), false);
+      E.exec_contract("lI,Ii->li", 1.0, E.v(to), false, SIO, false, woo, true);
+    }, true);
+  }
+  // ---- X1, X2 in the rotated basis ------------------------------------------------
+  const View T3 = E.v(t3p);
+  const int dd = E.node(s6, false, false);
+  E.combine({{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}}, E.v(dd), true);
+  const int Ljk = E.node({o, o, v, v}, false, false);
+  E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
+            E.v(Ljk), true);
+  // contracted indices take S (contravariant), free rotated indices S^-1
+  View Lp = rot("jJ,jkbc->Jkbc", SO, E.v(Ljk), {o, o, v, v});
+  Lp = rot("kK,Jkbc->JKbc", SO, Lp, {o, o, v, v});
+  Lp = rot("bB,JKbc->JKBc", SV, Lp, {o, o, v, v});
+  Lp = rot("cC,JKBc->JKBC", SV, Lp, {o, o, v, v});
+  const int X1p = E.node({o, v});
+  E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), Lp, E.v(X1p), true);
+  View Fp = rot("kK,kc->Kc", SO, blk(ft, "ov"), {o, v});
+  Fp = rot("cC,Kc->KC", SV, Fp, {o, v});
+  const int S3p = E.node({o, o, v, v});
+  E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), Fp, E.v(S3p), true);
+  const int Ub = E.node(s6, false, false);
+  E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
+            E.v(Ub), true);
+  View Gb = rot("Aa,acke->Acke", SIV, G("vvov"), {v, v, o, v});
+  Gb = rot("cC,Acke->ACke", SV, Gb, {v, v, o, v});
+  Gb = rot("kK,ACke->ACKe", SO, Gb, {v, v, o, v});
+  Gb = rot("eE,ACKe->ACKE", SV, Gb, {v, v, o, v});
+  E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), Gb, E.v(S3p), true);
+  const int Uc = E.node(s6, false, false);
+  E.combine({{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}},
+            E.v(Uc), true);
+  View Gc = rot("kK,kimc->Kimc", SO, G("ooov"), {o, o, o, v});
+  Gc = rot("Ii,Kimc->KImc", SIO, Gc, {o, o, o, v});
+  Gc = rot("mM,KImc->KIMc", SO, Gc, {o, o, o, v});
+  Gc = rot("cC,KIMc->KIMC", SV, Gc, {o, o, o, v});
+  E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), Gc, E.v(S3p), true);
+  // ---- rotate the results back: X = (S_o x S_v) X' -----------------------------
+  const View X1t = rot("iI,IA->iA", SO, E.v(X1p), {o, v});
+  E.contract("aA,iA->ia", 1.0, SV, X1t, R1, true);
+  View S3 = rot("iI,IJAB->iJAB", SO, E.v(S3p), {o, o, v, v});
+  S3 = rot("jJ,iJAB->ijAB", SO, S3, {o, o, v, v});
+  S3 = rot("aA,ijAB->ijaB", SV, S3, {o, o, v, v});
+  E.contract("bB,ijaB->ijab", 1.0, SV, S3, SD, true);
+  return t3p;
+}
 
 // A t3 = rhs with A = eps3 + [V~, .] (Eq. 4 / Eq. A12 with dt3/dt = 0): +v~_ad on
 // each virtual slot, -v~_li on each occupied slot.  Forward: `sweeps`
@@ -182,7 +335,11 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   }  // opt.ccsd
 
   // ---- triples ---------------------------------------------------------------
-  if (opt.triples) {
+  if (opt.triples && opt.field_terms && opt.rotation) {
+    E.set_tc_region(true);  // the dense triples contractions may use tensor cores
+    S.t3 = rotated_triples(E, H, T, wt, g, ft, R1, SD, blk);
+    E.set_tc_region(false);
+  } else if (opt.triples) {
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores
     const std::vector<int> s6 = {o, o, o, v, v, v};
     // Z = sum_e t_ij^ae <cb|ke>~ - sum_m t_im^ab <mc|jk>~ ; W = P_ijk^abc Z (Eqs. A25, A30)
