@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "contract_small.h"
 #include "tc_gemm.h"
 #include <cstring>
 #include <sstream>
@@ -14,6 +15,7 @@ namespace {
 
 constexpr int kBM = 64, kBN = 64, kBK = 16, kThreads = 256;
 constexpr int kSBM = 16, kSBK = 64;  // small-tile variant
+constexpr int kTBK = 8;               // thin (16 x 256) tiles
 
 struct EpsArgs {
   int sign[kMaxDim];
@@ -64,6 +66,51 @@ __global__ void k_div_eps_dense6(const Cx<R>* __restrict__ X, Cx<R>* __restrict_
   }
 }
 
+// Y (+)= alpha P_ijk^abc(X) / D for X, Y dense (o,o,o,v,v,v): the six
+// simultaneous permutations of (ijk, abc) summed and divided by the triples
+// denominator D[ijk abc] = vsum[abc] - osum[ijk] (FP64 sums; complex sums
+// when CPLX).  D is invariant under those permutations, so the same kernel
+// is its own adjoint.
+template <typename R, typename I, bool CPLX>
+__global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx,
+                           long long offy, const double* __restrict__ osum,
+                           const double* __restrict__ vsum, const double2* __restrict__ osum_c,
+                           const double2* __restrict__ vsum_c, int o, int v, I n, R alpha,
+                           int overwrite) {
+  const I v2 = I(v) * v, v3 = v2 * v, o2 = I(o) * o;
+  const Cx<R>* Xb = X + offx;
+  for (I t = I(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += I(gridDim.x) * blockDim.x) {
+    const I ijk = t / v3;
+    const I abc = t - ijk * v3;
+    const I i = ijk / o2, jk = ijk - i * o2, j = jk / o, k = jk - j * o;
+    const I a = abc / v2, bc = abc - a * v2, b = bc / v, c = bc - b * v;
+    auto O = [&](I x, I y, I z) { return ((x * o + y) * o + z) * v3; };
+    auto V = [&](I x, I y, I z) { return (x * v + y) * v + z; };
+    const Cx<R> x0 = Xb[O(i, j, k) + V(a, b, c)];
+    const Cx<R> x1 = Xb[O(j, i, k) + V(b, a, c)];
+    const Cx<R> x2 = Xb[O(i, k, j) + V(a, c, b)];
+    const Cx<R> x3 = Xb[O(k, j, i) + V(c, b, a)];
+    const Cx<R> x4 = Xb[O(k, i, j) + V(c, a, b)];
+    const Cx<R> x5 = Xb[O(j, k, i) + V(b, c, a)];
+    const R sr = alpha * (((x0.x + x1.x) + (x2.x + x3.x)) + (x4.x + x5.x));
+    const R si = alpha * (((x0.y + x1.y) + (x2.y + x3.y)) + (x4.y + x5.y));
+    Cx<R> y = overwrite ? cmake<R>(R(0), R(0)) : Y[offy + t];
+    if (CPLX) {
+      const double2 vs = vsum_c[abc], os = osum_c[ijk];
+      const R dr = R(vs.x - os.x), di = R(vs.y - os.y);
+      const R m = R(1) / (dr * dr + di * di);
+      const R ir = dr * m, ii = -di * m;
+      y.x += sr * ir - si * ii;
+      y.y += sr * ii + si * ir;
+    } else {
+      const R inv = R(1) / R(vsum[abc] - osum[ijk]);
+      y.x += sr * inv;
+      y.y += si * inv;
+    }
+    Y[offy + t] = y;
+  }
+}
+
 struct StridedDesc {
   int nd;
   int shape[kMaxDim];
@@ -83,11 +130,12 @@ __device__ __forceinline__ void cfma(R& ar, R& ai, Cx<R> a, Cx<R> b) {
 
 // Generic strided complex contraction as a gather-GEMM: C[b,m,n] (+)= alpha *
 // sum_k A[b,m,k] B[b,n,k] with every (b,m,n,k) -> address mapping given by
-// offset tables.  64x64 output tile per CTA, 16-deep K slices in shared
-// memory, 4x4 complex micro-tile per thread.  With nsplit > 1 each CTA sums a
-// K chunk into a partial buffer and k_split_reduce adds the chunks in fixed
-// order (deterministic results).
-template <typename R, bool A_KC, bool B_KC, int BM, int BN, int BK>
+// offset tables.  BM x BN output tile per CTA, BK-deep K slices in shared
+// memory (odd row pitch: the transposing stores of K-contiguous loads do not
+// share a bank), TM x TN complex micro-tile per thread on a (BM/TM) x (BN/TN)
+// thread grid.  With nsplit > 1 each CTA sums a K chunk into a partial buffer
+// and k_split_reduce adds the chunks in fixed order (deterministic results).
+template <typename R, bool A_KC, bool B_KC, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(kThreads)
 k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __restrict__ Cp,
            const long long* __restrict__ aM, const long long* __restrict__ aK,
@@ -96,9 +144,10 @@ k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __re
            const long long* __restrict__ aB, const long long* __restrict__ bB,
            const long long* __restrict__ cB, int M, int N, int K, int nsplit, int kchunk,
            R alpha, int accumulate, Cx<R>* __restrict__ part) {
-  constexpr int TM = BM / 16, TN = BN / 16;  // 16 x 16 threads, TM x TN outputs each
-  __shared__ Cx<R> As[BK][BM];
-  __shared__ Cx<R> Bs[BK][BN];
+  constexpr int RY = BM / TM, RX = BN / TN;  // thread grid, TM x TN outputs each
+  static_assert(RY * RX == kThreads, "thread grid");
+  __shared__ Cx<R> As[BK][BM + 1];
+  __shared__ Cx<R> Bs[BK][BN + 1];
   const int bz = blockIdx.z;
   const int b = bz / nsplit, split = bz % nsplit;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -106,7 +155,7 @@ k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __re
   const int kend = min(K, kbeg + kchunk);
   const Cx<R>* Ab = A + aB[b];
   const Cx<R>* Bb = B + bB[b];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % RX, ty = tid / RX;
   R accr[TM][TN], acci[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -117,6 +166,7 @@ k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __re
 #pragma unroll
     for (int e0 = 0; e0 < BM * BK; e0 += kThreads) {
       const int e = e0 + tid;
+      if ((BM * BK) % kThreads != 0 && e >= BM * BK) break;
       int mm, kk;
       if (A_KC) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
       const int m = m0 + mm, k = k0 + kk;
@@ -125,6 +175,7 @@ k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __re
 #pragma unroll
     for (int e0 = 0; e0 < BN * BK; e0 += kThreads) {
       const int e = e0 + tid;
+      if ((BN * BK) % kThreads != 0 && e >= BN * BK) break;
       int nn, kk;
       if (B_KC) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
       const int n = n0 + nn, k = k0 + kk;
@@ -135,9 +186,9 @@ k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __re
     for (int kk = 0; kk < BK; ++kk) {
       Cx<R> a[TM], bv[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + RY * i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + RX * j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -147,11 +198,11 @@ k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __re
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
-    const int m = m0 + ty + 16 * i;
+    const int m = m0 + ty + RY * i;
     if (m >= M) continue;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int n = n0 + tx + 16 * j;
+      const int n = n0 + tx + RX * j;
       if (n >= N) continue;
       if (nsplit == 1) {
         const long long idx = cB[b] + cM[m] + cN[n];
@@ -352,6 +403,51 @@ std::string view_key(const View& v) {
 
 }  // namespace
 
+static bool same_view(const View& a, const View& b) {
+  if (a.node != b.node || a.off != b.off || a.nd != b.nd) return false;
+  for (int d = 0; d < a.nd; ++d)
+    if (a.shape[d] != b.shape[d] || a.stride[d] != b.stride[d]) return false;
+  return true;
+}
+
+// If X covers its whole node as a permutation of the node's dense layout,
+// reorder the dimensions of X and of the same-shaped view Y so that X
+// becomes that dense layout (returned as `dense`, Y's matching view as
+// `src`); extent-1 dimensions are dropped.  Returns false otherwise.
+static bool invert_view(const View& X, const View& Y, View& dense, View& src) {
+  if (X.off != 0 || X.nd != Y.nd) return false;
+  int idx[kMaxDim];
+  int nd = 0;
+  for (int d = 0; d < X.nd; ++d) {
+    if (X.shape[d] != Y.shape[d]) return false;
+    if (X.shape[d] == 0) return false;
+    if (X.shape[d] > 1) idx[nd++] = d;
+  }
+  std::stable_sort(idx, idx + nd, [&](int p, int q) { return X.stride[p] > X.stride[q]; });
+  long long expect = 1;
+  for (int k = nd - 1; k >= 0; --k) {
+    if (X.stride[idx[k]] != expect) return false;
+    expect *= X.shape[idx[k]];
+  }
+  dense = View();
+  dense.node = X.node;
+  dense.off = 0;
+  src = View();
+  src.node = Y.node;
+  src.off = Y.off;
+  dense.nd = src.nd = nd > 0 ? nd : 1;
+  if (nd == 0) {
+    dense.shape[0] = src.shape[0] = 1;
+    dense.stride[0] = src.stride[0] = 1;
+  }
+  for (int k = 0; k < nd; ++k) {
+    dense.shape[k] = src.shape[k] = X.shape[idx[k]];
+    dense.stride[k] = X.stride[idx[k]];
+    src.stride[k] = Y.stride[idx[k]];
+  }
+  return true;
+}
+
 template <typename R>
 void launch_fill(Cx<R>* p, size_t n, double re, double im, cudaStream_t s) {
   if (n == 0) return;
@@ -525,10 +621,20 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
     RTCC3_CHECK(l.ia && l.ib, kErrArg, "index summed in one operand only: " + spec);
     gk.push_back(l);
   }
-  // K order: smallest |stride in A| fastest (last)
-  std::stable_sort(gk.begin(), gk.end(), [](const Letter& x, const Letter& y) {
-    return std::llabs(x.sa) > std::llabs(y.sa);
-  });
+  // Letter order inside each group: the larger of the two tensors that carry
+  // the group decides (its smallest stride fastest), so the loads or stores
+  // of the big tensor run along its contiguous index.
+  const double nA = double(A.numel()), nB = double(B.numel()), nC = double(Cv.numel());
+  auto by = [](int which) {
+    return [which](const Letter& x, const Letter& y) {
+      const long long sx = which == 0 ? x.sa : (which == 1 ? x.sb : x.sc);
+      const long long sy = which == 0 ? y.sa : (which == 1 ? y.sb : y.sc);
+      return std::llabs(sx) > std::llabs(sy);
+    };
+  };
+  std::stable_sort(gk.begin(), gk.end(), by(nA >= nB ? 0 : 1));
+  std::stable_sort(gm.begin(), gm.end(), by(nA > nC ? 0 : 2));
+  std::stable_sort(gn.begin(), gn.end(), by(nB > nC ? 1 : 2));
   auto P = std::make_unique<ContractPlan>();
   auto count = [](const std::vector<Letter>& g) {
     long long n = 1;
@@ -578,11 +684,48 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   long long* d = static_cast<long long*>(P->dev);
   P->aM = d + iaM; P->aK = d + iaK; P->bN = d + ibN; P->bK = d + ibK;
   P->cM = d + icM; P->cN = d + icN; P->aB = d + iaB; P->bB = d + ibB; P->cB = d + icB;
-  // skinny outputs with long sums use 16 x 16 tiles and 64-deep K slices
+  P->a_off0 = h[iaB];
+  P->b_off0 = h[ibB];
+  P->c_off0 = h[icB];
+  // small outputs (held whole by every CTA, K split over the GPU) and single
+  // long output columns get their own kernels
+  {
+    const long long mx = std::max(M, N), mn = std::min(M, N);
+    if (NB == 1 && mn == 1 && mx > 512 && K <= 65536) {
+      P->kind = 2;
+      P->small_swap = M == 1;
+      P->gemv_boff = P->small_swap ? P->a_off0 + h[iaM] : P->b_off0 + h[ibN];
+      P->gemv_coff = P->c_off0 + (P->small_swap ? h[icM] : h[icN]);
+    } else if (NB == 1 && K >= 256 && small_output_config(mx, mn) != kSmallNone) {
+      P->kind = 1;
+      P->small_cfg = small_output_config(mx, mn);
+      P->small_swap = N > M;
+      const int bk = small_output_bk(P->small_cfg, int(sizeof(C)));
+      const long long want = 4 * 152;
+      const long long maxs = (K + 4 * bk - 1) / (4 * bk);  // at least four slices per CTA
+      int ns = int(std::max<long long>(1, std::min(want, maxs)));
+      int kc = int((K + ns - 1) / ns);
+      kc = ((kc + bk - 1) / bk) * bk;
+      P->nsplit = int((K + kc - 1) / kc);
+      P->kchunk = kc;
+    }
+  }
+  if (P->kind != 0) {
+    ContractPlan& ref = *P;
+    plans_[key] = std::move(P);
+    return ref;
+  }
+  // tile shape: 64 x 64; 16 x 256 (256 x 16) when one side is at most 16;
+  // 16 x 16 with 64-deep K slices for skinny outputs with long sums
   P->small_tile = std::max(M, N) <= 48 && K >= 1024;
-  const int bm = P->small_tile ? kSBM : kBM, bk = P->small_tile ? kSBK : kBK;
+  if (!P->small_tile && M <= 16 && N > 64) P->tile = 1;
+  else if (!P->small_tile && N <= 16 && M > 64) P->tile = 2;
+  int bmm = kBM, bnn = kBN, bk = kBK;
+  if (P->small_tile) { bmm = bnn = kSBM; bk = kSBK; }
+  else if (P->tile == 1) { bmm = 16; bnn = 256; bk = kTBK; }
+  else if (P->tile == 2) { bmm = 256; bnn = 16; bk = kTBK; }
   // split-K when the output tiles alone do not fill the GPU
-  const long long tiles = ((M + bm - 1) / bm) * ((N + bm - 1) / bm) * NB;
+  const long long tiles = ((M + bmm - 1) / bmm) * ((N + bnn - 1) / bnn) * NB;
   int nsplit = 1;
   if (tiles < 2 * 152 && K > 4 * bk) {
     const long long want = (4 * 152 + tiles - 1) / tiles;
@@ -594,12 +737,12 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   nsplit = int((K + kchunk - 1) / kchunk);
   P->nsplit = nsplit;
   P->kchunk = kchunk;
-  P->a_off0 = h[iaB];
-  P->b_off0 = h[ibB];
-  P->c_off0 = h[icB];
   // tensor-core route: one batch, a large output side and enough work
   // (a short K would make the packed operands cost more traffic than the
   // product saves: those stay on CUDA cores)
+  // (short sums that write a large output stay on the CUDA cores: they are
+  // bound by the output write, which the tensor-core epilogue does not
+  // stream as well, and they keep the connected triples in FP32)
   if (std::is_same<R, float>::value && tc_ok && NB == 1 && std::max(M, N) >= 128 &&
       std::min(M, N) >= 4 && K >= 64 && M * N * K >= (1LL << 21)) {
     P->use_tc = true;
@@ -639,26 +782,37 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
     run_contract_tc(P, alpha, pa, pb, pc, accumulate);
     return;
   }
+  if (P.kind != 0) {
+    run_contract_small(P, alpha, pa, pb, pc, accumulate);
+    return;
+  }
   C* part = nullptr;
   if (P.nsplit > 1)
     part = static_cast<C*>(scratch(0, size_t(P.nb) * P.nsplit * P.M * P.N * sizeof(C)));
-  const int bm = P.small_tile ? kSBM : kBM;
-  dim3 grid((P.N + bm - 1) / bm, (P.M + bm - 1) / bm, P.nb * P.nsplit);
+  int bmm = kBM, bnn = kBN;
+  if (P.small_tile) bmm = bnn = kSBM;
+  else if (P.tile == 1) { bmm = 16; bnn = 256; }
+  else if (P.tile == 2) { bmm = 256; bnn = 16; }
+  dim3 grid((P.N + bnn - 1) / bnn, (P.M + bmm - 1) / bmm, P.nb * P.nsplit);
   RTCC3_CHECK(grid.y < 65536 && grid.z < 65536, kErrArg, "contraction grid too large: " + spec);
   const int pk = pbegin();
-#define RTCC3_LAUNCH(AK, BK, TBM, TBK)                                                           \
-  k_contract<R, AK, BK, TBM, TBM, TBK><<<grid, kThreads, 0, stream_>>>(                          \
+#define RTCC3_LAUNCH(AK, BK, TBM, TBN, TBK, TTM, TTN)                                            \
+  k_contract<R, AK, BK, TBM, TBN, TBK, TTM, TTN><<<grid, kThreads, 0, stream_>>>(                \
       pa, pb, pc, P.aM, P.aK, P.bN, P.bK, P.cM, P.cN, P.aB, P.bB, P.cB, P.M, P.N, P.K, P.nsplit, \
       P.kchunk, R(alpha), accumulate ? 1 : 0, part)
-#define RTCC3_LAUNCH4(TBM, TBK)                                                  \
-  if (P.a_kcontig && P.b_kcontig) RTCC3_LAUNCH(true, true, TBM, TBK);             \
-  else if (P.a_kcontig) RTCC3_LAUNCH(true, false, TBM, TBK);                     \
-  else if (P.b_kcontig) RTCC3_LAUNCH(false, true, TBM, TBK);                     \
-  else RTCC3_LAUNCH(false, false, TBM, TBK)
+#define RTCC3_LAUNCH4(...)                                                       \
+  if (P.a_kcontig && P.b_kcontig) RTCC3_LAUNCH(true, true, __VA_ARGS__);          \
+  else if (P.a_kcontig) RTCC3_LAUNCH(true, false, __VA_ARGS__);                  \
+  else if (P.b_kcontig) RTCC3_LAUNCH(false, true, __VA_ARGS__);                  \
+  else RTCC3_LAUNCH(false, false, __VA_ARGS__)
   if (P.small_tile) {
-    RTCC3_LAUNCH4(kSBM, kSBK);
+    RTCC3_LAUNCH4(kSBM, kSBM, kSBK, 1, 1);
+  } else if (P.tile == 1) {
+    RTCC3_LAUNCH4(16, 256, kTBK, 4, 4);
+  } else if (P.tile == 2) {
+    RTCC3_LAUNCH4(256, 16, kTBK, 4, 4);
   } else {
-    RTCC3_LAUNCH4(kBM, kBK);
+    RTCC3_LAUNCH4(kBM, kBN, kBK, 4, 4);
   }
 #undef RTCC3_LAUNCH4
 #undef RTCC3_LAUNCH
@@ -680,6 +834,38 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
     RTCC3_CUDA(cudaGetLastError());
     pend(pr, "split_reduce", 2.0 * n * P.nsplit, double(n) * (P.nsplit + 2) * sizeof(C));
   }
+}
+
+template <typename R>
+void Engine<R>::run_contract_small(ContractPlan& P, double alpha, const C* pa, const C* pb, C* pc,
+                                   bool accumulate) {
+  const bool sw = P.small_swap;
+  const int Mk = sw ? P.N : P.M, Nk = sw ? P.M : P.N;
+  const long long* kM = sw ? P.cN : P.cM;
+  const long long* kN = sw ? P.cM : P.cN;
+  const double mnk = double(P.M) * P.N * P.K;
+  const double bytes = (double(P.M) * P.K + double(P.N) * P.K +
+                        double(P.M) * P.N * (accumulate ? 2.0 : 1.0)) * sizeof(C);
+  const char* tag = sizeof(R) == 8 ? "c128" : "c64";
+  if (P.kind == 2) {
+    const int pk = pbegin();
+    launch_gemv<R>(sw ? P.b_kcontig : P.a_kcontig, sw ? pb : pa, sw ? P.b_off0 : P.a_off0,
+                   sw ? P.bN : P.aM, sw ? P.bK : P.aK, sw ? pa : pb, P.gemv_boff, sw ? P.aK : P.bK,
+                   pc, P.gemv_coff, kM, Mk, P.K, alpha, accumulate, stream_);
+    ++launches_;
+    pend(pk, (std::string("contract_gemv_") + tag).c_str(), 8.0 * mnk, bytes, cur_detail_);
+    return;
+  }
+  C* part = nullptr;
+  if (P.nsplit > 1) part = static_cast<C*>(scratch(0, size_t(P.nsplit) * P.M * P.N * sizeof(C)));
+  const int pk = pbegin();
+  launch_reduce_small<R>(P.small_cfg, sw ? P.b_kcontig : P.a_kcontig, sw ? P.a_kcontig : P.b_kcontig,
+                         sw ? pb : pa, sw ? P.b_off0 : P.a_off0, sw ? P.bN : P.aM, sw ? P.bK : P.aK,
+                         sw ? pa : pb, sw ? P.a_off0 : P.b_off0, sw ? P.aM : P.bN, sw ? P.aK : P.bK,
+                         pc, P.c_off0, kM, kN, Mk, Nk, P.K, P.nsplit, P.kchunk, alpha, accumulate,
+                         part, stream_);
+  launches_ += P.nsplit > 1 ? 2 : 1;
+  pend(pk, (std::string("contract_small_") + tag).c_str(), 8.0 * mnk, bytes, cur_detail_);
 }
 
 template <typename R>
@@ -712,8 +898,10 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     const double pbytes = double(op.M + 2.0 * op.N) * op.K * 2.0 * sizeof(float);
     int pk = pbegin();
     const int segs = tc_eb_ == 4 ? 3 : 1;
-    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, segs, tc_eb_, apk, stream_);
-    tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, segs, tc_eb_, bpk, stream_);
+    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, segs, tc_eb_, sw ? P.b_kcontig : P.a_kcontig,
+              apk, stream_);
+    tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, segs, tc_eb_, sw ? P.a_kcontig : P.b_kcontig,
+              bpk, stream_);
     pend(pk, "tc_pack", 0.0, pbytes + double(op.M + 2.0 * op.N) * op.Kp * tc_eb_, cur_detail_);
     launches_ += 2;
     pk = pbegin();
@@ -764,19 +952,26 @@ void Engine<R>::run_combine(const View* xs, const bool* xg, const double* alphas
   d.nsrc = ns;
   d.overwrite = overwrite ? 1 : 0;
   d.offy = Y.off;
-  // copy dims, then merge neighbours that are contiguous in every operand
+  // copy dims in the destination's memory order (largest stride first: the
+  // writes stay coalesced whatever the sources' order), then merge
+  // neighbours that are contiguous in every operand
   int nd = Y.nd;
   int shape[kMaxDim];
   long long sy[kMaxDim], sx[kMaxSrc][kMaxDim];
+  int ord[kMaxDim];
+  for (int k = 0; k < nd; ++k) ord[k] = k;
+  std::stable_sort(ord, ord + nd, [&](int p, int q) {
+    return std::llabs(Y.stride[p]) > std::llabs(Y.stride[q]);
+  });
   for (int k = 0; k < nd; ++k) {
-    shape[k] = Y.shape[k];
-    sy[k] = Y.stride[k];
+    shape[k] = Y.shape[ord[k]];
+    sy[k] = Y.stride[ord[k]];
   }
   for (int s = 0; s < ns; ++s) {
     RTCC3_CHECK(xs[s].nd == Y.nd, kErrArg, "combine rank mismatch");
     for (int k = 0; k < nd; ++k) {
-      RTCC3_CHECK(xs[s].shape[k] == Y.shape[k], kErrArg, "combine shape mismatch");
-      sx[s][k] = xs[s].stride[k];
+      RTCC3_CHECK(xs[s].shape[ord[k]] == Y.shape[ord[k]], kErrArg, "combine shape mismatch");
+      sx[s][k] = xs[s].stride[ord[k]];
     }
     d.offx[s] = xs[s].off;
     d.alpha[s] = R(alphas[s]);
@@ -852,6 +1047,53 @@ void Engine<R>::sym6(double alpha, const View& X, const View& Y, bool overwrite)
   if (nodes_[X.node].needs_grad) nodes_[Y.node].needs_grad = true;
   Op op{kSym6, "", alpha, X, View(), Y, EpsSpec()};
   tape_.push_back(op);
+}
+
+template <typename R>
+void Engine<R>::sym6_div(double alpha, const View& X, const EpsSpec& es, const View& Y) {
+  RTCC3_CHECK(X.node != Y.node, kErrArg, "sym6_div output aliases input");
+  run_sym6_div(alpha, X, false, es, Y, false, true);
+  if (nodes_[X.node].needs_grad) nodes_[Y.node].needs_grad = true;
+  Op op{kSym6Div, "", alpha, X, View(), Y, es};
+  tape_.push_back(op);
+}
+
+template <typename R>
+void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y,
+                             bool yg, bool overwrite) {
+  const bool cplx = es.osum_c && es.vsum_c;
+  RTCC3_CHECK(cplx || (es.osum && es.vsum), kErrArg, "sym6_div needs denominator sum tables");
+  auto dense6 = [&](const View& w) {
+    if (w.nd != 6) return false;
+    const int dims[6] = {es.o, es.o, es.o, es.v, es.v, es.v};
+    long long st = 1;
+    for (int k = 5; k >= 0; --k) {
+      if (w.shape[k] != dims[k] || w.stride[k] != st) return false;
+      st *= dims[k];
+    }
+    return true;
+  };
+  RTCC3_CHECK(dense6(X) && dense6(Y), kErrArg, "sym6_div needs dense triples views");
+  const size_t n = Y.numel();
+  if (n == 0) return;
+  const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
+  C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
+  const int pk = pbegin();
+#define RTCC3_S6D(I, CP)                                                                       \
+  k_sym6_div<R, I, CP><<<grid_for(n), 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum, es.vsum, \
+                                                         es.osum_c, es.vsum_c, es.o, es.v, I(n), \
+                                                         R(alpha), overwrite ? 1 : 0)
+  if (n < (size_t(1) << 31)) {
+    if (cplx) RTCC3_S6D(unsigned, true);
+    else RTCC3_S6D(unsigned, false);
+  } else {
+    if (cplx) RTCC3_S6D(size_t, true);
+    else RTCC3_S6D(size_t, false);
+  }
+#undef RTCC3_S6D
+  pend(pk, "sym6_div", 20.0 * n, double(n) * sizeof(C) * (6 + (overwrite ? 1 : 2)));
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
 }
 
 template <typename R>
@@ -1049,8 +1291,41 @@ void Engine<R>::backward() {
       if (nodes_[op.b.node].needs_grad)
         run_contract(s.a + "," + s.c + "->" + s.b, op.alpha, op.a, false, op.c, true, op.b, true, true);
     } else if (op.kind == kAxpy) {
-      if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
-      run_axpy(op.alpha, op.c, true, op.a, true);
+      // the run of axpy ops recorded by one combine share their gradient
+      // source; their adjoints into one node become one gather pass over
+      // that node in its own memory order
+      auto jt = it;
+      std::vector<const Op*> run;
+      while (jt != tape_.rend() && jt->kind == kAxpy && same_view(jt->c, op.c)) {
+        run.push_back(&*jt);
+        ++jt;
+      }
+      it = std::prev(jt);
+      if (!nodes_[op.c.node].needs_grad) continue;
+      std::vector<bool> done(run.size(), false);
+      for (size_t i = 0; i < run.size(); ++i) {
+        if (done[i] || !nodes_[run[i]->a.node].needs_grad) continue;
+        View dense, src;
+        if (!invert_view(run[i]->a, run[i]->c, dense, src)) {
+          run_axpy(run[i]->alpha, run[i]->c, true, run[i]->a, true);
+          continue;
+        }
+        View xs[kMaxSrc];
+        bool xg[kMaxSrc];
+        double al[kMaxSrc];
+        int ns = 0;
+        for (size_t j = i; j < run.size() && ns < kMaxSrc; ++j) {
+          if (done[j] || run[j]->a.node != run[i]->a.node) continue;
+          View dj, sj;
+          if (!invert_view(run[j]->a, run[j]->c, dj, sj) || !same_view(dj, dense)) continue;
+          xs[ns] = sj;
+          xg[ns] = true;
+          al[ns] = run[j]->alpha;
+          ++ns;
+          done[j] = true;
+        }
+        run_combine(xs, xg, al, ns, dense, true, false, "axpy_gather");
+      }
     } else if (op.kind == kMulc) {
       if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
       run_mulc(op.c, true, op.b, op.a, true);
@@ -1060,6 +1335,9 @@ void Engine<R>::backward() {
     } else if (op.kind == kSym6) {
       if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
       run_sym6(op.alpha, op.c, true, op.a, true, false);
+    } else if (op.kind == kSym6Div) {
+      if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
+      run_sym6_div(op.alpha, op.c, true, op.es, op.a, true, false);
     } else {
       const bool saved = tc_region_;
       tc_region_ = op.tc;

@@ -51,6 +51,13 @@ struct ContractPlan {
   int nsplit = 1, kchunk = 1;
   bool a_kcontig = false, b_kcontig = false;
   bool small_tile = false;  // 16x16 output tiles with 64-deep K slices (skinny shapes)
+  int tile = 0;             // 0: 64 x 64, 1: 16 x 256, 2: 256 x 16 output tiles
+  // kind 0: tiled gather-GEMM; 1: small output held whole by every CTA
+  // (reduce_small, config small_cfg); 2: single long output column (gemv).
+  // small_swap: the kernels run with A and B exchanged (larger side first).
+  int kind = 0, small_cfg = 0;
+  bool small_swap = false;
+  long long gemv_boff = 0, gemv_coff = 0;  // B and C offsets of the single column
   // tensor-core route (complex64 graphs with TF32/BF16 operands)
   bool use_tc = false, tc_swap = false;
   int tc_nsplit = 1, tc_kp = 0;
@@ -113,6 +120,9 @@ class Engine {
     const double2* vsum_c = nullptr;
   };
   void div_eps(const View& X, const EpsSpec& es, const View& Y, bool overwrite = false);
+  // Y = alpha P_ijk^abc(X) / D (Eq. A30 and the denominators of Eq. 6 in one
+  // pass; X, Y dense triples, es with FP64 sum tables; Y is overwritten).
+  void sym6_div(double alpha, const View& X, const EpsSpec& es, const View& Y);
   // Non-differentiable initialisation.
   void fill_identity(int node);
   void fill_ones(int node);
@@ -211,7 +221,7 @@ class Engine {
     if (prof_) prof_->end(k, stream_, name, flops, bytes, detail);
   }
   std::string cur_detail_;  // spec and extents of the operation being run (profiling)
-  enum OpKind { kContract, kAxpy, kMulc, kDiv, kCustom, kSym6 };
+  enum OpKind { kContract, kAxpy, kMulc, kDiv, kCustom, kSym6, kSym6Div };
   struct Op {
     OpKind kind;
     std::string spec;
@@ -227,6 +237,8 @@ class Engine {
   void run_combine(const View* xs, const bool* xg, const double* alphas, int ns, const View& Y,
                    bool yg, bool overwrite, const char* name);
   void run_sym6(double alpha, const View& X, bool xg, const View& Y, bool yg, bool overwrite);
+  void run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
+                    bool overwrite);
   void run_contract(const std::string& spec, double alpha, const View& A, bool a_grad, const View& B,
                     bool b_grad, const View& Cv, bool c_grad, bool accumulate);
   void run_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg);
@@ -245,6 +257,8 @@ class Engine {
   bool tc_region_ = false;
   int* err_ = nullptr;
   DevicePool* pool_ = nullptr;
+  void run_contract_small(ContractPlan& P, double alpha, const C* pa, const C* pb, C* pc,
+                          bool accumulate);
   void run_contract_tc(ContractPlan& P, double alpha, const C* pa, const C* pb, C* pc,
                        bool accumulate);
   int launches_ = 0;

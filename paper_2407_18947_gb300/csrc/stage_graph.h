@@ -78,9 +78,8 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, int 
   const int Z = E.node(s6);
   E.contract("ijae,ckbe->ijkabc", 1.0, T1p, G1p, E.v(Z), true);
   E.contract("imab,mjck->ijkabc", -1.0, T2p, G2p, E.v(Z), true);
-  const int rhs = E.node(s6, false, false);
-  E.sym6(-1.0, E.v(Z), E.v(rhs), true);
-  // source -P sum_ld v~_ld t_ij^ad t_kl^cb, rotated the same way
+  // source -P sum_ld v~_ld t_ij^ad t_kl^cb, rotated the same way; P is linear,
+  // so it is folded into Z before the one permutation sum
   const int Yl = E.node({o, o, o, v});
   E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), true);
   View Ylp = rot("Ii,lija->lIja", SIO, E.v(Yl), {o, o, o, v});
@@ -89,17 +88,15 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, int 
   View T3p_ = rot("Kk,klcb->Klcb", SIO, T, {o, o, v, v});
   T3p_ = rot("Cc,Klcb->KlCb", SIV, T3p_, {o, o, v, v});
   T3p_ = rot("Bb,KlCb->KlCB", SIV, T3p_, {o, o, v, v});
-  const int Z2 = E.node(s6);
-  E.contract("lija,klcb->ijkabc", 1.0, Ylp, T3p_, E.v(Z2), true);
-  E.sym6(1.0, E.v(Z2), E.v(rhs), false);
-  // ---- complex denominators ---------------------------------------------------
+  E.contract("lija,klcb->ijkabc", -1.0, Ylp, T3p_, E.v(Z), true);
+  // ---- t3' = -P(Z) / D' with the complex denominators ---------------------------
   typename Engine<R>::EpsSpec es;
   es.o = o;
   es.v = v;
   es.osum_c = osum;
   es.vsum_c = vsum;
   const int t3p = E.node(s6, false, false);
-  E.div_eps(E.v(rhs), es, E.v(t3p), true);
+  E.sym6_div(-1.0, E.v(Z), es, E.v(t3p));
   const int wtn = wt;
   if (E.needs_grad(t3p) && E.needs_grad(wtn)) {
     const View wvv = blk(wt, "vv"), woo = blk(wt, "oo");
@@ -346,16 +343,13 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     const int Z = E.node(s6);
     E.contract("ijae,ckbe->ijkabc", 1.0, T, G("vovv"), E.v(Z), true);
     E.contract("imab,mjck->ijkabc", -1.0, T, G("oovo"), E.v(Z), true);
-    // rhs = -(W + <mu3|1/2[[V~,T2],T2]|0>), the latter = -P sum_ld v~_ld t_ij^ad t_kl^cb
-    const int rhs = E.node(s6, false, false);
-    E.sym6(-1.0, E.v(Z), E.v(rhs), true);
+    // rhs = -(W + <mu3|1/2[[V~,T2],T2]|0>), the latter = -P sum_ld v~_ld t_ij^ad t_kl^cb:
+    // P is linear, so the source is folded into Z and rhs = -P(Z)
     const bool field = opt.field_terms;
     if (field) {
       const int Yl = E.node({o, o, o, v});
       E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), true);
-      const int Z2 = E.node(s6);
-      E.contract("lija,klcb->ijkabc", 1.0, E.v(Yl), T, E.v(Z2), true);
-      E.sym6(1.0, E.v(Z2), E.v(rhs), false);
+      E.contract("lija,klcb->ijkabc", -1.0, E.v(Yl), T, E.v(Z), true);
     }
     typename Engine<R>::EpsSpec es;
     es.eps = H.eps;
@@ -368,8 +362,10 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     int t3;
     if (!field) {
       t3 = E.node(s6, false, false);
-      E.div_eps(E.v(rhs), es, E.v(t3), true);
+      E.sym6_div(-1.0, E.v(Z), es, E.v(t3));
     } else {
+      const int rhs = E.node(s6, false, false);
+      E.sym6(-1.0, E.v(Z), E.v(rhs), true);
       t3 = field_coupled_solve(E, rhs, blk(wt, "vv"), blk(wt, "oo"), wt, es, s6,
                                std::max(1, opt.field_iters));
     }

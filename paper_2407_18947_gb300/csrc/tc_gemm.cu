@@ -278,66 +278,93 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-__device__ __forceinline__ void put(void* out, size_t idx, float v, int elem_bytes) {
-  if (elem_bytes == 4) {
-    static_cast<uint32_t*>(out)[idx] = to_tf32(v);
+// One thread per complex source element: its (re, im) pair is written to
+// every K segment (and, for B, to both rows of its 2x2 embedding) with one
+// vector store each.  I is the index type of the flattened (row, k) loop.
+template <int EB>
+__device__ __forceinline__ void put_pair(void* out, size_t idx, float x, float y) {
+  if (EB == 4) {
+    *reinterpret_cast<uint2*>(static_cast<uint32_t*>(out) + idx) = make_uint2(to_tf32(x), to_tf32(y));
   } else {
-    const uint32_t u = __float_as_uint(v);
+    const uint32_t ux = __float_as_uint(x), uy = __float_as_uint(y);
     // round to nearest even on the upper 16 bits (finite inputs)
-    const uint32_t rounded = u + 0x7FFFu + ((u >> 16) & 1u);
-    static_cast<unsigned short*>(out)[idx] = static_cast<unsigned short>(rounded >> 16);
+    const uint32_t rx = (ux + 0x7FFFu + ((ux >> 16) & 1u)) >> 16;
+    const uint32_t ry = (uy + 0x7FFFu + ((uy >> 16) & 1u)) >> 16;
+    *reinterpret_cast<uint32_t*>(static_cast<unsigned short*>(out) + idx) = rx | (ry << 16);
   }
 }
 
-// hi/lo TF32 split of v for segment seg: A takes (hi, hi, lo), B (hi, lo, hi)
-__device__ __forceinline__ float split_part(float v, int seg, bool is_a) {
-  const float hi = __uint_as_float(to_tf32(v));
-  const bool lo = is_a ? (seg == 2) : (seg == 1);
-  return lo ? v - hi : hi;
-}
-
-__global__ void k_pack_a(const float2* __restrict__ A, const long long* __restrict__ aM,
-                         const long long* __restrict__ aK, long long aoff, int M, int K, int Kp,
-                         int segs, int elem_bytes, void* out) {
-  const size_t total = size_t(M) * Kp;
-  const int seg_w = Kp / segs;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int kq = int(t % Kp);
-    const int m = int(t / Kp);
-    const int seg = kq / seg_w, kp = kq - seg * seg_w;
-    const int k = kp >> 1;
-    float v = 0.f;
-    if (k < K) {
-      const float2 a = A[aoff + aM[m] + aK[k]];
-      v = (kp & 1) ? a.y : a.x;
-      if (segs == 3) v = split_part(v, seg, true);
-    }
-    put(out, t, v, elem_bytes);
+// Packing runs on 32 x 32 (row, complex k) tiles staged in shared memory:
+// the source is read with consecutive threads on its contiguous index (k when
+// KFAST, else the row), the packed rows are written with consecutive threads
+// along k.  B rows expand to the two rows of their 2x2 real embedding.
+template <int EB, bool KFAST, bool IS_B>
+__global__ void __launch_bounds__(256)
+k_pack(const float2* __restrict__ X, const long long* __restrict__ xR, const long long* __restrict__ xK,
+       long long xoff, int R, int K, int Kp, int segs, void* out) {
+  __shared__ float2 tile[32][33];
+  const int seg_w = Kp / segs, hw = seg_w >> 1;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int a = w + 8 * u;
+    const int rr = KFAST ? a : lane, kk = KFAST ? lane : a;
+    const int r = r0 + rr, k = k0 + kk;
+    tile[rr][kk] = (r < R && k < K) ? X[xoff + xR[r] + xK[k]] : make_float2(0.f, 0.f);
   }
-}
-
-__global__ void k_pack_b(const float2* __restrict__ B, const long long* __restrict__ bN,
-                         const long long* __restrict__ bK, long long boff, int N, int K, int Kp,
-                         int segs, int elem_bytes, void* out) {
-  const size_t total = size_t(2 * N) * Kp;
-  const int seg_w = Kp / segs;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int kq = int(t % Kp);
-    const int r = int(t / Kp);
-    const int seg = kq / seg_w, kp = kq - seg * seg_w;
-    const int n = r >> 1, k = kp >> 1;
-    float v = 0.f;
-    if (k < K) {
-      const float2 b = B[boff + bN[n] + bK[k]];
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = w + 8 * u, r = r0 + rr, k = k0 + lane;
+    if (r >= R || k >= hw) continue;
+    const float2 v = tile[rr][lane];
+    const size_t row = (IS_B ? size_t(2 * r) : size_t(r)) * Kp + 2 * size_t(k);
+    if (!IS_B) {
+      if (segs == 3) {
+        const float hx = __uint_as_float(to_tf32(v.x)), hy = __uint_as_float(to_tf32(v.y));
+        put_pair<EB>(out, row, hx, hy);
+        put_pair<EB>(out, row + seg_w, hx, hy);
+        put_pair<EB>(out, row + 2 * seg_w, v.x - hx, v.y - hy);
+      } else {
+        put_pair<EB>(out, row, v.x, v.y);
+      }
+    } else {
       // row 2n: (Br, -Bi); row 2n+1: (Bi, Br) along (re, im) of K
-      if ((r & 1) == 0) v = (kp & 1) ? -b.y : b.x;
-      else v = (kp & 1) ? b.x : b.y;
-      if (segs == 3) v = split_part(v, seg, false);
+      const size_t r1 = row + Kp;
+      if (segs == 3) {
+        const float hx = __uint_as_float(to_tf32(v.x)), hy = __uint_as_float(to_tf32(v.y));
+        const float lx = v.x - hx, ly = v.y - hy;
+        put_pair<EB>(out, row, hx, -hy);
+        put_pair<EB>(out, r1, hy, hx);
+        put_pair<EB>(out, row + seg_w, lx, -ly);
+        put_pair<EB>(out, r1 + seg_w, ly, lx);
+        put_pair<EB>(out, row + 2 * seg_w, hx, -hy);
+        put_pair<EB>(out, r1 + 2 * seg_w, hy, hx);
+      } else {
+        put_pair<EB>(out, row, v.x, -v.y);
+        put_pair<EB>(out, r1, v.y, v.x);
+      }
     }
-    put(out, t, v, elem_bytes);
   }
+}
+
+template <bool IS_B>
+void launch_pack(const float2* X, const long long* xR, const long long* xK, long long xoff, int R,
+                 int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
+  const int hw = Kp / segs / 2;
+  dim3 grid((hw + 31) / 32, (R + 31) / 32);
+  RTCC3_CHECK(grid.y < 65536, kErrArg, "packed operand has too many rows");
+#define RTCC3_PK(EBV, KF) k_pack<EBV, KF, IS_B><<<grid, 256, 0, s>>>(X, xR, xK, xoff, R, K, Kp, segs, out)
+  if (elem_bytes == 4) {
+    if (kfast) RTCC3_PK(4, true);
+    else RTCC3_PK(4, false);
+  } else {
+    if (kfast) RTCC3_PK(2, true);
+    else RTCC3_PK(2, false);
+  }
+#undef RTCC3_PK
+  RTCC3_CUDA(cudaGetLastError());
 }
 
 __global__ void k_split_finish(const float* __restrict__ partial, int nsplit, int M, int N,
@@ -418,17 +445,13 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
 }  // namespace
 
 void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
-               int K, int Kp, int segs, int elem_bytes, void* out, cudaStream_t s) {
-  k_pack_a<<<grid_for(size_t(M) * Kp), 256, 0, s>>>(A, aM, aK, aoff, M, K, Kp, segs, elem_bytes,
-                                                     out);
-  RTCC3_CUDA(cudaGetLastError());
+               int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
+  launch_pack<false>(A, aM, aK, aoff, M, K, Kp, segs, elem_bytes, kfast, out, s);
 }
 
 void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
-               int K, int Kp, int segs, int elem_bytes, void* out, cudaStream_t s) {
-  k_pack_b<<<grid_for(size_t(2 * N) * Kp), 256, 0, s>>>(B, bN, bK, boff, N, K, Kp, segs,
-                                                         elem_bytes, out);
-  RTCC3_CUDA(cudaGetLastError());
+               int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
+  launch_pack<true>(B, bN, bK, boff, N, K, Kp, segs, elem_bytes, kfast, out, s);
 }
 
 bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2* C,

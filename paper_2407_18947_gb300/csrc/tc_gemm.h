@@ -24,11 +24,13 @@ struct TcOperands {
 // packed width Kp.  segs = 3 (TF32 only) writes the three K segments
 // [hi | hi | lo] of a hi + lo TF32 split (B gets [hi | lo | hi]), so one GEMM
 // over the whole width sums hi.hi + hi.lo + lo.hi.
+// kfast: the source is contiguous along k (else along the row index); the
+// packing kernel reads along that index and writes packed rows along k.
 void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
-               int K, int Kp, int segs, int elem_bytes, void* out, cudaStream_t s);
+               int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s);
 // Pack B as its 2x2 real embedding: rows 2n (real part) and 2n+1 (imaginary part).
 void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
-               int K, int Kp, int segs, int elem_bytes, void* out, cudaStream_t s);
+               int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s);
 
 // C[cB + cM[m] + cN[n]] (+)= alpha * (Apack Bpack^T)[m, 2n..2n+1] as complex.
 // nsplit > 1: K is split over CTAs; partial sums (M x 2N FP32 per split) go
