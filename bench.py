@@ -187,9 +187,10 @@ def run_reference(args, wl, rank):
 
 
 def workload_config(wl, precision, nbatch):
-    o, v = 5 * wl["n"], 19 * wl["n"]
+    o, v = wl.get("size", (5 * wl["n"], 19 * wl["n"]))
     field = ("static" if wl["kind"] == 1 else f"cos omega={wl['omega']} au") + f" A={wl['amp']} au along z"
-    return {"workload": f"(H2O){wl['n']}-sized RT-CC3: nocc={o} nvir={v} naux={3 * (o + v)}, {field}, "
+    name = f"(H2O){wl['n']}-sized" if "size" not in wl else "reduced (profiling)"
+    return {"workload": f"{name} RT-CC3: nocc={o} nvir={v} naux={3 * (o + v)}, {field}, "
                         f"h={wl['h']} au, T and lambda propagated",
             "nocc": o, "nvir": v, "precision": precision, "fields_per_gpu": nbatch,
             "l2": "working set larger than L2 (o^3 v^3 triples tensors)"}
@@ -200,13 +201,17 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--precision", default="tf32", choices=sorted(PRECISIONS))
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", type=int, default=2, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", default=None,
+                    help="nocc,nvir of a reduced same-recipe system (profiling captures only)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.size:
+        wl["size"] = tuple(int(x) for x in args.size.split(","))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -221,9 +226,12 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     from paper_2407_18947_gb300.api import RTCC3
-    from paper_2407_18947_gb300.synth import water_system
+    from paper_2407_18947_gb300.synth import BASE_SEED, make_system, water_system
 
-    s = water_system(wl["n"])
+    if "size" in wl:
+        s = make_system(*wl["size"], seed=BASE_SEED + wl["n"])
+    else:
+        s = water_system(wl["n"])
     o, v = s.nocc, s.nvir
     prec = PRECISIONS[args.precision]
     eng = RTCC3(o, v, nbatch=1, precision=prec, device=local)

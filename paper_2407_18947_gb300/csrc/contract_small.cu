@@ -25,7 +25,8 @@ struct SmallShape {
   static constexpr int MP = RM * UM, NP = RN * UN, G = kThreads / (RM * RN);
   static constexpr int EB = int(sizeof(Cx<R>));
   static constexpr int BK0 = 40960 / ((MP + NP + 2) * EB);
-  static constexpr int BK = BK0 >= 32 ? 32 : (BK0 >= 16 ? 16 : (BK0 >= 8 ? 8 : 4));
+  // deep slices keep more loads in flight per thread (128 for the 16 x 16 tile)
+  static constexpr int BK = BK0 >= 128 ? 128 : (BK0 >= 64 ? 64 : (BK0 >= 32 ? 32 : (BK0 >= 16 ? 16 : (BK0 >= 8 ? 8 : 4))));
   // thread groups sharing a warp (summed by shuffles) and the rest (by shared memory)
   static constexpr int WG = RM * RN >= 32 ? 1 : 32 / (RM * RN);
   static constexpr int GS = G / WG;

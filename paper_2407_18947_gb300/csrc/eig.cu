@@ -1,283 +1,283 @@
 // Eigendecomposition of the small complex non-Hermitian matrices that carry
 // the field coupling of the triples equation (see rotation.h).
 //
-// One CTA per matrix, FP64 complex.  M is reduced to upper Hessenberg form by
-// Householder reflections, then to Schur form T = Q^H M Q by single-shift QR
-// sweeps (Wilkinson shift, Givens rotations, deflation of negligible
-// subdiagonal entries); the eigenvectors X of the upper-triangular T are found
-// by back substitution (unit diagonal), so S = Q X, S^-1 = X^-1 Q^H and
-// M = S diag(T_kk) S^-1.  H lives in shared memory; Q, X and X^-1 in a global
-// workspace.  A non-converging sweep count raises *status instead of looping.
+// One warp per matrix, no block-wide barriers: M is reduced to upper
+// Hessenberg form by Householder reflections, then to Schur form
+// T = Q^H M Q by single-shift QR sweeps (Wilkinson shift, Givens rotations,
+// deflation of negligible subdiagonal entries, an exceptional shift every
+// eleventh sweep); the eigenvectors X of the upper-triangular T follow by back
+// substitution (unit diagonal), so S = Q X, S^-1 = X^-1 Q^H and
+// M = S diag(T_kk) S^-1.  Every lane computes the rotation parameters itself
+// from the same shared-memory values (identical control flow), then the lanes
+// update disjoint rows and columns.  The arithmetic type T is float for the
+// complex64 graphs and double for the complex128 one.  H lives in shared
+// memory, Q, X and X^-1 in a global workspace; a non-converging sweep count or
+// a non-finite matrix raises *status (codes in rotation.h) instead of looping.
 #include "rotation.h"
+
+#include <algorithm>
 
 namespace rtcc3 {
 
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+template <typename T> struct C2T;
+template <> struct C2T<float> { using type = float2; };
+template <> struct C2T<double> { using type = double2; };
+
+template <typename T>
+struct Cplx {
+  using V = typename C2T<T>::type;
+  static __device__ __forceinline__ V mk(T a, T b) { V r; r.x = a; r.y = b; return r; }
+  static __device__ __forceinline__ V mul(V a, V b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+  static __device__ __forceinline__ V conj(V a) { return mk(a.x, -a.y); }
+  static __device__ __forceinline__ V add(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ V sub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ V scale(V a, T s) { return mk(a.x * s, a.y * s); }
+  static __device__ __forceinline__ T abs(V a) { return sqrt(a.x * a.x + a.y * a.y); }
   // Smith's algorithm
-  if (fabs(b.x) >= fabs(b.y)) {
-    const double r = b.y / b.x, d = b.x + b.y * r;
-    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  static __device__ __forceinline__ V div(V a, V b) {
+    if (fabs(b.x) >= fabs(b.y)) {
+      const T r = b.y / b.x, d = b.x + b.y * r;
+      return mk((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    }
+    const T r = b.x / b.y, d = b.y + b.x * r;
+    return mk((a.x * r + a.y) / d, (a.y * r - a.x) / d);
   }
-  const double r = b.x / b.y, d = b.y + b.x * r;
-  return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
-}
-// Principal square root without cancellation: t = sqrt((|x| + |z|) / 2) is
-// the larger of |Re|, |Im| and the other part follows as y / (2 t).
-__device__ __forceinline__ double2 csqrt(double2 z) {
-  const double m = cabs2(z);
-  if (m == 0.0) return make_double2(0.0, 0.0);
-  const double t = sqrt(0.5 * (fabs(z.x) + m));
-  if (z.x >= 0.0) return make_double2(t, z.y / (2.0 * t));
-  return make_double2(fabs(z.y) / (2.0 * t), copysign(t, z.y));
-}
+  // principal square root without cancellation: t = sqrt((|x| + |z|) / 2) is
+  // the larger of |Re|, |Im| and the other part follows as y / (2 t)
+  static __device__ __forceinline__ V sqrt_(V z) {
+    const T m = abs(z);
+    if (m == T(0)) return mk(T(0), T(0));
+    const T t = sqrt(T(0.5) * (fabs(z.x) + m));
+    if (z.x >= T(0)) return mk(t, z.y / (T(2) * t));
+    return mk(fabs(z.y) / (T(2) * t), copysign(t, z.y));
+  }
+};
 
-// Block-wide sum of one double (blockDim.x <= 1024).
-__device__ double block_sum(double v, double* red) {
+// Sum over the warp, returned identically in every lane (lane 0's value:
+// the lanes' butterfly sums may round differently, and every lane takes the
+// same branches on the result).
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  return s;
+  return __shfl_sync(0xffffffffu, v, 0);
 }
 
-__global__ void k_eig(const double2* __restrict__ Min, int n, double2* __restrict__ S,
-                      double2* __restrict__ Sinv, double2* __restrict__ lam,
-                      double2* __restrict__ ws, int* __restrict__ status) {
-  extern __shared__ double2 H[];  // n x n, row-major
-  __shared__ double red[32];
-  __shared__ double2 v[kEigMaxN];
-  __shared__ double2 gcs[2];  // (c, 0), s
-  __shared__ int ctl[4];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const size_t nn = size_t(n) * n;
-  const double2* M = Min + size_t(blockIdx.x) * nn;
-  double2* Q = ws + size_t(blockIdx.x) * 3 * nn;
-  double2* X = Q + nn;
-  double2* Xi = X + nn;
-  S += size_t(blockIdx.x) * nn;
-  Sinv += size_t(blockIdx.x) * nn;
-  lam += size_t(blockIdx.x) * n;
-  for (size_t t = tid; t < nn; t += nt) {
-    H[t] = M[t];
-    Q[t] = make_double2((t / n) == (t % n) ? 1.0 : 0.0, 0.0);
+template <typename T>
+__global__ void __launch_bounds__(32) k_eig_warp(EigJob ja, EigJob jb, int* __restrict__ status) {
+  using X = Cplx<T>;
+  using V = typename C2T<T>::type;
+  const EigJob J = blockIdx.x == 0 ? ja : jb;
+  const int n = J.n;
+  if (n <= 0) return;
+  const int lane = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  V* H = reinterpret_cast<V*>(sm_raw);  // n x n, row-major
+  V* vb = H + size_t(n) * n;            // Householder vector
+  V* Q = reinterpret_cast<V*>(J.ws);
+  V* Xv = Q + size_t(n) * n;
+  V* Xi = Xv + size_t(n) * n;
+  const int nn = n * n;
+  T fro = T(0);
+  for (int t = lane; t < nn; t += 32) {
+    const double2 m = J.M[t];
+    H[t] = X::mk(T(m.x), T(m.y));
+    Q[t] = X::mk((t / n) == (t % n) ? T(1) : T(0), T(0));
+    fro += T(m.x) * T(m.x) + T(m.y) * T(m.y);
   }
-  __syncthreads();
-  double fro = 0.0;
-  for (size_t t = tid; t < nn; t += nt) fro += H[t].x * H[t].x + H[t].y * H[t].y;
-  fro = sqrt(block_sum(fro, red));
-  const double tiny = 1e-300;
+  fro = sqrt(warp_sum(fro));
+  __syncwarp();
   if (!isfinite(fro)) {
-    if (tid == 0) atomicExch(status, eig_status(kEigNonFinite, n, n - 1));
+    if (lane == 0) atomicExch(status, eig_status(kEigNonFinite, n, n - 1));
     return;
   }
+  const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-300);
+  const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.2e-16);
 
   // ---- Householder reduction to upper Hessenberg form -------------------------
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
-    double s2 = 0.0;
-    for (int i = tid; i < m; i += nt) {
-      const double2 x = H[(k + 1 + i) * n + k];
+    T s2 = T(0);
+    for (int i = lane; i < m; i += 32) {
+      const V x = H[(k + 1 + i) * n + k];
       s2 += x.x * x.x + x.y * x.y;
     }
-    const double xnorm = sqrt(block_sum(s2, red));
-    const double2 x0 = H[(k + 1) * n + k];
-    const double ax0 = cabs2(x0);
-    double tail = xnorm * xnorm - ax0 * ax0;
-    if (xnorm <= tiny || tail <= 1e-30 * xnorm * xnorm) {
-      __syncthreads();
-      continue;  // column already reduced
+    s2 = warp_sum(s2);
+    const T xnorm = sqrt(s2);
+    const V x0 = H[(k + 1) * n + k];
+    const T ax0 = X::abs(x0);
+    if (xnorm <= tiny || s2 - ax0 * ax0 <= T(1e-30) * s2) continue;  // column already reduced
+    const V ph = ax0 > T(0) ? X::scale(x0, T(1) / ax0) : X::mk(T(1), T(0));
+    const V alpha = X::scale(ph, -xnorm);
+    for (int i = lane; i < m; i += 32) vb[i] = i == 0 ? X::sub(x0, alpha) : H[(k + 1 + i) * n + k];
+    __syncwarp();
+    T vv = T(0);
+    for (int i = lane; i < m; i += 32) vv += vb[i].x * vb[i].x + vb[i].y * vb[i].y;
+    const T beta = T(2) / warp_sum(vv);
+    // left: rows k+1.., columns k..n-1 (one column per lane)
+    for (int j = k + lane; j < n; j += 32) {
+      V sd = X::mk(T(0), T(0));
+      for (int i = 0; i < m; ++i) sd = X::add(sd, X::mul(X::conj(vb[i]), H[(k + 1 + i) * n + j]));
+      sd = X::scale(sd, beta);
+      for (int i = 0; i < m; ++i) H[(k + 1 + i) * n + j] = X::sub(H[(k + 1 + i) * n + j], X::mul(vb[i], sd));
     }
-    const double2 ph = ax0 > 0.0 ? cscale(x0, 1.0 / ax0) : make_double2(1.0, 0.0);
-    const double2 alpha = cscale(ph, -xnorm);
-    for (int i = tid; i < m; i += nt) v[i] = H[(k + 1 + i) * n + k];
-    __syncthreads();
-    if (tid == 0) v[0] = csub(x0, alpha);
-    __syncthreads();
-    double vv = 0.0;
-    for (int i = tid; i < m; i += nt) vv += v[i].x * v[i].x + v[i].y * v[i].y;
-    vv = block_sum(vv, red);
-    const double beta = 2.0 / vv;
-    // left: rows k+1.., columns k..n-1
-    for (int j = k + tid; j < n; j += nt) {
-      double2 sdot = make_double2(0.0, 0.0);
-      for (int i = 0; i < m; ++i) sdot = cadd(sdot, cmul(cconj(v[i]), H[(k + 1 + i) * n + j]));
-      sdot = cscale(sdot, beta);
-      for (int i = 0; i < m; ++i) H[(k + 1 + i) * n + j] = csub(H[(k + 1 + i) * n + j], cmul(v[i], sdot));
+    __syncwarp();
+    // right: all rows of H and Q, columns k+1..n-1 (one row per lane)
+    for (int r = lane; r < 2 * n; r += 32) {
+      V* row = r < n ? &H[r * n] : &Q[size_t(r - n) * n];
+      V sd = X::mk(T(0), T(0));
+      for (int j = 0; j < m; ++j) sd = X::add(sd, X::mul(row[k + 1 + j], vb[j]));
+      sd = X::scale(sd, beta);
+      for (int j = 0; j < m; ++j) row[k + 1 + j] = X::sub(row[k + 1 + j], X::mul(sd, X::conj(vb[j])));
     }
-    __syncthreads();
-    // right: all rows, columns k+1..n-1 (H and Q)
-    for (int r = tid; r < 2 * n; r += nt) {
-      double2* row = r < n ? &H[r * n] : &Q[size_t(r - n) * n];
-      double2 sdot = make_double2(0.0, 0.0);
-      for (int j = 0; j < m; ++j) sdot = cadd(sdot, cmul(row[k + 1 + j], v[j]));
-      sdot = cscale(sdot, beta);
-      for (int j = 0; j < m; ++j) row[k + 1 + j] = csub(row[k + 1 + j], cmul(sdot, cconj(v[j])));
-    }
-    __syncthreads();
-    for (int i = tid; i < m; i += nt)
-      if (i > 0) H[(k + 1 + i) * n + k] = make_double2(0.0, 0.0);
-    __syncthreads();
+    __syncwarp();
+    for (int i = 1 + lane; i < m; i += 32) H[(k + 1 + i) * n + k] = X::mk(T(0), T(0));
+    __syncwarp();
   }
 
   // ---- shifted QR sweeps to Schur form ---------------------------------------
-  const double eps = 2.2e-16;
   int hi = n - 1, iter = 0, its_here = 0;
   const int max_iter = 60 * n + 100;
+  bool failed = false;
   while (hi > 0) {
-    if (tid == 0) {
-      int l = hi;
-      while (l > 0) {
-        const double off = cabs2(H[l * n + l - 1]);
-        const double dg = cabs2(H[l * n + l]) + cabs2(H[(l - 1) * n + l - 1]);
-        if (off <= eps * (dg > 0.0 ? dg : fro)) {
-          H[l * n + l - 1] = make_double2(0.0, 0.0);
-          break;
-        }
-        --l;
-      }
-      ctl[0] = l;
+    int l = hi;
+    while (l > 0) {
+      const T off = X::abs(H[l * n + l - 1]);
+      const T dg = X::abs(H[l * n + l]) + X::abs(H[(l - 1) * n + l - 1]);
+      if (off <= eps * (dg > T(0) ? dg : fro)) break;
+      --l;
     }
-    __syncthreads();
-    const int l = ctl[0];
+    __syncwarp();
+    if (l > 0 && lane == 0) H[l * n + l - 1] = X::mk(T(0), T(0));
+    __syncwarp();
     if (l == hi) {
       --hi;
       its_here = 0;
-      __syncthreads();
       continue;
     }
     if (++iter > max_iter) {
-      if (tid == 0) atomicExch(status, eig_status(kEigNoConvergence, n, hi));
+      failed = true;
       break;
     }
     ++its_here;
     for (int k = l; k < hi; ++k) {
-      if (tid == 0) {
-        double2 x, y;
-        if (k == l) {
-          // Wilkinson shift: eigenvalue of the trailing 2x2 closest to H[hi][hi]
-          const double2 a = H[(hi - 1) * n + hi - 1], b = H[(hi - 1) * n + hi];
-          const double2 c = H[hi * n + hi - 1], d = H[hi * n + hi];
-          const double2 tr2 = cscale(cadd(a, d), 0.5);
-          const double2 hd = cscale(csub(a, d), 0.5);
-          const double2 disc = csqrt(cadd(cmul(hd, hd), cmul(b, c)));
-          const double2 l1 = cadd(tr2, disc), l2 = csub(tr2, disc);
-          double2 mu = cabs2(csub(l1, d)) < cabs2(csub(l2, d)) ? l1 : l2;
-          if (its_here % 11 == 10 || !isfinite(mu.x) || !isfinite(mu.y)) {  // exceptional shift
-            mu = cadd(d, make_double2(0.75 * cabs2(c), 0.0));
-          }
-          x = csub(H[l * n + l], mu);
-          y = H[(l + 1) * n + l];
-        } else {
-          x = H[k * n + k - 1];
-          y = H[(k + 1) * n + k - 1];
-        }
-        const double ax = cabs2(x), ay = cabs2(y);
-        const double r = hypot(ax, ay);
-        double c;
-        double2 s;
-        if (r == 0.0) {
-          c = 1.0;
-          s = make_double2(0.0, 0.0);
-        } else if (ax == 0.0) {
-          c = 0.0;
-          s = cscale(cconj(y), 1.0 / ay);
-        } else {
-          c = ax / r;
-          s = cscale(cmul(cscale(x, 1.0 / ax), cconj(y)), 1.0 / r);
-        }
-        gcs[0] = make_double2(c, 0.0);
-        gcs[1] = s;
+      V x, y;
+      if (k == l) {
+        // Wilkinson shift: eigenvalue of the trailing 2x2 closest to H[hi][hi]
+        const V a = H[(hi - 1) * n + hi - 1], b = H[(hi - 1) * n + hi];
+        const V c = H[hi * n + hi - 1], d = H[hi * n + hi];
+        const V tr2 = X::scale(X::add(a, d), T(0.5));
+        const V hd = X::scale(X::sub(a, d), T(0.5));
+        const V disc = X::sqrt_(X::add(X::mul(hd, hd), X::mul(b, c)));
+        const V l1 = X::add(tr2, disc), l2 = X::sub(tr2, disc);
+        V mu = X::abs(X::sub(l1, d)) < X::abs(X::sub(l2, d)) ? l1 : l2;
+        if (its_here % 11 == 10 || !isfinite(mu.x) || !isfinite(mu.y))  // exceptional shift
+          mu = X::add(d, X::mk(T(0.75) * X::abs(c), T(0)));
+        x = X::sub(H[l * n + l], mu);
+        y = H[(l + 1) * n + l];
+      } else {
+        x = H[k * n + k - 1];
+        y = H[(k + 1) * n + k - 1];
       }
-      __syncthreads();
-      const double c = gcs[0].x;
-      const double2 s = gcs[1];
+      const T ax = X::abs(x), ay = X::abs(y);
+      const T r = sqrt(ax * ax + ay * ay);
+      T c;
+      V s;
+      if (r == T(0)) {
+        c = T(1);
+        s = X::mk(T(0), T(0));
+      } else if (ax == T(0)) {
+        c = T(0);
+        s = X::scale(X::conj(y), T(1) / ay);
+      } else {
+        c = ax / r;
+        s = X::scale(X::mul(X::scale(x, T(1) / ax), X::conj(y)), T(1) / r);
+      }
+      __syncwarp();  // every lane has read the entries the rotation is built from
       // rows k, k+1 <- G rows
-      for (int j = (k == l ? k : k - 1) + tid; j < n; j += nt) {
-        const double2 a = H[k * n + j], b = H[(k + 1) * n + j];
-        H[k * n + j] = cadd(cscale(a, c), cmul(s, b));
-        H[(k + 1) * n + j] = csub(cscale(b, c), cmul(cconj(s), a));
+      for (int j = (k == l ? k : k - 1) + lane; j < n; j += 32) {
+        const V a = H[k * n + j], b = H[(k + 1) * n + j];
+        H[k * n + j] = X::add(X::scale(a, c), X::mul(s, b));
+        H[(k + 1) * n + j] = X::sub(X::scale(b, c), X::mul(X::conj(s), a));
       }
-      __syncthreads();
-      // columns k, k+1 <- columns G^H (H rows 0..min(k+2,hi), all of Q)
+      __syncwarp();
+      // columns k, k+1 <- columns G^H (H rows 0..min(k+2,hi), all rows of Q)
       const int rmax = min(k + 2, hi);
-      for (int r = tid; r <= rmax + n; r += nt) {
-        double2* row;
-        if (r <= rmax) row = &H[r * n];
-        else row = &Q[size_t(r - rmax - 1) * n];
-        const double2 a = row[k], b = row[k + 1];
-        row[k] = cadd(cscale(a, c), cmul(cconj(s), b));
-        row[k + 1] = csub(cscale(b, c), cmul(s, a));
+      for (int rr = lane; rr <= rmax + n; rr += 32) {
+        V* row = rr <= rmax ? &H[rr * n] : &Q[size_t(rr - rmax - 1) * n];
+        const V a = row[k], b = row[k + 1];
+        row[k] = X::add(X::scale(a, c), X::mul(X::conj(s), b));
+        row[k + 1] = X::sub(X::scale(b, c), X::mul(s, a));
       }
-      __syncthreads();
-      if (k > l && tid == 0) H[(k + 1) * n + k - 1] = make_double2(0.0, 0.0);
-      __syncthreads();
+      __syncwarp();
+      if (k > l && lane == 0) H[(k + 1) * n + k - 1] = X::mk(T(0), T(0));
+      __syncwarp();
     }
   }
-  __syncthreads();
+  if (failed) {
+    if (lane == 0) atomicExch(status, eig_status(kEigNoConvergence, n, hi));
+    return;
+  }
 
   // ---- eigenvectors of T (unit upper triangular X), S = Q X, S^-1 = X^-1 Q^H --
-  const double smin = fmax(eps * fro, tiny);
-  for (int k = tid; k < n; k += nt) {
-    const double2 tk = H[k * n + k];
-    lam[k] = tk;
-    for (int i = 0; i < n; ++i) X[size_t(i) * n + k] = make_double2(i == k ? 1.0 : 0.0, 0.0);
+  const T smin = fmax(eps * fro, tiny);
+  for (int k = lane; k < n; k += 32) {
+    const V tk = H[k * n + k];
+    J.lam[k] = make_double2(double(tk.x), double(tk.y));
+    for (int i = 0; i < n; ++i) Xv[size_t(i) * n + k] = X::mk(i == k ? T(1) : T(0), T(0));
     for (int i = k - 1; i >= 0; --i) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int j = i + 1; j <= k; ++j) acc = cadd(acc, cmul(H[i * n + j], X[size_t(j) * n + k]));
-      double2 den = csub(H[i * n + i], tk);
-      if (cabs2(den) < smin) den = make_double2(smin, 0.0);
-      X[size_t(i) * n + k] = cscale(cdiv(acc, den), -1.0);
+      V acc = X::mk(T(0), T(0));
+      for (int j = i + 1; j <= k; ++j) acc = X::add(acc, X::mul(H[i * n + j], Xv[size_t(j) * n + k]));
+      V den = X::sub(H[i * n + i], tk);
+      if (X::abs(den) < smin) den = X::mk(smin, T(0));
+      Xv[size_t(i) * n + k] = X::scale(X::div(acc, den), T(-1));
     }
   }
-  __syncthreads();
-  for (int k = tid; k < n; k += nt) {
+  __syncwarp();
+  for (int k = lane; k < n; k += 32) {
     // column k of X^-1: unit upper triangular back substitution
-    for (int i = 0; i < n; ++i) Xi[size_t(i) * n + k] = make_double2(i == k ? 1.0 : 0.0, 0.0);
+    for (int i = 0; i < n; ++i) Xi[size_t(i) * n + k] = X::mk(i == k ? T(1) : T(0), T(0));
     for (int i = k - 1; i >= 0; --i) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int j = i + 1; j <= k; ++j) acc = cadd(acc, cmul(X[size_t(i) * n + j], Xi[size_t(j) * n + k]));
-      Xi[size_t(i) * n + k] = cscale(acc, -1.0);
+      V acc = X::mk(T(0), T(0));
+      for (int j = i + 1; j <= k; ++j) acc = X::add(acc, X::mul(Xv[size_t(i) * n + j], Xi[size_t(j) * n + k]));
+      Xi[size_t(i) * n + k] = X::scale(acc, T(-1));
     }
   }
-  __syncthreads();
-  for (size_t t = tid; t < nn; t += nt) {
-    const int i = int(t / n), k = int(t % n);
-    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
-    for (int j = 0; j <= k; ++j) a = cadd(a, cmul(Q[size_t(i) * n + j], X[size_t(j) * n + k]));
-    for (int j = i; j < n; ++j) b = cadd(b, cmul(Xi[size_t(i) * n + j], cconj(Q[size_t(k) * n + j])));
-    S[t] = a;
-    Sinv[t] = b;
+  __syncwarp();
+  for (int t = lane; t < nn; t += 32) {
+    const int i = t / n, k = t % n;
+    V a = X::mk(T(0), T(0)), b = X::mk(T(0), T(0));
+    for (int j = 0; j <= k; ++j) a = X::add(a, X::mul(Q[size_t(i) * n + j], Xv[size_t(j) * n + k]));
+    for (int j = i; j < n; ++j) b = X::add(b, X::mul(Xi[size_t(i) * n + j], X::conj(Q[size_t(k) * n + j])));
+    J.S[t] = make_double2(double(a.x), double(a.y));
+    J.Sinv[t] = make_double2(double(b.x), double(b.y));
   }
+}
+
+template <typename T>
+void launch_t(const EigJob& a, const EigJob& b, int* status, cudaStream_t s) {
+  const int nmax = std::max(a.n, b.n);
+  const size_t smem = (size_t(nmax) * nmax + nmax) * sizeof(typename C2T<T>::type);
+  static bool attr = false;
+  if (!attr) {
+    RTCC3_CUDA(cudaFuncSetAttribute(k_eig_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int((size_t(kEigMaxN) * kEigMaxN + kEigMaxN) *
+                                        sizeof(typename C2T<T>::type))));
+    attr = true;
+  }
+  k_eig_warp<T><<<2, 32, smem, s>>>(a, b, status);
+  RTCC3_CUDA(cudaGetLastError());
 }
 
 }  // namespace
 
-void launch_eig(const double2* M, int n, int count, double2* S, double2* Sinv, double2* lam,
-                double2* ws, int* status, cudaStream_t s) {
-  RTCC3_CHECK(n >= 1 && n <= kEigMaxN, kErrArg, "eigensolver supports n <= " + std::to_string(kEigMaxN));
-  const size_t smem = size_t(n) * n * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    RTCC3_CUDA(cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    int(size_t(kEigMaxN) * kEigMaxN * sizeof(double2))));
-    attr = true;
-  }
-  k_eig<<<count, 256, smem, s>>>(M, n, S, Sinv, lam, ws, status);
-  RTCC3_CUDA(cudaGetLastError());
+void launch_eig(const EigJob& a, const EigJob& b, bool fp32, int* status, cudaStream_t s) {
+  RTCC3_CHECK(a.n >= 1 && a.n <= kEigMaxN && b.n >= 1 && b.n <= kEigMaxN, kErrArg,
+              "eigensolver supports n <= " + std::to_string(kEigMaxN));
+  if (fp32) launch_t<float>(a, b, status, s);
+  else launch_t<double>(a, b, status, s);
 }
 
 }  // namespace rtcc3

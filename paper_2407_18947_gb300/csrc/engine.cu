@@ -456,12 +456,41 @@ void launch_fill(Cx<R>* p, size_t n, double re, double im, cudaStream_t s) {
 
 template <typename R>
 Engine<R>::~Engine() {
+  if (side_) cudaStreamDestroy(side_);
+  if (fork_ev_) cudaEventDestroy(fork_ev_);
+  if (join_ev_) cudaEventDestroy(join_ev_);
   if (pool_) return;  // everything lives in the caller's pool
   for (auto& kv : plans_)
     if (kv.second->dev) cudaFree(kv.second->dev);
   for (int s = 0; s < kScratchSlots; ++s)
     if (scratch_[s]) cudaFree(scratch_[s]);
   if (err_) cudaFree(err_);
+}
+
+template <typename R>
+cudaStream_t Engine<R>::side_stream() {
+  if (pool_) return stream_;
+  if (!side_) {
+    RTCC3_CUDA(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
+    RTCC3_CUDA(cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming));
+    RTCC3_CUDA(cudaEventCreateWithFlags(&join_ev_, cudaEventDisableTiming));
+  }
+  return side_;
+}
+
+template <typename R>
+void Engine<R>::fork() {
+  cudaStream_t s = side_stream();
+  if (s == stream_) return;
+  RTCC3_CUDA(cudaEventRecord(fork_ev_, stream_));
+  RTCC3_CUDA(cudaStreamWaitEvent(s, fork_ev_, 0));
+}
+
+template <typename R>
+void Engine<R>::join() {
+  if (!side_ || pool_) return;
+  RTCC3_CUDA(cudaEventRecord(join_ev_, side_));
+  RTCC3_CUDA(cudaStreamWaitEvent(stream_, join_ev_, 0));
 }
 
 template <typename R>
@@ -740,13 +769,23 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   // tensor-core route: one batch, a large output side and enough work
   // (a short K would make the packed operands cost more traffic than the
   // product saves: those stay on CUDA cores)
-  // (short sums that write a large output stay on the CUDA cores: they are
-  // bound by the output write, which the tensor-core epilogue does not
-  // stream as well, and they keep the connected triples in FP32)
+  // With split TF32 operands (FP32-level products) short sums that write a
+  // large output (outer-product-like, e.g. the connected triples Z) go to
+  // the tensor cores too: their packed operands are small and the product
+  // is bound by the output write.  BF16 keeps them on the CUDA cores (FP32),
+  // so the connected triples stay accurate enough for the amplitude
+  // equations to converge.
+  const long long kp_tc = tc_ok ? 3LL * tc_packed_k(int(K), 4) : 0;
+  const bool long_k = K >= 64 && M * N * K >= (1LL << 21);
+  const bool out_bound = tc_eb_ == 4 && M * N >= (1LL << 22) && M * N >= 2 * (M + 2 * N) * kp_tc;
   if (std::is_same<R, float>::value && tc_ok && NB == 1 && std::max(M, N) >= 128 &&
-      std::min(M, N) >= 4 && K >= 64 && M * N * K >= (1LL << 21)) {
+      std::min(M, N) >= 4 && (long_k || out_bound)) {
     P->use_tc = true;
-    P->tc_swap = N > M;  // the expanded (2x2 real) operand is the smaller one
+    // long sums: the expanded (2x2 real) operand is the smaller one; short
+    // sums: the output's contiguous index goes to the GEMM columns, which
+    // the epilogue stores in runs
+    const bool c_unit_m = !gm.empty() && std::llabs(gm.back().sc) == 1;
+    P->tc_swap = long_k ? (N > M) : c_unit_m;
     const long long Mg = std::max(M, N), Ng = std::min(M, N);
     // TF32 operands are split into hi + lo TF32 parts and the three leading
     // products (hi.hi + hi.lo + lo.hi) are summed by one GEMM over a tripled

@@ -212,6 +212,18 @@ class Engine {
   // a captured CUDA graph recorded under an older generation is stale.
   int generation() const { return generation_; }
   void set_profiler(Profiler* p) { prof_ = p; }
+  // A second stream for independent work (created on first use; with a
+  // caller-owned pool the engine's own stream is used instead), and the
+  // points where it forks from and joins back into the engine's stream (also
+  // valid during stream capture).
+  cudaStream_t side_stream();
+  void fork();
+  void join();
+  int prof_begin(cudaStream_t s) { return prof_ ? prof_->begin(s) : -1; }
+  void prof_end(int k, cudaStream_t s, const char* name, double flops, double bytes) {
+    if (prof_) prof_->end(k, s, name, flops, bytes);
+  }
+  void add_launches(int n) { launches_ += n; }
 
  private:
   Profiler* prof_ = nullptr;
@@ -256,6 +268,8 @@ class Engine {
   int tc_eb_ = 0;
   bool tc_region_ = false;
   int* err_ = nullptr;
+  cudaStream_t side_ = nullptr;
+  cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
   DevicePool* pool_ = nullptr;
   void run_contract_small(ContractPlan& P, double alpha, const C* pa, const C* pb, C* pc,
                           bool accumulate);

@@ -26,11 +26,20 @@ __host__ __device__ constexpr int eig_status(int reason, int n, int row) {
   return kEigStatusBase | (reason << 20) | (n << 10) | row;
 }
 
-// count matrices M[count][n][n] (row-major, complex128) -> S, S^-1 (row-major)
-// and eigenvalues lam[count][n]; ws holds 3 n^2 complex per matrix; *status
-// is raised if the QR sweeps do not converge.
-void launch_eig(const double2* M, int n, int count, double2* S, double2* Sinv, double2* lam,
-                double2* ws, int* status, cudaStream_t s);
+// One matrix M[n][n] (row-major, complex128) -> S, S^-1 (row-major, complex128)
+// and eigenvalues lam[n]; ws holds 3 n^2 complex128 of scratch.
+struct EigJob {
+  const double2* M;
+  int n;
+  double2* S;
+  double2* Sinv;
+  double2* lam;
+  double2* ws;
+};
+// Both matrices of a stage in one launch (one warp each).  fp32: complex64
+// arithmetic (for the complex64 graphs), else complex128.  *status is raised
+// if the QR sweeps do not converge or a matrix is not finite.
+void launch_eig(const EigJob& a, const EigJob& b, bool fp32, int* status, cudaStream_t s);
 
 // O (o x o) and V (v x v) of the current stage from the dressed perturbation w~
 // (n x n, compute precision) and the orbital energies.

@@ -14,45 +14,67 @@
 
 namespace rtcc3 {
 
-// Triples with the field coupling in the field-dressed eigenbasis (see
-// rotation.h).  Forward: decompose O and V of this stage, rotate the inputs
-// of W and of the source 1/2[[V~,T2],T2], divide by the complex denominators,
-// form X1 and X2 in the rotated basis and rotate them back.  The rotations
-// are constants of the tape (A^-1 does not depend on the choice of
-// eigenbasis); the dependence of A on v~ is added by a custom adjoint: with
-// y' = grad(t3') / D', grad(v~_vv) -= S_v^-T D'_vv S_v^T and
-// grad(v~_oo) += S_o D'_oo S_o^-1, the slot densities D' of y' and t3'
-// (the triples density terms of Eqs. A31-A32 in the rotated basis).
-// Returns the node of t3' and accumulates into R1 and SD.
-template <typename R, typename BlkFn>
-int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, int g, int ft,
-                    const View& R1, const View& SD, BlkFn&& blk) {
+// Field-dressed eigenbasis of one stage (see rotation.h): O and V are built
+// from the dressed perturbation and decomposed on the engine's side stream,
+// overlapping the CCSD part of the stage; rotated_triples joins before use.
+struct FieldBasis {
+  int So = -1, Sio = -1, Sv = -1, Siv = -1;  // S and S^-1 (compute precision)
+  double2* osum = nullptr;                   // eigenvalue sums (complex128)
+  double2* vsum = nullptr;
+};
+
+template <typename R>
+FieldBasis start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt) {
   const int o = H.o, v = H.v;
-  const cudaStream_t st = E.stream();
-  // ---- eigendecomposition of O and V (FP64) ------------------------------------
   Arena& A = E.arena();
-  double2* Mo = static_cast<double2*>(A.alloc(sizeof(double2) * o * o));
-  double2* Mv = static_cast<double2*>(A.alloc(sizeof(double2) * v * v));
-  double2* So64 = static_cast<double2*>(A.alloc(sizeof(double2) * o * o));
-  double2* Sio64 = static_cast<double2*>(A.alloc(sizeof(double2) * o * o));
-  double2* Sv64 = static_cast<double2*>(A.alloc(sizeof(double2) * v * v));
-  double2* Siv64 = static_cast<double2*>(A.alloc(sizeof(double2) * v * v));
-  double2* lo = static_cast<double2*>(A.alloc(sizeof(double2) * o));
-  double2* lv = static_cast<double2*>(A.alloc(sizeof(double2) * v));
-  double2* wso = static_cast<double2*>(A.alloc(sizeof(double2) * 3 * o * o));
-  double2* wsv = static_cast<double2*>(A.alloc(sizeof(double2) * 3 * v * v));
-  double2* osum = static_cast<double2*>(A.alloc(sizeof(double2) * o * o * o));
-  double2* vsum = static_cast<double2*>(A.alloc(sizeof(double2) * v * v * v));
-  launch_field_matrices<R>(E.data(wt), H.eps, o, v, Mo, Mv, st);
-  launch_eig(Mo, o, 1, So64, Sio64, lo, wso, E.error_flag(), st);
-  launch_eig(Mv, v, 1, Sv64, Siv64, lv, wsv, E.error_flag(), st);
-  launch_lambda_sums(lo, lv, o, v, osum, vsum, st);
-  const int So = E.node({o, o}, false, false), Sio = E.node({o, o}, false, false);
-  const int Sv = E.node({v, v}, false, false), Siv = E.node({v, v}, false, false);
-  launch_to_precision<R>(So64, E.data(So), size_t(o) * o, st);
-  launch_to_precision<R>(Sio64, E.data(Sio), size_t(o) * o, st);
-  launch_to_precision<R>(Sv64, E.data(Sv), size_t(v) * v, st);
-  launch_to_precision<R>(Siv64, E.data(Siv), size_t(v) * v, st);
+  auto c2 = [&](size_t n) { return static_cast<double2*>(A.alloc(sizeof(double2) * n)); };
+  double2 *Mo = c2(size_t(o) * o), *Mv = c2(size_t(v) * v);
+  double2 *So64 = c2(size_t(o) * o), *Sio64 = c2(size_t(o) * o);
+  double2 *Sv64 = c2(size_t(v) * v), *Siv64 = c2(size_t(v) * v);
+  double2 *lo = c2(o), *lv = c2(v);
+  double2 *wso = c2(3 * size_t(o) * o), *wsv = c2(3 * size_t(v) * v);
+  FieldBasis B;
+  B.osum = c2(size_t(o) * o * o);
+  B.vsum = c2(size_t(v) * v * v);
+  B.So = E.node({o, o}, false, false);
+  B.Sio = E.node({o, o}, false, false);
+  B.Sv = E.node({v, v}, false, false);
+  B.Siv = E.node({v, v}, false, false);
+  int* status = E.error_flag();
+  E.fork();
+  const cudaStream_t ss = E.side_stream();
+  const int pk = E.prof_begin(ss);
+  launch_field_matrices<R>(E.data(wt), H.eps, o, v, Mo, Mv, ss);
+  const EigJob jo{Mo, o, So64, Sio64, lo, wso}, jv{Mv, v, Sv64, Siv64, lv, wsv};
+  launch_eig(jo, jv, sizeof(R) == 4, status, ss);
+  launch_lambda_sums(lo, lv, o, v, B.osum, B.vsum, ss);
+  launch_to_precision<R>(So64, E.data(B.So), size_t(o) * o, ss);
+  launch_to_precision<R>(Sio64, E.data(B.Sio), size_t(o) * o, ss);
+  launch_to_precision<R>(Sv64, E.data(B.Sv), size_t(v) * v, ss);
+  launch_to_precision<R>(Siv64, E.data(B.Siv), size_t(v) * v, ss);
+  E.prof_end(pk, ss, "field_eig", 0.0, 0.0);
+  E.add_launches(7);
+  return B;
+}
+
+// Triples with the field coupling in the field-dressed eigenbasis (see
+// rotation.h).  Forward: with the eigenbasis of O and V of this stage (from
+// start_field_basis), rotate the inputs of W and of the source
+// 1/2[[V~,T2],T2], divide by the complex denominators, form X1 and X2 in the
+// rotated basis and rotate them back.  The rotations are constants of the
+// tape (A^-1 does not depend on the choice of eigenbasis); the dependence of
+// A on v~ is added by a custom adjoint: with y' = grad(t3') / D',
+// grad(v~_vv) -= S_v^-T D'_vv S_v^T and grad(v~_oo) += S_o D'_oo S_o^-1, the
+// slot densities D' of y' and t3' (the triples density terms of Eqs. A31-A32
+// in the rotated basis).  Returns the node of t3' and accumulates into R1 and SD.
+template <typename R, typename BlkFn>
+int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, const FieldBasis& B,
+                    int g, int ft, const View& R1, const View& SD, BlkFn&& blk) {
+  const int o = H.o, v = H.v;
+  E.join();
+  const double2* osum = B.osum;
+  const double2* vsum = B.vsum;
+  const int So = B.So, Sio = B.Sio, Sv = B.Sv, Siv = B.Siv;
   const View SO = E.v(So), SIO = E.v(Sio), SV = E.v(Sv), SIV = E.v(Siv);
   auto G = [&](const char* b) { return blk(g, b); };
   // rotate one index of a 4-index tensor: spec like "Ii,ijae->Ijae"
@@ -267,6 +289,9 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   const int wX = E.node({n, n}), wt = E.node({n, n});
   E.contract("pr,rs->ps", 1.0, E.v(X), E.v(S.w), E.v(wX), true);
   E.contract("ps,sq->pq", 1.0, E.v(wX), E.v(Y), E.v(wt), true);
+  // the field-dressed eigenbasis only needs w~: start it now, beside the CCSD part
+  FieldBasis fb;
+  if (opt.triples && opt.field_terms && opt.rotation) fb = start_field_basis(E, H, wt);
   const int g = E.node({n, n, n, n});
   E.contract("Ppq,Prs->pqrs", 1.0, E.v(Lt), E.v(Lt), E.v(g), true);
   // f~ = h~ + sum_k 2 g~_pqkk - g~_pkkq
@@ -334,7 +359,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   // ---- triples ---------------------------------------------------------------
   if (opt.triples && opt.field_terms && opt.rotation) {
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores
-    S.t3 = rotated_triples(E, H, T, wt, g, ft, R1, SD, blk);
+    S.t3 = rotated_triples(E, H, T, wt, fb, g, ft, R1, SD, blk);
     E.set_tc_region(false);
   } else if (opt.triples) {
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores

@@ -3,10 +3,10 @@
 // One CTA computes a 128 x BN tile of the real product Apack (M x Kp) times
 // Bpack^T (Nr x Kp), both K-major, staged by TMA (128-byte swizzle) through a
 // 4-deep shared-memory ring.  Warp 0 issues the TMA loads, warp 1 allocates
-// tensor memory and issues tcgen05.mma (one elected thread), warps 2-5 read
+// tensor memory and issues tcgen05.mma (one elected thread), warps 2-9 read
 // the FP32 accumulator back with tcgen05.ld and write the complex result
-// (coalesced through a per-warp shared-memory transpose) or FP32 split-K
-// partials.  Every mbarrier wait is bounded by a clock budget; on expiry the
+// (coalesced through a per-warp shared-memory transpose, 16 stores in flight
+// per warp) or FP32 split-K partials.  Every mbarrier wait is bounded by a clock budget; on expiry the
 // kernel raises *err and winds down, releasing its tensor memory.
 #include "tc_gemm.h"
 
@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kStages = 4;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -126,8 +126,9 @@ struct TcSmem {
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kBarOff = kStages * kStageBytes;
   static constexpr int kStageOutOff = kBarOff + 256;
-  static constexpr int kStageOutBytes = 4 * 32 * 33 * 4;
+  static constexpr int kStageOutBytes = 8 * 32 * 33 * 4;
   static constexpr int kTotal = kStageOutOff + kStageOutBytes + 1024;  // + alignment slack
+  static_assert(kTotal <= 232448, "shared memory per CTA");
 };
 
 template <int BN, bool BF16>
@@ -211,15 +212,18 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       mma_commit(smem_u32(done));
     }
   } else {
-    // epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
-    const int q = warp & 3;
+    // epilogue: warps 2..9, two per TMEM lane quarter (warp % 4), each taking
+    // every other 32-column chunk
+    const int q = warp & 3, ew = warp - 2, half = ew >> 2;
     ok = (nkb == 0) ? true : mbar_wait(smem_u32(done), 0);
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float* st = stage_out + (warp - 2) * 32 * 33;
+    float* st = stage_out + ew * 32 * 33;
     const int row = q * 32 + lane;
     const int m = m0 + row;
-    for (int c0 = 0; c0 < BN && ok; c0 += 32) {
+    // output row offsets of this warp's 32 rows, one per lane
+    const long long cm_lane = (!partial && m < M) ? cM[m] : 0;
+    for (int c0 = 32 * half; c0 < BN && ok; c0 += 64) {
       uint32_t r[32];
       if (nkb > 0) {
         tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c0), r);
@@ -245,19 +249,31 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const int n = (n0 + c0) / 2 + jc;
       const bool ncol = (2 * n) < Nr;
       const long long cn = ncol ? cN[n] : 0;
-      for (int rr = rh; rr < 32; rr += 2) {
-        const int mm = m0 + q * 32 + rr;
-        if (mm < M && ncol) {
-          float2 val = make_float2(alpha * st[rr * 33 + 2 * jc], alpha * st[rr * 33 + 2 * jc + 1]);
-          const long long idx = coff + cM[mm] + cn;
-          if (accumulate) {
-            const float2 old = C[idx];
-            val.x += old.x;
-            val.y += old.y;
-          }
-          C[idx] = val;
+      // all addresses and values first, then (for accumulation) all loads,
+      // then all stores: the warp keeps 16 memory operations in flight
+      long long idx[16];
+      float2 val[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int rr = rh + 2 * u;
+        const long long cmr = __shfl_sync(0xffffffffu, cm_lane, rr);
+        const bool in = ncol && (m0 + q * 32 + rr < M);
+        idx[u] = in ? coff + cmr + cn : -1;
+        val[u] = make_float2(alpha * st[rr * 33 + 2 * jc], alpha * st[rr * 33 + 2 * jc + 1]);
+      }
+      if (accumulate) {
+        float2 old[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) old[u] = idx[u] >= 0 ? C[idx[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          val[u].x += old[u].x;
+          val[u].y += old[u].y;
         }
       }
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (idx[u] >= 0) C[idx[u]] = val[u];
       __syncwarp();
     }
   }
