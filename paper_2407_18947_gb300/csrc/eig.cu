@@ -65,8 +65,11 @@ __device__ __forceinline__ T warp_sum(T v) {
   return __shfl_sync(0xffffffffu, v, 0);
 }
 
+// level: 2 = H, Q, X and X^-1 in shared memory, 1 = H and Q, 0 = H only (the
+// rest in the workspace).
 template <typename T>
-__global__ void __launch_bounds__(32) k_eig_warp(EigJob ja, EigJob jb, int* __restrict__ status) {
+__global__ void __launch_bounds__(32) k_eig_warp(EigJob ja, EigJob jb, int level,
+                                                 int* __restrict__ status) {
   using X = Cplx<T>;
   using V = typename C2T<T>::type;
   const EigJob J = blockIdx.x == 0 ? ja : jb;
@@ -74,12 +77,13 @@ __global__ void __launch_bounds__(32) k_eig_warp(EigJob ja, EigJob jb, int* __re
   if (n <= 0) return;
   const int lane = threadIdx.x;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  V* H = reinterpret_cast<V*>(sm_raw);  // n x n, row-major
-  V* vb = H + size_t(n) * n;            // Householder vector
-  V* Q = reinterpret_cast<V*>(J.ws);
-  V* Xv = Q + size_t(n) * n;
-  V* Xi = Xv + size_t(n) * n;
   const int nn = n * n;
+  V* H = reinterpret_cast<V*>(sm_raw);  // n x n, row-major
+  V* vb = H + nn;                       // Householder vector
+  V* wsv = reinterpret_cast<V*>(J.ws);
+  V* Q = level >= 1 ? vb + n : wsv;
+  V* Xv = level >= 2 ? Q + nn : wsv + nn;
+  V* Xi = Xv + nn;
   T fro = T(0);
   for (int t = lane; t < nn; t += 32) {
     const double2 m = J.M[t];
@@ -258,16 +262,25 @@ __global__ void __launch_bounds__(32) k_eig_warp(EigJob ja, EigJob jb, int* __re
 
 template <typename T>
 void launch_t(const EigJob& a, const EigJob& b, int* status, cudaStream_t s) {
-  const int nmax = std::max(a.n, b.n);
-  const size_t smem = (size_t(nmax) * nmax + nmax) * sizeof(typename C2T<T>::type);
+  constexpr size_t kMaxSmem = 200 * 1024;
+  const size_t nmax = size_t(std::max(a.n, b.n));
+  const size_t vs = sizeof(typename C2T<T>::type);
+  int level = 0;
+  size_t smem = (nmax * nmax + nmax) * vs;
+  if ((4 * nmax * nmax + nmax) * vs <= kMaxSmem) {
+    level = 2;
+    smem = (4 * nmax * nmax + nmax) * vs;
+  } else if ((2 * nmax * nmax + nmax) * vs <= kMaxSmem) {
+    level = 1;
+    smem = (2 * nmax * nmax + nmax) * vs;
+  }
   static bool attr = false;
   if (!attr) {
     RTCC3_CUDA(cudaFuncSetAttribute(k_eig_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    int((size_t(kEigMaxN) * kEigMaxN + kEigMaxN) *
-                                        sizeof(typename C2T<T>::type))));
+                                    int(kMaxSmem)));
     attr = true;
   }
-  k_eig_warp<T><<<2, 32, smem, s>>>(a, b, status);
+  k_eig_warp<T><<<2, 32, smem, s>>>(a, b, level, status);
   RTCC3_CUDA(cudaGetLastError());
 }
 

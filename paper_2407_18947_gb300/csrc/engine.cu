@@ -17,6 +17,22 @@ constexpr int kBM = 64, kBN = 64, kBK = 16, kThreads = 256;
 constexpr int kSBM = 16, kSBK = 64;  // small-tile variant
 constexpr int kTBK = 8;               // thin (16 x 256) tiles
 
+// Division of 32-bit n < 2^31 by an invariant d >= 1 with one multiply-high
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994; round-up variant): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l.
+struct FastDiv {
+  unsigned d = 1, m = 1;
+  int l = 0;
+  FastDiv() = default;
+  explicit FastDiv(unsigned dv) : d(dv) {
+    l = 0;
+    while ((1ull << l) < dv) ++l;
+    m = unsigned(((1ull << 32) * ((1ull << l) - dv)) / dv + 1);
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(n, m) + n) >> l; }
+};
+
 struct EpsArgs {
   int sign[kMaxDim];
   int base[kMaxDim];
@@ -71,19 +87,27 @@ __global__ void k_div_eps_dense6(const Cx<R>* __restrict__ X, Cx<R>* __restrict_
 // denominator D[ijk abc] = vsum[abc] - osum[ijk] (FP64 sums; complex sums
 // when CPLX).  D is invariant under those permutations, so the same kernel
 // is its own adjoint.
+struct Sym6Div {
+  FastDiv v3, o2, o, v2, v;
+};
+
 template <typename R, typename I, bool CPLX>
 __global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx,
                            long long offy, const double* __restrict__ osum,
                            const double* __restrict__ vsum, const double2* __restrict__ osum_c,
                            const double2* __restrict__ vsum_c, int o, int v, I n, R alpha,
-                           int overwrite) {
+                           int overwrite, const Sym6Div fd) {
   const I v2 = I(v) * v, v3 = v2 * v, o2 = I(o) * o;
   const Cx<R>* Xb = X + offx;
+  auto dv = [&](I x, const FastDiv& f, I d) -> I {
+    if constexpr (sizeof(I) == 4) return I(f.div(unsigned(x)));
+    else return x / d;
+  };
   for (I t = I(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += I(gridDim.x) * blockDim.x) {
-    const I ijk = t / v3;
+    const I ijk = dv(t, fd.v3, v3);
     const I abc = t - ijk * v3;
-    const I i = ijk / o2, jk = ijk - i * o2, j = jk / o, k = jk - j * o;
-    const I a = abc / v2, bc = abc - a * v2, b = bc / v, c = bc - b * v;
+    const I i = dv(ijk, fd.o2, o2), jk = ijk - i * o2, j = dv(jk, fd.o, I(o)), k = jk - j * o;
+    const I a = dv(abc, fd.v2, v2), bc = abc - a * v2, b = dv(bc, fd.v, I(v)), c = bc - b * v;
     auto O = [&](I x, I y, I z) { return ((x * o + y) * o + z) * v3; };
     auto V = [&](I x, I y, I z) { return (x * v + y) * v + z; };
     const Cx<R> x0 = Xb[O(i, j, k) + V(a, b, c)];
@@ -319,6 +343,7 @@ template <typename R>
 struct CombDesc {
   int nd, nsrc, overwrite;
   int shape[kMaxDim];
+  FastDiv fd[kMaxDim];  // divisors of the extents (32-bit index path)
   long long sy[kMaxDim];
   long long sx[kMaxSrc][kMaxDim];
   long long offy;
@@ -337,8 +362,11 @@ __global__ void k_combine(Cx<R>* __restrict__ Y, const CombDesc<R> d, I n) {
     for (int s = 0; s < kMaxSrc; ++s) ox[s] = d.offx[s];
     for (int k = d.nd - 1; k >= 0; --k) {
       const I sh = I(d.shape[k]);
-      const I i = rem % sh;
-      rem /= sh;
+      I q;
+      if constexpr (sizeof(I) == 4) q = I(d.fd[k].div(unsigned(rem)));
+      else q = rem / sh;
+      const I i = rem - q * sh;
+      rem = q;
       oy += (long long)i * d.sy[k];
 #pragma unroll
       for (int s = 0; s < kMaxSrc; ++s)
@@ -775,7 +803,7 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   // is bound by the output write.  BF16 keeps them on the CUDA cores (FP32),
   // so the connected triples stay accurate enough for the amplitude
   // equations to converge.
-  const long long kp_tc = tc_ok ? 3LL * tc_packed_k(int(K), 4) : 0;
+  const long long kp_tc = tc_ok ? 2LL * tc_packed_k(int(K), 4) : 0;
   const bool long_k = K >= 64 && M * N * K >= (1LL << 21);
   const bool out_bound = tc_eb_ == 4 && M * N >= (1LL << 22) && M * N >= 2 * (M + 2 * N) * kp_tc;
   if (std::is_same<R, float>::value && tc_ok && NB == 1 && std::max(M, N) >= 128 &&
@@ -788,10 +816,9 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
     P->tc_swap = long_k ? (N > M) : c_unit_m;
     const long long Mg = std::max(M, N), Ng = std::min(M, N);
     // TF32 operands are split into hi + lo TF32 parts and the three leading
-    // products (hi.hi + hi.lo + lo.hi) are summed by one GEMM over a tripled
-    // K: FP32-level accuracy at three times the tensor work
-    const int segs = tc_eb_ == 4 ? 3 : 1;
-    P->tc_kp = segs * tc_packed_k(int(K), tc_eb_);
+    // products (hi.hi + hi.lo + lo.hi) are summed by the GEMM: FP32-level
+    // accuracy at three times the tensor work
+    P->tc_kp = tc_packed_k(int(K), tc_eb_);
     const int nkb = P->tc_kp / (128 / tc_eb_);
     const long long nr = 2 * Ng;
     const long long bn = nr >= 192 ? 256 : (nr >= 96 ? 128 : 64);
@@ -918,6 +945,7 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     op.K = P.K;
     op.Kp = P.tc_kp;
     op.elem_bytes = tc_eb_;
+    op.split = tc_eb_ == 4;
     const float2* ga = sw ? pb : pa;
     const float2* gb = sw ? pa : pb;
     const long long* gaM = sw ? P.bN : P.aM;
@@ -929,18 +957,17 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     const long long goa = sw ? P.b_off0 : P.a_off0;
     const long long gob = sw ? P.a_off0 : P.b_off0;
     void* apk = scratch(1, size_t(op.M) * op.Kp * tc_eb_);
-    void* bpk = scratch(2, size_t(2 * op.N) * op.Kp * tc_eb_);
+    void* bpk = scratch(2, size_t(2 * op.N) * op.Kp * tc_eb_ * (op.split ? 2 : 1));
     float* part = nullptr;
     if (P.tc_nsplit > 1)
       part = static_cast<float*>(scratch(3, size_t(P.tc_nsplit) * op.M * 2 * op.N * sizeof(float)));
     int* err = error_flag();
     const double pbytes = double(op.M + 2.0 * op.N) * op.K * 2.0 * sizeof(float);
     int pk = pbegin();
-    const int segs = tc_eb_ == 4 ? 3 : 1;
-    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, segs, tc_eb_, sw ? P.b_kcontig : P.a_kcontig,
-              apk, stream_);
-    tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, segs, tc_eb_, sw ? P.a_kcontig : P.b_kcontig,
-              bpk, stream_);
+    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, tc_eb_, sw ? P.b_kcontig : P.a_kcontig, apk,
+              stream_);
+    tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, tc_eb_, sw ? P.a_kcontig : P.b_kcontig, bpk,
+              stream_);
     pend(pk, "tc_pack", 0.0, pbytes + double(op.M + 2.0 * op.N) * op.Kp * tc_eb_, cur_detail_);
     launches_ += 2;
     pk = pbegin();
@@ -1036,6 +1063,7 @@ void Engine<R>::run_combine(const View* xs, const bool* xg, const double* alphas
   d.nd = w;
   for (int k = 0; k < w; ++k) {
     d.shape[k] = shape[k];
+    d.fd[k] = FastDiv(unsigned(shape[k]));
     d.sy[k] = sy[k];
     for (int s = 0; s < ns; ++s) d.sx[s][k] = sx[s][k];
   }
@@ -1118,10 +1146,19 @@ void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec
   const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
   const int pk = pbegin();
+  Sym6Div fd;
+  if (n < (size_t(1) << 31)) {
+    const unsigned vv = unsigned(es.v);
+    fd.v3 = FastDiv(vv * vv * vv);
+    fd.o2 = FastDiv(unsigned(es.o) * unsigned(es.o));
+    fd.o = FastDiv(unsigned(es.o));
+    fd.v2 = FastDiv(vv * vv);
+    fd.v = FastDiv(vv);
+  }
 #define RTCC3_S6D(I, CP)                                                                       \
   k_sym6_div<R, I, CP><<<grid_for(n), 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum, es.vsum, \
                                                          es.osum_c, es.vsum_c, es.o, es.v, I(n), \
-                                                         R(alpha), overwrite ? 1 : 0)
+                                                         R(alpha), overwrite ? 1 : 0, fd)
   if (n < (size_t(1) << 31)) {
     if (cplx) RTCC3_S6D(unsigned, true);
     else RTCC3_S6D(unsigned, false);

@@ -2,11 +2,13 @@
 //
 // One CTA computes a 128 x BN tile of the real product Apack (M x Kp) times
 // Bpack^T (Nr x Kp), both K-major, staged by TMA (128-byte swizzle) through a
-// 4-deep shared-memory ring.  Warp 0 issues the TMA loads, warp 1 allocates
-// tensor memory and issues tcgen05.mma (one elected thread), warps 2-9 read
-// the FP32 accumulator back with tcgen05.ld and write the complex result
-// (coalesced through a per-warp shared-memory transpose, 16 stores in flight
-// per warp) or FP32 split-K partials.  Every mbarrier wait is bounded by a clock budget; on expiry the
+// shared-memory ring of 2-4 stages.  Warp 0 issues the TMA loads, warp 1
+// allocates tensor memory and issues tcgen05.mma (one elected thread), warps
+// 2-9 first split each TF32 A tile into hi + lo parts in shared memory (the
+// MMA warp then issues hi.hi, hi.lo and lo.hi) and afterwards read the FP32
+// accumulator back with tcgen05.ld and write the complex result (coalesced
+// through a per-warp shared-memory transpose, 16 stores in flight per warp)
+// or FP32 split-K partials.  Every mbarrier wait is bounded by a clock budget; on expiry the
 // kernel raises *err and winds down, releasing its tensor memory.
 #include "tc_gemm.h"
 
@@ -21,7 +23,6 @@ namespace rtcc3 {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kStages = 4;
 constexpr int kThreads = 320;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
 
@@ -42,6 +43,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (ok) return true;
     if (clock64() - t0 > kWaitBudget) return false;
   }
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -119,32 +130,43 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int BN>
+// Shared-memory plan of one CTA.  SPLIT (TF32 with a hi + lo split done in
+// shared memory): A arrives as raw FP32 and a second A buffer takes the low
+// parts; B arrives pre-split as [hi | lo] K halves.  The ring depth fills
+// 192 KB.
+template <int BN, bool SPLIT>
 struct TcSmem {
   static constexpr int kABytes = kBM * 128;
+  static constexpr int kALoBytes = SPLIT ? kBM * 128 : 0;
   static constexpr int kBBytes = BN * 128;
-  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kBLoBytes = SPLIT ? BN * 128 : 0;
+  static constexpr int kStageBytes = kABytes + kALoBytes + kBBytes + kBLoBytes;
+  static constexpr int kTmaBytes = kABytes + kBBytes + kBLoBytes;  // bytes the TMA delivers
+  static constexpr int kStages = 196608 / kStageBytes < 4 ? 196608 / kStageBytes : 4;
   static constexpr int kBarOff = kStages * kStageBytes;
   static constexpr int kStageOutOff = kBarOff + 256;
   static constexpr int kStageOutBytes = 8 * 32 * 33 * 4;
   static constexpr int kTotal = kStageOutOff + kStageOutBytes + 1024;  // + alignment slack
+  static_assert(kStages >= 2, "ring depth");
   static_assert(kTotal <= 232448, "shared memory per CTA");
 };
 
-template <int BN, bool BF16>
+template <int BN, bool BF16, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          int M, int Nr, int nkb_total, int kb_per_split, float2* __restrict__ C,
+          int M, int Nr, int nkb_total, int kb_per_split, int kb_lo, float2* __restrict__ C,
           const long long* __restrict__ cM, const long long* __restrict__ cN, long long coff,
           float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err) {
-  using L = TcSmem<BN>;
+  using L = TcSmem<BN, SPLIT>;
+  constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
-  uint64_t* done = bars + 2 * kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  uint64_t* conv = bars + 2 * kStages;  // SPLIT: low parts of A written
+  uint64_t* done = bars + 3 * kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 1);
   float* stage_out = reinterpret_cast<float*>(smem + L::kStageOutOff);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -158,6 +180,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     for (int s = 0; s < kStages; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&conv[s]), 8);  // one arrival per converter warp
     }
     mbar_init(smem_u32(done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -182,11 +205,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (i >= kStages) ok = mbar_wait(smem_u32(&empty[s]), ((i / kStages) - 1) & 1);
         if (!ok) break;
         const uint32_t fb = smem_u32(&full[s]);
-        mbar_expect_tx(fb, L::kStageBytes);
+        mbar_expect_tx(fb, L::kTmaBytes);
         uint8_t* sa = smem + s * L::kStageBytes;
+        uint8_t* sb = sa + L::kABytes + L::kALoBytes;
         const int kx = (kb0 + i) * kElemPerK;
         tma_load_2d(smem_u32(sa), &tmA, kx, m0, fb);
-        tma_load_2d(smem_u32(sa + L::kABytes), &tmB, kx, n0, fb);
+        tma_load_2d(smem_u32(sb), &tmB, kx, n0, fb);
+        if (SPLIT) tma_load_2d(smem_u32(sb + L::kBBytes), &tmB, kx + kb_lo * kElemPerK, n0, fb);
       }
       // drain: wait until the MMAs that read the last stages are done so no
       // copy into this CTA's shared memory is outstanding at exit
@@ -198,24 +223,58 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       constexpr uint32_t idesc = instr_desc<BF16>(kBM, BN);
       for (int i = 0; i < nkb && ok; ++i) {
         const int s = i % kStages;
-        ok = mbar_wait(smem_u32(&full[s]), (i / kStages) & 1);
+        ok = mbar_wait(smem_u32(SPLIT ? &conv[s] : &full[s]), (i / kStages) & 1);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t sa = smem_u32(smem + s * L::kStageBytes);
-        const uint32_t sb = sa + L::kABytes;
+        const uint32_t sb = sa + L::kABytes + L::kALoBytes;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma<BF16>(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc,
-                    (i > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+          mma<BF16>(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, acc);
+          if (SPLIT) {
+            // hi.lo and lo.hi: the leading corrections of the split product
+            mma<BF16>(tmem, smem_desc(sa + kk * 32), smem_desc(sb + L::kBBytes + kk * 32), idesc, 1u);
+            mma<BF16>(tmem, smem_desc(sa + L::kABytes + kk * 32), smem_desc(sb + kk * 32), idesc, 1u);
+          }
+        }
         mma_commit(smem_u32(&empty[s]));
       }
       mma_commit(smem_u32(done));
     }
   } else {
+    if (SPLIT) {
+      // converters (warps 2..9) while the main loop runs: A tile -> TF32 hi in
+      // place, the remainder x - hi into the low buffer (same offsets, so the
+      // swizzled layout is kept), then a proxy fence for the tensor cores
+      const int ct = threadIdx.x - 64;  // 0..255
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int s = i % kStages;
+        ok = mbar_wait(smem_u32(&full[s]), (i / kStages) & 1);
+        if (!ok) break;
+        float4* ah = reinterpret_cast<float4*>(smem + s * L::kStageBytes);
+        float4* al = reinterpret_cast<float4*>(smem + s * L::kStageBytes + L::kABytes);
+#pragma unroll
+        for (int u = 0; u < L::kABytes / 16 / 256; ++u) {
+          const int e = ct + 256 * u;
+          const float4 x = ah[e];
+          float4 h, lo;
+          h.x = __uint_as_float(to_tf32(x.x)); lo.x = x.x - h.x;
+          h.y = __uint_as_float(to_tf32(x.y)); lo.y = x.y - h.y;
+          h.z = __uint_as_float(to_tf32(x.z)); lo.z = x.z - h.z;
+          h.w = __uint_as_float(to_tf32(x.w)); lo.w = x.w - h.w;
+          ah[e] = h;
+          al[e] = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&conv[s]));
+      }
+    }
     // epilogue: warps 2..9, two per TMEM lane quarter (warp % 4), each taking
     // every other 32-column chunk
     const int q = warp & 3, ew = warp - 2, half = ew >> 2;
-    ok = (nkb == 0) ? true : mbar_wait(smem_u32(done), 0);
+    ok = ok && ((nkb == 0) ? true : mbar_wait(smem_u32(done), 0));
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float* st = stage_out + ew * 32 * 33;
@@ -288,11 +347,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
 }
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
 
 // One thread per complex source element: its (re, im) pair is written to
 // every K segment (and, for B, to both rows of its 2x2 embedding) with one
@@ -314,6 +368,9 @@ __device__ __forceinline__ void put_pair(void* out, size_t idx, float x, float y
 // the source is read with consecutive threads on its contiguous index (k when
 // KFAST, else the row), the packed rows are written with consecutive threads
 // along k.  B rows expand to the two rows of their 2x2 real embedding.
+// TF32 (EB 4): A is written as raw FP32 (split into hi + lo in the GEMM's
+// shared memory) and B as two K segments [hi | lo]; BF16 (EB 2): one
+// segment, rounded to nearest even.
 template <int EB, bool KFAST, bool IS_B>
 __global__ void __launch_bounds__(256)
 k_pack(const float2* __restrict__ X, const long long* __restrict__ xR, const long long* __restrict__ xK,
@@ -337,26 +394,18 @@ k_pack(const float2* __restrict__ X, const long long* __restrict__ xR, const lon
     const float2 v = tile[rr][lane];
     const size_t row = (IS_B ? size_t(2 * r) : size_t(r)) * Kp + 2 * size_t(k);
     if (!IS_B) {
-      if (segs == 3) {
-        const float hx = __uint_as_float(to_tf32(v.x)), hy = __uint_as_float(to_tf32(v.y));
-        put_pair<EB>(out, row, hx, hy);
-        put_pair<EB>(out, row + seg_w, hx, hy);
-        put_pair<EB>(out, row + 2 * seg_w, v.x - hx, v.y - hy);
-      } else {
-        put_pair<EB>(out, row, v.x, v.y);
-      }
+      if (EB == 4) *reinterpret_cast<float2*>(static_cast<float*>(out) + row) = v;  // raw FP32
+      else put_pair<EB>(out, row, v.x, v.y);
     } else {
       // row 2n: (Br, -Bi); row 2n+1: (Bi, Br) along (re, im) of K
       const size_t r1 = row + Kp;
-      if (segs == 3) {
+      if (EB == 4) {
         const float hx = __uint_as_float(to_tf32(v.x)), hy = __uint_as_float(to_tf32(v.y));
         const float lx = v.x - hx, ly = v.y - hy;
         put_pair<EB>(out, row, hx, -hy);
         put_pair<EB>(out, r1, hy, hx);
         put_pair<EB>(out, row + seg_w, lx, -ly);
         put_pair<EB>(out, r1 + seg_w, ly, lx);
-        put_pair<EB>(out, row + 2 * seg_w, hx, -hy);
-        put_pair<EB>(out, r1 + 2 * seg_w, hy, hx);
       } else {
         put_pair<EB>(out, row, v.x, -v.y);
         put_pair<EB>(out, r1, v.y, v.x);
@@ -438,22 +487,23 @@ bool make_map(CUtensorMap* map, const void* base, int elem_bytes, int Kp, int ro
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, bool BF16>
+template <int BN, bool BF16, bool SPLIT>
 void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, float2* C,
             const long long* cM, const long long* cN, long long coff, float alpha, bool accumulate,
             int nsplit, float* partial, int* err, cudaStream_t s) {
+  using L = TcSmem<BN, SPLIT>;
   static bool attr = false;
   if (!attr) {
-    RTCC3_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    TcSmem<BN>::kTotal));
+    RTCC3_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, BF16, SPLIT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal));
     attr = true;
   }
   const int Nr = 2 * op.N;
   const int nkb = op.Kp / (128 / op.elem_bytes);
   const int per = (nkb + nsplit - 1) / nsplit;
   dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, nsplit);
-  k_tc_gemm<BN, BF16><<<grid, kThreads, TcSmem<BN>::kTotal, s>>>(
-      ma, mb, op.M, Nr, nkb, per, C, cM, cN, coff, alpha, accumulate ? 1 : 0,
+  k_tc_gemm<BN, BF16, SPLIT><<<grid, kThreads, L::kTotal, s>>>(
+      ma, mb, op.M, Nr, nkb, per, nkb, C, cM, cN, coff, alpha, accumulate ? 1 : 0,
       nsplit > 1 ? partial : nullptr, err);
   RTCC3_CUDA(cudaGetLastError());
 }
@@ -461,13 +511,14 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
 }  // namespace
 
 void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
-               int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
-  launch_pack<false>(A, aM, aK, aoff, M, K, Kp, segs, elem_bytes, kfast, out, s);
+               int K, int Kp, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
+  launch_pack<false>(A, aM, aK, aoff, M, K, Kp, 1, elem_bytes, kfast, out, s);
 }
 
 void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
-               int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
-  launch_pack<true>(B, bN, bK, boff, N, K, Kp, segs, elem_bytes, kfast, out, s);
+               int K, int Kp, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
+  const int segs = elem_bytes == 4 ? 2 : 1;
+  launch_pack<true>(B, bN, bK, boff, N, K, segs * Kp, segs, elem_bytes, kfast, out, s);
 }
 
 bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2* C,
@@ -479,11 +530,12 @@ bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2*
   const int BN = Nr >= 192 ? 256 : (Nr >= 96 ? 128 : 64);
   CUtensorMap ma, mb;
   if (!make_map(&ma, Apack, op.elem_bytes, op.Kp, op.M, kBM)) return false;
-  if (!make_map(&mb, Bpack, op.elem_bytes, op.Kp, Nr, BN)) return false;
+  if (!make_map(&mb, Bpack, op.elem_bytes, op.split ? 2 * op.Kp : op.Kp, Nr, BN)) return false;
   const bool bf16 = op.elem_bytes == 2;
+  RTCC3_CHECK(bf16 || op.split, kErrArg, "TF32 operands are split in the GEMM (pack B as hi | lo)");
 #define RTCC3_TC(BNV)                                                                             \
-  (bf16 ? launch<BNV, true>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s) \
-        : launch<BNV, false>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s))
+  (bf16 ? launch<BNV, true, false>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s) \
+        : launch<BNV, false, true>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s))
   if (BN == 256) RTCC3_TC(256);
   else if (BN == 128) RTCC3_TC(128);
   else RTCC3_TC(64);

@@ -16,21 +16,25 @@ namespace rtcc3 {
 
 struct TcOperands {
   int M = 0, N = 0, K = 0;  // complex extents
-  int Kp = 0;               // packed real K (multiple of the K tile)
+  int Kp = 0;               // packed real K of A (multiple of the K tile)
   int elem_bytes = 4;       // 4: TF32 operands, 2: BF16 operands
+  // TF32: A is packed as raw FP32 and split into hi + lo TF32 parts in the
+  // GEMM's shared memory, B is packed as [hi | lo] (width 2 Kp); one GEMM
+  // sums hi.hi + hi.lo + lo.hi (FP32-level products at three times the
+  // tensor work, A read once).
+  bool split = false;
 };
 
-// Pack A (complex, addressed by tables) into a K-major real buffer of
-// packed width Kp.  segs = 3 (TF32 only) writes the three K segments
-// [hi | hi | lo] of a hi + lo TF32 split (B gets [hi | lo | hi]), so one GEMM
-// over the whole width sums hi.hi + hi.lo + lo.hi.
-// kfast: the source is contiguous along k (else along the row index); the
-// packing kernel reads along that index and writes packed rows along k.
+// Pack A (complex, addressed by tables) into a K-major real buffer of packed
+// width Kp: raw FP32 for TF32 (elem_bytes 4), BF16 otherwise.  kfast: the
+// source is contiguous along k (else along the row index); the packing
+// kernel reads along that index and writes packed rows along k.
 void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
-               int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s);
-// Pack B as its 2x2 real embedding: rows 2n (real part) and 2n+1 (imaginary part).
+               int K, int Kp, int elem_bytes, bool kfast, void* out, cudaStream_t s);
+// Pack B as its 2x2 real embedding: rows 2n (real part) and 2n+1 (imaginary
+// part); for TF32 as [hi | lo] K segments (row width 2 Kp).
 void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
-               int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s);
+               int K, int Kp, int elem_bytes, bool kfast, void* out, cudaStream_t s);
 
 // C[cB + cM[m] + cN[n]] (+)= alpha * (Apack Bpack^T)[m, 2n..2n+1] as complex.
 // nsplit > 1: K is split over CTAs; partial sums (M x 2N FP32 per split) go
