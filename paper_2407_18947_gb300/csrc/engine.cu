@@ -82,16 +82,17 @@ __global__ void k_div_eps_dense6(const Cx<R>* __restrict__ X, Cx<R>* __restrict_
   }
 }
 
-// Y (+)= alpha P_ijk^abc(X) / D for X, Y dense (o,o,o,v,v,v): the six
-// simultaneous permutations of (ijk, abc) summed and divided by the triples
-// denominator D[ijk abc] = vsum[abc] - osum[ijk] (FP64 sums; complex sums
-// when CPLX).  D is invariant under those permutations, so the same kernel
-// is its own adjoint.
+// Y (+)= alpha P(X) / D for X, Y dense (o,o,o,v,v,v): P sums the six
+// simultaneous permutations of (ijk, abc) (NP = 6) or the identity and the
+// exchanges of slot 1 with slots 2 and 3 (NP = 3), then divides by the
+// triples denominator D[ijk abc] = vsum[abc] - osum[ijk] (FP64 sums; complex
+// sums when CPLX).  D is invariant under those permutations, so for NP = 6
+// the same kernel is its own adjoint.
 struct Sym6Div {
   FastDiv v3, o2, o, v2, v;
 };
 
-template <typename R, typename I, bool CPLX>
+template <typename R, typename I, bool CPLX, int NP>
 __global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx,
                            long long offy, const double* __restrict__ osum,
                            const double* __restrict__ vsum, const double2* __restrict__ osum_c,
@@ -112,12 +113,19 @@ __global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, l
     auto V = [&](I x, I y, I z) { return (x * v + y) * v + z; };
     const Cx<R> x0 = Xb[O(i, j, k) + V(a, b, c)];
     const Cx<R> x1 = Xb[O(j, i, k) + V(b, a, c)];
-    const Cx<R> x2 = Xb[O(i, k, j) + V(a, c, b)];
     const Cx<R> x3 = Xb[O(k, j, i) + V(c, b, a)];
-    const Cx<R> x4 = Xb[O(k, i, j) + V(c, a, b)];
-    const Cx<R> x5 = Xb[O(j, k, i) + V(b, c, a)];
-    const R sr = alpha * (((x0.x + x1.x) + (x2.x + x3.x)) + (x4.x + x5.x));
-    const R si = alpha * (((x0.y + x1.y) + (x2.y + x3.y)) + (x4.y + x5.y));
+    R sr, si;
+    if (NP == 6) {
+      const Cx<R> x2 = Xb[O(i, k, j) + V(a, c, b)];
+      const Cx<R> x4 = Xb[O(k, i, j) + V(c, a, b)];
+      const Cx<R> x5 = Xb[O(j, k, i) + V(b, c, a)];
+      sr = alpha * (((x0.x + x1.x) + (x2.x + x3.x)) + (x4.x + x5.x));
+      si = alpha * (((x0.y + x1.y) + (x2.y + x3.y)) + (x4.y + x5.y));
+    } else {
+      // identity, (ij)(ab) and (ik)(ac): the three slot exchanges with slot 1
+      sr = alpha * ((x0.x + x1.x) + x3.x);
+      si = alpha * ((x0.y + x1.y) + x3.y);
+    }
     Cx<R> y = overwrite ? cmake<R>(R(0), R(0)) : Y[offy + t];
     if (CPLX) {
       const double2 vs = vsum_c[abc], os = osum_c[ijk];
@@ -635,6 +643,9 @@ void* Engine<R>::scratch(int slot, size_t bytes) {
 
 template <typename R>
 ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View& B, const View& Cv) {
+  // tensor cores only inside the tensor-core region (the triples): the
+  // split-TF32 products (about 5e-7 relative) are accurate enough for the
+  // small triples terms, not for the CCSD part at its full magnitude
   const bool tc_ok = cur_tc_ && tc_eb_ > 0;
   const std::string key = spec + "|" + view_key(A) + "|" + view_key(B) + "|" + view_key(Cv) +
                           (tc_ok ? "|tc" : "");
@@ -1119,7 +1130,7 @@ void Engine<R>::sym6(double alpha, const View& X, const View& Y, bool overwrite)
 template <typename R>
 void Engine<R>::sym6_div(double alpha, const View& X, const EpsSpec& es, const View& Y) {
   RTCC3_CHECK(X.node != Y.node, kErrArg, "sym6_div output aliases input");
-  run_sym6_div(alpha, X, false, es, Y, false, true);
+  run_sym6_div(alpha, X, false, es, Y, false, true, 6);
   if (nodes_[X.node].needs_grad) nodes_[Y.node].needs_grad = true;
   Op op{kSym6Div, "", alpha, X, View(), Y, es};
   tape_.push_back(op);
@@ -1127,7 +1138,7 @@ void Engine<R>::sym6_div(double alpha, const View& X, const EpsSpec& es, const V
 
 template <typename R>
 void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y,
-                             bool yg, bool overwrite) {
+                             bool yg, bool overwrite, int np) {
   const bool cplx = es.osum_c && es.vsum_c;
   RTCC3_CHECK(cplx || (es.osum && es.vsum), kErrArg, "sym6_div needs denominator sum tables");
   auto dense6 = [&](const View& w) {
@@ -1155,19 +1166,23 @@ void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec
     fd.v2 = FastDiv(vv * vv);
     fd.v = FastDiv(vv);
   }
-#define RTCC3_S6D(I, CP)                                                                       \
-  k_sym6_div<R, I, CP><<<grid_for(n), 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum, es.vsum, \
-                                                         es.osum_c, es.vsum_c, es.o, es.v, I(n), \
-                                                         R(alpha), overwrite ? 1 : 0, fd)
+#define RTCC3_S6D(I, CP, NPV)                                                                    \
+  k_sym6_div<R, I, CP, NPV><<<grid_for(n), 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum, es.vsum, \
+                                                              es.osum_c, es.vsum_c, es.o, es.v, I(n), \
+                                                              R(alpha), overwrite ? 1 : 0, fd)
+#define RTCC3_S6DN(I, CP) \
+  if (np == 6) RTCC3_S6D(I, CP, 6); else RTCC3_S6D(I, CP, 3)
   if (n < (size_t(1) << 31)) {
-    if (cplx) RTCC3_S6D(unsigned, true);
-    else RTCC3_S6D(unsigned, false);
+    if (cplx) RTCC3_S6DN(unsigned, true);
+    else RTCC3_S6DN(unsigned, false);
   } else {
-    if (cplx) RTCC3_S6D(size_t, true);
-    else RTCC3_S6D(size_t, false);
+    if (cplx) RTCC3_S6DN(size_t, true);
+    else RTCC3_S6DN(size_t, false);
   }
+#undef RTCC3_S6DN
 #undef RTCC3_S6D
-  pend(pk, "sym6_div", 20.0 * n, double(n) * sizeof(C) * (6 + (overwrite ? 1 : 2)));
+  pend(pk, np == 6 ? "sym6_div" : "sym3_div", (np * 2.0 + 8.0) * n,
+       double(n) * sizeof(C) * (np + (overwrite ? 1 : 2)));
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
 }
@@ -1413,7 +1428,7 @@ void Engine<R>::backward() {
       run_sym6(op.alpha, op.c, true, op.a, true, false);
     } else if (op.kind == kSym6Div) {
       if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
-      run_sym6_div(op.alpha, op.c, true, op.es, op.a, true, false);
+      run_sym6_div(op.alpha, op.c, true, op.es, op.a, true, false, 6);
     } else {
       const bool saved = tc_region_;
       tc_region_ = op.tc;

@@ -146,6 +146,11 @@ class Engine {
                 bool overwrite = false) {
     run_div(X, xg, es, Y, yg, overwrite);
   }
+  // Y = (X + X(jik,bac) + X(kji,cba)) / D over dense triples (X on its data
+  // or gradient buffer; untaped; es with FP64 sum tables).
+  void exec_sym3_div(const View& X, bool xg, const EpsSpec& es, const View& Y) {
+    run_sym6_div(1.0, X, xg, es, Y, false, true, 3);
+  }
   // Y = X (X on its data or gradient buffer; untaped).
   void exec_copy(const View& X, bool xg, const View& Y) {
     const double one = 1.0;
@@ -250,7 +255,7 @@ class Engine {
                    bool yg, bool overwrite, const char* name);
   void run_sym6(double alpha, const View& X, bool xg, const View& Y, bool yg, bool overwrite);
   void run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
-                    bool overwrite);
+                    bool overwrite, int np);
   void run_contract(const std::string& spec, double alpha, const View& A, bool a_grad, const View& B,
                     bool b_grad, const View& Cv, bool c_grad, bool accumulate);
   void run_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg);

@@ -125,12 +125,12 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
     E.custom([&E, t3p, wtn, es, s6, SO, SIO, SV, SIV, wvv, woo, o, v]() {
       if (!E.needs_grad(t3p) || !E.needs_grad(wtn)) return;
       const View T3 = E.v(t3p);
-      const int yp = E.node(s6, false, false);
-      const View Y = E.v(yp);
-      E.exec_div(T3, true, es, Y, false, true);  // y' = grad(t3') / D'
+      // y' = grad(t3') / D'; t3' is invariant under the simultaneous
+      // permutations, so the slot-2 and slot-3 densities of y' equal the
+      // slot-1 densities of the permuted y': ys = y' + y'(jik,bac) + y'(kji,cba)
+      // (D' is invariant too, so ys is formed from grad(t3') in one pass)
       const int ys = E.node(s6, false, false);
-      E.exec_combine({{1.0, Y}, {1.0, E.ev("jikbac->ijkabc", Y)}, {1.0, E.ev("kjicba->ijkabc", Y)}},
-                     E.v(ys), true);
+      E.exec_sym3_div(T3, true, es, E.v(ys));
       const int Dv = E.node({v, v}), Do = E.node({o, o});
       E.exec_contract("ijkabc,ijkdbc->ad", 1.0, E.v(ys), false, T3, false, E.v(Dv), false);
       E.exec_contract("ijkabc,ljkabc->li", 1.0, E.v(ys), false, T3, false, E.v(Do), false);
