@@ -825,17 +825,28 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
     // the epilogue stores in runs
     const bool c_unit_m = !gm.empty() && std::llabs(gm.back().sc) == 1;
     P->tc_swap = long_k ? (N > M) : c_unit_m;
-    const long long Mg = std::max(M, N), Ng = std::min(M, N);
-    // TF32 operands are split into hi + lo TF32 parts and the three leading
-    // products (hi.hi + hi.lo + lo.hi) are summed by the GEMM: FP32-level
-    // accuracy at three times the tensor work
+    P->tc_out = !long_k;
+    const long long Mg = P->tc_swap ? N : M, Ng = P->tc_swap ? M : N;
     P->tc_kp = tc_packed_k(int(K), tc_eb_);
     const int nkb = P->tc_kp / (128 / tc_eb_);
     const long long nr = 2 * Ng;
-    const long long bn = nr >= 192 ? 256 : (nr >= 96 ? 128 : 64);
+    const long long bn = tc_tile_n(int(std::min<long long>(nr, 1 << 30)), P->tc_out);
     const long long tcs = ((nr + bn - 1) / bn) * ((Mg + 127) / 128);
+    // split K so that the CTAs fill whole waves of the GPU (each split sums
+    // at least 32 K tiles; a larger split must gain 3% of wave occupancy)
     int ts = 1;
-    if (tcs < 152 && nkb >= 8) ts = int(std::max<long long>(1, std::min<long long>((304 + tcs - 1) / tcs, nkb / 4)));
+    if (!P->tc_out && nkb >= 64) {
+      const long long slots = 152LL * tc_ctas_per_sm(false);
+      double best = double(tcs) / double(((tcs + slots - 1) / slots) * slots);
+      for (int c = 2; c <= nkb / 32 && c <= 64; ++c) {
+        const long long ctas = tcs * c;
+        const double eff = double(ctas) / double(((ctas + slots - 1) / slots) * slots);
+        if (eff > best + 0.03) {
+          best = eff;
+          ts = c;
+        }
+      }
+    }
     P->tc_nsplit = ts;
   }
   ContractPlan& ref = *P;
@@ -957,6 +968,7 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     op.Kp = P.tc_kp;
     op.elem_bytes = tc_eb_;
     op.split = tc_eb_ == 4;
+    op.out_bound = P.tc_out;
     const float2* ga = sw ? pb : pa;
     const float2* gb = sw ? pa : pb;
     const long long* gaM = sw ? P.bN : P.aM;

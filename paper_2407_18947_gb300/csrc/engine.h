@@ -61,6 +61,7 @@ struct ContractPlan {
   // tensor-core route (complex64 graphs with TF32/BF16 operands)
   bool use_tc = false, tc_swap = false;
   int tc_nsplit = 1, tc_kp = 0;
+  bool tc_out = false;  // short sum bound by its output (two CTAs per SM)
   long long a_off0 = 0, b_off0 = 0, c_off0 = 0;  // batch-0 offsets (host copies)
   long long *aM = nullptr, *aK = nullptr, *bN = nullptr, *bK = nullptr;
   long long *cM = nullptr, *cN = nullptr, *aB = nullptr, *bB = nullptr, *cB = nullptr;

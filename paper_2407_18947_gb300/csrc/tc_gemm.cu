@@ -23,7 +23,6 @@ namespace rtcc3 {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kThreads = 320;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -132,9 +131,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // Shared-memory plan of one CTA.  SPLIT (TF32 with a hi + lo split done in
 // shared memory): A arrives as raw FP32 and a second A buffer takes the low
-// parts; B arrives pre-split as [hi | lo] K halves.  The ring depth fills
-// 192 KB.
-template <int BN, bool SPLIT>
+// parts; B arrives pre-split as [hi | lo] K halves.  EW epilogue warps: 8
+// with a ring of up to four stages in 192 KB (one CTA per SM, long sums), or
+// 4 with the ring in 80 KB (two CTAs per SM: one CTA's epilogue overlaps the
+// other's main loop, for products bound by their output).
+template <int BN, bool SPLIT, int EW>
 struct TcSmem {
   static constexpr int kABytes = kBM * 128;
   static constexpr int kALoBytes = SPLIT ? kBM * 128 : 0;
@@ -142,22 +143,24 @@ struct TcSmem {
   static constexpr int kBLoBytes = SPLIT ? BN * 128 : 0;
   static constexpr int kStageBytes = kABytes + kALoBytes + kBBytes + kBLoBytes;
   static constexpr int kTmaBytes = kABytes + kBBytes + kBLoBytes;  // bytes the TMA delivers
-  static constexpr int kStages = 196608 / kStageBytes < 4 ? 196608 / kStageBytes : 4;
+  static constexpr int kRing = EW == 8 ? 196608 : 81920;
+  static constexpr int kStages = kRing / kStageBytes < 4 ? kRing / kStageBytes : 4;
   static constexpr int kBarOff = kStages * kStageBytes;
   static constexpr int kStageOutOff = kBarOff + 256;
-  static constexpr int kStageOutBytes = 8 * 32 * 33 * 4;
+  static constexpr int kStageOutBytes = EW * 32 * 33 * 4;
   static constexpr int kTotal = kStageOutOff + kStageOutBytes + 1024;  // + alignment slack
-  static_assert(kStages >= 2, "ring depth");
-  static_assert(kTotal <= 232448, "shared memory per CTA");
+  static constexpr int kThreads = 64 + 32 * EW;  // TMA warp, MMA warp, EW epilogue warps
+  static_assert(kStages >= 1, "ring depth");
+  static_assert(kTotal <= (EW == 8 ? 232448 : 116224), "shared memory per CTA");
 };
 
-template <int BN, bool BF16, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int BN, bool BF16, bool SPLIT, int EW>
+__global__ void __launch_bounds__(64 + 32 * EW, EW == 4 ? 2 : 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           int M, int Nr, int nkb_total, int kb_per_split, int kb_lo, float2* __restrict__ C,
           const long long* __restrict__ cM, const long long* __restrict__ cN, long long coff,
           float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err) {
-  using L = TcSmem<BN, SPLIT>;
+  using L = TcSmem<BN, SPLIT, EW>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -180,7 +183,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     for (int s = 0; s < kStages; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
-      mbar_init(smem_u32(&conv[s]), 8);  // one arrival per converter warp
+      mbar_init(smem_u32(&conv[s]), EW);  // one arrival per converter warp
     }
     mbar_init(smem_u32(done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -247,7 +250,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       // converters (warps 2..9) while the main loop runs: A tile -> TF32 hi in
       // place, the remainder x - hi into the low buffer (same offsets, so the
       // swizzled layout is kept), then a proxy fence for the tensor cores
-      const int ct = threadIdx.x - 64;  // 0..255
+      const int ct = threadIdx.x - 64;  // 0 .. 32 EW - 1
       for (int i = 0; i < nkb && ok; ++i) {
         const int s = i % kStages;
         ok = mbar_wait(smem_u32(&full[s]), (i / kStages) & 1);
@@ -255,8 +258,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         float4* ah = reinterpret_cast<float4*>(smem + s * L::kStageBytes);
         float4* al = reinterpret_cast<float4*>(smem + s * L::kStageBytes + L::kABytes);
 #pragma unroll
-        for (int u = 0; u < L::kABytes / 16 / 256; ++u) {
-          const int e = ct + 256 * u;
+        for (int u = 0; u < L::kABytes / 16 / (32 * EW); ++u) {
+          const int e = ct + 32 * EW * u;
           const float4 x = ah[e];
           float4 h, lo;
           h.x = __uint_as_float(to_tf32(x.x)); lo.x = x.x - h.x;
@@ -271,8 +274,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (lane == 0) mbar_arrive(smem_u32(&conv[s]));
       }
     }
-    // epilogue: warps 2..9, two per TMEM lane quarter (warp % 4), each taking
-    // every other 32-column chunk
+    // epilogue: warps 2 .. 1 + EW, EW / 4 per TMEM lane quarter (warp % 4),
+    // taking every (EW / 4)-th 32-column chunk
     const int q = warp & 3, ew = warp - 2, half = ew >> 2;
     ok = ok && ((nkb == 0) ? true : mbar_wait(smem_u32(done), 0));
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
@@ -282,7 +285,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int m = m0 + row;
     // output row offsets of this warp's 32 rows, one per lane
     const long long cm_lane = (!partial && m < M) ? cM[m] : 0;
-    for (int c0 = 32 * half; c0 < BN && ok; c0 += 64) {
+    for (int c0 = 32 * half; c0 < BN && ok; c0 += 32 * (EW / 4)) {
       uint32_t r[32];
       if (nkb > 0) {
         tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c0), r);
@@ -487,14 +490,14 @@ bool make_map(CUtensorMap* map, const void* base, int elem_bytes, int Kp, int ro
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, bool BF16, bool SPLIT>
+template <int BN, bool BF16, bool SPLIT, int EW>
 void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, float2* C,
             const long long* cM, const long long* cN, long long coff, float alpha, bool accumulate,
             int nsplit, float* partial, int* err, cudaStream_t s) {
-  using L = TcSmem<BN, SPLIT>;
+  using L = TcSmem<BN, SPLIT, EW>;
   static bool attr = false;
   if (!attr) {
-    RTCC3_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, BF16, SPLIT>,
+    RTCC3_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, BF16, SPLIT, EW>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal));
     attr = true;
   }
@@ -502,7 +505,7 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
   const int nkb = op.Kp / (128 / op.elem_bytes);
   const int per = (nkb + nsplit - 1) / nsplit;
   dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, nsplit);
-  k_tc_gemm<BN, BF16, SPLIT><<<grid, kThreads, L::kTotal, s>>>(
+  k_tc_gemm<BN, BF16, SPLIT, EW><<<grid, L::kThreads, L::kTotal, s>>>(
       ma, mb, op.M, Nr, nkb, per, nkb, C, cM, cN, coff, alpha, accumulate ? 1 : 0,
       nsplit > 1 ? partial : nullptr, err);
   RTCC3_CUDA(cudaGetLastError());
@@ -527,18 +530,23 @@ bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2*
   const int Nr = 2 * op.N;
   if (op.M <= 0 || op.N <= 0 || op.Kp <= 0) return false;
   if (op.Kp % (128 / op.elem_bytes) != 0) return false;
-  const int BN = Nr >= 192 ? 256 : (Nr >= 96 ? 128 : 64);
+  const int BN = tc_tile_n(Nr, op.out_bound);
   CUtensorMap ma, mb;
   if (!make_map(&ma, Apack, op.elem_bytes, op.Kp, op.M, kBM)) return false;
   if (!make_map(&mb, Bpack, op.elem_bytes, op.split ? 2 * op.Kp : op.Kp, Nr, BN)) return false;
   const bool bf16 = op.elem_bytes == 2;
   RTCC3_CHECK(bf16 || op.split, kErrArg, "TF32 operands are split in the GEMM (pack B as hi | lo)");
-#define RTCC3_TC(BNV)                                                                             \
-  (bf16 ? launch<BNV, true, false>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s) \
-        : launch<BNV, false, true>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s))
-  if (BN == 256) RTCC3_TC(256);
-  else if (BN == 128) RTCC3_TC(128);
-  else RTCC3_TC(64);
+#define RTCC3_TC(BNV, EWV)                                                                        \
+  (bf16 ? launch<BNV, true, false, EWV>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s) \
+        : launch<BNV, false, true, EWV>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s))
+  if (op.out_bound) {
+    if (BN == 128) RTCC3_TC(128, 4);
+    else RTCC3_TC(64, 4);
+  } else {
+    if (BN == 256) RTCC3_TC(256, 8);
+    else if (BN == 128) RTCC3_TC(128, 8);
+    else RTCC3_TC(64, 8);
+  }
 #undef RTCC3_TC
   return true;
 }

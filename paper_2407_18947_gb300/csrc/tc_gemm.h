@@ -23,7 +23,22 @@ struct TcOperands {
   // sums hi.hi + hi.lo + lo.hi (FP32-level products at three times the
   // tensor work, A read once).
   bool split = false;
+  // the product is bound by its output (short sum): two CTAs per SM with
+  // narrower tiles, so that epilogues overlap main loops
+  bool out_bound = false;
 };
+
+// GEMM column tile (real columns) for Nr = 2N real output columns: the
+// narrowest of 64 / 128 / 256 that holds them (one column tile, the A tile
+// read once), at most 128 for output-bound products.
+inline int tc_tile_n(int Nr, bool out_bound) {
+  const int cap = out_bound ? 128 : 256;
+  if (Nr <= 64) return 64;
+  if (Nr <= 128 || cap == 128) return 128;
+  return 256;
+}
+// CTAs resident per SM for the two variants.
+inline int tc_ctas_per_sm(bool out_bound) { return out_bound ? 2 : 1; }
 
 // Pack A (complex, addressed by tables) into a K-major real buffer of packed
 // width Kp: raw FP32 for TF32 (elem_bytes 4), BF16 otherwise.  kfast: the
