@@ -115,40 +115,81 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def roofline_of(stats, peaks, peak_kind, precision):
-    """Dominant kernel (largest device time) against its own roofline."""
-    if not stats:
-        return None, None
-    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+# Profiler names (librtcc3 per-operation timing) grouped by the CUDA kernel
+# that runs them, with the roofline that bounds that kernel.
+KERNEL_FAMILIES = {
+    "k_combine": (("combine", "axpy_gather", "axpy_strided", "copy", "sym6"), "hbm"),
+    "k_tc_gemm": (("contract_tc_tf32", "contract_tc_bf16"), "tensor"),
+    "k_contract": (("contract_simt_c64", "contract_simt_c128"), "alu"),
+    "k_sym6_div": (("sym6_div", "sym3_div"), "hbm"),
+    "k_pack": (("tc_pack",), "hbm"),
+    "k_reduce_small": (("contract_small_c64", "contract_small_c128"), "hbm"),
+    "k_gemv": (("contract_gemv_c64", "contract_gemv_c128"), "hbm"),
+    "k_div_eps": (("div_eps",), "hbm"),
+    "k_split_reduce": (("split_reduce", "tc_split_finish"), "hbm"),
+}
+
+# DRAM bytes per launch of the dominant kernel from the committed ncu capture
+# (profiles/k_combine_traffic_h2o2_tf32.md): (kernel, precision, workload) ->
+# bytes per launch averaged over the launches of one RK4 step; None once the
+# kernel has changed since the counters were taken.
+MEASURED_TRAFFIC = {}
+
+
+def _family_roofline(fam, st, total_ms, peaks, peak_kind, precision, workload):
     sec = st["ms"] / 1e3
-    per_launch = sec / max(st["launches"], 1)
     tflops = st["flops"] / sec / 1e12 if sec > 0 else 0.0
     gbs = st["bytes"] / sec / 1e9 if sec > 0 else 0.0
+    bound = KERNEL_FAMILIES[fam][1]
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    if name.startswith("contract_simt"):
+    if bound == "alu":
         # CUDA-core complex FMA: 152 SMs x 128 FP32 lanes x 2 flop/cycle (FP32),
         # FP64 at the GB300 nominal 1.25 TFLOP/s
-        if "c128" in name:
+        if precision == "fp64":
             peak, note = 1.25, "nominal FP64 (recipe table)"
         else:
             peak, note = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "152 SM x 128 FP32 lanes x 2 x max SM clock"
         rl = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-              "frac": round(tflops / peak, 4), "traffic": None, "kernel": name, "peak_source": note}
-    elif name.startswith("contract_tc"):
-        ratio = 1.1 / 2.25 if "tf32" in name else 1.0
+              "frac": round(tflops / peak, 4)}
+    elif bound == "tensor":
+        ratio = 1.1 / 2.25 if precision == "tf32" else 1.0
         peak = peaks["bf16_tflops_sustained"] * ratio
+        note = f"{peak_kind} bf16 sustained x nominal dtype ratio ({'tf32' if ratio < 1 else 'bf16'})"
         rl = {"bound": "tensor", "achieved": round(tflops, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-              "frac": round(tflops / peak, 4), "traffic": None, "kernel": name,
-              "peak_source": f"{peak_kind} bf16 sustained x nominal dtype ratio"}
+              "frac": round(tflops / peak, 4)}
     else:
         peak = peaks["hbm_gbs"]
+        note = f"{peak_kind} hbm_gbs"
         rl = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-              "frac": round(gbs / peak, 4), "traffic": None, "kernel": name,
-              "peak_source": f"{peak_kind} hbm_gbs"}
-    rl["launches"] = st["launches"]
-    rl["avg_launch_us"] = round(per_launch * 1e6, 3)
-    rl["share_of_step"] = round(st["ms"] / sum(s["ms"] for s in stats.values()), 4)
-    return rl, name
+              "frac": round(gbs / peak, 4)}
+    rl["traffic"] = MEASURED_TRAFFIC.get((fam, precision, workload))
+    rl.update({"kernel": fam, "peak_source": note, "launches": st["launches"],
+               "avg_launch_us": round(sec / max(st["launches"], 1) * 1e6, 3),
+               "share_of_step": round(st["ms"] / total_ms, 4) if total_ms > 0 else None})
+    return rl
+
+
+def roofline_of(stats, peaks, peak_kind, precision, workload):
+    """The dominant kernel (largest summed device time over the profiled
+    step) against its own roofline, plus the tensor-core kernel's when it ran."""
+    if not stats:
+        return None, None
+    fams = {}
+    for fam, (names, _) in KERNEL_FAMILIES.items():
+        acc = {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0}
+        for nm in names:
+            if nm in stats:
+                for k in acc:
+                    acc[k] += stats[nm][k]
+        if acc["launches"]:
+            fams[fam] = acc
+    total_ms = sum(v["ms"] for v in stats.values())
+    dom = max(fams.items(), key=lambda kv: kv[1]["ms"])[0]
+    rl = _family_roofline(dom, fams[dom], total_ms, peaks, peak_kind, precision, workload)
+    if dom != "k_tc_gemm" and "k_tc_gemm" in fams:
+        rl["tensor_kernel"] = _family_roofline("k_tc_gemm", fams["k_tc_gemm"], total_ms, peaks, peak_kind,
+                                               precision, workload)
+    return rl, dom
 
 
 def oracle_stage_seconds(wl, threads=None):
@@ -301,7 +342,8 @@ def main():
     kstats = eng.kernel_stats()
     eng.set_profiling(False)
     peaks, peak_kind = load_peaks()
-    roofline, dom = roofline_of(kstats, peaks, peak_kind, args.precision)
+    roofline, dom = roofline_of(kstats, peaks, peak_kind, args.precision,
+                                wl.get("size", args.workload))
     flops = nominal_flops(o, v)
 
     cpu = None

@@ -397,6 +397,45 @@ __global__ void k_combine(Cx<R>* __restrict__ Y, const CombDesc<R> d, I n) {
   }
 }
 
+// k_combine with the rank ND a compile-time constant (every descriptor index
+// constant: the strides stay in the parameter bank, no local-memory copy) and
+// OFF32: all element offsets fit 31 bits (32-bit index arithmetic).
+template <typename R, int ND, bool OFF32>
+__global__ void __launch_bounds__(256) k_combine_nd(Cx<R>* __restrict__ Y, const CombDesc<R> d, unsigned n) {
+  using O = typename std::conditional<OFF32, int, long long>::type;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    unsigned rem = t;
+    O oy = O(d.offy);
+    O ox[kMaxSrc];
+#pragma unroll
+    for (int s = 0; s < kMaxSrc; ++s) ox[s] = O(d.offx[s]);
+#pragma unroll
+    for (int k = ND - 1; k >= 0; --k) {
+      const unsigned q = k > 0 ? d.fd[k].div(rem) : 0u;
+      const O i = O(rem - q * unsigned(d.shape[k]));
+      rem = q;
+      oy += i * O(d.sy[k]);
+#pragma unroll
+      for (int s = 0; s < kMaxSrc; ++s)
+        if (s < d.nsrc) ox[s] += i * O(d.sx[s][k]);
+    }
+    R re = R(0), im = R(0);
+#pragma unroll
+    for (int s = 0; s < kMaxSrc; ++s)
+      if (s < d.nsrc) {
+        const Cx<R> x = d.src[s][ox[s]];
+        re += d.alpha[s] * x.x;
+        im += d.alpha[s] * x.y;
+      }
+    if (!d.overwrite) {
+      const Cx<R> y = Y[oy];
+      re += y.x;
+      im += y.y;
+    }
+    Y[oy] = cmake<R>(re, im);
+  }
+}
+
 template <typename R>
 __global__ void k_fill(Cx<R>* p, size_t n, R re, R im) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
@@ -1094,10 +1133,37 @@ void Engine<R>::run_combine(const View* xs, const bool* xg, const double* alphas
   if (n == 0) return;
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
   const int pk = pbegin();
-  if (n < (size_t(1) << 31))
+  // largest element offset any operand reaches (decides 32-bit indexing)
+  long long span = std::llabs(d.offy);
+  {
+    long long ey = std::llabs(d.offy);
+    for (int k = 0; k < w; ++k) ey += std::llabs(d.sy[k]) * (d.shape[k] - 1);
+    span = ey;
+    for (int s = 0; s < ns; ++s) {
+      long long e = std::llabs(d.offx[s]);
+      for (int k = 0; k < w; ++k) e += std::llabs(d.sx[s][k]) * (d.shape[k] - 1);
+      span = std::max(span, e);
+    }
+  }
+  const bool off32 = span < (1LL << 31);
+  if (n < (size_t(1) << 31) && w <= 6) {
+#define RTCC3_CND(NDV)                                                                       \
+  if (off32) k_combine_nd<R, NDV, true><<<grid_for(n), 256, 0, stream_>>>(py, d, unsigned(n)); \
+  else k_combine_nd<R, NDV, false><<<grid_for(n), 256, 0, stream_>>>(py, d, unsigned(n))
+    switch (w) {
+      case 1: RTCC3_CND(1); break;
+      case 2: RTCC3_CND(2); break;
+      case 3: RTCC3_CND(3); break;
+      case 4: RTCC3_CND(4); break;
+      case 5: RTCC3_CND(5); break;
+      default: RTCC3_CND(6); break;
+    }
+#undef RTCC3_CND
+  } else if (n < (size_t(1) << 31)) {
     k_combine<R, unsigned><<<grid_for(n), 256, 0, stream_>>>(py, d, unsigned(n));
-  else
+  } else {
     k_combine<R, size_t><<<grid_for(n), 256, 0, stream_>>>(py, d, n);
+  }
   pend(pk, name, 2.0 * ns * n, double(n) * sizeof(C) * (ns + (overwrite ? 1 : 2)),
        prof_ && prof_->detail() ? "n=" + std::to_string(n) + " nsrc=" + std::to_string(ns) +
                                       " nd=" + std::to_string(w)
