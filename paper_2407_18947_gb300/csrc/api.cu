@@ -271,6 +271,13 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
     H.vsum = rn->template alloc<double>(vs.size());
     RTCC3_CUDA(cudaMemcpy(H.osum, os.data(), os.size() * sizeof(double), cudaMemcpyHostToDevice));
     RTCC3_CUDA(cudaMemcpy(H.vsum, vs.data(), vs.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // the sums rounded once to the compute precision (the dense triples
+    // kernels divide in R; every term of D = vsum - osum has the same sign)
+    std::vector<R> osr(os.begin(), os.end()), vsr(vs.begin(), vs.end());
+    H.osum_r = rn->template alloc<R>(osr.size());
+    H.vsum_r = rn->template alloc<R>(vsr.size());
+    RTCC3_CUDA(cudaMemcpy(H.osum_r, osr.data(), osr.size() * sizeof(R), cudaMemcpyHostToDevice));
+    RTCC3_CUDA(cudaMemcpy(H.vsum_r, vsr.data(), vsr.size() * sizeof(R), cudaMemcpyHostToDevice));
   }
   H.h = rn->template alloc<Cx<R>>(hc.size());
   H.L = rn->template alloc<Cx<R>>(Lc.size());

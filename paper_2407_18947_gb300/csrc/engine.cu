@@ -94,10 +94,9 @@ struct Sym6Div {
 
 template <typename R, typename I, bool CPLX, int NP>
 __global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx,
-                           long long offy, const double* __restrict__ osum,
-                           const double* __restrict__ vsum, const double2* __restrict__ osum_c,
-                           const double2* __restrict__ vsum_c, int o, int v, I n, R alpha,
-                           int overwrite, const Sym6Div fd) {
+                           long long offy, const R* __restrict__ osum, const R* __restrict__ vsum,
+                           const Cx<R>* __restrict__ osum_c, const Cx<R>* __restrict__ vsum_c,
+                           int o, int v, I n, R alpha, int overwrite, const Sym6Div fd) {
   const I v2 = I(v) * v, v3 = v2 * v, o2 = I(o) * o;
   const Cx<R>* Xb = X + offx;
   auto dv = [&](I x, const FastDiv& f, I d) -> I {
@@ -128,14 +127,14 @@ __global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, l
     }
     Cx<R> y = overwrite ? cmake<R>(R(0), R(0)) : Y[offy + t];
     if (CPLX) {
-      const double2 vs = vsum_c[abc], os = osum_c[ijk];
-      const R dr = R(vs.x - os.x), di = R(vs.y - os.y);
+      const Cx<R> vs = vsum_c[abc], os = osum_c[ijk];
+      const R dr = vs.x - os.x, di = vs.y - os.y;
       const R m = R(1) / (dr * dr + di * di);
       const R ir = dr * m, ii = -di * m;
       y.x += sr * ir - si * ii;
       y.y += sr * ii + si * ir;
     } else {
-      const R inv = R(1) / R(vsum[abc] - osum[ijk]);
+      const R inv = R(1) / (vsum[abc] - osum[ijk]);
       y.x += sr * inv;
       y.y += si * inv;
     }
@@ -1217,8 +1216,8 @@ void Engine<R>::sym6_div(double alpha, const View& X, const EpsSpec& es, const V
 template <typename R>
 void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y,
                              bool yg, bool overwrite, int np) {
-  const bool cplx = es.osum_c && es.vsum_c;
-  RTCC3_CHECK(cplx || (es.osum && es.vsum), kErrArg, "sym6_div needs denominator sum tables");
+  const bool cplx = es.osum_cr && es.vsum_cr;
+  RTCC3_CHECK(cplx || (es.osum_r && es.vsum_r), kErrArg, "sym6_div needs denominator sum tables");
   auto dense6 = [&](const View& w) {
     if (w.nd != 6) return false;
     const int dims[6] = {es.o, es.o, es.o, es.v, es.v, es.v};
@@ -1245,9 +1244,9 @@ void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec
     fd.v = FastDiv(vv);
   }
 #define RTCC3_S6D(I, CP, NPV)                                                                    \
-  k_sym6_div<R, I, CP, NPV><<<grid_for(n), 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum, es.vsum, \
-                                                              es.osum_c, es.vsum_c, es.o, es.v, I(n), \
-                                                              R(alpha), overwrite ? 1 : 0, fd)
+  k_sym6_div<R, I, CP, NPV><<<grid_for(n), 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum_r,      \
+                                                              es.vsum_r, es.osum_cr, es.vsum_cr, es.o, \
+                                                              es.v, I(n), R(alpha), overwrite ? 1 : 0, fd)
 #define RTCC3_S6DN(I, CP) \
   if (np == 6) RTCC3_S6D(I, CP, 6); else RTCC3_S6D(I, CP, 3)
   if (n < (size_t(1) << 31)) {

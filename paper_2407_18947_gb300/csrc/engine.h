@@ -119,6 +119,12 @@ class Engine {
     // Complex sums of eigenvalues in the field-dressed basis (take precedence).
     const double2* osum_c = nullptr;
     const double2* vsum_c = nullptr;
+    // The sums in the compute precision, for the fused P_ijk^abc + division
+    // kernels (real, or complex when osum_cr / vsum_cr are set).
+    const R* osum_r = nullptr;
+    const R* vsum_r = nullptr;
+    const Cx<R>* osum_cr = nullptr;
+    const Cx<R>* vsum_cr = nullptr;
   };
   void div_eps(const View& X, const EpsSpec& es, const View& Y, bool overwrite = false);
   // Y = alpha P_ijk^abc(X) / D (Eq. A30 and the denominators of Eq. 6 in one

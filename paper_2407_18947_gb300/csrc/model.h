@@ -26,6 +26,8 @@ struct Hamil {
   double* mu = nullptr;   // 3 x n x n dipole matrices (FP64)
   double* osum = nullptr;  // o^3 sums e_i + e_j + e_k (FP64)
   double* vsum = nullptr;  // v^3 sums e_a + e_b + e_c (FP64)
+  R* osum_r = nullptr;     // the same sums rounded once to R
+  R* vsum_r = nullptr;
   double e_ref = 0.0;     // sum_i (h_ii + eps_i)
 };
 

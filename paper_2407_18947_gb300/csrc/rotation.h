@@ -46,9 +46,11 @@ void launch_eig(const EigJob& a, const EigJob& b, bool fp32, int* status, cudaSt
 template <typename R>
 void launch_field_matrices(const Cx<R>* wt, const double* eps, int o, int v, double2* Mo,
                            double2* Mv, cudaStream_t s);
-// osum[(i o + j) o + k] = l_i + l_j + l_k and vsum likewise (complex128).
-void launch_lambda_sums(const double2* lo, const double2* lv, int o, int v, double2* osum,
-                        double2* vsum, cudaStream_t s);
+// osum[(i o + j) o + k] = l_i + l_j + l_k and vsum likewise (summed in FP64,
+// rounded once to the compute precision R).
+template <typename R>
+void launch_lambda_sums(const double2* lo, const double2* lv, int o, int v, Cx<R>* osum,
+                        Cx<R>* vsum, cudaStream_t s);
 // dst (compute precision) = src (complex128), n elements.
 template <typename R>
 void launch_to_precision(const double2* src, Cx<R>* dst, size_t n, cudaStream_t s);

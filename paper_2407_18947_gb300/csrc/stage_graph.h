@@ -17,14 +17,15 @@ namespace rtcc3 {
 // Field-dressed eigenbasis of one stage (see rotation.h): O and V are built
 // from the dressed perturbation and decomposed on the engine's side stream,
 // overlapping the CCSD part of the stage; rotated_triples joins before use.
+template <typename R>
 struct FieldBasis {
   int So = -1, Sio = -1, Sv = -1, Siv = -1;  // S and S^-1 (compute precision)
-  double2* osum = nullptr;                   // eigenvalue sums (complex128)
-  double2* vsum = nullptr;
+  Cx<R>* osum = nullptr;                     // eigenvalue sums (compute precision)
+  Cx<R>* vsum = nullptr;
 };
 
 template <typename R>
-FieldBasis start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt) {
+FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt) {
   const int o = H.o, v = H.v;
   Arena& A = E.arena();
   auto c2 = [&](size_t n) { return static_cast<double2*>(A.alloc(sizeof(double2) * n)); };
@@ -33,9 +34,9 @@ FieldBasis start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt) {
   double2 *Sv64 = c2(size_t(v) * v), *Siv64 = c2(size_t(v) * v);
   double2 *lo = c2(o), *lv = c2(v);
   double2 *wso = c2(3 * size_t(o) * o), *wsv = c2(3 * size_t(v) * v);
-  FieldBasis B;
-  B.osum = c2(size_t(o) * o * o);
-  B.vsum = c2(size_t(v) * v * v);
+  FieldBasis<R> B;
+  B.osum = static_cast<Cx<R>*>(A.alloc(sizeof(Cx<R>) * size_t(o) * o * o));
+  B.vsum = static_cast<Cx<R>*>(A.alloc(sizeof(Cx<R>) * size_t(v) * v * v));
   B.So = E.node({o, o}, false, false);
   B.Sio = E.node({o, o}, false, false);
   B.Sv = E.node({v, v}, false, false);
@@ -47,7 +48,7 @@ FieldBasis start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt) {
   launch_field_matrices<R>(E.data(wt), H.eps, o, v, Mo, Mv, ss);
   const EigJob jo{Mo, o, So64, Sio64, lo, wso}, jv{Mv, v, Sv64, Siv64, lv, wsv};
   launch_eig(jo, jv, sizeof(R) == 4, status, ss);
-  launch_lambda_sums(lo, lv, o, v, B.osum, B.vsum, ss);
+  launch_lambda_sums<R>(lo, lv, o, v, B.osum, B.vsum, ss);
   launch_to_precision<R>(So64, E.data(B.So), size_t(o) * o, ss);
   launch_to_precision<R>(Sio64, E.data(B.Sio), size_t(o) * o, ss);
   launch_to_precision<R>(Sv64, E.data(B.Sv), size_t(v) * v, ss);
@@ -68,12 +69,10 @@ FieldBasis start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt) {
 // slot densities D' of y' and t3' (the triples density terms of Eqs. A31-A32
 // in the rotated basis).  Returns the node of t3' and accumulates into R1 and SD.
 template <typename R, typename BlkFn>
-int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, const FieldBasis& B,
+int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, const FieldBasis<R>& B,
                     int g, int ft, const View& R1, const View& SD, BlkFn&& blk) {
   const int o = H.o, v = H.v;
   E.join();
-  const double2* osum = B.osum;
-  const double2* vsum = B.vsum;
   const int So = B.So, Sio = B.Sio, Sv = B.Sv, Siv = B.Siv;
   const View SO = E.v(So), SIO = E.v(Sio), SV = E.v(Sv), SIV = E.v(Siv);
   auto G = [&](const char* b) { return blk(g, b); };
@@ -115,8 +114,8 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   typename Engine<R>::EpsSpec es;
   es.o = o;
   es.v = v;
-  es.osum_c = osum;
-  es.vsum_c = vsum;
+  es.osum_cr = B.osum;
+  es.vsum_cr = B.vsum;
   const int t3p = E.node(s6, false, false);
   E.sym6_div(-1.0, E.v(Z), es, E.v(t3p));
   const int wtn = wt;
@@ -290,7 +289,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   E.contract("pr,rs->ps", 1.0, E.v(X), E.v(S.w), E.v(wX), true);
   E.contract("ps,sq->pq", 1.0, E.v(wX), E.v(Y), E.v(wt), true);
   // the field-dressed eigenbasis only needs w~: start it now, beside the CCSD part
-  FieldBasis fb;
+  FieldBasis<R> fb;
   if (opt.triples && opt.field_terms && opt.rotation) fb = start_field_basis(E, H, wt);
   const int g = E.node({n, n, n, n});
   E.contract("Ppq,Prs->pqrs", 1.0, E.v(Lt), E.v(Lt), E.v(g), true);
@@ -382,6 +381,8 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     for (int d = 3; d < 6; ++d) { es.sign[d] = 1; es.base[d] = o; }
     es.osum = H.osum;
     es.vsum = H.vsum;
+    es.osum_r = H.osum_r;
+    es.vsum_r = H.vsum_r;
     es.o = o;
     es.v = v;
     int t3;
