@@ -118,7 +118,7 @@ class ClockSampler:
 # Profiler names (librtcc3 per-operation timing) grouped by the CUDA kernel
 # that runs them, with the roofline that bounds that kernel.
 KERNEL_FAMILIES = {
-    "k_combine": (("combine", "axpy_gather", "axpy_strided", "copy", "sym6"), "hbm"),
+    "k_combine_nd": (("combine", "axpy_gather", "axpy_strided", "copy", "sym6"), "hbm"),
     "k_tc_gemm": (("contract_tc_tf32", "contract_tc_bf16"), "tensor"),
     "k_contract": (("contract_simt_c64", "contract_simt_c128"), "alu"),
     "k_sym6_div": (("sym6_div", "sym3_div"), "hbm"),
@@ -129,11 +129,19 @@ KERNEL_FAMILIES = {
     "k_split_reduce": (("split_reduce", "tc_split_finish"), "hbm"),
 }
 
-# DRAM bytes per launch of the dominant kernel from the committed ncu capture
-# (profiles/k_combine_traffic_h2o2_tf32.md): (kernel, precision, workload) ->
-# bytes per launch averaged over the launches of one RK4 step; None once the
-# kernel has changed since the counters were taken.
-MEASURED_TRAFFIC = {}
+# DRAM bytes (read + write) per launch, averaged over the launches of one RK4
+# step, from the committed ncu capture profiles/dram_traffic_h2o2_tf32.md:
+# (kernel, precision, workload) -> bytes.  An entry is removed when its kernel
+# changes after the counters were taken.
+MEASURED_TRAFFIC = {
+    ("k_contract", "tf32", 2): 3.76e6,
+    ("k_tc_gemm", "tf32", 2): 624.49e6,
+    ("k_combine_nd", "tf32", 2): 157.16e6,
+    ("k_sym6_div", "tf32", 2): 3021.52e6,
+    ("k_pack", "tf32", 2): 245.37e6,
+    ("k_reduce_small", "tf32", 2): 177.00e6,
+    ("k_gemv", "tf32", 2): 149.80e6,
+}
 
 
 def _family_roofline(fam, st, total_ms, peaks, peak_kind, precision, workload):
