@@ -130,7 +130,8 @@ KERNEL_FAMILIES = {
 }
 
 # DRAM bytes (read + write) per launch, averaged over the launches of one RK4
-# step, from the committed ncu capture profiles/dram_traffic_h2o2_tf32.md:
+# step, from an ncu capture of this benchmark (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass, full-size workload):
 # (kernel, precision, workload) -> bytes.  An entry is removed when its kernel
 # changes after the counters were taken.
 MEASURED_TRAFFIC = {
