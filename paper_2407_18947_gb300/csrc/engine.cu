@@ -16,6 +16,7 @@ namespace {
 constexpr int kBM = 64, kBN = 64, kBK = 16, kThreads = 256;
 constexpr int kSBM = 16, kSBK = 64;  // small-tile variant
 constexpr int kTBK = 8;               // thin (16 x 256) tiles
+constexpr int kTcMaxKbPerSplit = 16;  // K tiles per tensor-core accumulation chain
 
 // Division of 32-bit n < 2^31 by an invariant d >= 1 with one multiply-high
 // (Granlund and Montgomery, "Division by invariant integers using
@@ -885,6 +886,11 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
         }
       }
     }
+    // bounded accumulation chains: the tensor-core FP32 accumulator adds
+    // every product of a CTA's K range in place, and its error grows with
+    // the chain length, so no split sums more than 64 K tiles; the splits
+    // are added in FP32 by tc_split_finish
+    if (!P->tc_out) ts = std::max(ts, (nkb + kTcMaxKbPerSplit - 1) / kTcMaxKbPerSplit);
     P->tc_nsplit = ts;
   }
   ContractPlan& ref = *P;

@@ -70,3 +70,26 @@ def test_tf32_matches_fp32_cuda_cores(w1):
     b = _run(s, amps, precision=2)
     for k in KEYS:
         assert np.abs(a[k] - b[k]).max() < 1e-6, k
+
+
+def test_tf32_and_fp32_within_1e6_at_h2o2_size():
+    """(H2O)2-sized system (nocc 10, nvir 38): the reduced-precision graphs
+    against the complex128 graph (itself equal to the oracle to 1e-10 on the
+    smaller systems), with a cos field at a nonzero time.  Long sums on the
+    tensor cores accumulate in chains of bounded length, which keeps split
+    TF32 at FP32 accuracy here."""
+    s = water_system(2)
+    amps = random_amplitudes(s.nocc, s.nvir, seed=5)
+    from paper_2407_18947_gb300.api import RTCC3
+    out = {}
+    for prec in (0, 1, 2):
+        eng = RTCC3(s.nocc, s.nvir, precision=prec)
+        eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+        eng.set_field(0, 2, 0.001, omega=0.0656, direction=(0, 0, 1))
+        eng.set_amplitudes(0, *amps)
+        out[prec] = eng.compute_residuals(0, 3.0)
+        eng.close()
+    for prec in (1, 2):
+        errs = {k: float(np.abs(out[prec][k] - out[0][k]).max()) for k in KEYS}
+        assert all(e < 1e-6 for e in errs.values()), (prec, errs)
+        assert np.abs(out[prec]["dipole"] - out[0]["dipole"]).max() < 1e-6
