@@ -213,8 +213,14 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
       PScope ps(ctx->prof, ctx->stream, "seeds", 0.0, double(ctx->ny) * sizeof(Cx<R>));
       launch_seeds<R>(E.grad(S.e), E.grad(S.r1), E.grad(S.r2), Rn.l1s, Rn.l2s, ctx->o, ctx->v,
                       ctx->stream);
+      E.mark_grad_written(S.e);
+      E.mark_grad_written(S.r1);
+      E.mark_grad_written(S.r2);
     }
     E.backward();
+    E.ensure_grad(S.t1);  // read outside the engine
+    E.ensure_grad(S.t2);
+    E.ensure_grad(S.w);
   }
   return S;
 }
@@ -641,7 +647,11 @@ void triples_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1, const d
   if (vjp) {
     E.prepare_backward();  // grad(e) stays zero: only u . X is differentiated
     launch_load_amplitudes<R>(u1, u2, E.grad(S.r1), E.grad(S.r2), ctx->o, ctx->v, ctx->stream);
+    E.mark_grad_written(S.r1);
+    E.mark_grad_written(S.r2);
     E.backward();
+    E.ensure_grad(S.t1);  // read outside the engine
+    E.ensure_grad(S.t2);
     launch_export<R>(E.grad(S.t1), g1, n1, ctx->stream);
     launch_export<R>(E.grad(S.t2), g2, n2, ctx->stream);
   } else {

@@ -17,6 +17,7 @@ constexpr int kBM = 64, kBN = 64, kBK = 16, kThreads = 256;
 constexpr int kSBM = 16, kSBK = 64;  // small-tile variant
 constexpr int kTBK = 8;               // thin (16 x 256) tiles
 constexpr int kTcMaxKbPerSplit = 16;  // K tiles per tensor-core accumulation chain
+constexpr size_t kLazyGradMin = 65536;  // gradients this large are not zero-filled up front
 
 // Division of 32-bit n < 2^31 by an invariant d >= 1 with one multiply-high
 // (Granlund and Montgomery, "Division by invariant integers using
@@ -906,6 +907,14 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
   if (prof_ && prof_->detail())
     cur_detail_ = spec + " M=" + std::to_string(P.M) + " N=" + std::to_string(P.N) +
                   " K=" + std::to_string(P.K) + (P.use_tc ? (P.tc_swap ? " tc-swap" : " tc") : "");
+  if ((a_grad && !nodes_[A.node].grad_ready) || (b_grad && !nodes_[B.node].grad_ready)) {
+    // a cotangent never written is zero: nothing to add; an overwriting
+    // product needs its zeros, so the cotangent is zero-filled first
+    if (accumulate) return;
+    if (a_grad) zero_grad_if_unset(A.node);
+    if (b_grad) zero_grad_if_unset(B.node);
+  }
+  if (c_grad) accumulate = begin_grad_write(Cv, accumulate);
   const C* pa = (a_grad ? nodes_[A.node].grad : nodes_[A.node].data);
   const C* pb = (b_grad ? nodes_[B.node].grad : nodes_[B.node].data);
   C* pc = (c_grad ? nodes_[Cv.node].grad : nodes_[Cv.node].data);
@@ -1081,6 +1090,31 @@ template <typename R>
 void Engine<R>::run_combine(const View* xs, const bool* xg, const double* alphas, int ns,
                             const View& Y, bool yg, bool overwrite, const char* name) {
   RTCC3_CHECK(ns >= 1 && ns <= kMaxSrc, kErrArg, "combine takes 1..6 sources");
+  {
+    // sources on unset (zero) gradients drop out; none left: nothing to add
+    View keep[kMaxSrc];
+    bool kg[kMaxSrc];
+    double ka[kMaxSrc];
+    int nk = 0;
+    for (int s = 0; s < ns; ++s) {
+      if (xg[s] && !nodes_[xs[s].node].grad_ready) continue;
+      keep[nk] = xs[s];
+      kg[nk] = xg[s];
+      ka[nk] = alphas[s];
+      ++nk;
+    }
+    if (nk < ns) {
+      if (nk == 0) {
+        if (!overwrite) return;
+        zero_grad_if_unset(xs[0].node);  // an overwrite still needs its zeros
+        run_combine(xs, xg, alphas, 1, Y, yg, overwrite, name);
+        return;
+      }
+      run_combine(keep, kg, ka, nk, Y, yg, overwrite, name);
+      return;
+    }
+  }
+  if (yg) overwrite = !begin_grad_write(Y, !overwrite);
   CombDesc<R> d{};
   d.nsrc = ns;
   d.overwrite = overwrite ? 1 : 0;
@@ -1235,6 +1269,11 @@ void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec
     return true;
   };
   RTCC3_CHECK(dense6(X) && dense6(Y), kErrArg, "sym6_div needs dense triples views");
+  if (xg && !nodes_[X.node].grad_ready) {
+    if (!overwrite) return;  // zero cotangent
+    zero_grad_if_unset(X.node);
+  }
+  if (yg) overwrite = !begin_grad_write(Y, !overwrite);
   const size_t n = Y.numel();
   if (n == 0) return;
   const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
@@ -1299,6 +1338,8 @@ void Engine<R>::axpy(double alpha, const View& X, const View& Y) {
 template <typename R>
 void Engine<R>::run_mulc(const View& X, bool xg, const View& Cst, const View& Y, bool yg) {
   RTCC3_CHECK(X.nd == Y.nd && Cst.nd == Y.nd, kErrArg, "mulc rank mismatch");
+  if (xg && !nodes_[X.node].grad_ready) return;  // zero cotangent (mulc accumulates)
+  if (yg) zero_grad_if_unset(Y.node);  // k_mulc always accumulates
   StridedDesc d{};
   d.nd = Y.nd;
   for (int k = 0; k < Y.nd; ++k) {
@@ -1334,6 +1375,11 @@ template <typename R>
 void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
                         bool overwrite) {
   RTCC3_CHECK(X.nd == Y.nd, kErrArg, "div_eps rank mismatch");
+  if (xg && !nodes_[X.node].grad_ready) {
+    if (!overwrite) return;  // zero cotangent
+    zero_grad_if_unset(X.node);
+  }
+  if (yg) overwrite = !begin_grad_write(Y, !overwrite);
   if (es.osum_c && es.vsum_c) {
     auto dense6 = [&](const View& w) {
       if (w.nd != 6) return false;
@@ -1448,8 +1494,43 @@ void Engine<R>::prepare_backward() {
   for (auto& nd : nodes_) {
     if (!nd.needs_grad) continue;
     nd.grad = static_cast<C*>(arena_.alloc(nd.numel * sizeof(C)));
-    RTCC3_CUDA(cudaMemsetAsync(nd.grad, 0, nd.numel * sizeof(C), stream_));
+    nd.grad_ready = nd.numel < kLazyGradMin;
+    if (nd.grad_ready) RTCC3_CUDA(cudaMemsetAsync(nd.grad, 0, nd.numel * sizeof(C), stream_));
   }
+}
+
+template <typename R>
+bool Engine<R>::begin_grad_write(const View& dst, bool accumulate) {
+  Node& nd = nodes_[dst.node];
+  if (nd.grad_ready) return accumulate;
+  nd.grad_ready = true;
+  // does the view cover the whole node, each element once?
+  bool covers = dst.off == 0 && dst.numel() == nd.numel;
+  if (covers) {
+    long long st[kMaxDim];
+    int ext[kMaxDim], m = 0;
+    for (int d = 0; d < dst.nd; ++d)
+      if (dst.shape[d] > 1) { st[m] = std::llabs(dst.stride[d]); ext[m] = dst.shape[d]; ++m; }
+    int idx[kMaxDim];
+    for (int d = 0; d < m; ++d) idx[d] = d;
+    std::sort(idx, idx + m, [&](int p, int q) { return st[p] > st[q]; });
+    long long expect = 1;
+    for (int d = m - 1; d >= 0 && covers; --d) {
+      covers = st[idx[d]] == expect;
+      expect *= ext[idx[d]];
+    }
+  }
+  if (covers) return false;
+  RTCC3_CUDA(cudaMemsetAsync(nd.grad, 0, nd.numel * sizeof(C), stream_));
+  return accumulate;
+}
+
+template <typename R>
+void Engine<R>::zero_grad_if_unset(int node) {
+  Node& nd = nodes_[node];
+  if (nd.grad_ready) return;
+  RTCC3_CUDA(cudaMemsetAsync(nd.grad, 0, nd.numel * sizeof(C), stream_));
+  nd.grad_ready = true;
 }
 
 template <typename R>

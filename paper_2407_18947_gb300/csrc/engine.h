@@ -79,6 +79,7 @@ class Engine {
     size_t numel = 0;
     std::vector<int> shape;
     bool needs_grad = false;
+    bool grad_ready = false;  // grad holds valid values (zeroed or written)
   };
 
   explicit Engine(cudaStream_t s) : stream_(s) {}
@@ -134,9 +135,17 @@ class Engine {
   void fill_identity(int node);
   void fill_ones(int node);
 
-  // Allocate and zero gradient buffers of every node that needs one; after
-  // writing the seeds into grad(), call backward().
+  // Allocate gradient buffers of every node that needs one (small ones
+  // zeroed; large ones are left unset: their first full-coverage write
+  // overwrites, a partial first write zeroes them first, and an adjoint whose
+  // cotangent was never written contributes nothing and is skipped).  After
+  // writing the seeds into grad() and calling mark_grad_written() on them,
+  // call backward().
   void prepare_backward();
+  void mark_grad_written(int node) { nodes_[node].grad_ready = true; }
+  // Zero a gradient that no operation wrote (before reading it outside the engine).
+  void ensure_grad(int node) { zero_grad_if_unset(node); }
+  bool grad_ready(int node) const { return nodes_[node].grad_ready; }
   void backward();
 
   // Untaped execution on data (g = false) or gradient (g = true) buffers,
@@ -186,6 +195,7 @@ class Engine {
     tape_.push_back(std::move(op));
   }
   void zero(int node, bool grad = false) {
+    if (grad) nodes_[node].grad_ready = true;
     RTCC3_CUDA(cudaMemsetAsync(grad ? nodes_[node].grad : nodes_[node].data, 0,
                                nodes_[node].numel * sizeof(C), stream_));
   }
@@ -245,6 +255,10 @@ class Engine {
     if (prof_) prof_->end(k, stream_, name, flops, bytes, detail);
   }
   std::string cur_detail_;  // spec and extents of the operation being run (profiling)
+  // Before writing into the gradient of dst.node: returns the accumulate flag
+  // to use (false = overwrite when the write covers a gradient not yet set).
+  bool begin_grad_write(const View& dst, bool accumulate);
+  void zero_grad_if_unset(int node);
   enum OpKind { kContract, kAxpy, kMulc, kDiv, kCustom, kSym6, kSym6Div };
   struct Op {
     OpKind kind;
