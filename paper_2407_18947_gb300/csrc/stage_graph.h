@@ -78,8 +78,8 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   auto G = [&](const char* b) { return blk(g, b); };
   // rotate one index of a 4-index tensor: spec like "Ii,ijae->Ijae"
   auto rot = [&](const char* spec, const View& S, const View& X, const std::vector<int>& shape) {
-    const int out = E.node(shape);
-    E.contract(spec, 1.0, S, X, E.v(out), true);
+    const int out = E.node(shape, false, false);  // first write overwrites: no zero fill
+    E.contract(spec, 1.0, S, X, E.v(out), false);
     return E.v(out);
   };
   const std::vector<int> s6 = {o, o, o, v, v, v};
@@ -96,13 +96,13 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   View G2p = rot("Jj,mjck->mJck", SIO, G("oovo"), {o, o, v, o});
   G2p = rot("Cc,mJck->mJCk", SIV, G2p, {o, o, v, o});
   G2p = rot("Kk,mJCk->mJCK", SIO, G2p, {o, o, v, o});
-  const int Z = E.node(s6);
-  E.contract("ijae,ckbe->ijkabc", 1.0, T1p, G1p, E.v(Z), true);
+  const int Z = E.node(s6, false, false);
+  E.contract("ijae,ckbe->ijkabc", 1.0, T1p, G1p, E.v(Z), false);
   E.contract("imab,mjck->ijkabc", -1.0, T2p, G2p, E.v(Z), true);
   // source -P sum_ld v~_ld t_ij^ad t_kl^cb, rotated the same way; P is linear,
   // so it is folded into Z before the one permutation sum
-  const int Yl = E.node({o, o, o, v});
-  E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), true);
+  const int Yl = E.node({o, o, o, v}, false, false);
+  E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), false);
   View Ylp = rot("Ii,lija->lIja", SIO, E.v(Yl), {o, o, o, v});
   Ylp = rot("Jj,lIja->lIJa", SIO, Ylp, {o, o, o, v});
   Ylp = rot("Aa,lIJa->lIJA", SIV, Ylp, {o, o, o, v});
@@ -152,12 +152,12 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   Lp = rot("kK,Jkbc->JKbc", SO, Lp, {o, o, v, v});
   Lp = rot("bB,JKbc->JKBc", SV, Lp, {o, o, v, v});
   Lp = rot("cC,JKBc->JKBC", SV, Lp, {o, o, v, v});
-  const int X1p = E.node({o, v});
-  E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), Lp, E.v(X1p), true);
+  const int X1p = E.node({o, v}, false, false);
+  E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), Lp, E.v(X1p), false);
   View Fp = rot("kK,kc->Kc", SO, blk(ft, "ov"), {o, v});
   Fp = rot("cC,Kc->KC", SV, Fp, {o, v});
-  const int S3p = E.node({o, o, v, v});
-  E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), Fp, E.v(S3p), true);
+  const int S3p = E.node({o, o, v, v}, false, false);
+  E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), Fp, E.v(S3p), false);
   const int Ub = E.node(s6, false, false);
   E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
             E.v(Ub), true);
@@ -277,22 +277,22 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   const View t1T = E.ev("ia->ai", E.v(S.t1));
   E.axpy(-1.0, t1T, E.v(X).sub(0, o, v).sub(1, 0, o));
   E.axpy(1.0, t1T, E.v(Y).sub(0, o, v).sub(1, 0, o));
-  const int LX = E.node({na, n, n}), Lt = E.node({na, n, n});
-  E.contract("pr,Prs->Pps", 1.0, E.v(X), E.v(Lc), E.v(LX), true);
-  E.contract("Pps,sq->Ppq", 1.0, E.v(LX), E.v(Y), E.v(Lt), true);
-  const int hw = E.node({n, n}), hX = E.node({n, n}), ht = E.node({n, n});
+  const int LX = E.node({na, n, n}, false, false), Lt = E.node({na, n, n}, false, false);
+  E.contract("pr,Prs->Pps", 1.0, E.v(X), E.v(Lc), E.v(LX), false);
+  E.contract("Pps,sq->Ppq", 1.0, E.v(LX), E.v(Y), E.v(Lt), false);
+  const int hw = E.node({n, n}), hX = E.node({n, n}, false, false), ht = E.node({n, n}, false, false);
   E.axpy(1.0, E.v(hc), E.v(hw));
   E.axpy(1.0, E.v(S.w), E.v(hw));
-  E.contract("pr,rs->ps", 1.0, E.v(X), E.v(hw), E.v(hX), true);
-  E.contract("ps,sq->pq", 1.0, E.v(hX), E.v(Y), E.v(ht), true);
-  const int wX = E.node({n, n}), wt = E.node({n, n});
-  E.contract("pr,rs->ps", 1.0, E.v(X), E.v(S.w), E.v(wX), true);
-  E.contract("ps,sq->pq", 1.0, E.v(wX), E.v(Y), E.v(wt), true);
+  E.contract("pr,rs->ps", 1.0, E.v(X), E.v(hw), E.v(hX), false);
+  E.contract("ps,sq->pq", 1.0, E.v(hX), E.v(Y), E.v(ht), false);
+  const int wX = E.node({n, n}, false, false), wt = E.node({n, n}, false, false);
+  E.contract("pr,rs->ps", 1.0, E.v(X), E.v(S.w), E.v(wX), false);
+  E.contract("ps,sq->pq", 1.0, E.v(wX), E.v(Y), E.v(wt), false);
   // the field-dressed eigenbasis only needs w~: start it now, beside the CCSD part
   FieldBasis<R> fb;
   if (opt.triples && opt.field_terms && opt.rotation) fb = start_field_basis(E, H, wt);
-  const int g = E.node({n, n, n, n});
-  E.contract("Ppq,Prs->pqrs", 1.0, E.v(Lt), E.v(Lt), E.v(g), true);
+  const int g = E.node({n, n, n, n}, false, false);
+  E.contract("Ppq,Prs->pqrs", 1.0, E.v(Lt), E.v(Lt), E.v(g), false);
   // f~ = h~ + sum_k 2 g~_pqkk - g~_pkkq
   const int ft = E.node({n, n});
   E.axpy(1.0, E.v(ht), E.v(ft));
@@ -364,15 +364,15 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores
     const std::vector<int> s6 = {o, o, o, v, v, v};
     // Z = sum_e t_ij^ae <cb|ke>~ - sum_m t_im^ab <mc|jk>~ ; W = P_ijk^abc Z (Eqs. A25, A30)
-    const int Z = E.node(s6);
-    E.contract("ijae,ckbe->ijkabc", 1.0, T, G("vovv"), E.v(Z), true);
+    const int Z = E.node(s6, false, false);
+    E.contract("ijae,ckbe->ijkabc", 1.0, T, G("vovv"), E.v(Z), false);
     E.contract("imab,mjck->ijkabc", -1.0, T, G("oovo"), E.v(Z), true);
     // rhs = -(W + <mu3|1/2[[V~,T2],T2]|0>), the latter = -P sum_ld v~_ld t_ij^ad t_kl^cb:
     // P is linear, so the source is folded into Z and rhs = -P(Z)
     const bool field = opt.field_terms;
     if (field) {
-      const int Yl = E.node({o, o, o, v});
-      E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), true);
+      const int Yl = E.node({o, o, o, v}, false, false);
+      E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), false);
       E.contract("lija,klcb->ijkabc", -1.0, E.v(Yl), T, E.v(Z), true);
     }
     typename Engine<R>::EpsSpec es;
@@ -404,8 +404,8 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
               E.v(Ljk), true);
     E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), E.v(Ljk), R1, true);
-    const int S3 = E.node({o, o, v, v});
-    E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), F("ov"), E.v(S3), true);
+    const int S3 = E.node({o, o, v, v}, false, false);
+    E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), F("ov"), E.v(S3), false);
     const int Ub = E.node(s6, false, false);  // 2 t^cbe - t^ceb - t^ebc  as [ijk cbe]
     E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
               E.v(Ub), true);
