@@ -203,3 +203,27 @@ def test_triples_autograd_function_matches_oracle():
     exp2 = (ref.r_l2 - ref0.r_l2).numpy()
     assert _rel(got2, exp2) < 1e-9
     eng.close()
+
+
+def test_residuals_fp64_match_oracle_at_h2o2_size():
+    """The benchmark's system size (nocc 10, nvir 38, naux 144) with a cos
+    field at a nonzero time: the complex128 path against the oracle (one
+    residual evaluation with the lambda residuals and the density).  This is
+    the size at which the large-gradient, small-output and field-eigenbasis
+    code paths all engage."""
+    s = water_system(2)
+    ham = cc3.Hamiltonian.from_system(s)
+    t1, t2, l1, l2 = random_amplitudes(s.nocc, s.nvir, seed=5)
+    eng = _engine(s)
+    eng.set_field(0, 2, 0.001, omega=0.0656, direction=(0, 0, 1))
+    eng.set_amplitudes(0, t1, t2, l1, l2)
+    time = 3.0
+    got = eng.compute_residuals(0, time)
+    field = cc3.FieldSpec(cc3.FIELD_COS, 0.001, omega=0.0656, direction=(0.0, 0.0, 1.0))
+    w = ham.field_operator(field.vector(time))
+    ref = cc3.evaluate(ham, t1, t2, l1, l2, w)
+    for k in ("r_t1", "r_t2", "r_l1", "r_l2"):
+        assert _rel(got[k], getattr(ref, k).numpy()) < 1e-10, k
+    assert abs(got["energy"] - ref.energy) < 1e-10 * max(1.0, abs(ref.energy))
+    assert _rel(got["dipole"], ref.dipole) < 1e-10
+    eng.close()
