@@ -2,6 +2,7 @@
 // residual evaluation, ground state, RK4 propagation and checkpoints.
 #include "../../include/rtcc3.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -284,6 +285,24 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
     H.vsum_r = rn->template alloc<R>(vsr.size());
     RTCC3_CUDA(cudaMemcpy(H.osum_r, osr.data(), osr.size() * sizeof(R), cudaMemcpyHostToDevice));
     RTCC3_CUDA(cudaMemcpy(H.vsum_r, vsr.data(), vsr.size() * sizeof(R), cudaMemcpyHostToDevice));
+    // occupied blocks in orbit order: for each i <= j <= k its distinct
+    // permutations, one after the other
+    std::vector<int> order;
+    order.reserve(size_t(o) * o * o);
+    for (int i = 0; i < o; ++i)
+      for (int j = i; j < o; ++j)
+        for (int k = j; k < o; ++k) {
+          const int p[6][3] = {{i, j, k}, {j, i, k}, {i, k, j}, {k, j, i}, {k, i, j}, {j, k, i}};
+          const size_t first = order.size();
+          for (auto& q : p) {
+            const int id = (q[0] * o + q[1]) * o + q[2];
+            if (std::find(order.begin() + first, order.end(), id) == order.end()) order.push_back(id);
+          }
+        }
+    RTCC3_CHECK(order.size() == size_t(o) * o * o, kErrState, "orbit order incomplete");
+    H.orbit_order = rn->template alloc<int>(order.size());
+    RTCC3_CUDA(cudaMemcpy(H.orbit_order, order.data(), order.size() * sizeof(int),
+                          cudaMemcpyHostToDevice));
   }
   H.h = rn->template alloc<Cx<R>>(hc.size());
   H.L = rn->template alloc<Cx<R>>(Lc.size());

@@ -90,36 +90,43 @@ __global__ void k_div_eps_dense6(const Cx<R>* __restrict__ X, Cx<R>* __restrict_
 // triples denominator D[ijk abc] = vsum[abc] - osum[ijk] (FP64 sums; complex
 // sums when CPLX).  D is invariant under those permutations, so for NP = 6
 // the same kernel is its own adjoint.
-struct Sym6Div {
-  FastDiv v3, o2, o, v2, v;
-};
-
-template <typename R, typename I, bool CPLX, int NP>
-__global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx,
-                           long long offy, const R* __restrict__ osum, const R* __restrict__ vsum,
-                           const Cx<R>* __restrict__ osum_c, const Cx<R>* __restrict__ vsum_c,
-                           int o, int v, I n, R alpha, int overwrite, const Sym6Div fd) {
-  const I v2 = I(v) * v, v3 = v2 * v, o2 = I(o) * o;
-  const Cx<R>* Xb = X + offx;
-  auto dv = [&](I x, const FastDiv& f, I d) -> I {
-    if constexpr (sizeof(I) == 4) return I(f.div(unsigned(x)));
-    else return x / d;
-  };
-  for (I t = I(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += I(gridDim.x) * blockDim.x) {
-    const I ijk = dv(t, fd.v3, v3);
-    const I abc = t - ijk * v3;
-    const I i = dv(ijk, fd.o2, o2), jk = ijk - i * o2, j = dv(jk, fd.o, I(o)), k = jk - j * o;
-    const I a = dv(abc, fd.v2, v2), bc = abc - a * v2, b = dv(bc, fd.v, I(v)), c = bc - b * v;
-    auto O = [&](I x, I y, I z) { return ((x * o + y) * o + z) * v3; };
-    auto V = [&](I x, I y, I z) { return (x * v + y) * v + z; };
-    const Cx<R> x0 = Xb[O(i, j, k) + V(a, b, c)];
-    const Cx<R> x1 = Xb[O(j, i, k) + V(b, a, c)];
-    const Cx<R> x3 = Xb[O(k, j, i) + V(c, b, a)];
+// Y (+)= alpha P(X) / D for X, Y dense (o,o,o,v,v,v): P sums the six
+// simultaneous permutations of (ijk, abc) (NP = 6) or the identity and the
+// exchanges of slot 1 with slots 2 and 3 (NP = 3), then divides by the
+// triples denominator D[ijk abc] = vsum[abc] - osum[ijk] (sums in the compute
+// precision; complex when CPLX).  D is invariant under those permutations, so
+// for NP = 6 the same kernel is its own adjoint.  Grid: (abc chunks, occupied
+// blocks); the occupied blocks are visited in `order` (the distinct
+// permutations of each i <= j <= k consecutively), so the source blocks of
+// one orbit are read while they are resident in L2.
+template <typename R, bool CPLX, int NP>
+__global__ void __launch_bounds__(256)
+k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx, long long offy,
+           const R* __restrict__ osum, const R* __restrict__ vsum, const Cx<R>* __restrict__ osum_c,
+           const Cx<R>* __restrict__ vsum_c, const int* __restrict__ order, int o, int v, R alpha,
+           int overwrite, const FastDiv fv2, const FastDiv fv) {
+  const int ijk = order ? order[blockIdx.y] : int(blockIdx.y);
+  const int i = ijk / (o * o), j = (ijk / o) % o, k = ijk % o;
+  const unsigned v2 = unsigned(v) * v, v3 = v2 * v;
+  auto O = [&](int x, int y, int z) { return (long long)((x * o + y) * o + z) * v3; };
+  const Cx<R>* b0 = X + offx + O(i, j, k);
+  const Cx<R>* b1 = X + offx + O(j, i, k);
+  const Cx<R>* b2 = X + offx + O(i, k, j);
+  const Cx<R>* b3 = X + offx + O(k, j, i);
+  const Cx<R>* b4 = X + offx + O(k, i, j);
+  const Cx<R>* b5 = X + offx + O(j, k, i);
+  Cx<R>* yb = Y + offy + O(i, j, k);
+  for (unsigned abc = blockIdx.x * blockDim.x + threadIdx.x; abc < v3; abc += gridDim.x * blockDim.x) {
+    const unsigned a = fv2.div(abc), bc = abc - a * v2, b = fv.div(bc), c = bc - b * v;
+    auto V = [&](unsigned x, unsigned y, unsigned z) { return (x * v + y) * v + z; };
+    const Cx<R> x0 = b0[abc];
+    const Cx<R> x1 = b1[V(b, a, c)];
+    const Cx<R> x3 = b3[V(c, b, a)];
     R sr, si;
     if (NP == 6) {
-      const Cx<R> x2 = Xb[O(i, k, j) + V(a, c, b)];
-      const Cx<R> x4 = Xb[O(k, i, j) + V(c, a, b)];
-      const Cx<R> x5 = Xb[O(j, k, i) + V(b, c, a)];
+      const Cx<R> x2 = b2[V(a, c, b)];
+      const Cx<R> x4 = b4[V(c, a, b)];
+      const Cx<R> x5 = b5[V(b, c, a)];
       sr = alpha * (((x0.x + x1.x) + (x2.x + x3.x)) + (x4.x + x5.x));
       si = alpha * (((x0.y + x1.y) + (x2.y + x3.y)) + (x4.y + x5.y));
     } else {
@@ -127,7 +134,7 @@ __global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, l
       sr = alpha * ((x0.x + x1.x) + x3.x);
       si = alpha * ((x0.y + x1.y) + x3.y);
     }
-    Cx<R> y = overwrite ? cmake<R>(R(0), R(0)) : Y[offy + t];
+    Cx<R> y = overwrite ? cmake<R>(R(0), R(0)) : yb[abc];
     if (CPLX) {
       const Cx<R> vs = vsum_c[abc], os = osum_c[ijk];
       const R dr = vs.x - os.x, di = vs.y - os.y;
@@ -140,7 +147,7 @@ __global__ void k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, l
       y.x += sr * inv;
       y.y += si * inv;
     }
-    Y[offy + t] = y;
+    yb[abc] = y;
   }
 }
 
@@ -1279,29 +1286,22 @@ void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec
   const C* px = xg ? nodes_[X.node].grad : nodes_[X.node].data;
   C* py = yg ? nodes_[Y.node].grad : nodes_[Y.node].data;
   const int pk = pbegin();
-  Sym6Div fd;
-  if (n < (size_t(1) << 31)) {
-    const unsigned vv = unsigned(es.v);
-    fd.v3 = FastDiv(vv * vv * vv);
-    fd.o2 = FastDiv(unsigned(es.o) * unsigned(es.o));
-    fd.o = FastDiv(unsigned(es.o));
-    fd.v2 = FastDiv(vv * vv);
-    fd.v = FastDiv(vv);
-  }
-#define RTCC3_S6D(I, CP, NPV)                                                                    \
-  k_sym6_div<R, I, CP, NPV><<<grid_for(n), 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum_r,      \
-                                                              es.vsum_r, es.osum_cr, es.vsum_cr, es.o, \
-                                                              es.v, I(n), R(alpha), overwrite ? 1 : 0, fd)
-#define RTCC3_S6DN(I, CP) \
-  if (np == 6) RTCC3_S6D(I, CP, 6); else RTCC3_S6D(I, CP, 3)
-  if (n < (size_t(1) << 31)) {
-    if (cplx) RTCC3_S6DN(unsigned, true);
-    else RTCC3_S6DN(unsigned, false);
+  const unsigned v2 = unsigned(es.v) * unsigned(es.v), v3 = v2 * unsigned(es.v);
+  const FastDiv fv2(v2), fv(unsigned(es.v));
+  // about four elements per thread along abc; one grid row per occupied block
+  dim3 grid(std::max(1u, (v3 + 1023u) / 1024u), unsigned(es.o) * es.o * es.o);
+  RTCC3_CHECK(grid.y < 65536u, kErrArg, "sym6_div: too many occupied blocks");
+#define RTCC3_S6D(CP, NPV)                                                                         \
+  k_sym6_div<R, CP, NPV><<<grid, 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum_r, es.vsum_r,     \
+                                                    es.osum_cr, es.vsum_cr, es.order, es.o, es.v,  \
+                                                    R(alpha), overwrite ? 1 : 0, fv2, fv)
+  if (cplx) {
+    if (np == 6) RTCC3_S6D(true, 6);
+    else RTCC3_S6D(true, 3);
   } else {
-    if (cplx) RTCC3_S6DN(size_t, true);
-    else RTCC3_S6DN(size_t, false);
+    if (np == 6) RTCC3_S6D(false, 6);
+    else RTCC3_S6D(false, 3);
   }
-#undef RTCC3_S6DN
 #undef RTCC3_S6D
   pend(pk, np == 6 ? "sym6_div" : "sym3_div", (np * 2.0 + 8.0) * n,
        double(n) * sizeof(C) * (np + (overwrite ? 1 : 2)));

@@ -126,6 +126,10 @@ class Engine {
     const R* vsum_r = nullptr;
     const Cx<R>* osum_cr = nullptr;
     const Cx<R>* vsum_cr = nullptr;
+    // o^3 occupied-block indices (i o + j) o + k in orbit order (the distinct
+    // permutations of each i <= j <= k consecutively), the visiting order of
+    // the fused kernels; null: natural order
+    const int* order = nullptr;
   };
   void div_eps(const View& X, const EpsSpec& es, const View& Y, bool overwrite = false);
   // Y = alpha P_ijk^abc(X) / D (Eq. A30 and the denominators of Eq. 6 in one

@@ -28,6 +28,7 @@ struct Hamil {
   double* vsum = nullptr;  // v^3 sums e_a + e_b + e_c (FP64)
   R* osum_r = nullptr;     // the same sums rounded once to R
   R* vsum_r = nullptr;
+  int* orbit_order = nullptr;  // o^3 occupied blocks, permutation orbits consecutive
   double e_ref = 0.0;     // sum_i (h_ii + eps_i)
 };
 

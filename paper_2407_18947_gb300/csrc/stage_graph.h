@@ -116,6 +116,7 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   es.v = v;
   es.osum_cr = B.osum;
   es.vsum_cr = B.vsum;
+  es.order = H.orbit_order;
   const int t3p = E.node(s6, false, false);
   E.sym6_div(-1.0, E.v(Z), es, E.v(t3p));
   const int wtn = wt;
@@ -383,6 +384,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
     es.vsum = H.vsum;
     es.osum_r = H.osum_r;
     es.vsum_r = H.vsum_r;
+    es.order = H.orbit_order;
     es.o = o;
     es.v = v;
     int t3;
