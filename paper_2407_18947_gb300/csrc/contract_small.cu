@@ -281,6 +281,7 @@ void launch_cfg(bool a_kc, bool b_kc, const Cx<R>* A, long long aoff, const long
 int small_output_config(long long M, long long N) {
   if (M <= 16 && N <= 16) return kSmall16;
   if (M <= 48 && N <= 48) return kSmall48;
+  if (M <= 64 && N <= 64) return kSmall64;
   if (N == 1 && M <= 256) return kSmallCol256;
   if (N == 1 && M <= 512) return kSmallCol512;
   return kSmallNone;
@@ -291,6 +292,7 @@ int small_output_bk(int cfg, int elem_bytes) {
   switch (cfg) {
     case kSmall16: return d ? SmallShape<double, 4, 4, 4, 4>::BK : SmallShape<float, 4, 4, 4, 4>::BK;
     case kSmall48: return d ? SmallShape<double, 16, 16, 3, 3>::BK : SmallShape<float, 16, 16, 3, 3>::BK;
+    case kSmall64: return d ? SmallShape<double, 16, 16, 4, 4>::BK : SmallShape<float, 16, 16, 4, 4>::BK;
     case kSmallCol256: return d ? SmallShape<double, 64, 1, 4, 1>::BK : SmallShape<float, 64, 1, 4, 1>::BK;
     case kSmallCol512: return d ? SmallShape<double, 128, 1, 4, 1>::BK : SmallShape<float, 128, 1, 4, 1>::BK;
     default: return 0;
@@ -310,6 +312,10 @@ void launch_reduce_small(int cfg, bool a_kc, bool b_kc, const Cx<R>* A, long lon
       break;
     case kSmall48:
       launch_cfg<R, 16, 16, 3, 3>(a_kc, b_kc, A, aoff, aM, aK, B, boff, bN, bK, C, coff, cM, cN, M, N,
+                                  K, nsplit, kchunk, alpha, accumulate, part, s);
+      break;
+    case kSmall64:
+      launch_cfg<R, 16, 16, 4, 4>(a_kc, b_kc, A, aoff, aM, aK, B, boff, bN, bK, C, coff, cM, cN, M, N,
                                   K, nsplit, kchunk, alpha, accumulate, part, s);
       break;
     case kSmallCol256:

@@ -2,7 +2,7 @@
 // 64 x 64 tiled kernel wastes most of its tile and re-reads the long operand.
 //
 //   reduce_small: C[m,n] = sum_k A[m,k] B[n,k] with the whole M x N output held
-//     by every CTA (M, N <= 48, or N = 1 and M <= 512); each CTA sums one K
+//     by every CTA (M, N <= 64, or N = 1 and M <= 512); each CTA sums one K
 //     chunk, so both operands stream from HBM exactly once.  Used for the
 //     triples slot densities (ijkabc,ijkdbc->ad; ijkabc,ljkabc->li) and the
 //     X1-type back-contractions (ijkabc,jkbc->ia).
@@ -18,7 +18,9 @@
 namespace rtcc3 {
 
 // Output-tile configurations of reduce_small (0 = not applicable).
-enum SmallCfg : int { kSmallNone = 0, kSmall48 = 1, kSmall16 = 2, kSmallCol256 = 3, kSmallCol512 = 4 };
+enum SmallCfg : int {
+  kSmallNone = 0, kSmall48 = 1, kSmall16 = 2, kSmallCol256 = 3, kSmallCol512 = 4, kSmall64 = 5
+};
 
 // Configuration for an M x N output (N <= M expected; returns kSmallNone
 // when the shape is not small).

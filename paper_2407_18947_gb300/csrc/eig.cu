@@ -58,6 +58,12 @@ struct Cplx {
 // Sum over the warp, returned identically in every lane (lane 0's value:
 // the lanes' butterfly sums may round differently, and every lane takes the
 // same branches on the result).
+// 1/sqrt(x) from the correctly rounded square root and division: the rotation
+// stays unitary to rounding, with no systematic drift of |c|^2 + |s|^2 over the
+// thousands of rotations accumulated into Q
+template <typename T>
+__device__ __forceinline__ T rsqrt_(T x) { return T(1) / sqrt(x); }
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -185,38 +191,42 @@ __global__ void __launch_bounds__(32) k_eig_warp(EigJob ja, EigJob jb, int level
         x = H[k * n + k - 1];
         y = H[(k + 1) * n + k - 1];
       }
-      const T ax = X::abs(x), ay = X::abs(y);
-      const T r = sqrt(ax * ax + ay * ay);
-      T c;
-      V s;
-      if (r == T(0)) {
-        c = T(1);
-        s = X::mk(T(0), T(0));
-      } else if (ax == T(0)) {
-        c = T(0);
-        s = X::scale(X::conj(y), T(1) / ay);
-      } else {
-        c = ax / r;
-        s = X::scale(X::mul(X::scale(x, T(1) / ax), X::conj(y)), T(1) / r);
+      // G = [[c, s], [-conj(s), conj(c)]] with c = conj(x) / r, s = conj(y) / r,
+      // r = |(x, y)|: unitary, maps (x, y) to (r, 0); one reciprocal square root
+      T r2 = x.x * x.x + x.y * x.y + y.x * y.x + y.y * y.y;
+      V c, s;
+      if (!(r2 > tiny && r2 < T(1) / tiny)) {  // rescale out of the under/overflow range
+        const T m = fmax(fmax(fabs(x.x), fabs(x.y)), fmax(fabs(y.x), fabs(y.y)));
+        if (m > T(0) && isfinite(m)) {
+          x = X::scale(x, T(1) / m);
+          y = X::scale(y, T(1) / m);
+        } else {
+          x = X::mk(T(1), T(0));
+          y = X::mk(T(0), T(0));
+        }
+        r2 = x.x * x.x + x.y * x.y + y.x * y.x + y.y * y.y;
       }
+      const T ri = rsqrt_(r2);
+      c = X::mk(x.x * ri, -x.y * ri);
+      s = X::mk(y.x * ri, -y.y * ri);
       __syncwarp();  // every lane has read the entries the rotation is built from
-      // rows k, k+1 <- G rows
+      // rows k, k+1 <- G rows; the bulge H[k+1][k-1] becomes exactly zero
       for (int j = (k == l ? k : k - 1) + lane; j < n; j += 32) {
         const V a = H[k * n + j], b = H[(k + 1) * n + j];
-        H[k * n + j] = X::add(X::scale(a, c), X::mul(s, b));
-        H[(k + 1) * n + j] = X::sub(X::scale(b, c), X::mul(X::conj(s), a));
+        H[k * n + j] = X::add(X::mul(c, a), X::mul(s, b));
+        H[(k + 1) * n + j] = (k > l && j == k - 1)
+                                 ? X::mk(T(0), T(0))
+                                 : X::sub(X::mul(X::conj(c), b), X::mul(X::conj(s), a));
       }
       __syncwarp();
-      // columns k, k+1 <- columns G^H (H rows 0..min(k+2,hi), all rows of Q)
+      // columns k, k+1 <- columns times G^H (H rows 0..min(k+2,hi), all rows of Q)
       const int rmax = min(k + 2, hi);
       for (int rr = lane; rr <= rmax + n; rr += 32) {
         V* row = rr <= rmax ? &H[rr * n] : &Q[size_t(rr - rmax - 1) * n];
         const V a = row[k], b = row[k + 1];
-        row[k] = X::add(X::scale(a, c), X::mul(X::conj(s), b));
-        row[k + 1] = X::sub(X::scale(b, c), X::mul(s, a));
+        row[k] = X::add(X::mul(a, X::conj(c)), X::mul(b, X::conj(s)));
+        row[k + 1] = X::sub(X::mul(b, c), X::mul(a, s));
       }
-      __syncwarp();
-      if (k > l && lane == 0) H[(k + 1) * n + k - 1] = X::mk(T(0), T(0));
       __syncwarp();
     }
   }
