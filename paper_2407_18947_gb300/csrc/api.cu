@@ -42,6 +42,24 @@ struct Runner : Base {
   ~Runner() override {
     for (void* p : owned) cudaFree(p);
   }
+  // FP64 eigenbasis of the next Runge-Kutta stage, decomposed ahead of it
+  BasisBuffers ahead;
+  const BasisBuffers& ahead_buffers() {
+    if (!ahead.Mo) {
+      const size_t oo = size_t(o) * o, vv = size_t(v) * v;
+      ahead.Mo = alloc<double2>(oo);
+      ahead.So = alloc<double2>(oo);
+      ahead.Sio = alloc<double2>(oo);
+      ahead.wso = alloc<double2>(3 * oo);
+      ahead.lo = alloc<double2>(o);
+      ahead.Mv = alloc<double2>(vv);
+      ahead.Sv = alloc<double2>(vv);
+      ahead.Siv = alloc<double2>(vv);
+      ahead.wsv = alloc<double2>(3 * vv);
+      ahead.lv = alloc<double2>(v);
+    }
+    return ahead;
+  }
   template <typename T>
   T* alloc(size_t count) {
     void* p = nullptr;
@@ -185,13 +203,24 @@ int field_sweeps(const rtcc3_ctx* ctx, int b) {
   return std::max(1, std::min(k, 200));
 }
 
+// Field eigenbasis look-ahead inside one Runge-Kutta step: the next stage's
+// O and V depend only on its t1 (known once this stage's forward residual r1
+// is) and its field, so their decomposition runs on the side stream during
+// this stage's backward pass instead of stalling the next stage.
+struct Ahead {
+  bool use = false;     // this stage's basis was decomposed ahead
+  bool launch = false;  // decompose the next stage's basis after the forward pass
+  double ch = 0.0, dt = 0.0;  // the next stage's input step and time offset
+};
+
 // One stage evaluation for slot b: records the graph with inputs
 // y_b + ch * kprev at time *tsrc + dt and, if need_grad, runs the backward
 // pass with the Lagrangian seeds.
 template <typename R>
 StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2* kprev, double ch,
                       const double* tsrc, double dt, bool need_grad, const FieldDev* f,
-                      bool field_terms, int sweeps, bool ccsd_terms = true) {
+                      bool field_terms, int sweeps, bool ccsd_terms = true,
+                      const Ahead& ahead = Ahead{}) {
   Runner<R>& Rn = ctx->run<R>();
   Engine<R>& E = Rn.E;
   E.begin();
@@ -201,19 +230,41 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
   so.field_terms = field_terms;
   so.field_iters = sweeps;
   so.rotation = ctx->opt.field_solver == 0;
+  const bool basis_stage = so.triples && so.field_terms && so.rotation;
+  if (ahead.use && basis_stage) so.basis = &Rn.ahead_buffers();
   (void)ccsd_terms;
   StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
     PScope ps(ctx->prof, ctx->stream, "stage_inputs", 0.0,
               double(ctx->ny) * (kprev ? 32.0 : 16.0) + double(ctx->ny) * sizeof(Cx<R>));
     launch_stage_inputs<R>(ybase, kprev, ch, E.data(s.t1), E.data(s.t2), Rn.l1s, Rn.l2s,
                            E.data(s.w), ctx->mu, f, tsrc, dt, ctx->o, ctx->v, ctx->n, ctx->stream);
+    E.add_launches(1);
   });
+  if (ahead.launch && basis_stage) {
+    // M on the main stream (this stage's r1 lives in its arena), the
+    // decomposition on the side stream; the next stage's join orders both
+    const BasisBuffers& bb = Rn.ahead_buffers();
+    {
+      PScope ps(ctx->prof, ctx->stream, "field_matrices_ahead", 0.0, 0.0);
+      launch_next_field_matrices<R>(ybase, E.data(S.r1), ahead.ch, ctx->mu, f, tsrc, ahead.dt,
+                                    ctx->eps, ctx->o, ctx->v, bb.Mo, bb.Mv, ctx->stream);
+    }
+    E.fork();
+    const cudaStream_t ss = E.side_stream();
+    const int pk = E.prof_begin(ss);
+    const EigJob jo{bb.Mo, ctx->o, bb.So, bb.Sio, bb.lo, bb.wso};
+    const EigJob jv{bb.Mv, ctx->v, bb.Sv, bb.Siv, bb.lv, bb.wsv};
+    launch_eig(jo, jv, sizeof(R) == 4, E.error_flag(), ss);
+    E.prof_end(pk, ss, "field_eig_ahead", 0.0, 0.0);
+    E.add_launches(2);
+  }
   if (need_grad) {
     E.prepare_backward();
     {
       PScope ps(ctx->prof, ctx->stream, "seeds", 0.0, double(ctx->ny) * sizeof(Cx<R>));
       launch_seeds<R>(E.grad(S.e), E.grad(S.r1), E.grad(S.r2), Rn.l1s, Rn.l2s, ctx->o, ctx->v,
                       ctx->stream);
+      E.add_launches(1);
       E.mark_grad_written(S.e);
       E.mark_grad_written(S.r1);
       E.mark_grad_written(S.r2);
@@ -341,26 +392,35 @@ void rk4_step(rtcc3_ctx* ctx, double h, const std::vector<int>& sweeps) {
     {
       PScope ps(ctx->prof, ctx->stream, "rk4_update", 0.0, 2.0 * ybytes);
       launch_stage_prep_acc(ctx->acc, yb, ctx->ny, ctx->stream);
+      E.add_launches(1);
     }
     for (int s = 0; s < 4; ++s) {
+      Ahead ah;
+      ah.use = s > 0;
+      ah.launch = s < 3;
+      ah.ch = ah.dt = s < 3 ? cs[s + 1] * h : 0.0;
       StageNodes S = eval_stage<R>(ctx, b, yb, s == 0 ? nullptr : ctx->kbuf, cs[s] * h, ctx->tdev,
-                                   cs[s] * h, true, ctx->fdev + b, true, sweeps[b]);
+                                   cs[s] * h, true, ctx->fdev + b, true, sweeps[b], true, ah);
       if (s == 0) {
         PScope ps(ctx->prof, ctx->stream, "observables", 8.0 * ctx->n * ctx->n,
                   double(ctx->n) * ctx->n * (sizeof(Cx<R>) + 24.0));
         launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->tdesc,
                               b, ctx->stepdev, ctx->stream);
+        E.add_launches(1);
       }
       PScope ps(ctx->prof, ctx->stream, "rk4_update", 4.0 * ctx->ny,
                 double(ctx->ny) * sizeof(Cx<R>) + (s < 3 ? 3.0 : 2.0) * ybytes);
       launch_stage_output<R>(E.data(S.r1), E.data(S.r2), E.grad(S.t1), E.grad(S.t2),
                              s < 3 ? ctx->kbuf : nullptr, ctx->acc, h * ws[s] / 6.0, ctx->o, ctx->v,
                              ctx->stream);
+      E.add_launches(1);
     }
     PScope ps(ctx->prof, ctx->stream, "rk4_update", 0.0, 2.0 * ybytes);
     launch_step_finish(yb, ctx->acc, ctx->ny, ctx->stepdev, ctx->baddev, ctx->stream);
+    E.add_launches(1);
   }
   launch_step_advance(ctx->tdev, h, ctx->stepdev, ctx->stream);
+  E.add_launches(1);
 }
 
 template <typename R>

@@ -389,6 +389,66 @@ void launch_export(const Cx<R>* in, double2* out, size_t n, cudaStream_t s) {
 }
 
 template <typename R>
+__global__ void k_next_field_matrices(const double2* __restrict__ y, const Cx<R>* __restrict__ r1,
+                                      double ch, const double* __restrict__ mu,
+                                      const FieldDev* __restrict__ f,
+                                      const double* __restrict__ tdev, double dt,
+                                      const double* __restrict__ eps, int o, int v,
+                                      double2* __restrict__ Mo, double2* __restrict__ Mv) {
+  const int n = o + v;
+  const size_t nn = size_t(n) * n;
+  const double E = field_strength(*f, *tdev + dt);
+  // the next stage's inputs, rounded as k_stage_inputs rounds them
+  auto t1 = [&](int i, int a) {
+    const size_t t = size_t(i) * v + a;
+    double vx = y[t].x, vy = y[t].y;
+    vx += ch * double(r1[t].y);  // k = -i r1
+    vy += ch * -double(r1[t].x);
+    return make_double2(double(R(vx)), double(R(vy)));
+  };
+  auto w = [&](int p, int q) {
+    const size_t pq = size_t(p) * n + q;
+    const double m = f->dir[0] * mu[pq] + f->dir[1] * mu[nn + pq] + f->dir[2] * mu[2 * nn + pq];
+    return double(R(-E * m));
+  };
+  const int total = o * o + v * v;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    if (t < o * o) {
+      const int i = t / o, l = t % o;
+      double re = w(l, i) + (i == l ? eps[i] : 0.0), im = 0.0;
+      for (int a = 0; a < v; ++a) {
+        const double2 x = t1(i, a);
+        const double wl = w(l, o + a);
+        re += wl * x.x;
+        im += wl * x.y;
+      }
+      Mo[t] = make_double2(re, im);
+    } else {
+      const int q = t - o * o, a = q / v, d = q % v;
+      double re = w(o + a, o + d) + (a == d ? eps[o + a] : 0.0), im = 0.0;
+      for (int i = 0; i < o; ++i) {
+        const double2 x = t1(i, a);
+        const double wi = w(i, o + d);
+        re -= x.x * wi;
+        im -= x.y * wi;
+      }
+      Mv[q] = make_double2(re, im);
+    }
+  }
+}
+
+template <typename R>
+void launch_next_field_matrices(const double2* y, const Cx<R>* r1, double ch, const double* mu,
+                                const FieldDev* f, const double* tdev, double dt,
+                                const double* eps, int o, int v, double2* Mo, double2* Mv,
+                                cudaStream_t s) {
+  const size_t total = size_t(o) * o + size_t(v) * v;
+  k_next_field_matrices<R><<<int((total + 127) / 128), 128, 0, s>>>(y, r1, ch, mu, f, tdev, dt,
+                                                                   eps, o, v, Mo, Mv);
+  RTCC3_CUDA(cudaGetLastError());
+}
+
+template <typename R>
 void launch_field_operator(Cx<R>* w, const double* mu, const FieldDev* f, const double* tdev,
                            double dt, int n, cudaStream_t s) {
   k_field_operator<R><<<grid_n(size_t(n) * n), 256, 0, s>>>(w, mu, f, tdev, dt, n);
@@ -420,7 +480,11 @@ void launch_stage_prep_acc(double2* acc, const double2* y, size_t ny, cudaStream
                                           int, cudaStream_t);                                     \
   template void launch_export<R>(const Cx<R>*, double2*, size_t, cudaStream_t);                   \
   template void launch_field_operator<R>(Cx<R>*, const double*, const FieldDev*, const double*,   \
-                                         double, int, cudaStream_t);
+                                         double, int, cudaStream_t);                              \
+  template void launch_next_field_matrices<R>(const double2*, const Cx<R>*, double, const double*, \
+                                              const FieldDev*, const double*, double,             \
+                                              const double*, int, int, double2*, double2*,        \
+                                              cudaStream_t);
 RTCC3_INST(double)
 RTCC3_INST(float)
 #undef RTCC3_INST

@@ -4,6 +4,7 @@
 
 #include "common.h"
 #include "engine.h"
+#include "rotation.h"
 
 namespace rtcc3 {
 
@@ -46,6 +47,9 @@ struct StageOptions {
   bool field_terms = true;  // include the V-coupling of the triples equation
   bool rotation = true;     // field-dressed eigenbasis (else fixed-point sweeps)
   int field_iters = 1;      // fixed-point sweeps of the triples equation
+  // eigenbasis of this stage's O and V already decomposed on the engine's side
+  // stream (enqueued there before this stage), else null: decomposed in-stage
+  const BasisBuffers* basis = nullptr;
 };
 
 // Records dressing, the CCSD residual, the triples and the energy (the same
@@ -62,6 +66,17 @@ template <typename R>
 void launch_stage_inputs(const double2* y, const double2* kprev, double ch, Cx<R>* t1, Cx<R>* t2,
                          Cx<R>* l1s, Cx<R>* l2s, Cx<R>* w, const double* mu, const FieldDev* f,
                          const double* tdev, double dt, int o, int v, int n, cudaStream_t s);
+// O and V (as launch_field_matrices) of the NEXT Runge-Kutta stage from this
+// stage's forward residual: that stage's t1 = y1 + ch * (-i r1) and
+// w = -E(*tdev + dt) dir . mu, both rounded to R exactly as the stage inputs
+// are, dressed as w~ = (1 - tau) w (1 + tau) with the FP64 sums
+//   O[i][l] = e_i d_il + w_li + sum_a w_l,a t1_ia,
+//   V[a][d] = e_a d_ad + w_ad - sum_i t1_ia w_i,d.
+template <typename R>
+void launch_next_field_matrices(const double2* y, const Cx<R>* r1, double ch, const double* mu,
+                                const FieldDev* f, const double* tdev, double dt,
+                                const double* eps, int o, int v, double2* Mo, double2* Mv,
+                                cudaStream_t s);
 // grad(e) = 1, grad(r1) = l1s, grad(r2) = l2s / 2 (Lagrangian E + l1.R1 + 1/2 l2.R2).
 template <typename R>
 void launch_seeds(Cx<R>* ge, Cx<R>* gr1, Cx<R>* gr2, const Cx<R>* l1s, const Cx<R>* l2s, int o,

@@ -41,6 +41,14 @@ struct EigJob {
 // if the QR sweeps do not converge or a matrix is not finite.
 void launch_eig(const EigJob& a, const EigJob& b, bool fp32, int* status, cudaStream_t s);
 
+// The eigenbasis of one stage computed ahead of it (complex128, owned by the
+// caller and kept between stages): M* the matrices, S*, Si* = S^-1, l* the
+// eigenvalues, ws* the eigensolver scratch (3 n^2 each).
+struct BasisBuffers {
+  double2 *Mo = nullptr, *Mv = nullptr, *So = nullptr, *Sio = nullptr, *Sv = nullptr,
+          *Siv = nullptr, *lo = nullptr, *lv = nullptr, *wso = nullptr, *wsv = nullptr;
+};
+
 // O (o x o) and V (v x v) of the current stage from the dressed perturbation w~
 // (n x n, compute precision) and the orbital energies.
 template <typename R>

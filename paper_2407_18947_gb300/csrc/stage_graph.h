@@ -24,16 +24,30 @@ struct FieldBasis {
   Cx<R>* vsum = nullptr;
 };
 
+// `ahead` (optional): the decomposition was enqueued on the side stream before
+// this stage (see launch_next_field_matrices); only the conversions remain.
 template <typename R>
-FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt) {
+FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt,
+                                const BasisBuffers* ahead = nullptr) {
   const int o = H.o, v = H.v;
   Arena& A = E.arena();
   auto c2 = [&](size_t n) { return static_cast<double2*>(A.alloc(sizeof(double2) * n)); };
-  double2 *Mo = c2(size_t(o) * o), *Mv = c2(size_t(v) * v);
-  double2 *So64 = c2(size_t(o) * o), *Sio64 = c2(size_t(o) * o);
-  double2 *Sv64 = c2(size_t(v) * v), *Siv64 = c2(size_t(v) * v);
-  double2 *lo = c2(o), *lv = c2(v);
-  double2 *wso = c2(3 * size_t(o) * o), *wsv = c2(3 * size_t(v) * v);
+  BasisBuffers bb;
+  if (ahead) {
+    bb = *ahead;
+  } else {
+    bb.Mo = c2(size_t(o) * o);
+    bb.Mv = c2(size_t(v) * v);
+    bb.So = c2(size_t(o) * o);
+    bb.Sio = c2(size_t(o) * o);
+    bb.Sv = c2(size_t(v) * v);
+    bb.Siv = c2(size_t(v) * v);
+    bb.lo = c2(o);
+    bb.lv = c2(v);
+    bb.wso = c2(3 * size_t(o) * o);
+    bb.wsv = c2(3 * size_t(v) * v);
+  }
+  double2 *So64 = bb.So, *Sio64 = bb.Sio, *Sv64 = bb.Sv, *Siv64 = bb.Siv, *lo = bb.lo, *lv = bb.lv;
   FieldBasis<R> B;
   B.osum = static_cast<Cx<R>*>(A.alloc(sizeof(Cx<R>) * size_t(o) * o * o));
   B.vsum = static_cast<Cx<R>*>(A.alloc(sizeof(Cx<R>) * size_t(v) * v * v));
@@ -45,16 +59,18 @@ FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt) {
   E.fork();
   const cudaStream_t ss = E.side_stream();
   const int pk = E.prof_begin(ss);
-  launch_field_matrices<R>(E.data(wt), H.eps, o, v, Mo, Mv, ss);
-  const EigJob jo{Mo, o, So64, Sio64, lo, wso}, jv{Mv, v, Sv64, Siv64, lv, wsv};
-  launch_eig(jo, jv, sizeof(R) == 4, status, ss);
+  if (!ahead) {
+    launch_field_matrices<R>(E.data(wt), H.eps, o, v, bb.Mo, bb.Mv, ss);
+    const EigJob jo{bb.Mo, o, So64, Sio64, lo, bb.wso}, jv{bb.Mv, v, Sv64, Siv64, lv, bb.wsv};
+    launch_eig(jo, jv, sizeof(R) == 4, status, ss);
+  }
   launch_lambda_sums<R>(lo, lv, o, v, B.osum, B.vsum, ss);
   launch_to_precision<R>(So64, E.data(B.So), size_t(o) * o, ss);
   launch_to_precision<R>(Sio64, E.data(B.Sio), size_t(o) * o, ss);
   launch_to_precision<R>(Sv64, E.data(B.Sv), size_t(v) * v, ss);
   launch_to_precision<R>(Siv64, E.data(B.Siv), size_t(v) * v, ss);
   E.prof_end(pk, ss, "field_eig", 0.0, 0.0);
-  E.add_launches(7);
+  E.add_launches(ahead ? 5 : 7);
   return B;
 }
 
@@ -291,7 +307,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   E.contract("ps,sq->pq", 1.0, E.v(wX), E.v(Y), E.v(wt), false);
   // the field-dressed eigenbasis only needs w~: start it now, beside the CCSD part
   FieldBasis<R> fb;
-  if (opt.triples && opt.field_terms && opt.rotation) fb = start_field_basis(E, H, wt);
+  if (opt.triples && opt.field_terms && opt.rotation) fb = start_field_basis(E, H, wt, opt.basis);
   const int g = E.node({n, n, n, n}, false, false);
   E.contract("Ppq,Prs->pqrs", 1.0, E.v(Lt), E.v(Lt), E.v(g), false);
   // f~ = h~ + sum_k 2 g~_pqkk - g~_pkkq
