@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -42,23 +43,27 @@ struct Runner : Base {
   ~Runner() override {
     for (void* p : owned) cudaFree(p);
   }
-  // FP64 eigenbasis of the next Runge-Kutta stage, decomposed ahead of it
-  BasisBuffers ahead;
-  const BasisBuffers& ahead_buffers() {
-    if (!ahead.Mo) {
+  // FP64 eigenbases decomposed ahead of their stage: set 0 for the stages
+  // inside a Runge-Kutta step, set 1 + b for the first stage of slot b's next
+  // step (allocated on first use, before any graph capture)
+  std::deque<BasisBuffers> ahead;  // growing keeps references valid
+  const BasisBuffers* ahead_buffers(int set) {
+    if (int(ahead.size()) <= set) ahead.resize(set + 1);
+    BasisBuffers& bb = ahead[set];
+    if (!bb.Mo) {
       const size_t oo = size_t(o) * o, vv = size_t(v) * v;
-      ahead.Mo = alloc<double2>(oo);
-      ahead.So = alloc<double2>(oo);
-      ahead.Sio = alloc<double2>(oo);
-      ahead.wso = alloc<double2>(3 * oo);
-      ahead.lo = alloc<double2>(o);
-      ahead.Mv = alloc<double2>(vv);
-      ahead.Sv = alloc<double2>(vv);
-      ahead.Siv = alloc<double2>(vv);
-      ahead.wsv = alloc<double2>(3 * vv);
-      ahead.lv = alloc<double2>(v);
+      bb.Mo = alloc<double2>(oo);
+      bb.So = alloc<double2>(oo);
+      bb.Sio = alloc<double2>(oo);
+      bb.wso = alloc<double2>(3 * oo);
+      bb.lo = alloc<double2>(o);
+      bb.Mv = alloc<double2>(vv);
+      bb.Sv = alloc<double2>(vv);
+      bb.Siv = alloc<double2>(vv);
+      bb.wsv = alloc<double2>(3 * vv);
+      bb.lv = alloc<double2>(v);
     }
-    return ahead;
+    return &bb;
   }
   template <typename T>
   T* alloc(size_t count) {
@@ -203,15 +208,46 @@ int field_sweeps(const rtcc3_ctx* ctx, int b) {
   return std::max(1, std::min(k, 200));
 }
 
-// Field eigenbasis look-ahead inside one Runge-Kutta step: the next stage's
-// O and V depend only on its t1 (known once this stage's forward residual r1
-// is) and its field, so their decomposition runs on the side stream during
-// this stage's backward pass instead of stalling the next stage.
+// Field eigenbasis look-ahead: the next stage's O and V depend only on its t1
+// (known once this stage's forward residual r1 is) and its field, so their
+// decomposition runs on the side stream during this stage's backward pass
+// instead of stalling the next stage.  The next stage's t1 = base + ch (-i r1)
+// with base = y inside a step and base = the RK4 accumulator at its last stage.
 struct Ahead {
-  bool use = false;     // this stage's basis was decomposed ahead
-  bool launch = false;  // decompose the next stage's basis after the forward pass
+  const BasisBuffers* use = nullptr;   // this stage's basis, decomposed ahead
+  const BasisBuffers* make = nullptr;  // decompose the next stage's basis into these
+  const double2* base = nullptr;
   double ch = 0.0, dt = 0.0;  // the next stage's input step and time offset
 };
+
+// Whether propagation stages use the field-dressed eigenbasis (the condition
+// under which record_stage starts one).
+bool basis_stages(const rtcc3_ctx* ctx) {
+  return ctx->opt.triples != 0 && ctx->opt.field_solver == 0;
+}
+
+// M and its decomposition into bb for a stage with t1 = base + ch (-i r1)
+// (r1 may be null: t1 = base) and the field of slot `f` at *tdev + dt.
+template <typename R>
+void launch_basis_ahead(rtcc3_ctx* ctx, const BasisBuffers& bb, const double2* base,
+                        const Cx<R>* r1, double ch, const FieldDev* f, double dt) {
+  Engine<R>& E = ctx->run<R>().E;
+  {
+    PScope ps(ctx->prof, ctx->stream, "field_matrices_ahead", 0.0, 0.0);
+    launch_next_field_matrices<R>(base, r1, ch, ctx->mu, f, ctx->tdev, dt, ctx->eps, ctx->o,
+                                  ctx->v, bb.Mo, bb.Mv, ctx->stream);
+  }
+  // M is written on the main stream (r1 lives in the stage's arena); the
+  // decomposition runs on the side stream, which the consuming stage joins
+  E.fork();
+  const cudaStream_t ss = E.side_stream();
+  const int pk = E.prof_begin(ss);
+  const EigJob jo{bb.Mo, ctx->o, bb.So, bb.Sio, bb.lo, bb.wso};
+  const EigJob jv{bb.Mv, ctx->v, bb.Sv, bb.Siv, bb.lv, bb.wsv};
+  launch_eig(jo, jv, sizeof(R) == 4, E.error_flag(), ss);
+  E.prof_end(pk, ss, "field_eig_ahead", 0.0, 0.0);
+  E.add_launches(2);
+}
 
 // One stage evaluation for slot b: records the graph with inputs
 // y_b + ch * kprev at time *tsrc + dt and, if need_grad, runs the backward
@@ -231,7 +267,7 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
   so.field_iters = sweeps;
   so.rotation = ctx->opt.field_solver == 0;
   const bool basis_stage = so.triples && so.field_terms && so.rotation;
-  if (ahead.use && basis_stage) so.basis = &Rn.ahead_buffers();
+  if (basis_stage) so.basis = ahead.use;
   (void)ccsd_terms;
   StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
     PScope ps(ctx->prof, ctx->stream, "stage_inputs", 0.0,
@@ -240,24 +276,8 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
                            E.data(s.w), ctx->mu, f, tsrc, dt, ctx->o, ctx->v, ctx->n, ctx->stream);
     E.add_launches(1);
   });
-  if (ahead.launch && basis_stage) {
-    // M on the main stream (this stage's r1 lives in its arena), the
-    // decomposition on the side stream; the next stage's join orders both
-    const BasisBuffers& bb = Rn.ahead_buffers();
-    {
-      PScope ps(ctx->prof, ctx->stream, "field_matrices_ahead", 0.0, 0.0);
-      launch_next_field_matrices<R>(ybase, E.data(S.r1), ahead.ch, ctx->mu, f, tsrc, ahead.dt,
-                                    ctx->eps, ctx->o, ctx->v, bb.Mo, bb.Mv, ctx->stream);
-    }
-    E.fork();
-    const cudaStream_t ss = E.side_stream();
-    const int pk = E.prof_begin(ss);
-    const EigJob jo{bb.Mo, ctx->o, bb.So, bb.Sio, bb.lo, bb.wso};
-    const EigJob jv{bb.Mv, ctx->v, bb.Sv, bb.Siv, bb.lv, bb.wsv};
-    launch_eig(jo, jv, sizeof(R) == 4, E.error_flag(), ss);
-    E.prof_end(pk, ss, "field_eig_ahead", 0.0, 0.0);
-    E.add_launches(2);
-  }
+  if (ahead.make && basis_stage)
+    launch_basis_ahead<R>(ctx, *ahead.make, ahead.base, E.data(S.r1), ahead.ch, f, ahead.dt);
   if (need_grad) {
     E.prepare_backward();
     {
@@ -396,9 +416,14 @@ void rk4_step(rtcc3_ctx* ctx, double h, const std::vector<int>& sweeps) {
     }
     for (int s = 0; s < 4; ++s) {
       Ahead ah;
-      ah.use = s > 0;
-      ah.launch = s < 3;
-      ah.ch = ah.dt = s < 3 ? cs[s + 1] * h : 0.0;
+      if (basis_stages(ctx)) {
+        // stage 0 was decomposed by the previous step (or by prime_basis_ahead)
+        ah.use = Rn.ahead_buffers(s == 0 ? 1 + b : 0);
+        ah.make = Rn.ahead_buffers(s == 3 ? 1 + b : 0);
+        ah.base = s == 3 ? ctx->acc : yb;
+        ah.ch = s == 3 ? h * ws[3] / 6.0 : cs[s + 1] * h;
+        ah.dt = s == 3 ? h : cs[s + 1] * h;
+      }
       StageNodes S = eval_stage<R>(ctx, b, yb, s == 0 ? nullptr : ctx->kbuf, cs[s] * h, ctx->tdev,
                                    cs[s] * h, true, ctx->fdev + b, true, sweeps[b], true, ah);
       if (s == 0) {
@@ -421,6 +446,22 @@ void rk4_step(rtcc3_ctx* ctx, double h, const std::vector<int>& sweeps) {
   }
   launch_step_advance(ctx->tdev, h, ctx->stepdev, ctx->stream);
   E.add_launches(1);
+  // the next step's first-stage bases were decomposed during the last stages'
+  // backward passes; a captured step must not leave side-stream work unjoined
+  E.join();
+}
+
+// Decompose the first-stage basis of every slot's next step from its current
+// state (the state or the field may have changed since the last step).
+template <typename R>
+void prime_basis_ahead(rtcc3_ctx* ctx) {
+  if (!basis_stages(ctx)) return;
+  Runner<R>& Rn = ctx->run<R>();
+  for (int b = 0; b < ctx->nb; ++b)
+    launch_basis_ahead<R>(ctx, *Rn.ahead_buffers(1 + b), ctx->y + size_t(b) * ctx->ny, nullptr,
+                          0.0, ctx->fdev + b, 0.0);
+  // a captured step graph orders itself after the main stream only
+  Rn.E.join();
 }
 
 template <typename R>
@@ -484,6 +525,11 @@ void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2*
     drop_graph(ctx);
   int done = 0;
   long long launches = 0;
+  if (nsteps > 0) {
+    prime_basis_ahead<R>(ctx);
+    launches += E.launches();
+    E.reset_launch_count();
+  }
   if (graphs && !ctx->gexec && nsteps > 0) {
     rk4_step<R>(ctx, h, sweeps);  // eager first step: builds plans, arena and scratch
     done = 1;

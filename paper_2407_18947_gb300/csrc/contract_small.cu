@@ -34,7 +34,7 @@ struct SmallShape {
   // stores of K-contiguous loads do not hit one bank
   static constexpr int MS = MP + 1, NS = NP + 1;
   static constexpr int TILE_BYTES = BK * (MS + NS) * EB;
-  static constexpr int RED_BYTES = GS > 1 ? GS * MP * NP * EB : 0;
+  static constexpr int RED_BYTES = GS > 1 ? MP * NP * EB : 0;
   static constexpr int SMEM = TILE_BYTES > RED_BYTES ? TILE_BYTES : RED_BYTES;
   static_assert(G >= 1 && BK >= G, "slice shallower than the thread groups");
   static_assert(SMEM <= 48 * 1024, "static shared memory");
@@ -152,25 +152,23 @@ k_reduce_small(const Cx<R>* __restrict__ A, long long aoff, const long long* __r
       for (int j = 0; j < UN; ++j) store(rm + RM * i, rn + RN * j, accr[i][j], acci[i][j]);
     return;
   }
-  Cx<R>* red = reinterpret_cast<Cx<R>*>(smem);  // [GS][MP][NP]
-  if (g % S::WG == 0) {
-    const int gs = g / S::WG;
+  // one [MP][NP] tile in shared memory, the warp-level partials added into it
+  // one group after another (fixed order)
+  Cx<R>* red = reinterpret_cast<Cx<R>*>(smem);
+  for (int gs = 0; gs < S::GS; ++gs) {
+    if (g % S::WG == 0 && g / S::WG == gs) {
 #pragma unroll
-    for (int i = 0; i < UM; ++i)
+      for (int i = 0; i < UM; ++i)
 #pragma unroll
-      for (int j = 0; j < UN; ++j)
-        red[(size_t(gs) * MP + rm + RM * i) * NP + rn + RN * j] = cmake<R>(accr[i][j], acci[i][j]);
-  }
-  __syncthreads();
-  for (int t = tid; t < MP * NP; t += kThreads) {
-    R re = 0, im = 0;
-    for (int gs = 0; gs < S::GS; ++gs) {
-      const Cx<R> p = red[size_t(gs) * MP * NP + t];
-      re += p.x;
-      im += p.y;
+        for (int j = 0; j < UN; ++j) {
+          Cx<R>& r = red[(rm + RM * i) * NP + rn + RN * j];
+          r = gs == 0 ? cmake<R>(accr[i][j], acci[i][j])
+                      : cmake<R>(r.x + accr[i][j], r.y + acci[i][j]);
+        }
     }
-    store(t / NP, t % NP, re, im);
+    __syncthreads();
   }
+  for (int t = tid; t < MP * NP; t += kThreads) store(t / NP, t % NP, red[t].x, red[t].y);
 }
 
 // C[cM[m] + cN[n]] (+)= alpha sum_s part[m][n][s]: one warp per output, the
@@ -279,7 +277,9 @@ void launch_cfg(bool a_kc, bool b_kc, const Cx<R>* A, long long aoff, const long
 }  // namespace
 
 int small_output_config(long long M, long long N) {
+  if (M <= 10 && N <= 10) return kSmall10;
   if (M <= 16 && N <= 16) return kSmall16;
+  if (M <= 40 && N <= 40) return kSmall40;
   if (M <= 48 && N <= 48) return kSmall48;
   if (M <= 64 && N <= 64) return kSmall64;
   if (N == 1 && M <= 256) return kSmallCol256;
@@ -290,7 +290,9 @@ int small_output_config(long long M, long long N) {
 int small_output_bk(int cfg, int elem_bytes) {
   const bool d = elem_bytes == 16;
   switch (cfg) {
+    case kSmall10: return d ? SmallShape<double, 2, 2, 5, 5>::BK : SmallShape<float, 2, 2, 5, 5>::BK;
     case kSmall16: return d ? SmallShape<double, 4, 4, 4, 4>::BK : SmallShape<float, 4, 4, 4, 4>::BK;
+    case kSmall40: return d ? SmallShape<double, 8, 8, 5, 5>::BK : SmallShape<float, 8, 8, 5, 5>::BK;
     case kSmall48: return d ? SmallShape<double, 16, 16, 3, 3>::BK : SmallShape<float, 16, 16, 3, 3>::BK;
     case kSmall64: return d ? SmallShape<double, 16, 16, 4, 4>::BK : SmallShape<float, 16, 16, 4, 4>::BK;
     case kSmallCol256: return d ? SmallShape<double, 64, 1, 4, 1>::BK : SmallShape<float, 64, 1, 4, 1>::BK;
@@ -306,6 +308,14 @@ void launch_reduce_small(int cfg, bool a_kc, bool b_kc, const Cx<R>* A, long lon
                          const long long* cM, const long long* cN, int M, int N, int K, int nsplit,
                          int kchunk, double alpha, bool accumulate, Cx<R>* part, cudaStream_t s) {
   switch (cfg) {
+    case kSmall10:
+      launch_cfg<R, 2, 2, 5, 5>(a_kc, b_kc, A, aoff, aM, aK, B, boff, bN, bK, C, coff, cM, cN, M, N, K,
+                                nsplit, kchunk, alpha, accumulate, part, s);
+      break;
+    case kSmall40:
+      launch_cfg<R, 8, 8, 5, 5>(a_kc, b_kc, A, aoff, aM, aK, B, boff, bN, bK, C, coff, cM, cN, M, N, K,
+                                nsplit, kchunk, alpha, accumulate, part, s);
+      break;
     case kSmall16:
       launch_cfg<R, 4, 4, 4, 4>(a_kc, b_kc, A, aoff, aM, aK, B, boff, bN, bK, C, coff, cM, cN, M, N, K,
                                 nsplit, kchunk, alpha, accumulate, part, s);

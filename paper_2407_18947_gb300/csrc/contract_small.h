@@ -19,7 +19,8 @@ namespace rtcc3 {
 
 // Output-tile configurations of reduce_small (0 = not applicable).
 enum SmallCfg : int {
-  kSmallNone = 0, kSmall48 = 1, kSmall16 = 2, kSmallCol256 = 3, kSmallCol512 = 4, kSmall64 = 5
+  kSmallNone = 0, kSmall48 = 1, kSmall16 = 2, kSmallCol256 = 3, kSmallCol512 = 4, kSmall64 = 5,
+  kSmall10 = 6, kSmall40 = 7
 };
 
 // Configuration for an M x N output (N <= M expected; returns kSmallNone

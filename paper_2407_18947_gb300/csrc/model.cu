@@ -402,8 +402,10 @@ __global__ void k_next_field_matrices(const double2* __restrict__ y, const Cx<R>
   auto t1 = [&](int i, int a) {
     const size_t t = size_t(i) * v + a;
     double vx = y[t].x, vy = y[t].y;
-    vx += ch * double(r1[t].y);  // k = -i r1
-    vy += ch * -double(r1[t].x);
+    if (r1) {
+      vx += ch * double(r1[t].y);  // k = -i r1
+      vy += ch * -double(r1[t].x);
+    }
     return make_double2(double(R(vx)), double(R(vy)));
   };
   auto w = [&](int p, int q) {

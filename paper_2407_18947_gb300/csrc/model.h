@@ -67,7 +67,8 @@ void launch_stage_inputs(const double2* y, const double2* kprev, double ch, Cx<R
                          Cx<R>* l1s, Cx<R>* l2s, Cx<R>* w, const double* mu, const FieldDev* f,
                          const double* tdev, double dt, int o, int v, int n, cudaStream_t s);
 // O and V (as launch_field_matrices) of the NEXT Runge-Kutta stage from this
-// stage's forward residual: that stage's t1 = y1 + ch * (-i r1) and
+// stage's forward residual: that stage's t1 = y1 + ch * (-i r1) (y1 alone if
+// r1 is null) and
 // w = -E(*tdev + dt) dir . mu, both rounded to R exactly as the stage inputs
 // are, dressed as w~ = (1 - tau) w (1 + tau) with the FP64 sums
 //   O[i][l] = e_i d_il + w_li + sum_a w_l,a t1_ia,

@@ -32,21 +32,19 @@ FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt,
   const int o = H.o, v = H.v;
   Arena& A = E.arena();
   auto c2 = [&](size_t n) { return static_cast<double2*>(A.alloc(sizeof(double2) * n)); };
+  // the arena layout does not depend on `ahead`
   BasisBuffers bb;
-  if (ahead) {
-    bb = *ahead;
-  } else {
-    bb.Mo = c2(size_t(o) * o);
-    bb.Mv = c2(size_t(v) * v);
-    bb.So = c2(size_t(o) * o);
-    bb.Sio = c2(size_t(o) * o);
-    bb.Sv = c2(size_t(v) * v);
-    bb.Siv = c2(size_t(v) * v);
-    bb.lo = c2(o);
-    bb.lv = c2(v);
-    bb.wso = c2(3 * size_t(o) * o);
-    bb.wsv = c2(3 * size_t(v) * v);
-  }
+  bb.Mo = c2(size_t(o) * o);
+  bb.Mv = c2(size_t(v) * v);
+  bb.So = c2(size_t(o) * o);
+  bb.Sio = c2(size_t(o) * o);
+  bb.Sv = c2(size_t(v) * v);
+  bb.Siv = c2(size_t(v) * v);
+  bb.lo = c2(o);
+  bb.lv = c2(v);
+  bb.wso = c2(3 * size_t(o) * o);
+  bb.wsv = c2(3 * size_t(v) * v);
+  if (ahead) bb = *ahead;
   double2 *So64 = bb.So, *Sio64 = bb.Sio, *Sv64 = bb.Sv, *Siv64 = bb.Siv, *lo = bb.lo, *lv = bb.lv;
   FieldBasis<R> B;
   B.osum = static_cast<Cx<R>*>(A.alloc(sizeof(Cx<R>) * size_t(o) * o * o));

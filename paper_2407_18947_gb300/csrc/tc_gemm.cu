@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, EW == 4 ? 2 : 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           int M, int Nr, int nkb_total, int kb_per_split, int kb_lo, float2* __restrict__ C,
           const long long* __restrict__ cM, const long long* __restrict__ cN, long long coff,
-          float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err) {
+          float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err,
+          int m_fast) {
   using L = TcSmem<BN, SPLIT, EW>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -173,7 +174,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   float* stage_out = reinterpret_cast<float*>(smem + L::kStageOutOff);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+  // m_fast: consecutive CTAs walk the M tiles of one N tile (the B tile is
+  // fetched from DRAM once and served from L2; A, the smaller operand, stays
+  // resident), else the N tiles of one M tile
+  const int m0 = (m_fast ? blockIdx.x : blockIdx.y) * kBM;
+  const int n0 = (m_fast ? blockIdx.y : blockIdx.x) * BN;
   const int split = blockIdx.z;
   const int kb0 = split * kb_per_split;
   const int nkb = max(0, min(nkb_total, kb0 + kb_per_split) - kb0);
@@ -504,10 +509,16 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
   const int Nr = 2 * op.N;
   const int nkb = op.Kp / (128 / op.elem_bytes);
   const int per = (nkb + nsplit - 1) / nsplit;
-  dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, nsplit);
+  // walk the tiles of the operand that is re-read (once per tile of the other
+  // dimension) over the smaller one, so that the larger streams from DRAM once
+  const int mt = (op.M + kBM - 1) / kBM, nt = (Nr + BN - 1) / BN;
+  const double a_bytes = double(op.M) * op.Kp * op.elem_bytes;
+  const double b_bytes = double(Nr) * op.Kp * op.elem_bytes * (SPLIT ? 2 : 1);
+  const bool m_fast = mt > 1 && nt > 1 && a_bytes < b_bytes;
+  const dim3 grid(m_fast ? mt : nt, m_fast ? nt : mt, nsplit);
   k_tc_gemm<BN, BF16, SPLIT, EW><<<grid, L::kThreads, L::kTotal, s>>>(
       ma, mb, op.M, Nr, nkb, per, nkb, C, cM, cN, coff, alpha, accumulate ? 1 : 0,
-      nsplit > 1 ? partial : nullptr, err);
+      nsplit > 1 ? partial : nullptr, err, m_fast ? 1 : 0);
   RTCC3_CUDA(cudaGetLastError());
 }
 
