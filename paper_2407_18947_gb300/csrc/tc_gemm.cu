@@ -137,6 +137,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // other's main loop, for products bound by their output).
 template <int BN, bool SPLIT, int EW>
 struct TcSmem {
+  // TMEM columns of the FP32 accumulator (an allocation is a power of two >= 32)
+  static constexpr int kTmemCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
   static constexpr int kABytes = kBM * 128;
   static constexpr int kALoBytes = SPLIT ? kBM * 128 : 0;
   static constexpr int kBBytes = BN * 128;
@@ -159,8 +161,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, EW == 4 ? 2 : 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           int M, int Nr, int nkb_total, int kb_per_split, int kb_lo, float2* __restrict__ C,
           const long long* __restrict__ cM, const long long* __restrict__ cN, long long coff,
-          float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err,
-          int m_fast) {
+          float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err) {
   using L = TcSmem<BN, SPLIT, EW>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -174,11 +175,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   float* stage_out = reinterpret_cast<float*>(smem + L::kStageOutOff);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // m_fast: consecutive CTAs walk the M tiles of one N tile (the B tile is
-  // fetched from DRAM once and served from L2; A, the smaller operand, stays
-  // resident), else the N tiles of one M tile
-  const int m0 = (m_fast ? blockIdx.x : blockIdx.y) * kBM;
-  const int n0 = (m_fast ? blockIdx.y : blockIdx.x) * BN;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
   const int split = blockIdx.z;
   const int kb0 = split * kb_per_split;
   const int nkb = max(0, min(nkb_total, kb0 + kb_per_split) - kb0);
@@ -197,7 +194,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(BN)
+                 "r"(L::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -350,11 +347,204 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (warp == 1) {
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols)
                  : "memory");
   }
 }
 
+
+// Shared-memory plan of the chained long-sum kernel: the same stage layout as
+// TcSmem, a ring of up to 224 KB (no transpose staging), two accumulators.
+template <int BN, bool SPLIT>
+struct TcChainSmem {
+  using T = TcSmem<BN, SPLIT, 8>;
+  static constexpr int kStageBytes = T::kStageBytes;
+  static constexpr int kRing = 229376;
+  static constexpr int kStages = kRing / kStageBytes < 6 ? kRing / kStageBytes : 6;
+  static constexpr int kBarOff = kStages * kStageBytes;
+  static constexpr int kTotal = kBarOff + 256 + 1024;  // barriers + alignment slack
+  // two accumulators, the second at column kTmemCols / 2 (a power of two)
+  static constexpr int kTmemCols = 2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512));
+  static_assert(kStages >= 2 && kTotal <= 232448, "shared memory per CTA");
+};
+
+// Long sums split into accumulation chains of at most `per` K tiles (the
+// FP32 accumulator's error grows with the chain).  One CTA streams the K
+// tiles of `cpc` consecutive chains through its ring without draining the
+// pipeline between them: the MMA warp alternates two TMEM accumulators and,
+// while it fills one, four drain warps copy the other's finished chain to its
+// FP32 partial (partial[(chain M + m) Nr + n], summed later by
+// tc_split_finish).  Warps: 0 TMA, 1 MMA, 2-5 TF32 hi/lo split of A, 6-9
+// drain.  The chains and the products in each are those of the one-chain-per-
+// CTA kernel, so the partials are the same.
+template <int BN, bool BF16, bool SPLIT>
+__global__ void __launch_bounds__(320, 1)
+k_tc_gemm_chains(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 int M, int Nr, int nkb_total, int per, int nchains, int cpc, int kb_lo,
+                 float* __restrict__ partial, int* __restrict__ err) {
+  using T = TcSmem<BN, SPLIT, 8>;
+  using L = TcChainSmem<BN, SPLIT>;
+  constexpr int kStages = L::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* conv = bars + 2 * kStages;   // SPLIT: low parts of A written
+  uint64_t* cfull = bars + 3 * kStages;  // [2] accumulator holds a finished chain
+  uint64_t* cfree = cfull + 2;           // [2] accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+  const int ch0 = blockIdx.z * cpc;
+  const int nch = max(0, min(nchains, ch0 + cpc) - ch0);
+  const int kb0 = ch0 * per;
+  const int nkb = max(0, min(nkb_total, kb0 + nch * per) - kb0);
+  constexpr int kElemPerK = BF16 ? 64 : 32;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(smem_u32(&full[st]), 1);
+      mbar_init(smem_u32(&empty[st]), 1);
+      mbar_init(smem_u32(&conv[st]), 4);  // one arrival per splitting warp
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&cfull[b]), 1);
+      mbar_init(smem_u32(&cfree[b]), 4);  // one arrival per drain warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(L::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int st = i % kStages;
+        if (i >= kStages) ok = mbar_wait(smem_u32(&empty[st]), ((i / kStages) - 1) & 1);
+        if (!ok) break;
+        const uint32_t fb = smem_u32(&full[st]);
+        mbar_expect_tx(fb, T::kTmaBytes);
+        uint8_t* sa = smem + st * T::kStageBytes;
+        uint8_t* sb = sa + T::kABytes + T::kALoBytes;
+        const int kx = (kb0 + i) * kElemPerK;
+        tma_load_2d(smem_u32(sa), &tmA, kx, m0, fb);
+        tma_load_2d(smem_u32(sb), &tmB, kx, n0, fb);
+        if (SPLIT) tma_load_2d(smem_u32(sb + T::kBBytes), &tmB, kx + kb_lo * kElemPerK, n0, fb);
+      }
+      // no copy into shared memory may be outstanding at exit
+      for (int i = max(0, nkb - kStages); i < nkb && ok; ++i)
+        ok = mbar_wait(smem_u32(&empty[i % kStages]), (i / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = instr_desc<BF16>(kBM, BN);
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int st = i % kStages, j = i / per, pos = i - j * per, b = j & 1;
+        // the accumulator's previous chain (j - 2) must have been drained
+        if (pos == 0 && j >= 2) ok = mbar_wait(smem_u32(&cfree[b]), ((j >> 1) - 1) & 1);
+        if (!ok) break;
+        ok = mbar_wait(smem_u32(SPLIT ? &conv[st] : &full[st]), (i / kStages) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_t = tmem + uint32_t(b * (L::kTmemCols / 2));
+        const uint32_t sa = smem_u32(smem + st * T::kStageBytes);
+        const uint32_t sb = sa + T::kABytes + T::kALoBytes;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t acc = (pos > 0 || kk > 0) ? 1u : 0u;
+          mma<BF16>(acc_t, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, acc);
+          if (SPLIT) {
+            mma<BF16>(acc_t, smem_desc(sa + kk * 32), smem_desc(sb + T::kBBytes + kk * 32), idesc, 1u);
+            mma<BF16>(acc_t, smem_desc(sa + T::kABytes + kk * 32), smem_desc(sb + kk * 32), idesc, 1u);
+          }
+        }
+        mma_commit(smem_u32(&empty[st]));
+        if (pos == per - 1 || i == nkb - 1) mma_commit(smem_u32(&cfull[b]));
+      }
+    }
+  } else if (warp < 6) {
+    if (SPLIT) {
+      const int ct = threadIdx.x - 64;  // 0 .. 127
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int st = i % kStages;
+        ok = mbar_wait(smem_u32(&full[st]), (i / kStages) & 1);
+        if (!ok) break;
+        float4* ah = reinterpret_cast<float4*>(smem + st * T::kStageBytes);
+        float4* al = reinterpret_cast<float4*>(smem + st * T::kStageBytes + T::kABytes);
+#pragma unroll
+        for (int u = 0; u < T::kABytes / 16 / 128; ++u) {
+          const int e = ct + 128 * u;
+          const float4 x = ah[e];
+          float4 h, lo;
+          h.x = __uint_as_float(to_tf32(x.x)); lo.x = x.x - h.x;
+          h.y = __uint_as_float(to_tf32(x.y)); lo.y = x.y - h.y;
+          h.z = __uint_as_float(to_tf32(x.z)); lo.z = x.z - h.z;
+          h.w = __uint_as_float(to_tf32(x.w)); lo.w = x.w - h.w;
+          ah[e] = h;
+          al[e] = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&conv[st]));
+      }
+    }
+  } else {
+    // drain warps 6-9: TMEM lane quarter warp % 4, all BN columns
+    const int q = warp & 3;
+    const int m = m0 + q * 32 + lane;
+    const bool vec = (Nr & 3) == 0;
+    for (int j = 0; j < nch && ok; ++j) {
+      const int b = j & 1;
+      ok = mbar_wait(smem_u32(&cfull[b]), (j >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* dst = partial + (size_t(ch0 + j) * M + (m < M ? m : 0)) * size_t(Nr) + n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(b * (L::kTmemCols / 2) + c0), r);
+        if (m < M) {
+          if (vec && n0 + c0 + 32 <= Nr) {
+#pragma unroll
+            for (int jj = 0; jj < 32; jj += 4)
+              *reinterpret_cast<float4*>(dst + c0 + jj) =
+                  make_float4(__uint_as_float(r[jj]), __uint_as_float(r[jj + 1]),
+                              __uint_as_float(r[jj + 2]), __uint_as_float(r[jj + 3]));
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj)
+              if (n0 + c0 + jj < Nr) dst[c0 + jj] = __uint_as_float(r[jj]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&cfree[b]));
+    }
+  }
+  if (!ok && err) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols)
+                 : "memory");
+  }
+}
 
 // One thread per complex source element: its (re, im) pair is written to
 // every K segment (and, for B, to both rows of its 2x2 embedding) with one
@@ -509,17 +699,51 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
   const int Nr = 2 * op.N;
   const int nkb = op.Kp / (128 / op.elem_bytes);
   const int per = (nkb + nsplit - 1) / nsplit;
-  // walk the tiles of the operand that is re-read (once per tile of the other
-  // dimension) over the smaller one, so that the larger streams from DRAM once
-  const int mt = (op.M + kBM - 1) / kBM, nt = (Nr + BN - 1) / BN;
-  const double a_bytes = double(op.M) * op.Kp * op.elem_bytes;
-  const double b_bytes = double(Nr) * op.Kp * op.elem_bytes * (SPLIT ? 2 : 1);
-  const bool m_fast = mt > 1 && nt > 1 && a_bytes < b_bytes;
-  const dim3 grid(m_fast ? mt : nt, m_fast ? nt : mt, nsplit);
+  dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, nsplit);
   k_tc_gemm<BN, BF16, SPLIT, EW><<<grid, L::kThreads, L::kTotal, s>>>(
       ma, mb, op.M, Nr, nkb, per, nkb, C, cM, cN, coff, alpha, accumulate ? 1 : 0,
-      nsplit > 1 ? partial : nullptr, err, m_fast ? 1 : 0);
+      nsplit > 1 ? partial : nullptr, err);
   RTCC3_CUDA(cudaGetLastError());
+}
+
+// Chained long-sum launch (see k_tc_gemm_chains); false if the split does
+// not map onto whole chains.
+template <int BN, bool BF16, bool SPLIT>
+bool launch_chains(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, int nsplit,
+                   float* partial, int* err, cudaStream_t s) {
+  using L = TcChainSmem<BN, SPLIT>;
+  const int Nr = 2 * op.N;
+  const int nkb = op.Kp / (128 / op.elem_bytes);
+  const int per = (nkb + nsplit - 1) / nsplit;
+  const int nchains = (nkb + per - 1) / per;
+  if (nchains != nsplit) return false;  // every partial slice must be written
+  static bool attr = false;
+  if (!attr) {
+    RTCC3_CUDA(cudaFuncSetAttribute(k_tc_gemm_chains<BN, BF16, SPLIT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal));
+    attr = true;
+  }
+  // CTAs per output tile: the fewest that fill whole waves of one CTA per SM
+  // to 90 % (else the best fill), each streaming its share of the chains
+  const long long tiles = (long long)((Nr + BN - 1) / BN) * ((op.M + kBM - 1) / kBM);
+  int z = 1;
+  double best = 0.0;
+  for (int c = 1; c <= nchains; ++c) {
+    const long long ctas = tiles * c;
+    const double eff = double(ctas) / double(((ctas + 151) / 152) * 152);
+    if (eff > best + 1e-9) {
+      best = eff;
+      z = c;
+    }
+    if (eff >= 0.9) break;
+  }
+  const int cpc = (nchains + z - 1) / z;
+  const int zz = (nchains + cpc - 1) / cpc;
+  dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, zz);
+  k_tc_gemm_chains<BN, BF16, SPLIT><<<grid, 320, L::kTotal, s>>>(ma, mb, op.M, Nr, nkb, per,
+                                                                  nchains, cpc, nkb, partial, err);
+  RTCC3_CUDA(cudaGetLastError());
+  return true;
 }
 
 }  // namespace
@@ -550,13 +774,27 @@ bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2*
 #define RTCC3_TC(BNV, EWV)                                                                        \
   (bf16 ? launch<BNV, true, false, EWV>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s) \
         : launch<BNV, false, true, EWV>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s))
-  if (op.out_bound) {
+#define RTCC3_CH(BNV)                                                                     \
+  (bf16 ? launch_chains<BNV, true, false>(ma, mb, op, nsplit, partial, err_flag, s)        \
+        : launch_chains<BNV, false, true>(ma, mb, op, nsplit, partial, err_flag, s))
+  bool chained = false;
+  if (!op.out_bound && nsplit > 1 && partial) {
+    if (BN == 128) chained = RTCC3_CH(128);
+    else if (BN == 96) chained = RTCC3_CH(96);
+    else if (BN == 64) chained = RTCC3_CH(64);
+    else if (BN == 32) chained = RTCC3_CH(32);
+  }
+#undef RTCC3_CH
+  if (chained) {
+  } else if (op.out_bound) {
     if (BN == 128) RTCC3_TC(128, 4);
     else RTCC3_TC(64, 4);
   } else {
     if (BN == 256) RTCC3_TC(256, 8);
     else if (BN == 128) RTCC3_TC(128, 8);
-    else RTCC3_TC(64, 8);
+    else if (BN == 96) RTCC3_TC(96, 8);
+    else if (BN == 64) RTCC3_TC(64, 8);
+    else RTCC3_TC(32, 8);
   }
 #undef RTCC3_TC
   return true;

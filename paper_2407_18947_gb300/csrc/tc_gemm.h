@@ -32,9 +32,14 @@ struct TcOperands {
 // narrowest of 64 / 128 / 256 that holds them (one column tile, the A tile
 // read once), at most 128 for output-bound products.
 inline int tc_tile_n(int Nr, bool out_bound) {
-  const int cap = out_bound ? 128 : 256;
+  if (out_bound) return Nr <= 64 ? 64 : 128;
+  // long sums with narrow outputs: the tile's unused columns are tensor-core
+  // work the operand stream has to wait for (N = 10 complex -> 20 real
+  // columns, N = 38 -> 76)
+  if (Nr <= 32) return 32;
   if (Nr <= 64) return 64;
-  if (Nr <= 128 || cap == 128) return 128;
+  if (Nr <= 96) return 96;
+  if (Nr <= 128) return 128;
   return 256;
 }
 // CTAs resident per SM for the two variants.
