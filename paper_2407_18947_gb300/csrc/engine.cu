@@ -1039,7 +1039,9 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     const long long* gcN = sw ? P.cM : P.cN;
     const long long goa = sw ? P.b_off0 : P.a_off0;
     const long long gob = sw ? P.a_off0 : P.b_off0;
-    void* apk = scratch(1, size_t(op.M) * op.Kp * tc_eb_);
+    op.a_tiled = tc_chained(op, P.tc_nsplit);
+    const size_t a_rows = op.a_tiled ? size_t((op.M + 127) / 128) * 128 : size_t(op.M);
+    void* apk = scratch(1, a_rows * op.Kp * tc_eb_);
     void* bpk = scratch(2, size_t(2 * op.N) * op.Kp * tc_eb_ * (op.split ? 2 : 1));
     float* part = nullptr;
     if (P.tc_nsplit > 1)
@@ -1047,8 +1049,8 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     int* err = error_flag();
     const double pbytes = double(op.M + 2.0 * op.N) * op.K * 2.0 * sizeof(float);
     int pk = pbegin();
-    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, tc_eb_, sw ? P.b_kcontig : P.a_kcontig, apk,
-              stream_);
+    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, tc_eb_, sw ? P.b_kcontig : P.a_kcontig,
+              op.a_tiled, apk, stream_);
     tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, tc_eb_, sw ? P.a_kcontig : P.b_kcontig, bpk,
               stream_);
     pend(pk, "tc_pack", 0.0, pbytes + double(op.M + 2.0 * op.N) * op.Kp * tc_eb_, cur_detail_);

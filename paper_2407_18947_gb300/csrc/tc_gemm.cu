@@ -71,6 +71,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Contiguous global -> shared copy (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -374,12 +383,12 @@ struct TcChainSmem {
 // pipeline between them: the MMA warp alternates two TMEM accumulators and,
 // while it fills one, four drain warps copy the other's finished chain to its
 // FP32 partial (partial[(chain M + m) Nr + n], summed later by
-// tc_split_finish).  Warps: 0 TMA, 1 MMA, 2-5 TF32 hi/lo split of A, 6-9
+// tc_split_finish).  A comes tiled (TcOperands::a_tiled) by bulk copies.  Warps: 0 TMA, 1 MMA, 2-5 TF32 hi/lo split of A, 6-9
 // drain.  The chains and the products in each are those of the one-chain-per-
 // CTA kernel, so the partials are the same.
 template <int BN, bool BF16, bool SPLIT>
 __global__ void __launch_bounds__(320, 1)
-k_tc_gemm_chains(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUtensorMap tmB,
                  int M, int Nr, int nkb_total, int per, int nchains, int cpc, int kb_lo,
                  float* __restrict__ partial, int* __restrict__ err) {
   using T = TcSmem<BN, SPLIT, 8>;
@@ -439,7 +448,10 @@ k_tc_gemm_chains(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         uint8_t* sa = smem + st * T::kStageBytes;
         uint8_t* sb = sa + T::kABytes + T::kALoBytes;
         const int kx = (kb0 + i) * kElemPerK;
-        tma_load_2d(smem_u32(sa), &tmA, kx, m0, fb);
+        // A tile (row block blockIdx.y, K tile kb0 + i): one contiguous 16 KB
+        // block already in its swizzled shared-memory image
+        bulk_load(smem_u32(sa), Atiled + ((size_t(blockIdx.y) * nkb_total + kb0 + i) << 14),
+                  T::kABytes, fb);
         tma_load_2d(smem_u32(sb), &tmB, kx, n0, fb);
         if (SPLIT) tma_load_2d(smem_u32(sb + T::kBBytes), &tmB, kx + kb_lo * kElemPerK, n0, fb);
       }
@@ -569,7 +581,7 @@ __device__ __forceinline__ void put_pair(void* out, size_t idx, float x, float y
 // TF32 (EB 4): A is written as raw FP32 (split into hi + lo in the GEMM's
 // shared memory) and B as two K segments [hi | lo]; BF16 (EB 2): one
 // segment, rounded to nearest even.
-template <int EB, bool KFAST, bool IS_B>
+template <int EB, bool KFAST, bool IS_B, bool TILED>
 __global__ void __launch_bounds__(256)
 k_pack(const float2* __restrict__ X, const long long* __restrict__ xR, const long long* __restrict__ xK,
        long long xoff, int R, int K, int Kp, int segs, void* out) {
@@ -591,7 +603,16 @@ k_pack(const float2* __restrict__ X, const long long* __restrict__ xR, const lon
     if (r >= R || k >= hw) continue;
     const float2 v = tile[rr][lane];
     const size_t row = (IS_B ? size_t(2 * r) : size_t(r)) * Kp + 2 * size_t(k);
-    if (!IS_B) {
+    if (TILED) {
+      // tile (r / 128, kr / kpt) of 16 KB; row r % 128 at 128 bytes; its
+      // 16-byte chunks permuted by the 128-byte swizzle (chunk ^ row % 8)
+      constexpr int kpt = 128 / EB, epc = 16 / EB;
+      const int kr = 2 * k, kt = kr / kpt, kc = kr % kpt, rr = r & 127;
+      const size_t elem = ((size_t(r >> 7) * (Kp / kpt) + kt) << 14) / EB + size_t(rr) * kpt +
+                          size_t(((kc / epc) ^ (rr & 7)) * epc + kc % epc);
+      if (EB == 4) *reinterpret_cast<float2*>(static_cast<float*>(out) + elem) = v;  // raw FP32
+      else put_pair<EB>(out, elem, v.x, v.y);
+    } else if (!IS_B) {
       if (EB == 4) *reinterpret_cast<float2*>(static_cast<float*>(out) + row) = v;  // raw FP32
       else put_pair<EB>(out, row, v.x, v.y);
     } else {
@@ -612,13 +633,13 @@ k_pack(const float2* __restrict__ X, const long long* __restrict__ xR, const lon
   }
 }
 
-template <bool IS_B>
+template <bool IS_B, bool TILED>
 void launch_pack(const float2* X, const long long* xR, const long long* xK, long long xoff, int R,
                  int K, int Kp, int segs, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
   const int hw = Kp / segs / 2;
   dim3 grid((hw + 31) / 32, (R + 31) / 32);
   RTCC3_CHECK(grid.y < 65536, kErrArg, "packed operand has too many rows");
-#define RTCC3_PK(EBV, KF) k_pack<EBV, KF, IS_B><<<grid, 256, 0, s>>>(X, xR, xK, xoff, R, K, Kp, segs, out)
+#define RTCC3_PK(EBV, KF) k_pack<EBV, KF, IS_B, TILED><<<grid, 256, 0, s>>>(X, xR, xK, xoff, R, K, Kp, segs, out)
   if (elem_bytes == 4) {
     if (kfast) RTCC3_PK(4, true);
     else RTCC3_PK(4, false);
@@ -709,7 +730,7 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
 // Chained long-sum launch (see k_tc_gemm_chains); false if the split does
 // not map onto whole chains.
 template <int BN, bool BF16, bool SPLIT>
-bool launch_chains(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, int nsplit,
+bool launch_chains(const void* Atiled, const CUtensorMap& mb, const TcOperands& op, int nsplit,
                    float* partial, int* err, cudaStream_t s) {
   using L = TcChainSmem<BN, SPLIT>;
   const int Nr = 2 * op.N;
@@ -740,8 +761,8 @@ bool launch_chains(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperand
   const int cpc = (nchains + z - 1) / z;
   const int zz = (nchains + cpc - 1) / cpc;
   dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, zz);
-  k_tc_gemm_chains<BN, BF16, SPLIT><<<grid, 320, L::kTotal, s>>>(ma, mb, op.M, Nr, nkb, per,
-                                                                  nchains, cpc, nkb, partial, err);
+  k_tc_gemm_chains<BN, BF16, SPLIT><<<grid, 320, L::kTotal, s>>>(
+      static_cast<const uint8_t*>(Atiled), mb, op.M, Nr, nkb, per, nchains, cpc, nkb, partial, err);
   RTCC3_CUDA(cudaGetLastError());
   return true;
 }
@@ -749,14 +770,15 @@ bool launch_chains(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperand
 }  // namespace
 
 void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
-               int K, int Kp, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
-  launch_pack<false>(A, aM, aK, aoff, M, K, Kp, 1, elem_bytes, kfast, out, s);
+               int K, int Kp, int elem_bytes, bool kfast, bool tiled, void* out, cudaStream_t s) {
+  if (tiled) launch_pack<false, true>(A, aM, aK, aoff, M, K, Kp, 1, elem_bytes, kfast, out, s);
+  else launch_pack<false, false>(A, aM, aK, aoff, M, K, Kp, 1, elem_bytes, kfast, out, s);
 }
 
 void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
                int K, int Kp, int elem_bytes, bool kfast, void* out, cudaStream_t s) {
   const int segs = elem_bytes == 4 ? 2 : 1;
-  launch_pack<true>(B, bN, bK, boff, N, K, segs * Kp, segs, elem_bytes, kfast, out, s);
+  launch_pack<true, false>(B, bN, bK, boff, N, K, segs * Kp, segs, elem_bytes, kfast, out, s);
 }
 
 bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2* C,
@@ -767,7 +789,7 @@ bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2*
   if (op.Kp % (128 / op.elem_bytes) != 0) return false;
   const int BN = tc_tile_n(Nr, op.out_bound);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, Apack, op.elem_bytes, op.Kp, op.M, kBM)) return false;
+  if (!op.a_tiled && !make_map(&ma, Apack, op.elem_bytes, op.Kp, op.M, kBM)) return false;
   if (!make_map(&mb, Bpack, op.elem_bytes, op.split ? 2 * op.Kp : op.Kp, Nr, BN)) return false;
   const bool bf16 = op.elem_bytes == 2;
   RTCC3_CHECK(bf16 || op.split, kErrArg, "TF32 operands are split in the GEMM (pack B as hi | lo)");
@@ -775,17 +797,17 @@ bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2*
   (bf16 ? launch<BNV, true, false, EWV>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s) \
         : launch<BNV, false, true, EWV>(ma, mb, op, C, cM, cN, coff, alpha, accumulate, nsplit, partial, err_flag, s))
 #define RTCC3_CH(BNV)                                                                     \
-  (bf16 ? launch_chains<BNV, true, false>(ma, mb, op, nsplit, partial, err_flag, s)        \
-        : launch_chains<BNV, false, true>(ma, mb, op, nsplit, partial, err_flag, s))
-  bool chained = false;
-  if (!op.out_bound && nsplit > 1 && partial) {
-    if (BN == 128) chained = RTCC3_CH(128);
-    else if (BN == 96) chained = RTCC3_CH(96);
-    else if (BN == 64) chained = RTCC3_CH(64);
-    else if (BN == 32) chained = RTCC3_CH(32);
-  }
-#undef RTCC3_CH
-  if (chained) {
+  (bf16 ? launch_chains<BNV, true, false>(Apack, mb, op, nsplit, partial, err_flag, s)     \
+        : launch_chains<BNV, false, true>(Apack, mb, op, nsplit, partial, err_flag, s))
+  if (op.a_tiled) {
+    RTCC3_CHECK(tc_chained(op, nsplit) && partial, kErrArg,
+                "tiled A is for chained long sums with split partials");
+    bool launched = false;
+    if (BN == 128) launched = RTCC3_CH(128);
+    else if (BN == 96) launched = RTCC3_CH(96);
+    else if (BN == 64) launched = RTCC3_CH(64);
+    else if (BN == 32) launched = RTCC3_CH(32);
+    RTCC3_CHECK(launched, kErrArg, "chained long sum: unsupported tile");
   } else if (op.out_bound) {
     if (BN == 128) RTCC3_TC(128, 4);
     else RTCC3_TC(64, 4);
@@ -797,6 +819,7 @@ bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2*
     else RTCC3_TC(32, 8);
   }
 #undef RTCC3_TC
+#undef RTCC3_CH
   return true;
 }
 

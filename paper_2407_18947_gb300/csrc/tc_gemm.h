@@ -26,6 +26,11 @@ struct TcOperands {
   // the product is bound by its output (short sum): two CTAs per SM with
   // narrower tiles, so that epilogues overlap main loops
   bool out_bound = false;
+  // A packed in tiles of 128 rows x 128 bytes of K, each stored as the
+  // 128-byte-swizzled shared-memory image the MMA reads and the tiles of one
+  // row block consecutive along K, so a long sum streams A as contiguous
+  // 16 KB blocks (set iff tc_chained)
+  bool a_tiled = false;
 };
 
 // GEMM column tile (real columns) for Nr = 2N real output columns: the
@@ -45,12 +50,23 @@ inline int tc_tile_n(int Nr, bool out_bound) {
 // CTAs resident per SM for the two variants.
 inline int tc_ctas_per_sm(bool out_bound) { return out_bound ? 2 : 1; }
 
+// Whether a long sum split into nsplit accumulation chains runs as the
+// chained kernel (several chains per CTA, tiled A): every chain non-empty and
+// an N tile of at most 128 real columns.
+inline bool tc_chained(const TcOperands& op, int nsplit) {
+  if (op.out_bound || nsplit < 2 || tc_tile_n(2 * op.N, false) > 128) return false;
+  const int nkb = op.Kp / (128 / op.elem_bytes);
+  const int per = (nkb + nsplit - 1) / nsplit;
+  return (nkb + per - 1) / per == nsplit;
+}
+
 // Pack A (complex, addressed by tables) into a K-major real buffer of packed
 // width Kp: raw FP32 for TF32 (elem_bytes 4), BF16 otherwise.  kfast: the
 // source is contiguous along k (else along the row index); the packing
 // kernel reads along that index and writes packed rows along k.
+// tiled: the TcOperands::a_tiled layout (rows rounded up to 128).
 void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
-               int K, int Kp, int elem_bytes, bool kfast, void* out, cudaStream_t s);
+               int K, int Kp, int elem_bytes, bool kfast, bool tiled, void* out, cudaStream_t s);
 // Pack B as its 2x2 real embedding: rows 2n (real part) and 2n+1 (imaginary
 // part); for TF32 as [hi | lo] K segments (row width 2 Kp).
 void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long long boff, int N,
