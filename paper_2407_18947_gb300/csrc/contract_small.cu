@@ -247,6 +247,32 @@ k_gemv(const Cx<R>* __restrict__ A, long long aoff, const long long* __restrict_
   }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_outer(const Cx<R>* __restrict__ A, long long aoff, const long long* __restrict__ aM,
+        const long long* __restrict__ aK, const Cx<R>* __restrict__ B, long long boff,
+        const long long* __restrict__ bN, const long long* __restrict__ bK, Cx<R>* __restrict__ Cp,
+        long long coff, const long long* __restrict__ cM, const long long* __restrict__ cN, int M,
+        int N, R alpha, int accumulate) {
+  const long long ak = aK[0], bk = bK[0];
+  for (int m = blockIdx.y; m < M; m += gridDim.y) {
+    const Cx<R> a = A[aoff + aM[m] + ak];
+    const R ar = alpha * a.x, ai = alpha * a.y;
+    const long long cm = coff + cM[m];
+    for (int n = blockIdx.x * kThreads + threadIdx.x; n < N; n += gridDim.x * kThreads) {
+      const Cx<R> b = B[boff + bN[n] + bk];
+      const long long idx = cm + cN[n];
+      Cx<R> v = cmake<R>(ar * b.x - ai * b.y, ar * b.y + ai * b.x);
+      if (accumulate) {
+        const Cx<R> c = Cp[idx];
+        v.x += c.x;
+        v.y += c.y;
+      }
+      Cp[idx] = v;
+    }
+  }
+}
+
 template <typename R, int RM, int RN, int UM, int UN>
 void launch_cfg(bool a_kc, bool b_kc, const Cx<R>* A, long long aoff, const long long* aM,
                 const long long* aK, const Cx<R>* B, long long boff, const long long* bN,
@@ -275,6 +301,19 @@ void launch_cfg(bool a_kc, bool b_kc, const Cx<R>* A, long long aoff, const long
 }
 
 }  // namespace
+
+template <typename R>
+void launch_outer(const Cx<R>* A, long long aoff, const long long* aM, const long long* aK,
+                  const Cx<R>* B, long long boff, const long long* bN, const long long* bK,
+                  Cx<R>* C, long long coff, const long long* cM, const long long* cN, int M, int N,
+                  double alpha, bool accumulate, cudaStream_t s) {
+  // about four outputs per thread along n, rows spread over grid.y
+  const int gx = std::max(1, std::min(1024, (N + 4 * kThreads - 1) / (4 * kThreads)));
+  const int gy = std::max(1, std::min(M, std::max(1, 152 * 32 / gx)));
+  k_outer<R><<<dim3(gx, gy), kThreads, 0, s>>>(A, aoff, aM, aK, B, boff, bN, bK, C, coff, cM, cN,
+                                               M, N, R(alpha), accumulate ? 1 : 0);
+  RTCC3_CUDA(cudaGetLastError());
+}
 
 int small_output_config(long long M, long long N) {
   if (M <= 10 && N <= 10) return kSmall10;
@@ -365,7 +404,11 @@ void launch_gemv(bool a_kc, const Cx<R>* A, long long aoff, const long long* aM,
                                        Cx<R>*, cudaStream_t);                                       \
   template void launch_gemv<R>(bool, const Cx<R>*, long long, const long long*, const long long*,   \
                                const Cx<R>*, long long, const long long*, Cx<R>*, long long,        \
-                               const long long*, int, int, double, bool, cudaStream_t);
+                               const long long*, int, int, double, bool, cudaStream_t);         \
+  template void launch_outer<R>(const Cx<R>*, long long, const long long*, const long long*,       \
+                                const Cx<R>*, long long, const long long*, const long long*,       \
+                                Cx<R>*, long long, const long long*, const long long*, int, int,   \
+                                double, bool, cudaStream_t);
 RTCC3_INST(float)
 RTCC3_INST(double)
 #undef RTCC3_INST

@@ -39,6 +39,16 @@ void launch_reduce_small(int cfg, bool a_kc, bool b_kc, const Cx<R>* A, long lon
                          const long long* cM, const long long* cN, int M, int N, int K, int nsplit,
                          int kchunk, double alpha, bool accumulate, Cx<R>* part, cudaStream_t s);
 
+// Outer products (K = 1): C[coff + cM[m] + cN[n]] (+)= alpha A[aoff + aM[m] +
+// aK[0]] B[boff + bN[n] + bK[0]], n along the output's contiguous index: a
+// streaming pass over C (the reverse-pass products that spread a vector over
+// the o^3 v^3 cotangent).
+template <typename R>
+void launch_outer(const Cx<R>* A, long long aoff, const long long* aM, const long long* aK,
+                  const Cx<R>* B, long long boff, const long long* bN, const long long* bK,
+                  Cx<R>* C, long long coff, const long long* cM, const long long* cN, int M, int N,
+                  double alpha, bool accumulate, cudaStream_t s);
+
 template <typename R>
 void launch_gemv(bool a_kc, const Cx<R>* A, long long aoff, const long long* aM, const long long* aK,
                  const Cx<R>* B, long long boff, const long long* bK, Cx<R>* C, long long coff,

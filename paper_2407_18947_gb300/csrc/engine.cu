@@ -806,7 +806,11 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   // long output columns get their own kernels
   {
     const long long mx = std::max(M, N), mn = std::min(M, N);
-    if (NB == 1 && mn == 1 && mx > 512 && K <= 65536) {
+    if (NB == 1 && K == 1 && M * N >= 65536) {
+      // outer product: a streaming pass over C with n on its contiguous index
+      P->kind = 3;
+      P->small_swap = !gm.empty() && std::llabs(gm.back().sc) == 1;
+    } else if (NB == 1 && mn == 1 && mx > 512 && K <= 65536) {
       P->kind = 2;
       P->small_swap = M == 1;
       P->gemv_boff = P->small_swap ? P->a_off0 + h[iaM] : P->b_off0 + h[ibN];
@@ -995,6 +999,15 @@ void Engine<R>::run_contract_small(ContractPlan& P, double alpha, const C* pa, c
   const double bytes = (double(P.M) * P.K + double(P.N) * P.K +
                         double(P.M) * P.N * (accumulate ? 2.0 : 1.0)) * sizeof(C);
   const char* tag = sizeof(R) == 8 ? "c128" : "c64";
+  if (P.kind == 3) {
+    const int pk = pbegin();
+    launch_outer<R>(sw ? pb : pa, sw ? P.b_off0 : P.a_off0, sw ? P.bN : P.aM, sw ? P.bK : P.aK,
+                    sw ? pa : pb, sw ? P.a_off0 : P.b_off0, sw ? P.aM : P.bN, sw ? P.aK : P.bK,
+                    pc, P.c_off0, kM, kN, Mk, Nk, alpha, accumulate, stream_);
+    ++launches_;
+    pend(pk, (std::string("contract_outer_") + tag).c_str(), 8.0 * mnk, bytes, cur_detail_);
+    return;
+  }
   if (P.kind == 2) {
     const int pk = pbegin();
     launch_gemv<R>(sw ? P.b_kcontig : P.a_kcontig, sw ? pb : pa, sw ? P.b_off0 : P.a_off0,

@@ -53,8 +53,10 @@ struct ContractPlan {
   bool small_tile = false;  // 16x16 output tiles with 64-deep K slices (skinny shapes)
   int tile = 0;             // 0: 64 x 64, 1: 16 x 256, 2: 256 x 16 output tiles
   // kind 0: tiled gather-GEMM; 1: small output held whole by every CTA
-  // (reduce_small, config small_cfg); 2: single long output column (gemv).
-  // small_swap: the kernels run with A and B exchanged (larger side first).
+  // (reduce_small, config small_cfg); 2: single long output column (gemv);
+  // 3: outer product (K = 1, a streaming pass over C).
+  // small_swap: the kernels run with A and B exchanged (kinds 1, 2: larger
+  // side first; kind 3: the output's contiguous index on the second side).
   int kind = 0, small_cfg = 0;
   bool small_swap = false;
   long long gemv_boff = 0, gemv_coff = 0;  // B and C offsets of the single column

@@ -118,6 +118,30 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
   }
 }
 
+// D (+)= A B with A (128 rows = TMEM lanes, K = 8 TF32 columns) in tensor
+// memory and B from shared memory.
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+      "%29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -364,16 +388,25 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
 // Shared-memory plan of the chained long-sum kernel: the same stage layout as
 // TcSmem, a ring of up to 224 KB (no transpose staging), two accumulators.
+// SPLIT: a stage holds the raw A tile and B [hi | lo]; the A tile's TF32 hi
+// and lo parts go to tensor memory (the MMAs read A from there, so the three
+// products of a K tile do not re-read A from shared memory).
 template <int BN, bool SPLIT>
 struct TcChainSmem {
-  using T = TcSmem<BN, SPLIT, 8>;
-  static constexpr int kStageBytes = T::kStageBytes;
+  static constexpr int kABytes = kBM * 128;
+  static constexpr int kBBytes = BN * 128;
+  static constexpr int kStageBytes = kABytes + (SPLIT ? 2 : 1) * kBBytes;
   static constexpr int kRing = 229376;
-  static constexpr int kStages = kRing / kStageBytes < 6 ? kRing / kStageBytes : 6;
+  // SPLIT: at most 4 A stages (64 TMEM columns each: hi, lo) beside the accumulators
+  static constexpr int kMaxStages = SPLIT ? 4 : 6;
+  static constexpr int kStages = kRing / kStageBytes < kMaxStages ? kRing / kStageBytes : kMaxStages;
   static constexpr int kBarOff = kStages * kStageBytes;
   static constexpr int kTotal = kBarOff + 256 + 1024;  // barriers + alignment slack
-  // two accumulators, the second at column kTmemCols / 2 (a power of two)
-  static constexpr int kTmemCols = 2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512));
+  // two accumulators at columns 0 and kAccStride; SPLIT: A stages from column 256
+  static constexpr int kAccStride = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+  static constexpr int kACol = 256;
+  static constexpr int kTmemCols = SPLIT ? 512 : (2 * kAccStride < 64 ? 64 : 2 * kAccStride);
+  static_assert(!SPLIT || BN <= 128, "accumulators and A stages share 512 TMEM columns");
   static_assert(kStages >= 2 && kTotal <= 232448, "shared memory per CTA");
 };
 
@@ -383,15 +416,16 @@ struct TcChainSmem {
 // pipeline between them: the MMA warp alternates two TMEM accumulators and,
 // while it fills one, four drain warps copy the other's finished chain to its
 // FP32 partial (partial[(chain M + m) Nr + n], summed later by
-// tc_split_finish).  A comes tiled (TcOperands::a_tiled) by bulk copies.  Warps: 0 TMA, 1 MMA, 2-5 TF32 hi/lo split of A, 6-9
-// drain.  The chains and the products in each are those of the one-chain-per-
-// CTA kernel, so the partials are the same.
+// tc_split_finish).  A comes tiled (TcOperands::a_tiled) by bulk copies;
+// with the TF32 split its hi and lo parts are staged in tensor memory, so the
+// three products of a K tile read A from there instead of shared memory.
+// Warps: 0 TMA, 1 MMA, 2-5 TF32 hi/lo split of A, 6-9 drain.  The chains and
+// the products in each are those of the one-chain-per-CTA kernel.
 template <int BN, bool BF16, bool SPLIT>
 __global__ void __launch_bounds__(320, 1)
 k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUtensorMap tmB,
                  int M, int Nr, int nkb_total, int per, int nchains, int cpc, int kb_lo,
                  float* __restrict__ partial, int* __restrict__ err) {
-  using T = TcSmem<BN, SPLIT, 8>;
   using L = TcChainSmem<BN, SPLIT>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -444,16 +478,16 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
         if (i >= kStages) ok = mbar_wait(smem_u32(&empty[st]), ((i / kStages) - 1) & 1);
         if (!ok) break;
         const uint32_t fb = smem_u32(&full[st]);
-        mbar_expect_tx(fb, T::kTmaBytes);
-        uint8_t* sa = smem + st * T::kStageBytes;
-        uint8_t* sb = sa + T::kABytes + T::kALoBytes;
+        mbar_expect_tx(fb, L::kStageBytes);
+        uint8_t* sa = smem + st * L::kStageBytes;
+        uint8_t* sb = sa + L::kABytes;
         const int kx = (kb0 + i) * kElemPerK;
         // A tile (row block blockIdx.y, K tile kb0 + i): one contiguous 16 KB
         // block already in its swizzled shared-memory image
         bulk_load(smem_u32(sa), Atiled + ((size_t(blockIdx.y) * nkb_total + kb0 + i) << 14),
-                  T::kABytes, fb);
+                  L::kABytes, fb);
         tma_load_2d(smem_u32(sb), &tmB, kx, n0, fb);
-        if (SPLIT) tma_load_2d(smem_u32(sb + T::kBBytes), &tmB, kx + kb_lo * kElemPerK, n0, fb);
+        if (SPLIT) tma_load_2d(smem_u32(sb + L::kBBytes), &tmB, kx + kb_lo * kElemPerK, n0, fb);
       }
       // no copy into shared memory may be outstanding at exit
       for (int i = max(0, nkb - kStages); i < nkb && ok; ++i)
@@ -470,16 +504,20 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
         ok = mbar_wait(smem_u32(SPLIT ? &conv[st] : &full[st]), (i / kStages) & 1);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc_t = tmem + uint32_t(b * (L::kTmemCols / 2));
-        const uint32_t sa = smem_u32(smem + st * T::kStageBytes);
-        const uint32_t sb = sa + T::kABytes + T::kALoBytes;
+        const uint32_t acc_t = tmem + uint32_t(b * L::kAccStride);
+        const uint32_t sa = smem_u32(smem + st * L::kStageBytes);
+        const uint32_t sb = sa + L::kABytes;
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t acc = (pos > 0 || kk > 0) ? 1u : 0u;
-          mma<BF16>(acc_t, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, acc);
           if (SPLIT) {
-            mma<BF16>(acc_t, smem_desc(sa + kk * 32), smem_desc(sb + T::kBBytes + kk * 32), idesc, 1u);
-            mma<BF16>(acc_t, smem_desc(sa + T::kABytes + kk * 32), smem_desc(sb + kk * 32), idesc, 1u);
+            // A hi at columns kACol + 64 st, lo 32 columns further; 8 per K step
+            const uint32_t ah = tmem + uint32_t(L::kACol + 64 * st + 8 * kk);
+            mma_tf32_ta(acc_t, ah, smem_desc(sb + kk * 32), idesc, acc);
+            mma_tf32_ta(acc_t, ah, smem_desc(sb + L::kBBytes + kk * 32), idesc, 1u);
+            mma_tf32_ta(acc_t, ah + 32, smem_desc(sb + kk * 32), idesc, 1u);
+          } else {
+            mma<BF16>(acc_t, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, acc);
           }
         }
         mma_commit(smem_u32(&empty[st]));
@@ -488,26 +526,33 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
     }
   } else if (warp < 6) {
     if (SPLIT) {
-      const int ct = threadIdx.x - 64;  // 0 .. 127
+      // warp % 4 owns TMEM lanes (A rows) 32 (warp % 4) .. + 31: each thread
+      // reads its row's 32 FP32 values from the swizzled tile (16-byte chunk
+      // c of row r sits at chunk c ^ (r % 8)) and stores hi = tf32(x) and
+      // lo = x - hi to its TMEM lane
+      const int r = 32 * (warp & 3) + lane;
+      const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
       for (int i = 0; i < nkb && ok; ++i) {
         const int st = i % kStages;
         ok = mbar_wait(smem_u32(&full[st]), (i / kStages) & 1);
         if (!ok) break;
-        float4* ah = reinterpret_cast<float4*>(smem + st * T::kStageBytes);
-        float4* al = reinterpret_cast<float4*>(smem + st * T::kStageBytes + T::kABytes);
+        const float4* row = reinterpret_cast<const float4*>(smem + st * L::kStageBytes + r * 128);
+        uint32_t hi[32], lo[32];
 #pragma unroll
-        for (int u = 0; u < T::kABytes / 16 / 128; ++u) {
-          const int e = ct + 128 * u;
-          const float4 x = ah[e];
-          float4 h, lo;
-          h.x = __uint_as_float(to_tf32(x.x)); lo.x = x.x - h.x;
-          h.y = __uint_as_float(to_tf32(x.y)); lo.y = x.y - h.y;
-          h.z = __uint_as_float(to_tf32(x.z)); lo.z = x.z - h.z;
-          h.w = __uint_as_float(to_tf32(x.w)); lo.w = x.w - h.w;
-          ah[e] = h;
-          al[e] = lo;
+        for (int c = 0; c < 8; ++c) {
+          const float4 x = row[c ^ (r & 7)];
+          const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            hi[4 * c + e] = to_tf32(xv[e]);
+            lo[4 * c + e] = __float_as_uint(xv[e] - __uint_as_float(hi[4 * c + e]));
+          }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t ta = tmem + lane_base + uint32_t(L::kACol + 64 * st);
+        tmem_st32(ta, hi);
+        tmem_st32(ta + 32, lo);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&conv[st]));
       }
@@ -527,7 +572,7 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
-        tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(b * (L::kTmemCols / 2) + c0), r);
+        tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(b * L::kAccStride + c0), r);
         if (m < M) {
           if (vec && n0 + c0 + 32 <= Nr) {
 #pragma unroll
