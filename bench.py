@@ -120,6 +120,10 @@ class ClockSampler:
 KERNEL_FAMILIES = {
     "k_combine_nd": (("combine", "axpy_gather", "axpy_strided", "copy", "sym6"), "hbm"),
     "k_tc_gemm": (("contract_tc_tf32", "contract_tc_bf16"), "tensor"),
+    # long sums reading the o^3 v^3 operand from its source (tcgen05, TF32
+    # split): N = 10 or 38 complex columns, ~N flop per byte, HBM-bound
+    "k_tc_gemm_direct": (("contract_tc_direct_tf32",), "hbm"),
+    "k_outer": (("contract_outer_c64", "contract_outer_c128"), "hbm"),
     "k_contract": (("contract_simt_c64", "contract_simt_c128"), "alu"),
     "k_sym6_div": (("sym6_div", "sym3_div"), "hbm"),
     "k_pack": (("tc_pack",), "hbm"),

@@ -1052,30 +1052,38 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     const long long* gcN = sw ? P.cM : P.cN;
     const long long goa = sw ? P.b_off0 : P.a_off0;
     const long long gob = sw ? P.a_off0 : P.b_off0;
-    op.a_tiled = tc_chained(op, P.tc_nsplit);
+    // TF32 long sums read the big operand A straight from its source (no
+    // packed copy); the others pack A (tiled for chained long sums)
+    const bool direct = tc_direct(op, P.tc_nsplit);
+    op.a_tiled = !direct && tc_chained(op, P.tc_nsplit);
     const size_t a_rows = op.a_tiled ? size_t((op.M + 127) / 128) * 128 : size_t(op.M);
-    void* apk = scratch(1, a_rows * op.Kp * tc_eb_);
+    void* apk = direct ? nullptr : scratch(1, a_rows * op.Kp * tc_eb_);
     void* bpk = scratch(2, size_t(2 * op.N) * op.Kp * tc_eb_ * (op.split ? 2 : 1));
     float* part = nullptr;
     if (P.tc_nsplit > 1)
       part = static_cast<float*>(scratch(3, size_t(P.tc_nsplit) * op.M * 2 * op.N * sizeof(float)));
     int* err = error_flag();
-    const double pbytes = double(op.M + 2.0 * op.N) * op.K * 2.0 * sizeof(float);
+    const bool a_kc = sw ? P.b_kcontig : P.a_kcontig;
+    const double rows_packed = direct ? 2.0 * op.N : op.M + 2.0 * op.N;
     int pk = pbegin();
-    tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, tc_eb_, sw ? P.b_kcontig : P.a_kcontig,
-              op.a_tiled, apk, stream_);
+    if (!direct) tc_pack_a(ga, gaM, gaK, goa, op.M, op.K, op.Kp, tc_eb_, a_kc, op.a_tiled, apk, stream_);
     tc_pack_b(gb, gbN, gbK, gob, op.N, op.K, op.Kp, tc_eb_, sw ? P.a_kcontig : P.b_kcontig, bpk,
               stream_);
-    pend(pk, "tc_pack", 0.0, pbytes + double(op.M + 2.0 * op.N) * op.Kp * tc_eb_, cur_detail_);
-    launches_ += 2;
+    pend(pk, "tc_pack", 0.0, rows_packed * op.K * 8.0 + rows_packed * op.Kp * tc_eb_, cur_detail_);
+    launches_ += direct ? 1 : 2;
     pk = pbegin();
-    const bool ok = tc_gemm(apk, bpk, op, pc, gcM, gcN, P.c_off0, float(alpha), accumulate,
-                            P.tc_nsplit, part, err, stream_);
+    const bool ok = direct ? tc_gemm_direct(ga, goa, gaM, gaK, a_kc, bpk, op, P.tc_nsplit, part,
+                                            err, stream_)
+                           : tc_gemm(apk, bpk, op, pc, gcM, gcN, P.c_off0, float(alpha),
+                                     accumulate, P.tc_nsplit, part, err, stream_);
     RTCC3_CHECK(ok, kErrCuda, "tensor-core GEMM set-up failed (tensor map encoding)");
     const double mnk = double(op.M) * op.N * op.K;
-    const double bytes = (double(op.M) * op.Kp + 2.0 * op.N * op.Kp) * tc_eb_ +
-                         double(op.M) * op.N * sizeof(C) * (accumulate ? 2.0 : 1.0);
-    pend(pk, tc_eb_ == 4 ? "contract_tc_tf32" : "contract_tc_bf16", 8.0 * mnk, bytes, cur_detail_);
+    const double bytes = (direct ? double(op.M) * op.K * 8.0 : double(op.M) * op.Kp * tc_eb_) +
+                         2.0 * op.N * op.Kp * tc_eb_ * (op.split ? 2 : 1) +
+                         (P.tc_nsplit > 1 ? double(P.tc_nsplit) * op.M * 2 * op.N * 4.0
+                                          : double(op.M) * op.N * sizeof(C) * (accumulate ? 2.0 : 1.0));
+    pend(pk, direct ? "contract_tc_direct_tf32" : (tc_eb_ == 4 ? "contract_tc_tf32" : "contract_tc_bf16"),
+         8.0 * mnk, bytes, cur_detail_);
     ++launches_;
     if (P.tc_nsplit > 1) {
       pk = pbegin();

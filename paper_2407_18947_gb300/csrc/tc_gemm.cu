@@ -80,6 +80,19 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
+// 8-byte asynchronous global -> shared copy; src_bytes 0 writes zeros.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(src_bytes)
+               : "memory");
+}
+
+// Arrive on `bar` once this thread's earlier cp.async copies have landed (the
+// arrival is one of the barrier's expected arrivals).
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -397,14 +410,14 @@ struct TcChainSmem {
   static constexpr int kBBytes = BN * 128;
   static constexpr int kStageBytes = kABytes + (SPLIT ? 2 : 1) * kBBytes;
   static constexpr int kRing = 229376;
-  // SPLIT: at most 4 A stages (64 TMEM columns each: hi, lo) beside the accumulators
-  static constexpr int kMaxStages = SPLIT ? 4 : 6;
+  // two accumulators at columns 0 and kAccStride; SPLIT: A stages (64 TMEM
+  // columns each: hi, lo) from column kACol, as many as the 512 columns hold
+  static constexpr int kAccStride = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+  static constexpr int kACol = 2 * kAccStride;
+  static constexpr int kMaxStages = SPLIT ? ((512 - kACol) / 64 < 6 ? (512 - kACol) / 64 : 6) : 6;
   static constexpr int kStages = kRing / kStageBytes < kMaxStages ? kRing / kStageBytes : kMaxStages;
   static constexpr int kBarOff = kStages * kStageBytes;
   static constexpr int kTotal = kBarOff + 256 + 1024;  // barriers + alignment slack
-  // two accumulators at columns 0 and kAccStride; SPLIT: A stages from column 256
-  static constexpr int kAccStride = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
-  static constexpr int kACol = 256;
   static constexpr int kTmemCols = SPLIT ? 512 : (2 * kAccStride < 64 ? 64 : 2 * kAccStride);
   static_assert(!SPLIT || BN <= 128, "accumulators and A stages share 512 TMEM columns");
   static_assert(kStages >= 2 && kTotal <= 232448, "shared memory per CTA");
@@ -772,6 +785,295 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
   RTCC3_CUDA(cudaGetLastError());
 }
 
+// Chains per CTA for `tiles` output tiles and `nchains` chains: the fewest
+// CTAs per tile that fill whole waves of one CTA per SM to 90 % (else the
+// best fill).
+int chains_per_cta(long long tiles, int nchains) {
+  int z = 1;
+  double best = 0.0;
+  for (int c = 1; c <= nchains; ++c) {
+    const long long ctas = tiles * c;
+    const double eff = double(ctas) / double(((ctas + 151) / 152) * 152);
+    if (eff > best + 1e-9) {
+      best = eff;
+      z = c;
+    }
+    if (eff >= 0.9) break;
+  }
+  return (nchains + z - 1) / z;
+}
+
+// Shared-memory plan of the direct long-sum kernel: an A ring (raw FP32
+// tiles gathered by cp.async, freed once split into TMEM) and a B ring
+// ([hi | lo] by TMA, freed by the MMA commit) whose depth is the number of
+// TMEM A stages.
+template <int BN>
+struct TcDirectSmem {
+  static constexpr int kABytes = kBM * 128;
+  static constexpr int kBStage = 2 * BN * 128;
+  static constexpr int kAccStride = BN <= 32 ? 32 : (BN <= 64 ? 64 : 128);
+  static constexpr int kACol = 2 * kAccStride;
+  static constexpr int kBStages = (512 - kACol) / 64 < 6 ? (512 - kACol) / 64 : 6;
+  static constexpr int kRing = 229376;
+  static constexpr int kAStages0 = (kRing - kBStages * kBStage) / kABytes;
+  static constexpr int kAStages = kAStages0 < 8 ? kAStages0 : 8;
+  static constexpr int kBOff = kAStages * kABytes;
+  static constexpr int kBarOff = kBOff + kBStages * kBStage;
+  static constexpr int kTotal = kBarOff + 512 + 1024;  // barriers + alignment slack
+  static_assert(BN <= 128 && kAStages >= 2 && kBStages >= 2 && kTotal <= 232448, "plan");
+};
+
+// The chained long sum with A read straight from its source tensor through
+// its offset tables (TF32 split): no packed copy of the big operand is
+// written.  Warps 2-9 gather the 128 x 16 complex A tile of each K tile with
+// 8-byte cp.async copies into a shared-memory ring (zeros outside M and K),
+// consecutive threads on the source's contiguous index (a_kc: along k, else
+// along rows), in the swizzled row layout; warps 10-13 split each tile into
+// TF32 hi and lo in tensor memory; warp 0 brings B by TMA, warp 1 issues the
+// MMAs (A from TMEM), warps 14-17 drain the accumulators to the chain
+// partials as in k_tc_gemm_chains.
+template <int BN, bool AKC>
+__global__ void __launch_bounds__(576, 1)
+k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* __restrict__ aM,
+                 const long long* __restrict__ aK, int K, const __grid_constant__ CUtensorMap tmB,
+                 int M, int Nr, int nkb_total, int per, int nchains, int cpc,
+                 float* __restrict__ partial, int* __restrict__ err) {
+  using L = TcDirectSmem<BN>;
+  constexpr int SA = L::kAStages, SB = L::kBStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
+  uint64_t* afull = bars;            // [SA] A tile landed (256 loader threads)
+  uint64_t* aempty = afull + SA;     // [SA] A tile split into TMEM (4 warps)
+  uint64_t* bfull = aempty + SA;     // [SB] B tile landed (TMA)
+  uint64_t* empty = bfull + SB;      // [SB] MMAs of the stage done (commit)
+  uint64_t* conv = empty + SB;       // [SB] TMEM A stage written (4 warps)
+  uint64_t* cfull = conv + SB;       // [2] accumulator holds a finished chain
+  uint64_t* cfree = cfull + 2;       // [2] accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+  const int ch0 = blockIdx.z * cpc;
+  const int nch = max(0, min(nchains, ch0 + cpc) - ch0);
+  const int kb0 = ch0 * per;
+  const int nkb = max(0, min(nkb_total, kb0 + nch * per) - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < SA; ++st) {
+      mbar_init(smem_u32(&afull[st]), 256);
+      mbar_init(smem_u32(&aempty[st]), 4);
+    }
+    for (int st = 0; st < SB; ++st) {
+      mbar_init(smem_u32(&bfull[st]), 1);
+      mbar_init(smem_u32(&empty[st]), 1);
+      mbar_init(smem_u32(&conv[st]), 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&cfull[b]), 1);
+      mbar_init(smem_u32(&cfree[b]), 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int st = i % SB;
+        if (i >= SB) ok = mbar_wait(smem_u32(&empty[st]), ((i / SB) - 1) & 1);
+        if (!ok) break;
+        const uint32_t fb = smem_u32(&bfull[st]);
+        mbar_expect_tx(fb, L::kBStage);
+        const uint32_t sb = smem_u32(smem + L::kBOff + st * L::kBStage);
+        const int kx = (kb0 + i) * 32;
+        tma_load_2d(sb, &tmB, kx, n0, fb);
+        tma_load_2d(sb + BN * 128, &tmB, kx + nkb_total * 32, n0, fb);
+      }
+      for (int i = max(0, nkb - SB); i < nkb && ok; ++i)
+        ok = mbar_wait(smem_u32(&empty[i % SB]), (i / SB) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = instr_desc<false>(kBM, BN);
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int st = i % SB, j = i / per, pos = i - j * per, b = j & 1;
+        if (pos == 0 && j >= 2) ok = mbar_wait(smem_u32(&cfree[b]), ((j >> 1) - 1) & 1);
+        if (ok) ok = mbar_wait(smem_u32(&conv[st]), (i / SB) & 1);
+        if (ok) ok = mbar_wait(smem_u32(&bfull[st]), (i / SB) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_t = tmem + uint32_t(b * L::kAccStride);
+        const uint32_t sb = smem_u32(smem + L::kBOff + st * L::kBStage);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t acc = (pos > 0 || kk > 0) ? 1u : 0u;
+          const uint32_t ah = tmem + uint32_t(L::kACol + 64 * st + 8 * kk);
+          mma_tf32_ta(acc_t, ah, smem_desc(sb + kk * 32), idesc, acc);
+          mma_tf32_ta(acc_t, ah, smem_desc(sb + BN * 128 + kk * 32), idesc, 1u);
+          mma_tf32_ta(acc_t, ah + 32, smem_desc(sb + kk * 32), idesc, 1u);
+        }
+        mma_commit(smem_u32(&empty[st]));
+        if (pos == per - 1 || i == nkb - 1) mma_commit(smem_u32(&cfull[b]));
+      }
+    }
+  } else if (warp < 10) {
+    // loaders: element e = t + 256 u (u < 8) of the 128 x 16 complex tile;
+    // AKC: j = e % 16 (constant per thread), row e / 16; else row e % 128
+    // (constant), j = e / 128
+    const int t = threadIdx.x - 64;
+    const float2* Ab = A + aoff;
+    long long rowoff[8];
+    bool rowok[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = AKC ? (t >> 4) + 16 * u : (t & 127);
+      const int m = m0 + r;
+      rowok[u] = m < M;
+      rowoff[u] = rowok[u] ? aM[m] : 0;
+    }
+    for (int i = 0; i < nkb && ok; ++i) {
+      const int st = i % SA;
+      if (i >= SA) ok = mbar_wait(smem_u32(&aempty[st]), ((i / SA) - 1) & 1);
+      if (!ok) break;
+      const uint32_t sa = smem_u32(smem + st * L::kABytes);
+      const int kbase = (kb0 + i) * 16;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int r = AKC ? (t >> 4) + 16 * u : (t & 127);
+        const int j = AKC ? (t & 15) : (t >> 7) + 2 * u;
+        const int k = kbase + j;
+        const bool in = rowok[u] && k < K;
+        const float2* src = in ? Ab + rowoff[u] + aK[k] : Ab;
+        // float 2j of row r: 16-byte chunk j / 2 at position (j / 2) ^ (r % 8)
+        const uint32_t dst = sa + uint32_t(r * 128 + ((((j >> 1) ^ (r & 7)) << 4) | ((j & 1) << 3)));
+        cp_async8(dst, src, in ? 8u : 0u);
+      }
+      cp_async_arrive(smem_u32(&afull[st]));
+    }
+    // no copy may be outstanding at exit
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp < 14) {
+    // splitters: TMEM lanes 32 (warp % 4) .. + 31 = rows of the A tile
+    const int r = 32 * (warp & 3) + lane;
+    const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
+    for (int i = 0; i < nkb && ok; ++i) {
+      const int sa_i = i % SA, st = i % SB;
+      ok = mbar_wait(smem_u32(&afull[sa_i]), (i / SA) & 1);
+      // the TMEM stage's previous MMAs (K tile i - SB) must be done
+      if (ok && i >= SB) ok = mbar_wait(smem_u32(&empty[st]), ((i / SB) - 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.st below is warp-collective
+      if (!ok) break;
+      const float4* row = reinterpret_cast<const float4*>(smem + sa_i * L::kABytes + r * 128);
+      uint32_t hi[32], lo[32];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 x = row[c ^ (r & 7)];
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          hi[4 * c + e] = to_tf32(xv[e]);
+          lo[4 * c + e] = __float_as_uint(xv[e] - __uint_as_float(hi[4 * c + e]));
+        }
+      }
+      const uint32_t ta = tmem + lane_base + uint32_t(L::kACol + 64 * st);
+      tmem_st32(ta, hi);
+      tmem_st32(ta + 32, lo);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&aempty[sa_i]));
+        mbar_arrive(smem_u32(&conv[st]));
+      }
+    }
+  } else {
+    // drain warps 14-17: TMEM lane quarter warp % 4, all BN columns
+    const int q = warp & 3;
+    const int m = m0 + q * 32 + lane;
+    const bool vec = (Nr & 3) == 0;
+    for (int j = 0; j < nch && ok; ++j) {
+      const int b = j & 1;
+      ok = mbar_wait(smem_u32(&cfull[b]), (j >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* dst = partial + (size_t(ch0 + j) * M + (m < M ? m : 0)) * size_t(Nr) + n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(b * L::kAccStride + c0), r);
+        if (m < M) {
+          if (vec && n0 + c0 + 32 <= Nr) {
+#pragma unroll
+            for (int jj = 0; jj < 32; jj += 4)
+              *reinterpret_cast<float4*>(dst + c0 + jj) =
+                  make_float4(__uint_as_float(r[jj]), __uint_as_float(r[jj + 1]),
+                              __uint_as_float(r[jj + 2]), __uint_as_float(r[jj + 3]));
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj)
+              if (n0 + c0 + jj < Nr) dst[c0 + jj] = __uint_as_float(r[jj]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&cfree[b]));
+    }
+  }
+  if (!ok && err) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
+template <int BN>
+void launch_direct(const float2* A, long long aoff, const long long* aM, const long long* aK,
+                   bool a_kc, const CUtensorMap& mb, const TcOperands& op, int nsplit,
+                   float* partial, int* err, cudaStream_t s) {
+  using L = TcDirectSmem<BN>;
+  const int Nr = 2 * op.N;
+  const int nkb = op.Kp / 32;
+  const int per = (nkb + nsplit - 1) / nsplit;
+  const int nchains = (nkb + per - 1) / per;
+  static bool attr = false;
+  if (!attr) {
+    RTCC3_CUDA(cudaFuncSetAttribute(k_tc_gemm_direct<BN, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal));
+    RTCC3_CUDA(cudaFuncSetAttribute(k_tc_gemm_direct<BN, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal));
+    attr = true;
+  }
+  const long long tiles = (long long)((Nr + BN - 1) / BN) * ((op.M + kBM - 1) / kBM);
+  const int cpc = chains_per_cta(tiles, nchains);
+  const int zz = (nchains + cpc - 1) / cpc;
+  dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, zz);
+  if (a_kc)
+    k_tc_gemm_direct<BN, true><<<grid, 576, L::kTotal, s>>>(A, aoff, aM, aK, op.K, mb, op.M, Nr,
+                                                            nkb, per, nchains, cpc, partial, err);
+  else
+    k_tc_gemm_direct<BN, false><<<grid, 576, L::kTotal, s>>>(A, aoff, aM, aK, op.K, mb, op.M, Nr,
+                                                             nkb, per, nchains, cpc, partial, err);
+  RTCC3_CUDA(cudaGetLastError());
+}
+
 // Chained long-sum launch (see k_tc_gemm_chains); false if the split does
 // not map onto whole chains.
 template <int BN, bool BF16, bool SPLIT>
@@ -789,21 +1091,8 @@ bool launch_chains(const void* Atiled, const CUtensorMap& mb, const TcOperands& 
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal));
     attr = true;
   }
-  // CTAs per output tile: the fewest that fill whole waves of one CTA per SM
-  // to 90 % (else the best fill), each streaming its share of the chains
   const long long tiles = (long long)((Nr + BN - 1) / BN) * ((op.M + kBM - 1) / kBM);
-  int z = 1;
-  double best = 0.0;
-  for (int c = 1; c <= nchains; ++c) {
-    const long long ctas = tiles * c;
-    const double eff = double(ctas) / double(((ctas + 151) / 152) * 152);
-    if (eff > best + 1e-9) {
-      best = eff;
-      z = c;
-    }
-    if (eff >= 0.9) break;
-  }
-  const int cpc = (nchains + z - 1) / z;
+  const int cpc = chains_per_cta(tiles, nchains);
   const int zz = (nchains + cpc - 1) / cpc;
   dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, zz);
   k_tc_gemm_chains<BN, BF16, SPLIT><<<grid, 320, L::kTotal, s>>>(
@@ -865,6 +1154,21 @@ bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2*
   }
 #undef RTCC3_TC
 #undef RTCC3_CH
+  return true;
+}
+
+bool tc_gemm_direct(const float2* A, long long aoff, const long long* aM, const long long* aK,
+                    bool a_kc, const void* Bpack, const TcOperands& op, int nsplit, float* partial,
+                    int* err_flag, cudaStream_t s) {
+  RTCC3_CHECK(tc_direct(op, nsplit) && partial, kErrArg, "direct long sum: unsupported shape");
+  const int Nr = 2 * op.N;
+  const int BN = tc_tile_n(Nr, false);
+  CUtensorMap mb;
+  if (!make_map(&mb, Bpack, 4, 2 * op.Kp, Nr, BN)) return false;
+  if (BN == 128) launch_direct<128>(A, aoff, aM, aK, a_kc, mb, op, nsplit, partial, err_flag, s);
+  else if (BN == 96) launch_direct<96>(A, aoff, aM, aK, a_kc, mb, op, nsplit, partial, err_flag, s);
+  else if (BN == 64) launch_direct<64>(A, aoff, aM, aK, a_kc, mb, op, nsplit, partial, err_flag, s);
+  else launch_direct<32>(A, aoff, aM, aK, a_kc, mb, op, nsplit, partial, err_flag, s);
   return true;
 }
 

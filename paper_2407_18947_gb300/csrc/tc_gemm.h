@@ -60,6 +60,12 @@ inline bool tc_chained(const TcOperands& op, int nsplit) {
   return (nkb + per - 1) / per == nsplit;
 }
 
+// Whether a TF32 long sum runs as the direct kernel (A gathered from its
+// source through its tables, no packed copy): the chained kernel's shapes.
+inline bool tc_direct(const TcOperands& op, int nsplit) {
+  return op.split && op.elem_bytes == 4 && tc_chained(op, nsplit);
+}
+
 // Pack A (complex, addressed by tables) into a K-major real buffer of packed
 // width Kp: raw FP32 for TF32 (elem_bytes 4), BF16 otherwise.  kfast: the
 // source is contiguous along k (else along the row index); the packing
@@ -79,6 +85,12 @@ void tc_pack_b(const float2* B, const long long* bN, const long long* bK, long l
 bool tc_gemm(const void* Apack, const void* Bpack, const TcOperands& op, float2* C,
              const long long* cM, const long long* cN, long long coff, float alpha, bool accumulate,
              int nsplit, float* partial, int* err_flag, cudaStream_t s);
+// The long sum C = A B (TF32 split, nsplit chains into `partial`, reduced by
+// tc_split_finish) with A read from its source: element (m, k) at
+// A[aoff + aM[m] + aK[k]] (a_kc: the source is contiguous along k).
+bool tc_gemm_direct(const float2* A, long long aoff, const long long* aM, const long long* aK,
+                    bool a_kc, const void* Bpack, const TcOperands& op, int nsplit, float* partial,
+                    int* err_flag, cudaStream_t s);
 void tc_split_finish(const float* partial, int nsplit, int M, int N, float2* C, const long long* cM,
                      const long long* cN, long long coff, float alpha, bool accumulate,
                      cudaStream_t s);
