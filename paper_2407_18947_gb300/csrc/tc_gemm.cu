@@ -87,6 +87,13 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src))
+               : "memory");
+}
+
 // Arrive on `bar` once this thread's earlier cp.async copies have landed (the
 // arrival is one of the barrier's expected arrivals).
 __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
@@ -929,19 +936,20 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
       }
     }
   } else if (warp < 10) {
-    // loaders: element e = t + 256 u (u < 8) of the 128 x 16 complex tile;
-    // AKC: j = e % 16 (constant per thread), row e / 16; else row e % 128
-    // (constant), j = e / 128
+    // loaders.  AKC: pairs of consecutive k, pair p = t + 256 u (u < 4),
+    // k pair (p % 8) (constant per thread), row p / 8, one 16-byte copy when
+    // the pair is contiguous and aligned in the source; else element
+    // e = t + 256 u (u < 8), row e % 128 (constant), j = e / 128
     const int t = threadIdx.x - 64;
-    const float2* Ab = A + aoff;
-    long long rowoff[8];
-    bool rowok[8];
+    constexpr int NU = AKC ? 4 : 8;
+    long long rowoff[NU];
+    bool rowok[NU];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int r = AKC ? (t >> 4) + 16 * u : (t & 127);
+    for (int u = 0; u < NU; ++u) {
+      const int r = AKC ? (t >> 3) + 32 * u : (t & 127);
       const int m = m0 + r;
       rowok[u] = m < M;
-      rowoff[u] = rowok[u] ? aM[m] : 0;
+      rowoff[u] = rowok[u] ? aoff + aM[m] : 0;
     }
     for (int i = 0; i < nkb && ok; ++i) {
       const int st = i % SA;
@@ -949,16 +957,37 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
       if (!ok) break;
       const uint32_t sa = smem_u32(smem + st * L::kABytes);
       const int kbase = (kb0 + i) * 16;
+      if (AKC) {
+        const int j2 = t & 7, k = kbase + 2 * j2;
+        const bool k0in = k < K, k1in = k + 1 < K;
+        const long long o0 = k0in ? aK[k] : 0, o1 = k1in ? aK[k + 1] : 0;
+        const bool pair = k1in && o1 == o0 + 1;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int r = AKC ? (t >> 4) + 16 * u : (t & 127);
-        const int j = AKC ? (t & 15) : (t >> 7) + 2 * u;
-        const int k = kbase + j;
-        const bool in = rowok[u] && k < K;
-        const float2* src = in ? Ab + rowoff[u] + aK[k] : Ab;
-        // float 2j of row r: 16-byte chunk j / 2 at position (j / 2) ^ (r % 8)
-        const uint32_t dst = sa + uint32_t(r * 128 + ((((j >> 1) ^ (r & 7)) << 4) | ((j & 1) << 3)));
-        cp_async8(dst, src, in ? 8u : 0u);
+        for (int u = 0; u < NU; ++u) {
+          const int r = (t >> 3) + 32 * u;
+          // floats 4 j2 .. 4 j2 + 3 of row r: 16-byte chunk j2 at j2 ^ (r % 8)
+          const uint32_t dst = sa + uint32_t(r * 128 + ((j2 ^ (r & 7)) << 4));
+          const long long a0 = rowoff[u] + o0;
+          if (rowok[u] && pair && (reinterpret_cast<uintptr_t>(A + a0) & 15) == 0) {
+            cp_async16(dst, A + a0);
+          } else {
+            const bool in0 = rowok[u] && k0in, in1 = rowok[u] && k1in;
+            cp_async8(dst, in0 ? A + a0 : A, in0 ? 8u : 0u);
+            cp_async8(dst + 8, in1 ? A + rowoff[u] + o1 : A, in1 ? 8u : 0u);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int r = t & 127;
+          const int j = (t >> 7) + 2 * u;
+          const int k = kbase + j;
+          const bool in = rowok[u] && k < K;
+          const float2* src = in ? A + rowoff[u] + aK[k] : A;
+          // float 2j of row r: 16-byte chunk j / 2 at position (j / 2) ^ (r % 8)
+          const uint32_t dst = sa + uint32_t(r * 128 + ((((j >> 1) ^ (r & 7)) << 4) | ((j & 1) << 3)));
+          cp_async8(dst, src, in ? 8u : 0u);
+        }
       }
       cp_async_arrive(smem_u32(&afull[st]));
     }
