@@ -139,13 +139,15 @@ KERNEL_FAMILIES = {
 # (kernel, precision, workload) -> bytes.  An entry is removed when its kernel
 # changes after the counters were taken.
 MEASURED_TRAFFIC = {
-    ("k_contract", "tf32", 2): 3.76e6,
-    ("k_tc_gemm", "tf32", 2): 624.49e6,
-    ("k_combine_nd", "tf32", 2): 157.16e6,
-    ("k_sym6_div", "tf32", 2): 3021.52e6,
-    ("k_pack", "tf32", 2): 245.37e6,
-    ("k_reduce_small", "tf32", 2): 177.00e6,
-    ("k_gemv", "tf32", 2): 149.80e6,
+    ("k_contract", "tf32", 2): 2.79e6,
+    ("k_combine_nd", "tf32", 2): 146.86e6,
+    ("k_tc_gemm_direct", "tf32", 2): 476.81e6,
+    ("k_sym6_div", "tf32", 2): 842.18e6,
+    ("k_reduce_small", "tf32", 2): 176.91e6,
+    ("k_tc_gemm", "tf32", 2): 579.92e6,
+    ("k_outer", "tf32", 2): 241.72e6,
+    ("k_gemv", "tf32", 2): 221.79e6,
+    ("k_pack", "tf32", 2): 1.63e6,
 }
 
 

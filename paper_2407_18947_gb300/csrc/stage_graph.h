@@ -110,9 +110,6 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   View G2p = rot("Jj,mjck->mJck", SIO, G("oovo"), {o, o, v, o});
   G2p = rot("Cc,mJck->mJCk", SIV, G2p, {o, o, v, o});
   G2p = rot("Kk,mJCk->mJCK", SIO, G2p, {o, o, v, o});
-  const int Z = E.node(s6, false, false);
-  E.contract("ijae,ckbe->ijkabc", 1.0, T1p, G1p, E.v(Z), false);
-  E.contract("imab,mjck->ijkabc", -1.0, T2p, G2p, E.v(Z), true);
   // source -P sum_ld v~_ld t_ij^ad t_kl^cb, rotated the same way; P is linear,
   // so it is folded into Z before the one permutation sum
   const int Yl = E.node({o, o, o, v}, false, false);
@@ -123,7 +120,19 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   View T3p_ = rot("Kk,klcb->Klcb", SIO, T, {o, o, v, v});
   T3p_ = rot("Cc,Klcb->KlCb", SIV, T3p_, {o, o, v, v});
   T3p_ = rot("Bb,KlCb->KlCB", SIV, T3p_, {o, o, v, v});
-  E.contract("lija,klcb->ijkabc", -1.0, Ylp, T3p_, E.v(Z), true);
+  // Z = sum_e t'_ij^ae g'_ckbe - sum_m t'_im^ab g'_mjck - sum_l y'_lija t'_kl^cb:
+  // the first and last terms group Z's indices the same way ((ija) x (kbc)),
+  // so they are one product over the concatenated sum index E = (e | l)
+  // (one pass over Z instead of two, and one reverse product per operand)
+  const int Ac = E.node({o, o, v, v + o}, false, false);
+  E.combine({{1.0, T1p}}, E.v(Ac).sub(3, 0, v), true);
+  E.combine({{-1.0, E.ev("lija->ijal", Ylp)}}, E.v(Ac).sub(3, v, o), true);
+  const int Bc = E.node({v + o, o, v, v}, false, false);
+  E.combine({{1.0, E.ev("ckbe->ekbc", G1p)}}, E.v(Bc).sub(0, 0, v), true);
+  E.combine({{1.0, E.ev("klcb->lkbc", T3p_)}}, E.v(Bc).sub(0, v, o), true);
+  const int Z = E.node(s6, false, false);
+  E.contract("ijaE,Ekbc->ijkabc", 1.0, E.v(Ac), E.v(Bc), E.v(Z), false);
+  E.contract("imab,mjck->ijkabc", -1.0, T2p, G2p, E.v(Z), true);
   // ---- t3' = -P(Z) / D' with the complex denominators ---------------------------
   typename Engine<R>::EpsSpec es;
   es.o = o;
