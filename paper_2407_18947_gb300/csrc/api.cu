@@ -712,7 +712,10 @@ void ground_state_impl(rtcc3_ctx* ctx, double tol, int maxiter) {
       RTCC3_CUDA(cudaMemcpyAsync(&mx, ctx->maxr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       RTCC3_CUDA(cudaMemcpyAsync(d.data(), dots, mm * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
       RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
-      RTCC3_CHECK(std::isfinite(mx), RTCC3_ERR_NONFINITE, "non-finite residual in the ground-state solve");
+      if (!std::isfinite(mx)) {
+        check_device_timeout<R>(ctx);  // a device-side cause is reported (and its flag cleared) first
+        throw Error(RTCC3_ERR_NONFINITE, "non-finite residual in the ground-state solve");
+      }
       if (mx < tol) { conv = true; break; }
       m = mm;
       head = (head + 1) % kDiis;
