@@ -1,15 +1,24 @@
-// tcgen05 GEMM for the complex contractions (see tc_gemm.h).
+// tcgen05 GEMMs for the complex contractions (see tc_gemm.h).
 //
-// One CTA computes a 128 x BN tile of the real product Apack (M x Kp) times
-// Bpack^T (Nr x Kp), both K-major, staged by TMA (128-byte swizzle) through a
-// shared-memory ring of 2-4 stages.  Warp 0 issues the TMA loads, warp 1
-// allocates tensor memory and issues tcgen05.mma (one elected thread), warps
-// 2-9 first split each TF32 A tile into hi + lo parts in shared memory (the
-// MMA warp then issues hi.hi, hi.lo and lo.hi) and afterwards read the FP32
-// accumulator back with tcgen05.ld and write the complex result (coalesced
-// through a per-warp shared-memory transpose, 16 stores in flight per warp)
-// or FP32 split-K partials.  Every mbarrier wait is bounded by a clock budget; on expiry the
-// kernel raises *err and winds down, releasing its tensor memory.
+// k_tc_gemm: one CTA computes a 128 x BN tile of the real product Apack
+// (M x Kp) times Bpack^T (Nr x Kp), both K-major, staged by TMA (128-byte
+// swizzle) through a shared-memory ring.  Warp 0 issues the TMA loads, warp 1
+// allocates tensor memory and issues tcgen05.mma (one elected thread), the
+// epilogue warps first split each TF32 A tile into hi + lo parts in shared
+// memory (the MMA warp then issues hi.hi, hi.lo and lo.hi) and afterwards
+// read the FP32 accumulator back with tcgen05.ld and write the complex result
+// (coalesced through a per-warp shared-memory transpose, 16 stores in flight
+// per warp) or FP32 split-K partials.  Used for the short sums bound by their
+// output.
+//
+// k_tc_gemm_direct (TF32 long sums) and k_tc_gemm_chains (BF16 long sums)
+// cut the sum into accumulation chains and let one CTA stream several chains
+// through two TMEM accumulators (one filled while the other is drained to its
+// partial); the direct kernel gathers A from its source tensor with cp.async
+// (no packed copy) and keeps A's TF32 hi/lo parts in tensor memory.
+//
+// Every mbarrier wait is bounded by a clock budget; on expiry the kernel
+// raises *err and winds down, releasing its tensor memory.
 #include "tc_gemm.h"
 
 #include <cuda.h>

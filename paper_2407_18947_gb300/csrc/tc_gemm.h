@@ -4,10 +4,12 @@
 // real GEMM: A is packed K-major with (re, im) interleaved along K (M x 2K
 // real), B is packed as its real 2x2 embedding ([Br -Bi; Bi Br] per
 // element, 2N x 2K real), and the real product M x 2N is the interleaved
-// complex result.  Operands are rounded to TF32 (or converted to BF16) by the
-// packing kernels; accumulation is FP32 in tensor memory.  The epilogue
-// scatters into any strided output view through the contraction's offset
-// tables (or writes FP32 partials for split-K).
+// complex result.  Operands are rounded to TF32 (split into hi + lo parts,
+// three products) or converted to BF16; accumulation is FP32 in tensor
+// memory.  The epilogue scatters into any strided output view through the
+// contraction's offset tables (or writes FP32 partials for split-K).  Long
+// TF32 sums read A straight from its source through the offset tables
+// (tc_gemm_direct) instead of a packed copy.
 #pragma once
 
 #include "common.h"
