@@ -333,24 +333,33 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
   for (size_t t = 0; t < Lc.size(); ++t) Lc[t] = cmake<R>(R(Lfac[t]), R(0));
   for (int t = 0; t < n; ++t) ones[t] = cmake<R>(R(1), R(0));
   {
-    // FP64 sums of three occupied / three virtual orbital energies (Eq. A16)
+    // FP64 sums of three occupied / three virtual orbital energies (Eq. A16),
+    // each energy taken relative to the mid-gap energy (see Hamil::eshift)
     const int v = ctx->v;
+    double emax_o = -1e300, emin_v = 1e300;
+    for (int p = 0; p < o; ++p) emax_o = std::max(emax_o, ctx->eps_h[p]);
+    for (int p = o; p < n; ++p) emin_v = std::min(emin_v, ctx->eps_h[p]);
+    const double c = 0.5 * (emax_o + emin_v);
+    H.eshift = c;
     std::vector<double> os(size_t(o) * o * o), vs(size_t(v) * v * v);
     for (int i = 0; i < o; ++i)
       for (int j = 0; j < o; ++j)
         for (int k = 0; k < o; ++k)
-          os[(size_t(i) * o + j) * o + k] = ctx->eps_h[i] + ctx->eps_h[j] + ctx->eps_h[k];
+          os[(size_t(i) * o + j) * o + k] =
+              (ctx->eps_h[i] - c) + (ctx->eps_h[j] - c) + (ctx->eps_h[k] - c);
     for (int a = 0; a < v; ++a)
       for (int b = 0; b < v; ++b)
         for (int c = 0; c < v; ++c)
           vs[(size_t(a) * v + b) * v + c] =
-              ctx->eps_h[o + a] + ctx->eps_h[o + b] + ctx->eps_h[o + c];
+              (ctx->eps_h[o + a] - c) + (ctx->eps_h[o + b] - c) + (ctx->eps_h[o + c] - c);
     H.osum = rn->template alloc<double>(os.size());
     H.vsum = rn->template alloc<double>(vs.size());
     RTCC3_CUDA(cudaMemcpy(H.osum, os.data(), os.size() * sizeof(double), cudaMemcpyHostToDevice));
     RTCC3_CUDA(cudaMemcpy(H.vsum, vs.data(), vs.size() * sizeof(double), cudaMemcpyHostToDevice));
     // the sums rounded once to the compute precision (the dense triples
-    // kernels divide in R; every term of D = vsum - osum has the same sign)
+    // kernels divide in R; after the mid-gap shift every occupied sum is
+    // negative and every virtual sum positive, so D = vsum - osum adds two
+    // terms of one sign whatever the absolute orbital energies)
     std::vector<R> osr(os.begin(), os.end()), vsr(vs.begin(), vs.end());
     H.osum_r = rn->template alloc<R>(osr.size());
     H.vsum_r = rn->template alloc<R>(vsr.size());
@@ -803,8 +812,8 @@ static __device__ __align__(256) unsigned char g_rtcc3_noalloc_scratch[kNoAllocB
 
 namespace {
 
-// Device address of the static region for `dev` (the current device),
-// looked up once per device.  The first call on a device performs this
+// Device address of the static region for `dev` (which must be the current
+// device), looked up once per device.  The first call on a device performs this
 // lookup, so it should come before any stream capture.
 char* noalloc_scratch_address(int dev) {
   static std::mutex mu;
@@ -840,24 +849,33 @@ void triples_noalloc_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1,
   Engine<R> E(st);
   E.use_pool(&pool);
   E.set_tensor_cores(Rn.E.tensor_cores());
-  // the evaluation time lives in the region too (nothing else is written
-  // before the recorded graph reads it)
-  double* tdev = static_cast<double*>(pool.take(sizeof(double)));
-  RTCC3_CUDA(cudaMemcpyAsync(tdev, &time, sizeof(double), cudaMemcpyHostToDevice, st));
-  E.begin();
-  StageOptions so;
-  so.ccsd = false;
-  so.triples = true;
-  so.need_grad = false;
-  so.field_terms = true;
-  so.field_iters = field_sweeps(ctx, b);
-  so.rotation = ctx->opt.field_solver == 0;
-  StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
-    launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, st);
-    launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, tdev, 0.0, ctx->n, st);
-  });
-  launch_export<R>(E.data(S.r1), x1, ctx->n1, st);
-  launch_export<R>(E.data(S.r2), x2, ctx->n2, st);
+  E.set_profiler(&ctx->prof);  // records events only while profiling is enabled
+  try {
+    // the evaluation time lives in the region too (nothing else is written
+    // before the recorded graph reads it)
+    double* tdev = static_cast<double*>(pool.take(sizeof(double)));
+    RTCC3_CUDA(cudaMemcpyAsync(tdev, &time, sizeof(double), cudaMemcpyHostToDevice, st));
+    E.begin();
+    StageOptions so;
+    so.ccsd = false;
+    so.triples = true;
+    so.need_grad = false;
+    so.field_terms = true;
+    so.field_iters = field_sweeps(ctx, b);
+    so.rotation = ctx->opt.field_solver == 0;
+    StageNodes S = record_stage<R>(E, Rn.H, so, [&](const StageNodes& s) {
+      launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, st);
+      launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, tdev, 0.0, ctx->n, st);
+    });
+    launch_export<R>(E.data(S.r1), x1, ctx->n1, st);
+    launch_export<R>(E.data(S.r2), x2, ctx->n2, st);
+  } catch (...) {
+    // a request the region cannot serve (or any other failure) may come
+    // after kernels that write the region were enqueued: let them finish
+    // before the error returns, so the next call does not race with them
+    cudaStreamSynchronize(st);
+    throw;
+  }
   // the engine's host-side tables must outlive the copies it enqueued
   RTCC3_CUDA(cudaStreamSynchronize(st));
   if (E.tensor_cores()) {
@@ -1166,8 +1184,10 @@ int rtcc3_triples_forward_noalloc_dev(rtcc3_ctx* ctx, int b, double time, const 
     check_slot(ctx, b);
     RTCC3_CHECK(t1 && t2 && x1 && x2, RTCC3_ERR_ARG, "null device buffer");
     RTCC3_CHECK(ctx->opt.triples, RTCC3_ERR_STATE, "context created without triples");
-    int dev = 0;
-    RTCC3_CUDA(cudaGetDevice(&dev));
+    // the context's device: its Hamiltonian, stream and the region's copy
+    // used below all live there, whatever device the caller has current
+    const int dev = ctx->opt.device;
+    RTCC3_CUDA(cudaSetDevice(dev));
     char* base = noalloc_scratch_address(dev);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
     auto f = [&](auto tag) {

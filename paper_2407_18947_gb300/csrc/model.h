@@ -31,6 +31,12 @@ struct Hamil {
   R* vsum_r = nullptr;
   int* orbit_order = nullptr;  // o^3 occupied blocks, permutation orbits consecutive
   double e_ref = 0.0;     // sum_i (h_ii + eps_i)
+  // mid-gap energy c = (e_homo + e_lumo) / 2 subtracted from every orbital
+  // energy (and every field-dressed eigenvalue) entering a sum table: the
+  // denominators D = vsum - osum are unchanged (three terms on each side),
+  // and with occupied sums below zero and virtual sums above, the one
+  // rounding of each sum to the compute precision cannot cancel in D
+  double eshift = 0.0;
 };
 
 // Node ids of one recorded stage.

@@ -29,16 +29,18 @@ __global__ void k_field_matrices(const Cx<R>* __restrict__ wt, const double* __r
 
 template <typename R>
 __global__ void k_lambda_sums(const double2* __restrict__ lo, const double2* __restrict__ lv, int o,
-                              int v, Cx<R>* __restrict__ os, Cx<R>* __restrict__ vs) {
+                              int v, double c, Cx<R>* __restrict__ os, Cx<R>* __restrict__ vs) {
   const int no = o * o * o, nv = v * v * v;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < no + nv; t += gridDim.x * blockDim.x) {
     if (t < no) {
       const int k = t % o, j = (t / o) % o, i = t / (o * o);
-      os[t] = cmake<R>(R(lo[i].x + lo[j].x + lo[k].x), R(lo[i].y + lo[j].y + lo[k].y));
+      os[t] = cmake<R>(R((lo[i].x - c) + (lo[j].x - c) + (lo[k].x - c)),
+                       R(lo[i].y + lo[j].y + lo[k].y));
     } else {
       const int q = t - no;
-      const int c = q % v, b = (q / v) % v, a = q / (v * v);
-      vs[q] = cmake<R>(R(lv[a].x + lv[b].x + lv[c].x), R(lv[a].y + lv[b].y + lv[c].y));
+      const int cc = q % v, b = (q / v) % v, a = q / (v * v);
+      vs[q] = cmake<R>(R((lv[a].x - c) + (lv[b].x - c) + (lv[cc].x - c)),
+                       R(lv[a].y + lv[b].y + lv[cc].y));
     }
   }
 }
@@ -62,10 +64,10 @@ void launch_field_matrices(const Cx<R>* wt, const double* eps, int o, int v, dou
 }
 
 template <typename R>
-void launch_lambda_sums(const double2* lo, const double2* lv, int o, int v, Cx<R>* osum,
-                        Cx<R>* vsum, cudaStream_t s) {
+void launch_lambda_sums(const double2* lo, const double2* lv, int o, int v, double shift,
+                        Cx<R>* osum, Cx<R>* vsum, cudaStream_t s) {
   const size_t n = size_t(o) * o * o + size_t(v) * v * v;
-  k_lambda_sums<R><<<blocks_for(n), 256, 0, s>>>(lo, lv, o, v, osum, vsum);
+  k_lambda_sums<R><<<blocks_for(n), 256, 0, s>>>(lo, lv, o, v, shift, osum, vsum);
   RTCC3_CUDA(cudaGetLastError());
 }
 
@@ -80,9 +82,11 @@ template void launch_field_matrices<double>(const Cx<double>*, const double*, in
 template void launch_field_matrices<float>(const Cx<float>*, const double*, int, int, double2*,
                                            double2*, cudaStream_t);
 template void launch_to_precision<double>(const double2*, Cx<double>*, size_t, cudaStream_t);
-template void launch_lambda_sums<double>(const double2*, const double2*, int, int, Cx<double>*,
+template void launch_lambda_sums<double>(const double2*, const double2*, int, int, double,
+                                         Cx<double>*,
                                          Cx<double>*, cudaStream_t);
-template void launch_lambda_sums<float>(const double2*, const double2*, int, int, Cx<float>*,
+template void launch_lambda_sums<float>(const double2*, const double2*, int, int, double,
+                                        Cx<float>*,
                                         Cx<float>*, cudaStream_t);
 template void launch_to_precision<float>(const double2*, Cx<float>*, size_t, cudaStream_t);
 

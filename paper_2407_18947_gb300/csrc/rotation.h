@@ -57,8 +57,8 @@ void launch_field_matrices(const Cx<R>* wt, const double* eps, int o, int v, dou
 // osum[(i o + j) o + k] = l_i + l_j + l_k and vsum likewise (summed in FP64,
 // rounded once to the compute precision R).
 template <typename R>
-void launch_lambda_sums(const double2* lo, const double2* lv, int o, int v, Cx<R>* osum,
-                        Cx<R>* vsum, cudaStream_t s);
+void launch_lambda_sums(const double2* lo, const double2* lv, int o, int v, double shift,
+                        Cx<R>* osum, Cx<R>* vsum, cudaStream_t s);
 // dst (compute precision) = src (complex128), n elements.
 template <typename R>
 void launch_to_precision(const double2* src, Cx<R>* dst, size_t n, cudaStream_t s);

@@ -62,7 +62,7 @@ FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt,
     const EigJob jo{bb.Mo, o, So64, Sio64, lo, bb.wso}, jv{bb.Mv, v, Sv64, Siv64, lv, bb.wsv};
     launch_eig(jo, jv, sizeof(R) == 4, status, ss);
   }
-  launch_lambda_sums<R>(lo, lv, o, v, B.osum, B.vsum, ss);
+  launch_lambda_sums<R>(lo, lv, o, v, H.eshift, B.osum, B.vsum, ss);
   launch_to_precision<R>(So64, E.data(B.So), size_t(o) * o, ss);
   launch_to_precision<R>(Sio64, E.data(B.Sio), size_t(o) * o, ss);
   launch_to_precision<R>(Sv64, E.data(B.Sv), size_t(v) * v, ss);

@@ -122,6 +122,8 @@ def _ground_state_with_field(ham, w, tol=1e-12):
         if max(float(r1.abs().max()), float(r2.abs().max())) < tol:
             break
         t1, t2 = t1 - r1 / d1, t2 - r2 / d2
+    else:
+        raise RuntimeError("T amplitudes with the static field did not converge")
     l1 = torch.zeros(o, v, dtype=cc3.CD)
     l2 = torch.zeros(o, o, v, v, dtype=cc3.CD)
     for _ in range(300):
@@ -129,4 +131,6 @@ def _ground_state_with_field(ham, w, tol=1e-12):
         if max(float(res.r_l1.abs().max()), float(res.r_l2.abs().max())) < tol:
             break
         l1, l2 = l1 - res.r_l1 / d1, l2 - res.r_l2 / d2
+    else:
+        raise RuntimeError("lambda amplitudes with the static field did not converge")
     return t1, t2, l1, l2

@@ -40,13 +40,25 @@ def _forward(eng, T1, T2, noalloc):
     return x1.cpu().numpy(), x2.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision,o,v,tol", [(0, 3, 7, 1e-10), (1, 4, 9, 1e-5)])
+# FP64 and FP32 on CUDA cores; split TF32 and BF16, at a size whose long
+# triples sums (M = o*o*v = 256 rows) take the tcgen05 route, so that the
+# tensor-core kernels' tensor maps, packed operands, split-K partials and
+# error flag are all served from the static region
+@pytest.mark.parametrize("precision,o,v,tol", [(0, 3, 7, 1e-10), (1, 4, 9, 1e-5),
+                                               (2, 4, 16, 1e-5), (3, 4, 16, 1e-4)])
 def test_noalloc_matches_allocating_entry_point_twice(precision, o, v, tol):
     eng, T1, T2 = _case(precision, o, v, seed=77 + o)
     r1, r2 = _forward(eng, T1, T2, noalloc=False)
     assert np.abs(r2).max() > 0
     for _ in range(2):
+        if precision >= 2:
+            eng.set_profiling(True)
         a1, a2 = _forward(eng, T1, T2, noalloc=True)
+        if precision >= 2:
+            tc = sum(st["launches"] for name, st in eng.kernel_stats().items()
+                     if name.startswith("contract_tc"))
+            eng.set_profiling(False)
+            assert tc > 0, "no tensor-core launch in the allocation-free evaluation"
         assert np.abs(a1 - r1).max() <= tol * np.abs(r1).max()
         assert np.abs(a2 - r2).max() <= tol * np.abs(r2).max()
     eng.close()
