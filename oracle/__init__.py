@@ -16,13 +16,18 @@ Modules
                 and its Euler-Lagrange derivatives (Eqs. A10-A15), density and
                 dipole, RK4 and the ground-state solve.
 ``explicit``    the paper's printed lambda-side formulas (lambda_3 Eq. A26,
-                Y1 Eq. A23, Y2 Eq. A24, triples density Eqs. A31-A33) used as
-                cross-checks of the Lagrangian derivatives.
+                Y1 Eq. A23, Y2 Eq. A24, triples density Eqs. A31-A33), with
+                the readings of two garbled Y1 terms; compared with the
+                Lagrangian derivatives of ``cc3`` to 1e-12
+                (``tests/test_oracle_explicit.py``).
 ``bruteforce``  second quantisation in the full N-electron determinant
                 space for tiny systems: the pin for every convention.
 ``finite_field`` the finite-difference stencils of Eqs. 19-20.
 
-Parity status: every function is pinned by a test in ``tests/`` against
-brute force, exact time evolution, closed forms or finite differences; none
-is "parity unpinned".
+Parity status: every function is pinned by a test in ``tests/``:
+``cc3`` against brute force (``bruteforce``), exact two-electron time
+evolution, finite differences of the brute-force Lagrangian, stationarity and
+Hellmann-Feynman; ``explicit`` and the lambda side of ``cc3`` against each
+other (two independent routes); ``finite_field`` against exact polynomials.
+None is "parity unpinned".
 """
