@@ -72,9 +72,25 @@ typedef struct rtcc3_options {
   int field_solver;  /* field-coupled triples: 0 = field-dressed eigenbasis
                         (exact, default), 1 = fixed-point sweeps on the
                         stored triples (the paper's scheme)                   */
+  int triples_chunk; /* triples storage: 0 = automatic (whole o^3 v^3
+                        tensors when about 24 of them fit in 70% of the free
+                        device memory, else blocked), -1 = always whole,
+                        k > 0 = blocked: the (i,j,k) blocks in slabs of k
+                        first occupied indices, W and t3 recomputed in the
+                        reverse pass and never stored (Section 2.1 computes
+                        the triples per (i,j,k) block); field_solver = 1
+                        always stores                                         */
+  long long spin_budget; /* clock cycles a bounded device wait (tensor-core
+                        pipeline barriers) may spin before the kernel gives
+                        up, drains its copies and the call returns
+                        RTCC3_ERR_TIMEOUT; 0 = default (4e9, about 2 s)      */
+  int eig_sweep_cap; /* QR sweeps the field eigensolver may take per matrix
+                        before the call returns RTCC3_ERR_TIMEOUT; 0 =
+                        default (60 n + 100)                                   */
 } rtcc3_options;
 
-/* Fill *opt with defaults (FP64, triples on, device 0, graphs on). */
+/* Fill *opt with defaults (FP64, triples on, device 0, graphs on, automatic
+ * triples storage, default wait budgets). */
 void rtcc3_default_options(rtcc3_options* opt);
 
 /* Create a context for nbatch independent propagations (field slots).

@@ -26,7 +26,8 @@ _STATUS_NAMES = {ERR_ARG: "RTCC3_ERR_ARG", ERR_OOM: "RTCC3_ERR_OOM", ERR_CUDA: "
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("triples", ctypes.c_int), ("device", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("field_tol", ctypes.c_double),
-                ("field_solver", ctypes.c_int)]
+                ("field_solver", ctypes.c_int), ("triples_chunk", ctypes.c_int),
+                ("spin_budget", ctypes.c_longlong), ("eig_sweep_cap", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):

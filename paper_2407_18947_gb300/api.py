@@ -30,7 +30,8 @@ class RTCC3:
 
     def __init__(self, nocc: int, nvir: int, nbatch: int = 1, precision: int = PREC_FP64,
                  triples: bool = True, device: int = 0, use_graphs: bool = True,
-                 field_tol: float = 0.0, field_solver: int = 0):
+                 field_tol: float = 0.0, field_solver: int = 0, triples_chunk: int = 0,
+                 spin_budget: int = 0, eig_sweep_cap: int = 0):
         self.lib = _lib.load()
         self.nocc, self.nvir, self.nbatch = nocc, nvir, nbatch
         opt = _lib.Options()
@@ -41,6 +42,9 @@ class RTCC3:
         opt.use_graphs = 1 if use_graphs else 0
         opt.field_tol = field_tol
         opt.field_solver = field_solver
+        opt.triples_chunk = triples_chunk
+        opt.spin_budget = spin_budget
+        opt.eig_sweep_cap = eig_sweep_cap
         h = ctypes.c_void_p()
         rc = self.lib.rtcc3_create(nocc, nvir, nbatch, ctypes.byref(opt), ctypes.byref(h))
         if rc != 0:

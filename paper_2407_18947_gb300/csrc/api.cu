@@ -105,6 +105,7 @@ struct rtcc3_ctx {
   double2* dip_traj = nullptr;
   double2* en_traj = nullptr;
   size_t traj_cap = 0;
+  size_t free_at_setup = 0;  // free device memory when the Hamiltonian was set
   double time = 0.0;
   long long step_total = 0;
   long long last_launches = 0;
@@ -242,11 +243,31 @@ void launch_basis_ahead(rtcc3_ctx* ctx, const BasisBuffers& bb, const double2* b
   E.fork();
   const cudaStream_t ss = E.side_stream();
   const int pk = E.prof_begin(ss);
-  const EigJob jo{bb.Mo, ctx->o, bb.So, bb.Sio, bb.lo, bb.wso};
-  const EigJob jv{bb.Mv, ctx->v, bb.Sv, bb.Siv, bb.lv, bb.wsv};
+  const EigJob jo{bb.Mo, ctx->o, bb.So, bb.Sio, bb.lo, bb.wso, E.eig_sweep_cap()};
+  const EigJob jv{bb.Mv, ctx->v, bb.Sv, bb.Siv, bb.lv, bb.wsv, E.eig_sweep_cap()};
   launch_eig(jo, jv, sizeof(R) == 4, E.error_flag(), ss);
   E.prof_end(pk, ss, "field_eig_ahead", 0.0, 0.0);
   E.add_launches(2);
+}
+
+// Slab size of the blocked triples for this context (0: stored whole).
+// Automatic: the stored form keeps about a dozen o^3 v^3 tensors and their
+// cotangents alive in a stage; when 24 of them do not fit in 70% of the
+// device memory free at set-up, the triples are blocked in slabs of k first
+// occupied indices with the three slab buffers within a quarter of that
+// memory (at most 32 GB).
+int triples_chunk(const rtcc3_ctx* ctx) {
+  if (!ctx->opt.triples || ctx->opt.field_solver != 0) return 0;
+  const int o = ctx->o, v = ctx->v;
+  if (ctx->opt.triples_chunk > 0) return std::min(ctx->opt.triples_chunk, o);
+  if (ctx->opt.triples_chunk < 0) return 0;
+  const double elem = ctx->fp64() ? 16.0 : 8.0;
+  const double t3 = double(o) * o * o * v * v * v * elem;
+  const double freeb = double(ctx->free_at_setup);
+  if (24.0 * t3 <= 0.7 * freeb) return 0;
+  const double budget = std::min(0.25 * freeb, 32.0 * (1ull << 30));
+  const double slab = 3.0 * double(o) * o * v * v * v * elem;
+  return std::max(1, std::min(o, int(budget / slab)));
 }
 
 // One stage evaluation for slot b: records the graph with inputs
@@ -266,6 +287,7 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
   so.field_terms = field_terms;
   so.field_iters = sweeps;
   so.rotation = ctx->opt.field_solver == 0;
+  so.triples_chunk = triples_chunk(ctx);
   const bool basis_stage = so.triples && so.field_terms && so.rotation;
   if (basis_stage) so.basis = ahead.use;
   (void)ccsd_terms;
@@ -339,19 +361,20 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
     double emax_o = -1e300, emin_v = 1e300;
     for (int p = 0; p < o; ++p) emax_o = std::max(emax_o, ctx->eps_h[p]);
     for (int p = o; p < n; ++p) emin_v = std::min(emin_v, ctx->eps_h[p]);
-    const double c = 0.5 * (emax_o + emin_v);
-    H.eshift = c;
+    const double shift = 0.5 * (emax_o + emin_v);
+    H.eshift = shift;
     std::vector<double> os(size_t(o) * o * o), vs(size_t(v) * v * v);
     for (int i = 0; i < o; ++i)
       for (int j = 0; j < o; ++j)
         for (int k = 0; k < o; ++k)
           os[(size_t(i) * o + j) * o + k] =
-              (ctx->eps_h[i] - c) + (ctx->eps_h[j] - c) + (ctx->eps_h[k] - c);
+              (ctx->eps_h[i] - shift) + (ctx->eps_h[j] - shift) + (ctx->eps_h[k] - shift);
     for (int a = 0; a < v; ++a)
       for (int b = 0; b < v; ++b)
         for (int c = 0; c < v; ++c)
           vs[(size_t(a) * v + b) * v + c] =
-              (ctx->eps_h[o + a] - c) + (ctx->eps_h[o + b] - c) + (ctx->eps_h[o + c] - c);
+              (ctx->eps_h[o + a] - shift) + (ctx->eps_h[o + b] - shift) +
+              (ctx->eps_h[o + c] - shift);
     H.osum = rn->template alloc<double>(os.size());
     H.vsum = rn->template alloc<double>(vs.size());
     RTCC3_CUDA(cudaMemcpy(H.osum, os.data(), os.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -391,6 +414,8 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
   RTCC3_CUDA(cudaMemcpy(H.L, Lc.data(), Lc.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
   RTCC3_CUDA(cudaMemcpy(H.ones, ones.data(), ones.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
   rn->E.set_profiler(&ctx->prof);
+  rn->E.set_wait_budget(ctx->opt.spin_budget);
+  rn->E.set_eig_sweep_cap(ctx->opt.eig_sweep_cap);
   if (ctx->opt.precision == RTCC3_PREC_TF32) rn->E.set_tensor_cores(4);
   if (ctx->opt.precision == RTCC3_PREC_BF16) rn->E.set_tensor_cores(2);
   ctx->runner = std::move(rn);
@@ -774,6 +799,7 @@ void triples_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1, const d
   so.field_terms = true;
   so.field_iters = field_sweeps(ctx, b);
   so.rotation = ctx->opt.field_solver == 0;
+  so.triples_chunk = triples_chunk(ctx);
   auto fill = [&](const StageNodes& s) {
     launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, ctx->stream);
     launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, ctx->teval, 0.0, ctx->n, ctx->stream);
@@ -849,6 +875,8 @@ void triples_noalloc_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1,
   Engine<R> E(st);
   E.use_pool(&pool);
   E.set_tensor_cores(Rn.E.tensor_cores());
+  E.set_wait_budget(Rn.E.wait_budget());
+  E.set_eig_sweep_cap(Rn.E.eig_sweep_cap());
   E.set_profiler(&ctx->prof);  // records events only while profiling is enabled
   try {
     // the evaluation time lives in the region too (nothing else is written
@@ -911,6 +939,9 @@ void rtcc3_default_options(rtcc3_options* opt) {
   opt->use_graphs = 1;
   opt->field_tol = 0.0;
   opt->field_solver = 0;
+  opt->triples_chunk = 0;
+  opt->spin_budget = 0;
+  opt->eig_sweep_cap = 0;
 }
 
 int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3_ctx** out) {
@@ -987,6 +1018,9 @@ int rtcc3_set_hamiltonian(rtcc3_ctx* ctx, const double* eps, int naux, const dou
     ctx->time = 0.0;
     ctx->step_total = 0;
     RTCC3_CUDA(cudaMemcpy(ctx->tdev, &ctx->time, sizeof(double), cudaMemcpyHostToDevice));
+    size_t fr = 0, tot = 0;
+    RTCC3_CUDA(cudaMemGetInfo(&fr, &tot));
+    ctx->free_at_setup = fr;
     ctx->have_ham = true;
   });
 }

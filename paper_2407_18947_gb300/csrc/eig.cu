@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(32) k_eig_warp(EigJob ja, EigJob jb, int level
 
   // ---- shifted QR sweeps to Schur form ---------------------------------------
   int hi = n - 1, iter = 0, its_here = 0;
-  const int max_iter = 60 * n + 100;
+  const int max_iter = J.max_sweeps > 0 ? J.max_sweeps : 60 * n + 100;
   bool failed = false;
   while (hi > 0) {
     int l = hi;

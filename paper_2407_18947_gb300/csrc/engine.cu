@@ -84,6 +84,36 @@ __global__ void k_div_eps_dense6(const Cx<R>* __restrict__ X, Cx<R>* __restrict_
   }
 }
 
+// One slab of the triples, dense (I, o, o, v, v, v) with its first occupied
+// index starting at i0: Y = alpha X / D, D[ijk abc] = vsum[abc] - osum[ijk]
+// with the sums in the compute precision (complex when CPLX).  X may be Y.
+template <typename R, bool CPLX>
+__global__ void k_slab_div(const Cx<R>* X, Cx<R>* Y, const R* __restrict__ osum,
+                           const R* __restrict__ vsum, const Cx<R>* __restrict__ osum_c,
+                           const Cx<R>* __restrict__ vsum_c, size_t o2base, size_t v3, size_t n,
+                           R alpha) {
+  for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+       t += size_t(gridDim.x) * blockDim.x) {
+    const size_t ijk = t / v3;
+    const size_t abc = t - ijk * v3;
+    const Cx<R> x = X[t];
+    Cx<R> y;
+    if (CPLX) {
+      const Cx<R> vs = vsum_c[abc], os = osum_c[o2base + ijk];
+      const R dr = vs.x - os.x, di = vs.y - os.y;
+      const R m = alpha / (dr * dr + di * di);
+      const R ir = dr * m, ii = -di * m;  // alpha / (dr + i di)
+      y.x = x.x * ir - x.y * ii;
+      y.y = x.x * ii + x.y * ir;
+    } else {
+      const R inv = alpha / (vsum[abc] - osum[o2base + ijk]);
+      y.x = x.x * inv;
+      y.y = x.y * inv;
+    }
+    Y[t] = y;
+  }
+}
+
 // Y (+)= alpha P(X) / D for X, Y dense (o,o,o,v,v,v): P sums the six
 // simultaneous permutations of (ijk, abc) (NP = 6) or the identity and the
 // exchanges of slot 1 with slots 2 and 3 (NP = 3), then divides by the
@@ -913,7 +943,7 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
 template <typename R>
 void Engine<R>::run_contract(const std::string& spec, double alpha, const View& A, bool a_grad,
                              const View& B, bool b_grad, const View& Cv, bool c_grad,
-                             bool accumulate) {
+                             bool accumulate, long long sa, long long sb, long long sc) {
   ContractPlan& P = plan(spec, A, B, Cv);
   if (prof_ && prof_->detail())
     cur_detail_ = spec + " M=" + std::to_string(P.M) + " N=" + std::to_string(P.N) +
@@ -930,6 +960,9 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
   const C* pb = (b_grad ? nodes_[B.node].grad : nodes_[B.node].data);
   C* pc = (c_grad ? nodes_[Cv.node].grad : nodes_[Cv.node].data);
   RTCC3_CHECK(pa && pb && pc, kErrState, "contraction on an unallocated buffer: " + spec);
+  pa += sa;
+  pb += sb;
+  pc += sc;
   if (P.use_tc) {
     run_contract_tc(P, alpha, pa, pb, pc, accumulate);
     return;
@@ -1042,6 +1075,7 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     op.elem_bytes = tc_eb_;
     op.split = tc_eb_ == 4;
     op.out_bound = P.tc_out;
+    op.wait_budget = wait_budget_;
     const float2* ga = sw ? pb : pa;
     const float2* gb = sw ? pa : pb;
     const long long* gaM = sw ? P.bN : P.aM;
@@ -1554,6 +1588,33 @@ void Engine<R>::zero_grad_if_unset(int node) {
   if (nd.grad_ready) return;
   RTCC3_CUDA(cudaMemsetAsync(nd.grad, 0, nd.numel * sizeof(C), stream_));
   nd.grad_ready = true;
+}
+
+template <typename R>
+void Engine<R>::exec_slab_div(double alpha, const View& X, int i0, const EpsSpec& es,
+                              const View& Y) {
+  const bool cplx = es.osum_cr && es.vsum_cr;
+  RTCC3_CHECK(cplx || (es.osum_r && es.vsum_r), kErrArg, "slab division needs sum tables");
+  RTCC3_CHECK(X.nd == 6 && Y.nd == 6 && X.off == 0 && Y.off == 0, kErrArg,
+              "slab division takes whole dense slab nodes");
+  const size_t v3 = size_t(es.v) * es.v * es.v;
+  const size_t n = Y.numel();
+  RTCC3_CHECK(X.numel() == n && n % (v3 * es.o * es.o) == 0, kErrArg, "slab division extents");
+  RTCC3_CHECK(i0 >= 0 && i0 + int(n / (v3 * es.o * es.o)) <= es.o, kErrArg, "slab start");
+  const int pk = pbegin();
+  const size_t o2base = size_t(i0) * es.o * es.o;
+  if (cplx)
+    k_slab_div<R, true><<<grid_for(n), 256, 0, stream_>>>(nodes_[X.node].data, nodes_[Y.node].data,
+                                                          nullptr, nullptr, es.osum_cr, es.vsum_cr,
+                                                          o2base, v3, n, R(alpha));
+  else
+    k_slab_div<R, false><<<grid_for(n), 256, 0, stream_>>>(nodes_[X.node].data,
+                                                           nodes_[Y.node].data, es.osum_r,
+                                                           es.vsum_r, nullptr, nullptr, o2base, v3,
+                                                           n, R(alpha));
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
+  pend(pk, "slab_div", 8.0 * double(n), 2.0 * double(n) * sizeof(C));
 }
 
 template <typename R>

@@ -161,6 +161,24 @@ class Engine {
     cur_tc_ = tc_region_;
     run_contract(spec, alpha, A, ag, B, bg, Cv, cg, true);
   }
+  // As exec_contract, with each operand's data (or gradient) pointer moved by
+  // sa / sb / sc elements and an explicit accumulate flag.  The plan is made
+  // for the views as given, so a loop over slices of equal extent that
+  // differ only in their start (views at start 0 plus the start as a shift)
+  // reuses one plan.  Every kernel takes per-address decisions on
+  // alignment, so any whole-element shift is valid.
+  void exec_contract_at(const char* spec, double alpha, const View& A, bool ag, long long sa,
+                        const View& B, bool bg, long long sb, const View& Cv, bool cg, long long sc,
+                        bool accumulate) {
+    cur_tc_ = tc_region_;
+    run_contract(spec, alpha, A, ag, B, bg, Cv, cg, accumulate, sa, sb, sc);
+  }
+  // Slab of the triples (dense I x o x o x v x v x v, its first occupied
+  // index running over i0 .. i0+I-1): Y = alpha X / D with the triples
+  // denominators D[ijk abc] = vsum[abc] - osum[ijk] of es (the sum tables in
+  // the compute precision, real or complex); X and Y on data buffers, Y may
+  // be X.  Untaped.
+  void exec_slab_div(double alpha, const View& X, int i0, const EpsSpec& es, const View& Y);
   void exec_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg) {
     run_axpy(alpha, X, xg, Y, yg);
   }
@@ -230,6 +248,13 @@ class Engine {
   void set_tc_region(bool open) { tc_region_ = open; }
   // Device word raised by a bounded wait that gave up (tensor-core kernel).
   int* error_flag();
+  // Clock cycles a tensor-core kernel's wait on another warp may spin before
+  // it gives up and raises the error flag (0: the kernels' default).
+  void set_wait_budget(long long cycles) { wait_budget_ = cycles; }
+  long long wait_budget() const { return wait_budget_; }
+  // QR sweeps the field eigensolver may take per matrix (0: its default).
+  void set_eig_sweep_cap(int sweeps) { eig_cap_ = sweeps; }
+  int eig_sweep_cap() const { return eig_cap_; }
   // Take every device buffer (arena, tables, scratch, flag) from `p` instead
   // of cudaMalloc; the engine then frees nothing either.
   void use_pool(DevicePool* p) {
@@ -284,7 +309,8 @@ class Engine {
   void run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
                     bool overwrite, int np);
   void run_contract(const std::string& spec, double alpha, const View& A, bool a_grad, const View& B,
-                    bool b_grad, const View& Cv, bool c_grad, bool accumulate);
+                    bool b_grad, const View& Cv, bool c_grad, bool accumulate, long long sa = 0,
+                    long long sb = 0, long long sc = 0);
   void run_axpy(double alpha, const View& X, bool xg, const View& Y, bool yg);
   void run_mulc(const View& X, bool xg, const View& Cst, const View& Y, bool yg);
   ContractPlan& plan(const std::string& spec, const View& A, const View& B, const View& Cv);
@@ -298,6 +324,8 @@ class Engine {
   void* scratch_[kScratchSlots] = {nullptr, nullptr, nullptr, nullptr};
   size_t scratch_bytes_[kScratchSlots] = {0, 0, 0, 0};
   int tc_eb_ = 0;
+  long long wait_budget_ = 0;
+  int eig_cap_ = 0;
   bool tc_region_ = false;
   int* err_ = nullptr;
   cudaStream_t side_ = nullptr;

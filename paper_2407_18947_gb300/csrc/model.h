@@ -53,6 +53,10 @@ struct StageOptions {
   bool field_terms = true;  // include the V-coupling of the triples equation
   bool rotation = true;     // field-dressed eigenbasis (else fixed-point sweeps)
   int field_iters = 1;      // fixed-point sweeps of the triples equation
+  // 0: the triples tensors are stored whole (o^3 v^3 each); k > 0: blocked,
+  // slabs of k first occupied indices with W and t3 recomputed in the
+  // reverse pass (the fixed-point field solver always stores)
+  int triples_chunk = 0;
   // eigenbasis of this stage's O and V already decomposed on the engine's side
   // stream (enqueued there before this stage), else null: decomposed in-stage
   const BasisBuffers* basis = nullptr;

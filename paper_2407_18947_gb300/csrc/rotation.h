@@ -35,6 +35,7 @@ struct EigJob {
   double2* Sinv;
   double2* lam;
   double2* ws;
+  int max_sweeps = 0;  // QR sweeps before giving up (0: 60 n + 100)
 };
 // Both matrices of a stage in one launch (one warp each).  fp32: complex64
 // arithmetic (for the complex64 graphs), else complex128.  *status is raised

@@ -59,7 +59,8 @@ FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt,
   const int pk = E.prof_begin(ss);
   if (!ahead) {
     launch_field_matrices<R>(E.data(wt), H.eps, o, v, bb.Mo, bb.Mv, ss);
-    const EigJob jo{bb.Mo, o, So64, Sio64, lo, bb.wso}, jv{bb.Mv, v, Sv64, Siv64, lv, bb.wsv};
+    const EigJob jo{bb.Mo, o, So64, Sio64, lo, bb.wso, E.eig_sweep_cap()};
+    const EigJob jv{bb.Mv, v, Sv64, Siv64, lv, bb.wsv, E.eig_sweep_cap()};
     launch_eig(jo, jv, sizeof(R) == 4, status, ss);
   }
   launch_lambda_sums<R>(lo, lv, o, v, H.eshift, B.osum, B.vsum, ss);
@@ -70,6 +71,205 @@ FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt,
   E.prof_end(pk, ss, "field_eig", 0.0, 0.0);
   E.add_launches(ahead ? 5 : 7);
   return B;
+}
+
+// ---- Blocked triples: W and t3 recomputed per slab, never stored --------------
+//
+// The operands of the connected triples and of their contractions into X1 and
+// X2 (already in the basis in which the denominators are diagonal):
+//   Z[ijkabc] = sum_E Ac[i,j,a,E] Bc[E,k,b,c] - sum_m T2[i,m,a,b] G2[m,j,c,k]
+//   t3 = -P_ijk^abc(Z) / D                                  (Eqs. A25, A30, 6)
+//   X1[i,a]     = sum (t3 - t3(ijkcba)) Lp[j,k,b,c]              (Eq. A21)
+//   S3[i,j,a,b] = sum (t3 - t3(ijkcba)) Fp[k,c]
+//               + sum (2 t3 - t3(ijkacb) - t3(ijkcba))[ijk cbe] Gb[a,c,k,e]
+//               - sum (2 t3 - t3(mjkbac) - t3(mjkcba))[mjk cba] Gc[k,i,m,c]
+// (X2 = P_ij^ab S3, Eq. A22).  The (i,j,k) blocks are processed in slabs of
+// `chunk` first occupied indices (the paper's per-(i,j,k) evaluation with the
+// v^3 blocks of several (i,j,k) grouped into one slab, Section 2.1).
+template <typename R>
+struct TriplesOperands {
+  View Ac, Bc, T2, G2, Lp, Fp, Gb, Gc;
+};
+
+// Field-coupling adjoint in the rotated basis: grad(v~_vv) -= S_v^-T D'_vv S_v^T,
+// grad(v~_oo) += S_o D'_oo S_o^-1 with the slot densities D' of y' = grad(t3')/D'
+// and t3' (the triples density terms of Eqs. A31-A32 in the rotated basis).
+struct FieldAdjoint {
+  bool on = false;
+  int wt = -1;
+  View wvv, woo, SO, SIO, SV, SIV;
+};
+
+// Forward: for each slab, W = P_ijk^abc Z from the six permuted Z products
+// (the slab's index i in each of the three occupied positions), t3 = -W / D,
+// and its contributions to X1 (rows of the slab) and S3.  Reverse (custom
+// adjoint, given grad X1 and grad S3): per slab, t3 is rebuilt; the
+// cotangents of Lp, Fp, Gb, Gc follow from t3; the t3 cotangent Q is
+// needed symmetrised, P_ijk^abc(Q) = R + R(ikjacb) with R the sum of Q
+// evaluated with the slab index in each of the three occupied positions
+// (Q is a sum of products of small tensors, so any arrangement is cheap to
+// form); Z's cotangent is -P(Q)/D, which gives those of Ac, Bc, T2, G2, and
+// with t3 the field-coupling slot densities.  Memory: three slabs of
+// chunk * o^2 v^3 elements instead of the dozen o^3 v^3 tensors of the stored
+// form.  X1o, S3o: output nodes (written here, zero-initialised).
+template <typename R>
+void blocked_triples(Engine<R>& E, int o, int v, int chunk, const TriplesOperands<R>& in,
+                     const typename Engine<R>::EpsSpec& es, int X1o, int S3o,
+                     const FieldAdjoint& fa) {
+  const int I0 = std::max(1, std::min(chunk, o));
+  const bool g = E.needs_grad(in.Ac.node) || E.needs_grad(in.Bc.node) ||
+                 E.needs_grad(in.T2.node) || E.needs_grad(in.G2.node) ||
+                 E.needs_grad(in.Lp.node) || E.needs_grad(in.Fp.node) ||
+                 E.needs_grad(in.Gb.node) || E.needs_grad(in.Gc.node) ||
+                 (fa.on && E.needs_grad(fa.wt));
+  const int nb0 = E.node({I0, o, o, v, v, v}, false, false);
+  const int nb1 = E.node({I0, o, o, v, v, v}, false, false);
+  const int nb2 = g ? E.node({I0, o, o, v, v, v}, false, false) : -1;
+  E.set_needs_grad(X1o, g);
+  E.set_needs_grad(S3o, g);
+
+  // slab view (I rows) of a slab node
+  auto slab = [&E](int nb, int I) { return E.v(nb).sub(0, 0, I); };
+  // One product of the slab loop.  The letter i is the slab's index: a slab
+  // view (s = true) holds the slab's rows already; any other operand that
+  // carries i is sliced to the slab (view at start 0 plus the start as a
+  // pointer shift, so that all slabs of one extent share one plan).
+  struct Arg { View v; bool g; bool s; };
+  auto prod = [&E](const std::string& spec, double alpha, Arg a, Arg b, Arg c, int i0, int I,
+                   bool acc) {
+    const size_t comma = spec.find(','), arrow = spec.find("->");
+    const std::string sa = spec.substr(0, comma), sb = spec.substr(comma + 1, arrow - comma - 1),
+                      sc = spec.substr(arrow + 2);
+    long long sh[3] = {0, 0, 0};
+    Arg* ops[3] = {&a, &b, &c};
+    const std::string* lets[3] = {&sa, &sb, &sc};
+    for (int w = 0; w < 3; ++w) {
+      const size_t d = lets[w]->find('i');
+      if (d == std::string::npos || ops[w]->s) continue;
+      sh[w] = (long long)i0 * ops[w]->v.stride[d];
+      ops[w]->v = ops[w]->v.sub(int(d), 0, I);
+    }
+    E.exec_contract_at(spec.c_str(), alpha, a.v, a.g, sh[0], b.v, b.g, sh[1], c.v, c.g, sh[2], acc);
+  };
+  // t3 of the slab into T: the six permuted Z products, then -W / D
+  auto build_t3 = [&E, prod, in, es](const View& T, int i0, int I) {
+    static const char* kA[6] = {"ijaE,Ekbc->ijkabc", "jibE,Ekac->ijkabc", "ikaE,Ejcb->ijkabc",
+                                "kjcE,Eiba->ijkabc", "kicE,Ejab->ijkabc", "jkbE,Eica->ijkabc"};
+    static const char* kB[6] = {"imab,mjck->ijkabc", "jmba,mick->ijkabc", "imac,mkbj->ijkabc",
+                                "kmcb,mjai->ijkabc", "kmca,mibj->ijkabc", "jmbc,mkai->ijkabc"};
+    for (int p = 0; p < 6; ++p) {
+      prod(kA[p], 1.0, {in.Ac, false, false}, {in.Bc, false, false}, {T, false, true}, i0, I, p > 0);
+      prod(kB[p], -1.0, {in.T2, false, false}, {in.G2, false, false}, {T, false, true}, i0, I, true);
+    }
+    E.exec_slab_div(-1.0, T, i0, es, T);
+  };
+  const View X1v = E.v(X1o), S3v = E.v(S3o);
+  for (int i0 = 0; i0 < o; i0 += I0) {
+    const int I = std::min(I0, o - i0);
+    const View T = slab(nb0, I), U = slab(nb1, I);
+    build_t3(T, i0, I);
+    E.exec_combine({{1.0, T}, {-1.0, E.ev("ijkcba->ijkabc", T)}}, U, true);
+    prod("ijkabc,jkbc->ia", 1.0, {U, false, true}, {in.Lp, false, false}, {X1v, false, false}, i0, I, true);
+    prod("ijkabc,kc->ijab", 1.0, {U, false, true}, {in.Fp, false, false}, {S3v, false, false}, i0, I, true);
+    E.exec_combine({{2.0, T}, {-1.0, E.ev("ijkxzy->ijkxyz", T)}, {-1.0, E.ev("ijkzyx->ijkxyz", T)}},
+                   U, true);
+    prod("ijkcbe,acke->ijab", 1.0, {U, false, true}, {in.Gb, false, false}, {S3v, false, false}, i0, I, true);
+    E.exec_combine({{2.0, T}, {-1.0, E.ev("ijkyxz->ijkxyz", T)}, {-1.0, E.ev("ijkzyx->ijkxyz", T)}},
+                   U, true);
+    // the slab index is Uc's first occupied index (m), a sum index here
+    prod("imkcba,kjic->jmab", -1.0, {U, false, true}, {in.Gc, false, false}, {S3v, false, false}, i0, I, true);
+  }
+  if (!g) return;
+  const int Gb2 = E.node({v, v, o, v}, false, false);
+  E.exec_combine({{2.0, in.Gb}, {-1.0, E.ev("dzrx->dxrz", in.Gb)}}, E.v(Gb2), true);
+  const View GB2 = E.v(Gb2);
+  E.custom([&E, o, v, I0, in, es, fa, nb0, nb1, nb2, X1o, S3o, GB2, prod, build_t3, slab]() {
+    const View X1v = E.v(X1o), S3v = E.v(S3o);
+    const bool gl = E.needs_grad(in.Lp.node), gf = E.needs_grad(in.Fp.node),
+               gb = E.needs_grad(in.Gb.node), gc = E.needs_grad(in.Gc.node);
+    const bool gfield = fa.on && E.needs_grad(fa.wt);
+    int Dv = -1, Do = -1;
+    if (gfield) {
+      Dv = E.node({v, v});
+      Do = E.node({o, o});
+    }
+    // Q[p,q,r,x,y,z] (the t3 cotangent) as nine products of small tensors;
+    // placeholders p q r x y z are mapped to the output letters of one of
+    // the three arrangements, d and l are sums
+    struct QT { const char* a; int ga; const char* b; double alpha; };
+    // ga: 0 grad X1, 1 grad S3; b operand: 0 Lp, 1 Fp, 2 Gb2, 3 Gb, 4 Gc
+    static const char* kQa[9] = {"px", "pqxy", "pz", "pqzy", "pqdy", "pqdz", "lqzy", "lqzx", "lqxy"};
+    static const int kQga[9] = {0, 1, 0, 1, 1, 1, 1, 1, 1};
+    static const char* kQb[9] = {"qryz", "rz", "qryx", "rx", "dxrz", "dxry", "rlpx", "rlpy", "rlpz"};
+    static const int kQbw[9] = {0, 1, 0, 1, 2, 3, 4, 4, 4};
+    static const double kQal[9] = {1.0, 1.0, -1.0, -1.0, 1.0, -1.0, -2.0, 1.0, 1.0};
+    static const char* kPos[3] = {"ijkabc", "jikbac", "kjicba"};  // p q r x y z
+    const View bops[5] = {in.Lp, in.Fp, GB2, in.Gb, in.Gc};
+    auto map = [](const char* t, const char* pos) {
+      std::string r(t);
+      for (char& ch : r) {
+        const char* ph = "pqrxyz";
+        for (int k = 0; k < 6; ++k)
+          if (ch == ph[k]) { ch = pos[k]; break; }
+      }
+      return r;
+    };
+    for (int i0 = 0; i0 < o; i0 += I0) {
+      const int I = std::min(I0, o - i0);
+      const View T = slab(nb0, I), U = slab(nb1, I), W = slab(nb2, I);
+      build_t3(T, i0, I);
+      // cotangents of the X-side operands
+      if (gl || gf) {
+        E.exec_combine({{1.0, T}, {-1.0, E.ev("ijkcba->ijkabc", T)}}, U, true);
+        if (gl) prod("ijkabc,ia->jkbc", 1.0, {U, false, true}, {X1v, true, false}, {in.Lp, true, false}, i0, I, true);
+        if (gf) prod("ijkabc,ijab->kc", 1.0, {U, false, true}, {S3v, true, false}, {in.Fp, true, false}, i0, I, true);
+      }
+      if (gb) {
+        E.exec_combine({{2.0, T}, {-1.0, E.ev("ijkxzy->ijkxyz", T)},
+                        {-1.0, E.ev("ijkzyx->ijkxyz", T)}}, U, true);
+        prod("ijkcbe,ijab->acke", 1.0, {U, false, true}, {S3v, true, false}, {in.Gb, true, false}, i0, I, true);
+      }
+      if (gc) {
+        E.exec_combine({{2.0, T}, {-1.0, E.ev("ijkyxz->ijkxyz", T)},
+                        {-1.0, E.ev("ijkzyx->ijkxyz", T)}}, U, true);
+        prod("imkcba,jmab->kjic", -1.0, {U, false, true}, {S3v, true, false}, {in.Gc, true, false}, i0, I, true);
+      }
+      // R = sum over the three arrangements of Q; S = R + R(ikjacb) = P(Q)
+      bool first = true;
+      for (int ps = 0; ps < 3; ++ps)
+        for (int t = 0; t < 9; ++t) {
+          const std::string spec = map(kQa[t], kPos[ps]) + "," + map(kQb[t], kPos[ps]) + "->ijkabc";
+          prod(spec, kQal[t], {kQga[t] ? S3v : X1v, true, false}, {bops[kQbw[t]], false, false}, {U, false, true}, i0,
+               I, !first);
+          first = false;
+        }
+      E.exec_combine({{1.0, U}, {1.0, E.ev("ikjacb->ijkabc", U)}}, W, true);
+      E.exec_slab_div(1.0, W, i0, es, W);  // W = P(Q) / D = -grad Z
+      if (gfield) {
+        // slot densities of the symmetrised y' = P(Q) / (6 D) with t3,
+        // summed over the three slots: 1/2 of one slot of P(Q) / D
+        E.exec_contract_at("ijkabc,ijkdbc->ad", 0.5, W, false, 0, T, false, 0, E.v(Dv), false, 0,
+                           true);
+        E.exec_contract_at("jkiabc,jklabc->li", 0.5, W, false, 0, T, false, 0, E.v(Do), false, 0,
+                           true);
+      }
+      if (E.needs_grad(in.Ac.node))
+        prod("ijkabc,Ekbc->ijaE", -1.0, {W, false, true}, {in.Bc, false, false}, {in.Ac, true, false}, i0, I, true);
+      if (E.needs_grad(in.Bc.node))
+        prod("ijaE,ijkabc->Ekbc", -1.0, {in.Ac, false, false}, {W, false, true}, {in.Bc, true, false}, i0, I, true);
+      if (E.needs_grad(in.T2.node))
+        prod("ijkabc,mjck->imab", 1.0, {W, false, true}, {in.G2, false, false}, {in.T2, true, false}, i0, I, true);
+      if (E.needs_grad(in.G2.node))
+        prod("imab,ijkabc->mjck", 1.0, {in.T2, false, false}, {W, false, true}, {in.G2, true, false}, i0, I, true);
+    }
+    if (gfield) {
+      const int tv = E.node({v, v}), to = E.node({o, o});
+      E.exec_contract("Aa,AD->aD", 1.0, fa.SIV, false, E.v(Dv), false, E.v(tv), false);
+      E.exec_contract("aD,dD->ad", -1.0, E.v(tv), false, fa.SV, false, fa.wvv, true);
+      E.exec_contract("lL,LI->lI", 1.0, fa.SO, false, E.v(Do), false, E.v(to), false);
+      E.exec_contract("lI,Ii->li", 1.0, E.v(to), false, fa.SIO, false, fa.woo, true);
+    }
+  }, true);
 }
 
 // Triples with the field coupling in the field-dressed eigenbasis (see
@@ -84,7 +284,7 @@ FieldBasis<R> start_field_basis(Engine<R>& E, const Hamil<R>& H, int wt,
 // in the rotated basis).  Returns the node of t3' and accumulates into R1 and SD.
 template <typename R, typename BlkFn>
 int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, const FieldBasis<R>& B,
-                    int g, int ft, const View& R1, const View& SD, BlkFn&& blk) {
+                    int g, int ft, const View& R1, const View& SD, BlkFn&& blk, int chunk = 0) {
   const int o = H.o, v = H.v;
   E.join();
   const int So = B.So, Sio = B.Sio, Sv = B.Sv, Siv = B.Siv;
@@ -130,17 +330,53 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   const int Bc = E.node({v + o, o, v, v}, false, false);
   E.combine({{1.0, E.ev("ckbe->ekbc", G1p)}}, E.v(Bc).sub(0, 0, v), true);
   E.combine({{1.0, E.ev("klcb->lkbc", T3p_)}}, E.v(Bc).sub(0, v, o), true);
-  const int Z = E.node(s6, false, false);
-  E.contract("ijaE,Ekbc->ijkabc", 1.0, E.v(Ac), E.v(Bc), E.v(Z), false);
-  E.contract("imab,mjck->ijkabc", -1.0, T2p, G2p, E.v(Z), true);
-  // ---- t3' = -P(Z) / D' with the complex denominators ---------------------------
+  // ---- X-side operands in the rotated basis: contracted indices take S
+  // (contravariant), free rotated indices S^-1 ------------------------------------
+  const int Ljk = E.node({o, o, v, v}, false, false);
+  E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
+            E.v(Ljk), true);
+  View Lp = rot("jJ,jkbc->Jkbc", SO, E.v(Ljk), {o, o, v, v});
+  Lp = rot("kK,Jkbc->JKbc", SO, Lp, {o, o, v, v});
+  Lp = rot("bB,JKbc->JKBc", SV, Lp, {o, o, v, v});
+  Lp = rot("cC,JKBc->JKBC", SV, Lp, {o, o, v, v});
+  View Fp = rot("kK,kc->Kc", SO, blk(ft, "ov"), {o, v});
+  Fp = rot("cC,Kc->KC", SV, Fp, {o, v});
+  View Gb = rot("Aa,acke->Acke", SIV, G("vvov"), {v, v, o, v});
+  Gb = rot("cC,Acke->ACke", SV, Gb, {v, v, o, v});
+  Gb = rot("kK,ACke->ACKe", SO, Gb, {v, v, o, v});
+  Gb = rot("eE,ACKe->ACKE", SV, Gb, {v, v, o, v});
+  View Gc = rot("kK,kimc->Kimc", SO, G("ooov"), {o, o, o, v});
+  Gc = rot("Ii,Kimc->KImc", SIO, Gc, {o, o, o, v});
+  Gc = rot("mM,KImc->KIMc", SO, Gc, {o, o, o, v});
+  Gc = rot("cC,KIMc->KIMC", SV, Gc, {o, o, o, v});
   typename Engine<R>::EpsSpec es;
   es.o = o;
   es.v = v;
   es.osum_cr = B.osum;
   es.vsum_cr = B.vsum;
   es.order = H.orbit_order;
-  const int t3p = E.node(s6, false, false);
+  const int X1p = E.node({o, v}, false, chunk > 0);
+  const int S3p = E.node({o, o, v, v}, false, chunk > 0);
+  int t3p = -1;
+  if (chunk > 0) {
+    // blocked: W and t3' per slab of occupied indices, never stored
+    FieldAdjoint fa;
+    fa.on = true;
+    fa.wt = wt;
+    fa.wvv = blk(wt, "vv");
+    fa.woo = blk(wt, "oo");
+    fa.SO = SO;
+    fa.SIO = SIO;
+    fa.SV = SV;
+    fa.SIV = SIV;
+    blocked_triples<R>(E, o, v, chunk, {E.v(Ac), E.v(Bc), T2p, G2p, Lp, Fp, Gb, Gc}, es, X1p,
+                       S3p, fa);
+  } else {
+  const int Z = E.node(s6, false, false);
+  E.contract("ijaE,Ekbc->ijkabc", 1.0, E.v(Ac), E.v(Bc), E.v(Z), false);
+  E.contract("imab,mjck->ijkabc", -1.0, T2p, G2p, E.v(Z), true);
+  // ---- t3' = -P(Z) / D' with the complex denominators ---------------------------
+  t3p = E.node(s6, false, false);
   E.sym6_div(-1.0, E.v(Z), es, E.v(t3p));
   const int wtn = wt;
   if (E.needs_grad(t3p) && E.needs_grad(wtn)) {
@@ -168,36 +404,17 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   const View T3 = E.v(t3p);
   const int dd = E.node(s6, false, false);
   E.combine({{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}}, E.v(dd), true);
-  const int Ljk = E.node({o, o, v, v}, false, false);
-  E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
-            E.v(Ljk), true);
-  // contracted indices take S (contravariant), free rotated indices S^-1
-  View Lp = rot("jJ,jkbc->Jkbc", SO, E.v(Ljk), {o, o, v, v});
-  Lp = rot("kK,Jkbc->JKbc", SO, Lp, {o, o, v, v});
-  Lp = rot("bB,JKbc->JKBc", SV, Lp, {o, o, v, v});
-  Lp = rot("cC,JKBc->JKBC", SV, Lp, {o, o, v, v});
-  const int X1p = E.node({o, v}, false, false);
   E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), Lp, E.v(X1p), false);
-  View Fp = rot("kK,kc->Kc", SO, blk(ft, "ov"), {o, v});
-  Fp = rot("cC,Kc->KC", SV, Fp, {o, v});
-  const int S3p = E.node({o, o, v, v}, false, false);
   E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), Fp, E.v(S3p), false);
   const int Ub = E.node(s6, false, false);
   E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
             E.v(Ub), true);
-  View Gb = rot("Aa,acke->Acke", SIV, G("vvov"), {v, v, o, v});
-  Gb = rot("cC,Acke->ACke", SV, Gb, {v, v, o, v});
-  Gb = rot("kK,ACke->ACKe", SO, Gb, {v, v, o, v});
-  Gb = rot("eE,ACKe->ACKE", SV, Gb, {v, v, o, v});
   E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), Gb, E.v(S3p), true);
   const int Uc = E.node(s6, false, false);
   E.combine({{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}},
             E.v(Uc), true);
-  View Gc = rot("kK,kimc->Kimc", SO, G("ooov"), {o, o, o, v});
-  Gc = rot("Ii,Kimc->KImc", SIO, Gc, {o, o, o, v});
-  Gc = rot("mM,KImc->KIMc", SO, Gc, {o, o, o, v});
-  Gc = rot("cC,KIMc->KIMC", SV, Gc, {o, o, o, v});
   E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), Gc, E.v(S3p), true);
+  }
   // ---- rotate the results back: X = (S_o x S_v) X' -----------------------------
   const View X1t = rot("iI,IA->iA", SO, E.v(X1p), {o, v});
   E.contract("aA,iA->ia", 1.0, SV, X1t, R1, true);
@@ -382,64 +599,83 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   // ---- triples ---------------------------------------------------------------
   if (opt.triples && opt.field_terms && opt.rotation) {
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores
-    S.t3 = rotated_triples(E, H, T, wt, fb, g, ft, R1, SD, blk);
+    S.t3 = rotated_triples(E, H, T, wt, fb, g, ft, R1, SD, blk, opt.triples_chunk);
     E.set_tc_region(false);
   } else if (opt.triples) {
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores
     const std::vector<int> s6 = {o, o, o, v, v, v};
-    // Z = sum_e t_ij^ae <cb|ke>~ - sum_m t_im^ab <mc|jk>~ ; W = P_ijk^abc Z (Eqs. A25, A30)
-    const int Z = E.node(s6, false, false);
-    E.contract("ijae,ckbe->ijkabc", 1.0, T, G("vovv"), E.v(Z), false);
-    E.contract("imab,mjck->ijkabc", -1.0, T, G("oovo"), E.v(Z), true);
-    // rhs = -(W + <mu3|1/2[[V~,T2],T2]|0>), the latter = -P sum_ld v~_ld t_ij^ad t_kl^cb:
-    // P is linear, so the source is folded into Z and rhs = -P(Z)
     const bool field = opt.field_terms;
-    if (field) {
-      const int Yl = E.node({o, o, o, v}, false, false);
-      E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), false);
-      E.contract("lija,klcb->ijkabc", -1.0, E.v(Yl), T, E.v(Z), true);
-    }
-    typename Engine<R>::EpsSpec es;
-    es.eps = H.eps;
-    for (int d = 0; d < 3; ++d) { es.sign[d] = -1; es.base[d] = 0; }
-    for (int d = 3; d < 6; ++d) { es.sign[d] = 1; es.base[d] = o; }
-    es.osum = H.osum;
-    es.vsum = H.vsum;
-    es.osum_r = H.osum_r;
-    es.vsum_r = H.vsum_r;
-    es.order = H.orbit_order;
-    es.o = o;
-    es.v = v;
-    int t3;
-    if (!field) {
-      t3 = E.node(s6, false, false);
-      E.sym6_div(-1.0, E.v(Z), es, E.v(t3));
+    if (!field && opt.triples_chunk > 0) {
+      // field-free and blocked: W and t3 per slab, never stored
+      typename Engine<R>::EpsSpec es;
+      es.o = o;
+      es.v = v;
+      es.osum_r = H.osum_r;
+      es.vsum_r = H.vsum_r;
+      const int Ljk = E.node({o, o, v, v}, false, false);
+      E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
+                E.v(Ljk), true);
+      const int X1o = E.node({o, v}), S3o = E.node({o, o, v, v});
+      blocked_triples<R>(E, o, v, opt.triples_chunk,
+                         {T, E.ev("ckbe->ekbc", G("vovv")), T, G("oovo"), E.v(Ljk), F("ov"),
+                          G("vvov"), G("ooov")},
+                         es, X1o, S3o, FieldAdjoint());
+      E.axpy(1.0, E.v(X1o), R1);
+      E.axpy(1.0, E.v(S3o), SD);
     } else {
-      const int rhs = E.node(s6, false, false);
-      E.sym6(-1.0, E.v(Z), E.v(rhs), true);
-      t3 = field_coupled_solve(E, rhs, blk(wt, "vv"), blk(wt, "oo"), wt, es, s6,
-                               std::max(1, opt.field_iters));
+      // Z = sum_e t_ij^ae <cb|ke>~ - sum_m t_im^ab <mc|jk>~ ; W = P_ijk^abc Z (Eqs. A25, A30)
+      const int Z = E.node(s6, false, false);
+      E.contract("ijae,ckbe->ijkabc", 1.0, T, G("vovv"), E.v(Z), false);
+      E.contract("imab,mjck->ijkabc", -1.0, T, G("oovo"), E.v(Z), true);
+      // rhs = -(W + <mu3|1/2[[V~,T2],T2]|0>), the latter = -P sum_ld v~_ld t_ij^ad t_kl^cb:
+      // P is linear, so the source is folded into Z and rhs = -P(Z)
+      if (field) {
+        const int Yl = E.node({o, o, o, v}, false, false);
+        E.contract("ld,ijad->lija", 1.0, blk(wt, "ov"), T, E.v(Yl), false);
+        E.contract("lija,klcb->ijkabc", -1.0, E.v(Yl), T, E.v(Z), true);
+      }
+      typename Engine<R>::EpsSpec es;
+      es.eps = H.eps;
+      for (int d = 0; d < 3; ++d) { es.sign[d] = -1; es.base[d] = 0; }
+      for (int d = 3; d < 6; ++d) { es.sign[d] = 1; es.base[d] = o; }
+      es.osum = H.osum;
+      es.vsum = H.vsum;
+      es.osum_r = H.osum_r;
+      es.vsum_r = H.vsum_r;
+      es.order = H.orbit_order;
+      es.o = o;
+      es.v = v;
+      int t3;
+      if (!field) {
+        t3 = E.node(s6, false, false);
+        E.sym6_div(-1.0, E.v(Z), es, E.v(t3));
+      } else {
+        const int rhs = E.node(s6, false, false);
+        E.sym6(-1.0, E.v(Z), E.v(rhs), true);
+        t3 = field_coupled_solve(E, rhs, blk(wt, "vv"), blk(wt, "oo"), wt, es, s6,
+                                 std::max(1, opt.field_iters));
+      }
+      S.t3 = t3;
+      const View T3 = E.v(t3);
+      // X1 (Eq. A21) and X2 (Eq. A22)
+      const int dd = E.node(s6, false, false);  // t_ijk^abc - t_ijk^cba
+      E.combine({{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}}, E.v(dd), true);
+      const int Ljk = E.node({o, o, v, v}, false, false);
+      E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
+                E.v(Ljk), true);
+      E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), E.v(Ljk), R1, true);
+      const int S3 = E.node({o, o, v, v}, false, false);
+      E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), F("ov"), E.v(S3), false);
+      const int Ub = E.node(s6, false, false);  // 2 t^cbe - t^ceb - t^ebc  as [ijk cbe]
+      E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
+                E.v(Ub), true);
+      E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), G("vvov"), E.v(S3), true);
+      const int Uc = E.node(s6, false, false);  // 2 t_mjk^cba - t_mjk^bca - t_mjk^abc
+      E.combine({{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}},
+                E.v(Uc), true);
+      E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), G("ooov"), E.v(S3), true);
+      E.axpy(1.0, E.v(S3), SD);
     }
-    S.t3 = t3;
-    const View T3 = E.v(t3);
-    // X1 (Eq. A21) and X2 (Eq. A22)
-    const int dd = E.node(s6, false, false);  // t_ijk^abc - t_ijk^cba
-    E.combine({{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}}, E.v(dd), true);
-    const int Ljk = E.node({o, o, v, v}, false, false);
-    E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
-              E.v(Ljk), true);
-    E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), E.v(Ljk), R1, true);
-    const int S3 = E.node({o, o, v, v}, false, false);
-    E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), F("ov"), E.v(S3), false);
-    const int Ub = E.node(s6, false, false);  // 2 t^cbe - t^ceb - t^ebc  as [ijk cbe]
-    E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
-              E.v(Ub), true);
-    E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), G("vvov"), E.v(S3), true);
-    const int Uc = E.node(s6, false, false);  // 2 t_mjk^cba - t_mjk^bca - t_mjk^abc
-    E.combine({{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}},
-              E.v(Uc), true);
-    E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), G("ooov"), E.v(S3), true);
-    E.axpy(1.0, E.v(S3), SD);
     E.set_tc_region(false);
   }
   // P_ij^ab on the symmetrised part

@@ -32,13 +32,21 @@ namespace rtcc3 {
 namespace {
 
 constexpr int kBM = 128;
-constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
+// Waits on other warps' progress spin for at most a budget of clock cycles
+// (a kernel argument, kWaitBudget by default, about 2 s).  Waits for this
+// CTA's own asynchronous work to land (its TMA / bulk copies, its MMAs) at
+// exit use kDrainBudget: that work completes by itself, so these waits end
+// whatever the progress budget was; they are what makes giving up safe
+// (no copy or MMA may still target the CTA's shared or tensor memory when it
+// frees them).
+constexpr long long kWaitBudget = 4000000000LL;
+constexpr long long kDrainBudget = 4000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget) {
   const long long t0 = clock64();
   while (true) {
     uint32_t ok = 0;
@@ -49,7 +57,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > kWaitBudget) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 
@@ -223,7 +231,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, EW == 4 ? 2 : 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           int M, int Nr, int nkb_total, int kb_per_split, int kb_lo, float2* __restrict__ C,
           const long long* __restrict__ cM, const long long* __restrict__ cN, long long coff,
-          float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err) {
+          float alpha, int accumulate, float* __restrict__ partial, int* __restrict__ err,
+          long long budget) {
   using L = TcSmem<BN, SPLIT, EW>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -267,9 +276,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
   if (warp == 0) {
     if (lane == 0) {
+      int issued = 0;
       for (int i = 0; i < nkb && ok; ++i) {
         const int s = i % kStages;
-        if (i >= kStages) ok = mbar_wait(smem_u32(&empty[s]), ((i / kStages) - 1) & 1);
+        if (i >= kStages) ok = mbar_wait(smem_u32(&empty[s]), ((i / kStages) - 1) & 1, budget);
         if (!ok) break;
         const uint32_t fb = smem_u32(&full[s]);
         mbar_expect_tx(fb, L::kTmaBytes);
@@ -279,18 +289,20 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         tma_load_2d(smem_u32(sa), &tmA, kx, m0, fb);
         tma_load_2d(smem_u32(sb), &tmB, kx, n0, fb);
         if (SPLIT) tma_load_2d(smem_u32(sb + L::kBBytes), &tmB, kx + kb_lo * kElemPerK, n0, fb);
+        issued = i + 1;
       }
-      // drain: wait until the MMAs that read the last stages are done so no
-      // copy into this CTA's shared memory is outstanding at exit
-      for (int i = max(0, nkb - kStages); i < nkb && ok; ++i)
-        ok = mbar_wait(smem_u32(&empty[i % kStages]), (i / kStages) & 1);
+      // drain: every copy issued into this CTA's shared memory has landed
+      // before it exits (the last ring round; earlier rounds were consumed
+      // before their stage was reused), also after giving up
+      for (int i = max(0, issued - kStages); i < issued; ++i)
+        if (!mbar_wait(smem_u32(&full[i % kStages]), (i / kStages) & 1, kDrainBudget)) ok = false;
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = instr_desc<BF16>(kBM, BN);
       for (int i = 0; i < nkb && ok; ++i) {
         const int s = i % kStages;
-        ok = mbar_wait(smem_u32(SPLIT ? &conv[s] : &full[s]), (i / kStages) & 1);
+        ok = mbar_wait(smem_u32(SPLIT ? &conv[s] : &full[s]), (i / kStages) & 1, budget);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t sa = smem_u32(smem + s * L::kStageBytes);
@@ -307,7 +319,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
         mma_commit(smem_u32(&empty[s]));
       }
+      // committed also after giving up: `done` completes once every MMA
+      // issued has, and nothing leaves before that
       mma_commit(smem_u32(done));
+      if (!mbar_wait(smem_u32(done), 0, kDrainBudget)) ok = false;
     }
   } else {
     if (SPLIT) {
@@ -317,7 +332,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const int ct = threadIdx.x - 64;  // 0 .. 32 EW - 1
       for (int i = 0; i < nkb && ok; ++i) {
         const int s = i % kStages;
-        ok = mbar_wait(smem_u32(&full[s]), (i / kStages) & 1);
+        ok = mbar_wait(smem_u32(&full[s]), (i / kStages) & 1, budget);
         if (!ok) break;
         float4* ah = reinterpret_cast<float4*>(smem + s * L::kStageBytes);
         float4* al = reinterpret_cast<float4*>(smem + s * L::kStageBytes + L::kABytes);
@@ -341,7 +356,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     // epilogue: warps 2 .. 1 + EW, EW / 4 per TMEM lane quarter (warp % 4),
     // taking every (EW / 4)-th 32-column chunk
     const int q = warp & 3, ew = warp - 2, half = ew >> 2;
-    ok = ok && ((nkb == 0) ? true : mbar_wait(smem_u32(done), 0));
+    // the MMA warp always commits `done`: wait for it even after giving up
+    const bool dn = (nkb == 0) ? true : mbar_wait(smem_u32(done), 0, kDrainBudget);
+    ok = ok && dn;
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float* st = stage_out + ew * 32 * 33;
@@ -454,7 +471,7 @@ template <int BN, bool BF16, bool SPLIT>
 __global__ void __launch_bounds__(320, 1)
 k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUtensorMap tmB,
                  int M, int Nr, int nkb_total, int per, int nchains, int cpc, int kb_lo,
-                 float* __restrict__ partial, int* __restrict__ err) {
+                 float* __restrict__ partial, int* __restrict__ err, long long budget) {
   using L = TcChainSmem<BN, SPLIT>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -465,7 +482,8 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
   uint64_t* conv = bars + 2 * kStages;   // SPLIT: low parts of A written
   uint64_t* cfull = bars + 3 * kStages;  // [2] accumulator holds a finished chain
   uint64_t* cfree = cfull + 2;           // [2] accumulator drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 2);
+  uint64_t* fin = cfree + 2;             // every MMA issued has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
@@ -485,6 +503,7 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
       mbar_init(smem_u32(&cfull[b]), 1);
       mbar_init(smem_u32(&cfree[b]), 4);  // one arrival per drain warp
     }
+    mbar_init(smem_u32(fin), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -502,10 +521,12 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
 
   if (warp == 0) {
     if (lane == 0) {
+      int issued = 0;
       for (int i = 0; i < nkb && ok; ++i) {
         const int st = i % kStages;
-        if (i >= kStages) ok = mbar_wait(smem_u32(&empty[st]), ((i / kStages) - 1) & 1);
+        if (i >= kStages) ok = mbar_wait(smem_u32(&empty[st]), ((i / kStages) - 1) & 1, budget);
         if (!ok) break;
+        issued = i + 1;
         const uint32_t fb = smem_u32(&full[st]);
         mbar_expect_tx(fb, L::kStageBytes);
         uint8_t* sa = smem + st * L::kStageBytes;
@@ -518,9 +539,10 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
         tma_load_2d(smem_u32(sb), &tmB, kx, n0, fb);
         if (SPLIT) tma_load_2d(smem_u32(sb + L::kBBytes), &tmB, kx + kb_lo * kElemPerK, n0, fb);
       }
-      // no copy into shared memory may be outstanding at exit
-      for (int i = max(0, nkb - kStages); i < nkb && ok; ++i)
-        ok = mbar_wait(smem_u32(&empty[i % kStages]), (i / kStages) & 1);
+      // no copy into shared memory may be outstanding at exit (also after
+      // giving up): the last ring round of copies has landed
+      for (int i = max(0, issued - kStages); i < issued; ++i)
+        if (!mbar_wait(smem_u32(&full[i % kStages]), (i / kStages) & 1, kDrainBudget)) ok = false;
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -528,9 +550,9 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
       for (int i = 0; i < nkb && ok; ++i) {
         const int st = i % kStages, j = i / per, pos = i - j * per, b = j & 1;
         // the accumulator's previous chain (j - 2) must have been drained
-        if (pos == 0 && j >= 2) ok = mbar_wait(smem_u32(&cfree[b]), ((j >> 1) - 1) & 1);
+        if (pos == 0 && j >= 2) ok = mbar_wait(smem_u32(&cfree[b]), ((j >> 1) - 1) & 1, budget);
         if (!ok) break;
-        ok = mbar_wait(smem_u32(SPLIT ? &conv[st] : &full[st]), (i / kStages) & 1);
+        ok = mbar_wait(smem_u32(SPLIT ? &conv[st] : &full[st]), (i / kStages) & 1, budget);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc_t = tmem + uint32_t(b * L::kAccStride);
@@ -552,6 +574,10 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
         mma_commit(smem_u32(&empty[st]));
         if (pos == per - 1 || i == nkb - 1) mma_commit(smem_u32(&cfull[b]));
       }
+      // every MMA issued has completed before tensor memory is freed (also
+      // after giving up)
+      mma_commit(smem_u32(fin));
+      if (!mbar_wait(smem_u32(fin), 0, kDrainBudget)) ok = false;
     }
   } else if (warp < 6) {
     if (SPLIT) {
@@ -563,7 +589,7 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
       const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
       for (int i = 0; i < nkb && ok; ++i) {
         const int st = i % kStages;
-        ok = mbar_wait(smem_u32(&full[st]), (i / kStages) & 1);
+        ok = mbar_wait(smem_u32(&full[st]), (i / kStages) & 1, budget);
         if (!ok) break;
         const float4* row = reinterpret_cast<const float4*>(smem + st * L::kStageBytes + r * 128);
         uint32_t hi[32], lo[32];
@@ -593,7 +619,7 @@ k_tc_gemm_chains(const uint8_t* __restrict__ Atiled, const __grid_constant__ CUt
     const bool vec = (Nr & 3) == 0;
     for (int j = 0; j < nch && ok; ++j) {
       const int b = j & 1;
-      ok = mbar_wait(smem_u32(&cfull[b]), (j >> 1) & 1);
+      ok = mbar_wait(smem_u32(&cfull[b]), (j >> 1) & 1, budget);
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -797,7 +823,7 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcOperands& op, 
   dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, nsplit);
   k_tc_gemm<BN, BF16, SPLIT, EW><<<grid, L::kThreads, L::kTotal, s>>>(
       ma, mb, op.M, Nr, nkb, per, nkb, C, cM, cN, coff, alpha, accumulate ? 1 : 0,
-      nsplit > 1 ? partial : nullptr, err);
+      nsplit > 1 ? partial : nullptr, err, op.wait_budget > 0 ? op.wait_budget : kWaitBudget);
   RTCC3_CUDA(cudaGetLastError());
 }
 
@@ -853,7 +879,7 @@ __global__ void __launch_bounds__(576, 1)
 k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* __restrict__ aM,
                  const long long* __restrict__ aK, int K, const __grid_constant__ CUtensorMap tmB,
                  int M, int Nr, int nkb_total, int per, int nchains, int cpc,
-                 float* __restrict__ partial, int* __restrict__ err) {
+                 float* __restrict__ partial, int* __restrict__ err, long long budget) {
   using L = TcDirectSmem<BN>;
   constexpr int SA = L::kAStages, SB = L::kBStages;
   extern __shared__ uint8_t smem_raw[];
@@ -866,7 +892,8 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
   uint64_t* conv = empty + SB;       // [SB] TMEM A stage written (4 warps)
   uint64_t* cfull = conv + SB;       // [2] accumulator holds a finished chain
   uint64_t* cfree = cfull + 2;       // [2] accumulator drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 2);
+  uint64_t* fin = cfree + 2;         // every MMA issued has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
@@ -889,6 +916,7 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
       mbar_init(smem_u32(&cfull[b]), 1);
       mbar_init(smem_u32(&cfree[b]), 4);
     }
+    mbar_init(smem_u32(fin), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -906,10 +934,12 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
 
   if (warp == 0) {
     if (lane == 0) {
+      int issued = 0;
       for (int i = 0; i < nkb && ok; ++i) {
         const int st = i % SB;
-        if (i >= SB) ok = mbar_wait(smem_u32(&empty[st]), ((i / SB) - 1) & 1);
+        if (i >= SB) ok = mbar_wait(smem_u32(&empty[st]), ((i / SB) - 1) & 1, budget);
         if (!ok) break;
+        issued = i + 1;
         const uint32_t fb = smem_u32(&bfull[st]);
         mbar_expect_tx(fb, L::kBStage);
         const uint32_t sb = smem_u32(smem + L::kBOff + st * L::kBStage);
@@ -917,17 +947,18 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
         tma_load_2d(sb, &tmB, kx, n0, fb);
         tma_load_2d(sb + BN * 128, &tmB, kx + nkb_total * 32, n0, fb);
       }
-      for (int i = max(0, nkb - SB); i < nkb && ok; ++i)
-        ok = mbar_wait(smem_u32(&empty[i % SB]), (i / SB) & 1);
+      // the last ring round of B copies has landed (also after giving up)
+      for (int i = max(0, issued - SB); i < issued; ++i)
+        if (!mbar_wait(smem_u32(&bfull[i % SB]), (i / SB) & 1, kDrainBudget)) ok = false;
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = instr_desc<false>(kBM, BN);
       for (int i = 0; i < nkb && ok; ++i) {
         const int st = i % SB, j = i / per, pos = i - j * per, b = j & 1;
-        if (pos == 0 && j >= 2) ok = mbar_wait(smem_u32(&cfree[b]), ((j >> 1) - 1) & 1);
-        if (ok) ok = mbar_wait(smem_u32(&conv[st]), (i / SB) & 1);
-        if (ok) ok = mbar_wait(smem_u32(&bfull[st]), (i / SB) & 1);
+        if (pos == 0 && j >= 2) ok = mbar_wait(smem_u32(&cfree[b]), ((j >> 1) - 1) & 1, budget);
+        if (ok) ok = mbar_wait(smem_u32(&conv[st]), (i / SB) & 1, budget);
+        if (ok) ok = mbar_wait(smem_u32(&bfull[st]), (i / SB) & 1, budget);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc_t = tmem + uint32_t(b * L::kAccStride);
@@ -943,6 +974,10 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
         mma_commit(smem_u32(&empty[st]));
         if (pos == per - 1 || i == nkb - 1) mma_commit(smem_u32(&cfull[b]));
       }
+      // every MMA issued has completed before tensor memory is freed (also
+      // after giving up)
+      mma_commit(smem_u32(fin));
+      if (!mbar_wait(smem_u32(fin), 0, kDrainBudget)) ok = false;
     }
   } else if (warp < 10) {
     // loaders.  AKC: pairs of consecutive k, pair p = t + 256 u (u < 4),
@@ -962,7 +997,7 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
     }
     for (int i = 0; i < nkb && ok; ++i) {
       const int st = i % SA;
-      if (i >= SA) ok = mbar_wait(smem_u32(&aempty[st]), ((i / SA) - 1) & 1);
+      if (i >= SA) ok = mbar_wait(smem_u32(&aempty[st]), ((i / SA) - 1) & 1, budget);
       if (!ok) break;
       const uint32_t sa = smem_u32(smem + st * L::kABytes);
       const int kbase = (kb0 + i) * 16;
@@ -1008,9 +1043,9 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
     const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
     for (int i = 0; i < nkb && ok; ++i) {
       const int sa_i = i % SA, st = i % SB;
-      ok = mbar_wait(smem_u32(&afull[sa_i]), (i / SA) & 1);
+      ok = mbar_wait(smem_u32(&afull[sa_i]), (i / SA) & 1, budget);
       // the TMEM stage's previous MMAs (K tile i - SB) must be done
-      if (ok && i >= SB) ok = mbar_wait(smem_u32(&empty[st]), ((i / SB) - 1) & 1);
+      if (ok && i >= SB) ok = mbar_wait(smem_u32(&empty[st]), ((i / SB) - 1) & 1, budget);
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.st below is warp-collective
       if (!ok) break;
       const float4* row = reinterpret_cast<const float4*>(smem + sa_i * L::kABytes + r * 128);
@@ -1043,7 +1078,7 @@ k_tc_gemm_direct(const float2* __restrict__ A, long long aoff, const long long* 
     const bool vec = (Nr & 3) == 0;
     for (int j = 0; j < nch && ok; ++j) {
       const int b = j & 1;
-      ok = mbar_wait(smem_u32(&cfull[b]), (j >> 1) & 1);
+      ok = mbar_wait(smem_u32(&cfull[b]), (j >> 1) & 1, budget);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1103,12 +1138,15 @@ void launch_direct(const float2* A, long long aoff, const long long* aM, const l
   const int cpc = chains_per_cta(tiles, nchains);
   const int zz = (nchains + cpc - 1) / cpc;
   dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, zz);
+  const long long budget = op.wait_budget > 0 ? op.wait_budget : kWaitBudget;
   if (a_kc)
     k_tc_gemm_direct<BN, true><<<grid, 576, L::kTotal, s>>>(A, aoff, aM, aK, op.K, mb, op.M, Nr,
-                                                            nkb, per, nchains, cpc, partial, err);
+                                                            nkb, per, nchains, cpc, partial, err,
+                                                            budget);
   else
     k_tc_gemm_direct<BN, false><<<grid, 576, L::kTotal, s>>>(A, aoff, aM, aK, op.K, mb, op.M, Nr,
-                                                             nkb, per, nchains, cpc, partial, err);
+                                                             nkb, per, nchains, cpc, partial, err,
+                                                             budget);
   RTCC3_CUDA(cudaGetLastError());
 }
 
@@ -1134,7 +1172,8 @@ bool launch_chains(const void* Atiled, const CUtensorMap& mb, const TcOperands& 
   const int zz = (nchains + cpc - 1) / cpc;
   dim3 grid((Nr + BN - 1) / BN, (op.M + kBM - 1) / kBM, zz);
   k_tc_gemm_chains<BN, BF16, SPLIT><<<grid, 320, L::kTotal, s>>>(
-      static_cast<const uint8_t*>(Atiled), mb, op.M, Nr, nkb, per, nchains, cpc, nkb, partial, err);
+      static_cast<const uint8_t*>(Atiled), mb, op.M, Nr, nkb, per, nchains, cpc, nkb, partial, err,
+      op.wait_budget > 0 ? op.wait_budget : kWaitBudget);
   RTCC3_CUDA(cudaGetLastError());
   return true;
 }

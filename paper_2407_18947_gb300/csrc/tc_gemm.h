@@ -33,6 +33,10 @@ struct TcOperands {
   // row block consecutive along K, so a long sum streams A as contiguous
   // 16 KB blocks (set iff tc_chained)
   bool a_tiled = false;
+  // clock cycles a wait on another warp's progress may spin before the
+  // kernel gives up (raises its error flag, drains its own copies and MMAs,
+  // frees its tensor memory and returns); 0: the default of about 2 s
+  long long wait_budget = 0;
 };
 
 // GEMM column tile (real columns) for Nr = 2N real output columns: the
