@@ -59,6 +59,11 @@ extern "C" {
 #define RTCC3_FIELD_STATIC 1 /* E(t) = A                                   */
 #define RTCC3_FIELD_COS 2    /* E(t) = A cos(omega t)                (Eq. 14) */
 #define RTCC3_FIELD_GAUSS 3  /* E(t) = A exp(-(t - c)^2 / (2 w^2))   (Eq. 32) */
+/* Ramped continuous waves (Section 2.2.4), ramp duration t_r = width, zero
+ * for t < 0 and A cos(omega t) from t_r on:                                  */
+#define RTCC3_FIELD_LRCW 4   /* E(t) = A (t / t_r) cos(omega t), t < t_r          */
+#define RTCC3_FIELD_QRCW 5   /* E(t) = A 2 t^2 / t_r^2 cos(omega t), t < t_r / 2;
+                                A [1 - 2 (t - t_r)^2 / t_r^2] cos(omega t), t < t_r */
 
 typedef struct rtcc3_ctx rtcc3_ctx;
 
@@ -109,7 +114,8 @@ int rtcc3_set_hamiltonian(rtcc3_ctx* ctx, const double* eps, int naux, const dou
                           const double* dipole);
 
 /* Field of slot b (0 <= b < nbatch): kind RTCC3_FIELD_*, amplitude A (au),
- * omega, center, width (au) and a Cartesian direction dir[3]. */
+ * omega, center, width (au; the ramp duration t_r for LRCW / QRCW) and a
+ * Cartesian direction dir[3]; the perturbation is V = -E(t) dir . mu. */
 int rtcc3_set_field(rtcc3_ctx* ctx, int b, int kind, double amplitude, double omega,
                     double center, double width, const double* dir);
 
@@ -174,6 +180,14 @@ int rtcc3_triples_vjp_dev(rtcc3_ctx* ctx, int b, double time, const void* t1, co
  * `stream` (NULL: the context stream) and the call returns after it is done. */
 int rtcc3_triples_forward_noalloc_dev(rtcc3_ctx* ctx, int b, double time, const void* t1,
                                       const void* t2, void* x1, void* x2, void* stream);
+
+/* Change the wait budgets of an existing context (the rtcc3_options fields
+ * spin_budget and eig_sweep_cap; 0 restores a default); later calls use them.
+ * A wait that runs out of its budget does not hang or poison the context: the
+ * kernel drains its own copies and MMAs, frees its tensor memory and returns,
+ * the call returns RTCC3_ERR_TIMEOUT (the outputs of that call are
+ * undefined), and a later call with a sufficient budget succeeds. */
+int rtcc3_set_wait_budgets(rtcc3_ctx* ctx, long long spin_budget, int eig_sweep_cap);
 
 /* Checkpoint: FP64 state of all slots plus time and step counter, as a flat
  * byte image with a version word and checksum.  Query the size with

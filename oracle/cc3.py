@@ -44,7 +44,7 @@ import torch
 CD = torch.complex128
 RD = torch.float64
 
-FIELD_NONE, FIELD_STATIC, FIELD_COS, FIELD_GAUSS = 0, 1, 2, 3
+FIELD_NONE, FIELD_STATIC, FIELD_COS, FIELD_GAUSS, FIELD_LRCW, FIELD_QRCW = 0, 1, 2, 3, 4, 5
 
 
 def _ct(x):
@@ -104,7 +104,8 @@ class Hamiltonian:
 
 @dataclass
 class FieldSpec:
-    """Time profile of the field (Eq. 14 cosine, Eq. 32 Gaussian, or static)."""
+    """Time profile of the field (Eq. 14 cosine, Eq. 32 Gaussian, static, or the
+    linear / quadratic ramped continuous waves of Section 2.2.4)."""
 
     kind: int = FIELD_NONE
     amplitude: float = 0.0
@@ -122,6 +123,19 @@ class FieldSpec:
             return self.amplitude * math.cos(self.omega * t)
         if self.kind == FIELD_GAUSS:
             return self.amplitude * math.exp(-(t - self.center) ** 2 / (2.0 * self.width ** 2))
+        if self.kind in (FIELD_LRCW, FIELD_QRCW):
+            # ramped continuous waves of Section 2.2.4, ramp duration t_r = width
+            if t < 0.0:
+                return 0.0
+            tr = self.width
+            c = math.cos(self.omega * t)
+            if t >= tr:
+                return self.amplitude * c
+            if self.kind == FIELD_LRCW:
+                return self.amplitude * (t / tr) * c
+            if t < 0.5 * tr:
+                return self.amplitude * (2.0 * t * t / (tr * tr)) * c
+            return self.amplitude * (1.0 - 2.0 * (t - tr) ** 2 / (tr * tr)) * c
         raise ValueError(f"unknown field kind {self.kind}")
 
     def vector(self, t: float) -> np.ndarray:

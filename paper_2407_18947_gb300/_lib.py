@@ -16,7 +16,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR_STATE = (
     -1, -2, -3, -4, -5, -6, -7)
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3
-FIELD_NONE, FIELD_STATIC, FIELD_COS, FIELD_GAUSS = 0, 1, 2, 3
+FIELD_NONE, FIELD_STATIC, FIELD_COS, FIELD_GAUSS, FIELD_LRCW, FIELD_QRCW = 0, 1, 2, 3, 4, 5
 
 _STATUS_NAMES = {ERR_ARG: "RTCC3_ERR_ARG", ERR_OOM: "RTCC3_ERR_OOM", ERR_CUDA: "RTCC3_ERR_CUDA",
                  ERR_NONFINITE: "RTCC3_ERR_NONFINITE", ERR_TIMEOUT: "RTCC3_ERR_TIMEOUT",
@@ -63,6 +63,7 @@ SIGNATURES = {
     "rtcc3_get_state": (_I, [_P, _P, ctypes.c_longlong]),
     "rtcc3_set_state": (_I, [_P, _P, ctypes.c_longlong]),
     "rtcc3_stats": (_I, [_P, _LLP, _LLP]),
+    "rtcc3_set_wait_budgets": (_I, [_P, ctypes.c_longlong, _I]),
     "rtcc3_set_profiling": (_I, [_P, _I]),
     "rtcc3_kernel_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
 }

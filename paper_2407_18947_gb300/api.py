@@ -10,8 +10,8 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (FIELD_COS, FIELD_GAUSS, FIELD_NONE, FIELD_STATIC, PREC_BF16, PREC_FP32,  # noqa: F401
-                   PREC_FP64, PREC_TF32, RTCC3Error)
+from ._lib import (FIELD_COS, FIELD_GAUSS, FIELD_LRCW, FIELD_NONE, FIELD_QRCW,  # noqa: F401
+                   FIELD_STATIC, PREC_BF16, PREC_FP32, PREC_FP64, PREC_TF32, RTCC3Error)
 
 
 def _dp(a):
@@ -172,6 +172,10 @@ class RTCC3:
         a, b = ctypes.c_longlong(), ctypes.c_longlong()
         self._check(self.lib.rtcc3_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return {"launches": a.value, "device_bytes": b.value}
+
+    def set_wait_budgets(self, spin_budget: int = 0, eig_sweep_cap: int = 0):
+        """Wait budgets of the device kernels (0 restores a default)."""
+        self._check(self.lib.rtcc3_set_wait_budgets(self.h, int(spin_budget), int(eig_sweep_cap)))
 
     def set_profiling(self, enable: bool):
         self._check(self.lib.rtcc3_set_profiling(self.h, 1 if enable else 0))

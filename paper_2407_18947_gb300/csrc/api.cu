@@ -1030,10 +1030,12 @@ int rtcc3_set_field(rtcc3_ctx* ctx, int b, int kind, double amplitude, double om
   if (!ctx) return RTCC3_ERR_ARG;
   return guarded(ctx, [&] {
     check_slot(ctx, b);
-    RTCC3_CHECK(kind >= RTCC3_FIELD_NONE && kind <= RTCC3_FIELD_GAUSS, RTCC3_ERR_ARG, "unknown field kind");
+    RTCC3_CHECK(kind >= RTCC3_FIELD_NONE && kind <= RTCC3_FIELD_QRCW, RTCC3_ERR_ARG, "unknown field kind");
     RTCC3_CHECK(std::isfinite(amplitude) && std::isfinite(omega) && std::isfinite(center) &&
                     std::isfinite(width), RTCC3_ERR_ARG, "non-finite field parameter");
     RTCC3_CHECK(kind != RTCC3_FIELD_GAUSS || width > 0.0, RTCC3_ERR_ARG, "Gaussian width must be > 0");
+    RTCC3_CHECK((kind != RTCC3_FIELD_LRCW && kind != RTCC3_FIELD_QRCW) || width > 0.0, RTCC3_ERR_ARG,
+                "ramp duration (width) must be > 0");
     FieldDev f{kind, amplitude, omega, center, width, {0.0, 0.0, 1.0}};
     if (dir) { f.dir[0] = dir[0]; f.dir[1] = dir[1]; f.dir[2] = dir[2]; }
     ctx->fhost[b] = f;
@@ -1287,6 +1289,25 @@ int rtcc3_set_state(rtcc3_ctx* ctx, const void* buf, long long bytes) {
     ctx->time = hd.time;
     ctx->step_total = hd.step;
     RTCC3_CUDA(cudaMemcpy(ctx->tdev, &ctx->time, sizeof(double), cudaMemcpyHostToDevice));
+  });
+}
+
+int rtcc3_set_wait_budgets(rtcc3_ctx* ctx, long long spin_budget, int eig_sweep_cap) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  if (spin_budget < 0 || eig_sweep_cap < 0)
+    return fail(ctx, RTCC3_ERR_ARG, "negative wait budget");
+  return guarded(ctx, [&] {
+    ctx->opt.spin_budget = spin_budget;
+    ctx->opt.eig_sweep_cap = eig_sweep_cap;
+    if (ctx->runner) {
+      auto f = [&](auto tag) {
+        using R = decltype(tag);
+        ctx->run<R>().E.set_wait_budget(spin_budget);
+        ctx->run<R>().E.set_eig_sweep_cap(eig_sweep_cap);
+      };
+      if (ctx->fp64()) f(double()); else f(float());
+    }
+    drop_graph(ctx);  // a captured step holds the budgets as kernel arguments
   });
 }
 

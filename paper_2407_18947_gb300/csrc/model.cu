@@ -13,11 +13,32 @@ int grid_n(size_t n) {
   return int(std::max<size_t>(1, std::min<size_t>(g, 152 * 8)));
 }
 
+// E(t) of one field slot: static, A cos(wt) (Eq. 14), Gaussian pulse
+// (Eq. 32), and the ramped continuous waves of Section 2.2.4 with ramp
+// duration t_r = width: linear (t / t_r) cos(wt) for t < t_r, and quadratic
+// 2 t^2 / t_r^2 cos(wt) for t < t_r / 2, [1 - 2 (t - t_r)^2 / t_r^2] cos(wt)
+// for t_r / 2 <= t < t_r; both A cos(wt) from t_r on and zero before t = 0.
 __device__ double field_strength(const FieldDev& f, double t) {
   switch (f.kind) {
     case 1: return f.amp;
     case 2: return f.amp * cos(f.omega * t);
     case 3: return f.amp * exp(-(t - f.center) * (t - f.center) / (2.0 * f.width * f.width));
+    case 4:
+    case 5: {
+      if (t < 0.0) return 0.0;
+      const double tr = f.width;
+      double ramp = 1.0;
+      if (t < tr) {
+        if (f.kind == 4) {
+          ramp = t / tr;
+        } else if (t < 0.5 * tr) {
+          ramp = 2.0 * t * t / (tr * tr);
+        } else {
+          ramp = 1.0 - 2.0 * (t - tr) * (t - tr) / (tr * tr);
+        }
+      }
+      return f.amp * ramp * cos(f.omega * t);
+    }
     default: return 0.0;
   }
 }

@@ -10,7 +10,7 @@ namespace rtcc3 {
 
 // Field profile (Eq. 14 cosine, Eq. 32 Gaussian, static), one per batch slot.
 struct FieldDev {
-  int kind;  // 0 none, 1 static, 2 cos, 3 gauss
+  int kind;  // 0 none, 1 static, 2 cos, 3 gauss, 4 linear-ramped cos, 5 quadratic-ramped cos
   double amp, omega, center, width;
   double dir[3];
 };

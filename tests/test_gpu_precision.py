@@ -1,0 +1,69 @@
+"""Reduced-precision propagation at the (H2O)2 size (nocc 10, nvir 38).
+
+From the FP64 GPU CC3 ground state, the cos field of the benchmark workload
+(omega = 0.0656 au, A = 0.001 au, z) is propagated for 20 RK4 steps of
+h = 0.01 au in FP64 (complex128), split TF32 and BF16 (triples on tcgen05,
+FP64 RK4, dipole and energy).  The dipole and energy of the reduced forms
+are compared with the FP64 form over all steps, and all three with the
+oracle over the first step.
+"""
+import numpy as np
+import pytest
+
+from oracle import cc3
+from paper_2407_18947_gb300.synth import water_system
+
+pytestmark = pytest.mark.gpu
+
+STEPS, H = 20, 0.01
+FIELD = dict(kind=2, amplitude=0.001, omega=0.0656, direction=(0.0, 0.0, 1.0))
+
+
+@pytest.fixture(scope="module")
+def runs():
+    from paper_2407_18947_gb300.api import RTCC3
+    s = water_system(2)
+    eng = RTCC3(s.nocc, s.nvir, precision=0)
+    eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+    eng.solve_ground_state(tol=1e-9)
+    amps = eng.get_amplitudes(0)
+    eng.close()
+    out = {}
+    for prec in (0, 2, 3):
+        eng = RTCC3(s.nocc, s.nvir, precision=prec)
+        eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+        eng.set_field(0, FIELD["kind"], FIELD["amplitude"], omega=FIELD["omega"],
+                      direction=FIELD["direction"])
+        eng.set_amplitudes(0, *amps)
+        dip, en = eng.propagate_rk4(H, STEPS)
+        out[prec] = (np.asarray(dip)[0], np.asarray(en)[0])
+        eng.close()
+    return s, amps, out
+
+
+@pytest.mark.parametrize("precision,tol_dip,tol_en", [(2, 2e-7, 2e-7), (3, 2e-4, 2e-4)])
+def test_reduced_precision_trajectory_against_fp64(runs, precision, tol_dip, tol_en):
+    _, _, out = runs
+    d64, e64 = out[0]
+    d, e = out[precision]
+    ed = np.abs(d.real - d64.real).max()
+    ee = np.abs(e.real - e64.real).max()
+    # induced part of the dipole (what the properties are made of)
+    ind = np.abs(d64.real - d64.real[0]).max()
+    print(f"precision {precision}: dipole max abs err {ed:.3e} (induced dipole {ind:.3e}), "
+          f"energy max abs err {ee:.3e}")
+    assert ed < tol_dip and ee < tol_en
+
+
+def test_first_step_against_oracle(runs):
+    s, amps, out = runs
+    ham = cc3.Hamiltonian.from_system(s)
+    field = cc3.FieldSpec(kind=cc3.FIELD_COS, amplitude=FIELD["amplitude"], omega=FIELD["omega"],
+                          direction=FIELD["direction"])
+    _, dips, ens = cc3.propagate_rk4(ham, field, amps, H, 1)
+    d64, e64 = out[0]
+    assert np.abs(d64[:2] - dips).max() < 1e-10 * np.abs(dips).max()
+    assert np.abs(e64[:2] - ens).max() < 1e-10 * max(1.0, np.abs(ens).max())
+    for prec, tol in ((2, 2e-7), (3, 2e-4)):
+        d, _ = out[prec]
+        assert np.abs(d[:2].real - dips.real).max() < tol

