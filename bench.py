@@ -269,6 +269,46 @@ def workload_config(wl, precision, nbatch):
             "l2": "working set larger than L2 (o^3 v^3 triples tensors)"}
 
 
+def storage_note(o, v, prec, tune):
+    """How the triples were held in this run (the library's automatic rule
+    unless the autotuner chose)."""
+    if tune:
+        return dict(tune, rule="autotuned")
+    elem = 16 if prec == 0 else 8
+    t3 = o ** 3 * v ** 3 * elem
+    return {"rule": "automatic", "o3v3_tensor_GB": round(t3 / 1e9, 2)}
+
+
+def secondary_line(s, wl, precision, dev, stream, steps=3, warmup=1):
+    """RK4 steps/s of the same workload in another precision (a short
+    device-timed run from that precision's own ground state), for the
+    mixed-precision versus FP64 comparison; not the headline."""
+    import torch
+
+    from paper_2407_18947_gb300.api import RTCC3
+    prec = PRECISIONS[precision]
+    eng = RTCC3(s.nocc, s.nvir, precision=prec)
+    eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+    eng.set_field(0, wl["kind"], wl["amp"], omega=wl["omega"], direction=(0.0, 0.0, 1.0))
+    t0 = time.perf_counter()
+    eng.solve_ground_state(tol=1e-9 if prec == 0 else 1e-5, maxiter=400)
+    t_gs = time.perf_counter() - t0
+    n = max(steps, warmup) + 1
+    dip = torch.zeros((1, n, 3, 2), dtype=torch.float64, device=dev)
+    en = torch.zeros((1, n, 2), dtype=torch.float64, device=dev)
+    eng.propagate_rk4_dev(wl["h"], warmup, dip.data_ptr(), en.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    eng.propagate_rk4_dev(wl["h"], steps, dip.data_ptr(), en.data_ptr(), stream.cuda_stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    eng.close()
+    return {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "warmup": warmup, "dtype": DTYPES[precision], "ground_state_s": round(t_gs, 2)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,6 +324,15 @@ def main():
                          "value then counts field-steps/s")
     ap.add_argument("--size", default=None,
                     help="nocc,nvir of a reduced same-recipe system (profiling captures only)")
+    ap.add_argument("--init", default=None, choices=["cc3", "ccsd"],
+                    help="initial state: the CC3 ground state (default up to (H2O)2 size) or the "
+                         "CCSD ground state (default from (H2O)3 size on, where the CC3 iteration "
+                         "costs minutes)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time every triples storage form (whole / slabs of k occupied indices) "
+                         "before the warm-up and keep the fastest (stated in config)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 and BF16 lines of the default workload")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.size:
@@ -340,9 +389,14 @@ def main():
             e.set_amplitudes(b, *y)
 
     t0 = time.perf_counter()
+    init = args.init or ("cc3" if wl["n"] <= 2 else "ccsd")
     init_state = "CC3 ground state"
     try:
-        eng.solve_ground_state(tol=1e-10 if prec == 0 else 1e-5, maxiter=400)
+        if init == "ccsd":
+            init_state = "CCSD ground state (chosen: the CC3 iteration costs minutes at this size)"
+            ccsd_start(eng)
+        else:
+            eng.solve_ground_state(tol=1e-10 if prec == 0 else 1e-5, maxiter=400)
     except RTCC3Error as err:
         if err.code not in (ERR_NOT_CONVERGED, ERR_NONFINITE):
             raise
@@ -361,6 +415,11 @@ def main():
     en = torch.zeros((F, max(K, W) + 1, 2), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     y0 = eng.get_amplitudes(0)  # the initial state (re-uploaded by the e2e loop)
+    tune = None
+    if args.autotune:
+        choice, tms, table = eng.autotune_triples(0)
+        tune = {"choice": "whole o^3 v^3 tensors" if choice < 0 else f"slabs of {choice} occupied indices",
+                "stage_ms": {("whole" if k < 0 else str(k)): round(v_, 2) for k, v_ in table.items()}}
     # warm-up (captures the step graph)
     try:
         eng.propagate_rk4_dev(h, W, dip.data_ptr(), en.data_ptr(), stream.cuda_stream)
@@ -430,22 +489,33 @@ def main():
     flops = nominal_flops(o, v)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and o * o * o * v * v * v * 16 > 8e9:
+        cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+               "sample": f"not run: one o^3 v^3 complex128 tensor of the full-tensor oracle takes "
+                         f"{o ** 3 * v ** 3 * 16 / 1e9:.0f} GB of host memory at nocc={o} nvir={v}"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, cores = oracle_stage_seconds(wl)
         cpu = {"value": 1.0 / (4.0 * secs), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"one residual evaluation (1 of 4 RK4 stages) of the same workload on the host, "
                          f"{secs:.1f} s, extrapolated x4 per RK4 step"}
+    extras = None
+    if (rank == 0 and world == 1 and not args.no_extras and args.workload == 2 and "size" not in wl
+            and args.precision == "tf32" and F == 1):
+        extras = {p_: secondary_line(s, wl, p_, dev, stream) for p_ in ("fp64", "bf16")}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": DTYPES[args.precision], "data": "synthetic",
-                "config": dict(workload_config(wl, args.precision, F), initial_state=init_state),
+                "config": dict(workload_config(wl, args.precision, F), initial_state=init_state,
+                               triples_storage=storage_note(o, v, prec, tune)),
                 "triples_tflops_nominal": round(flops * world * K * F / (ms_max / 1e3) / 1e12, 3),
                 "nominal_flops_per_step": flops,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "ground_state_s": round(t_gs, 2),
                 "kernels": {k: {"launches": v_["launches"], "ms": round(v_["ms"], 4)}
                             for k, v_ in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])}}
+        if extras is not None:
+            line["other_precisions"] = extras
         print(json.dumps(line), flush=True)
     eng.close()
     if dist:

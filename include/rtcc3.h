@@ -55,6 +55,9 @@ extern "C" {
 #define RTCC3_PREC_TF32 2 /* complex64 graph, triples contractions on tcgen05 TF32 */
 #define RTCC3_PREC_BF16 3 /* complex64 graph, triples contractions on tcgen05 BF16 */
 
+#define RTCC3_STORAGE_C128 0
+#define RTCC3_STORAGE_C64 1
+
 #define RTCC3_FIELD_NONE 0
 #define RTCC3_FIELD_STATIC 1 /* E(t) = A                                   */
 #define RTCC3_FIELD_COS 2    /* E(t) = A cos(omega t)                (Eq. 14) */
@@ -92,6 +95,9 @@ typedef struct rtcc3_options {
   int eig_sweep_cap; /* QR sweeps the field eigensolver may take per matrix
                         before the call returns RTCC3_ERR_TIMEOUT; 0 =
                         default (60 n + 100)                                   */
+  int storage;       /* propagated state: RTCC3_STORAGE_C128 (default) or
+                        RTCC3_STORAGE_C64 (rounded to complex64 after every
+                        RK4 step; the step itself is FP64)                    */
 } rtcc3_options;
 
 /* Fill *opt with defaults (FP64, triples on, device 0, graphs on, automatic
@@ -180,6 +186,22 @@ int rtcc3_triples_vjp_dev(rtcc3_ctx* ctx, int b, double time, const void* t1, co
  * `stream` (NULL: the context stream) and the call returns after it is done. */
 int rtcc3_triples_forward_noalloc_dev(rtcc3_ctx* ctx, int b, double time, const void* t1,
                                       const void* t2, void* x1, void* x2, void* stream);
+
+/* Autotuner of the (i,j,k) slab size of the triples (Section 2.1 evaluates
+ * the triples per (i,j,k) block; the slab groups the blocks of `k` first
+ * occupied indices).  For slot b at its current state and time, times one
+ * full stage (forward and reverse pass, CUDA events on the context stream,
+ * after one untimed evaluation that builds the contraction plans) for every
+ * storage form that fits in the device memory free at set-up: the whole
+ * o^3 v^3 tensors (reported as -1) when about 24 of them fit in 70 % of it,
+ * and slabs of o, o/2, o/4, ..., 1 occupied indices whose three slab buffers
+ * fit in a quarter of it.  The fastest becomes the context's triples_chunk
+ * option.  Outputs (any may be NULL): *chunk the choice, *ms its time,
+ * candidates[] / candidate_ms[] the first max_candidates forms tried and
+ * their times, *count how many were tried.  The slot's state is not
+ * changed.  RTCC3_ERR_STATE without triples or with field_solver = 1. */
+int rtcc3_autotune_triples(rtcc3_ctx* ctx, int b, int* chunk, float* ms, int max_candidates,
+                           int* candidates, float* candidate_ms, int* count);
 
 /* Change the wait budgets of an existing context (the rtcc3_options fields
  * spin_budget and eig_sweep_cap; 0 restores a default); later calls use them.

@@ -27,7 +27,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("triples", ctypes.c_int), ("device", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("field_tol", ctypes.c_double),
                 ("field_solver", ctypes.c_int), ("triples_chunk", ctypes.c_int),
-                ("spin_budget", ctypes.c_longlong), ("eig_sweep_cap", ctypes.c_int)]
+                ("spin_budget", ctypes.c_longlong), ("eig_sweep_cap", ctypes.c_int),
+                ("storage", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -64,6 +65,9 @@ SIGNATURES = {
     "rtcc3_set_state": (_I, [_P, _P, ctypes.c_longlong]),
     "rtcc3_stats": (_I, [_P, _LLP, _LLP]),
     "rtcc3_set_wait_budgets": (_I, [_P, ctypes.c_longlong, _I]),
+    "rtcc3_autotune_triples": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float), _I,
+                                    ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(_I)]),
     "rtcc3_set_profiling": (_I, [_P, _I]),
     "rtcc3_kernel_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
 }

@@ -31,7 +31,7 @@ class RTCC3:
     def __init__(self, nocc: int, nvir: int, nbatch: int = 1, precision: int = PREC_FP64,
                  triples: bool = True, device: int = 0, use_graphs: bool = True,
                  field_tol: float = 0.0, field_solver: int = 0, triples_chunk: int = 0,
-                 spin_budget: int = 0, eig_sweep_cap: int = 0):
+                 spin_budget: int = 0, eig_sweep_cap: int = 0, storage_c64: bool = False):
         self.lib = _lib.load()
         self.nocc, self.nvir, self.nbatch = nocc, nvir, nbatch
         opt = _lib.Options()
@@ -45,6 +45,7 @@ class RTCC3:
         opt.triples_chunk = triples_chunk
         opt.spin_budget = spin_budget
         opt.eig_sweep_cap = eig_sweep_cap
+        opt.storage = 1 if storage_c64 else 0
         h = ctypes.c_void_p()
         rc = self.lib.rtcc3_create(nocc, nvir, nbatch, ctypes.byref(opt), ctypes.byref(h))
         if rc != 0:
@@ -172,6 +173,19 @@ class RTCC3:
         a, b = ctypes.c_longlong(), ctypes.c_longlong()
         self._check(self.lib.rtcc3_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return {"launches": a.value, "device_bytes": b.value}
+
+    def autotune_triples(self, b: int = 0):
+        """Time every storage form of the triples for slot b and keep the
+        fastest; returns (choice, ms, {form: ms}) with -1 = whole tensors,
+        k > 0 = slabs of k occupied indices."""
+        n = 32
+        ch, ms, cnt = ctypes.c_int(), ctypes.c_float(), ctypes.c_int()
+        cands = (ctypes.c_int * n)()
+        cms = (ctypes.c_float * n)()
+        self._check(self.lib.rtcc3_autotune_triples(self.h, b, ctypes.byref(ch), ctypes.byref(ms), n,
+                                                    cands, cms, ctypes.byref(cnt)))
+        k = min(cnt.value, n)
+        return ch.value, ms.value, {int(cands[i]): float(cms[i]) for i in range(k)}
 
     def set_wait_budgets(self, spin_budget: int = 0, eig_sweep_cap: int = 0):
         """Wait budgets of the device kernels (0 restores a default)."""

@@ -475,7 +475,8 @@ void rk4_step(rtcc3_ctx* ctx, double h, const std::vector<int>& sweeps) {
       E.add_launches(1);
     }
     PScope ps(ctx->prof, ctx->stream, "rk4_update", 0.0, 2.0 * ybytes);
-    launch_step_finish(yb, ctx->acc, ctx->ny, ctx->stepdev, ctx->baddev, ctx->stream);
+    launch_step_finish(yb, ctx->acc, ctx->ny, ctx->stepdev, ctx->baddev,
+                       ctx->opt.storage == RTCC3_STORAGE_C64, ctx->stream);
     E.add_launches(1);
   }
   launch_step_advance(ctx->tdev, h, ctx->stepdev, ctx->stream);
@@ -913,6 +914,79 @@ void triples_noalloc_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1,
   }
 }
 
+// Candidate storage forms of the triples for this context, in the order
+// they are timed: whole tensors when 24 of them fit in 70% of the free
+// memory (-1), then slabs of o, o/2, o/4, ..., 1 first occupied indices
+// whose three slab buffers fit in a quarter of it.
+std::vector<int> chunk_candidates(const rtcc3_ctx* ctx) {
+  std::vector<int> c;
+  const int o = ctx->o, v = ctx->v;
+  const double elem = ctx->fp64() ? 16.0 : 8.0;
+  const double freeb = double(ctx->free_at_setup);
+  if (24.0 * double(o) * o * o * v * v * v * elem <= 0.7 * freeb) c.push_back(-1);
+  for (int k = o; k >= 1; k = (k + 1) / 2) {
+    if (3.0 * double(k) * o * o * v * v * v * elem <= 0.25 * freeb &&
+        std::find(c.begin(), c.end(), k) == c.end())
+      c.push_back(k);
+    if (k == 1) break;
+  }
+  return c;
+}
+
+// Times one full stage (forward and reverse pass) of slot b for every
+// candidate triples storage form and keeps the fastest in the options.
+template <typename R>
+void autotune_impl(rtcc3_ctx* ctx, int b, int* best_chunk, float* best_ms, int max_out,
+                   int* cand_out, float* ms_out, int* count) {
+  Engine<R>& E = ctx->run<R>().E;
+  const std::vector<int> cands = chunk_candidates(ctx);
+  RTCC3_CHECK(!cands.empty(), RTCC3_ERR_OOM, "no triples storage form fits in device memory");
+  const int saved = ctx->opt.triples_chunk;
+  cudaEvent_t e0, e1;
+  RTCC3_CUDA(cudaEventCreate(&e0));
+  RTCC3_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float bms = 0.f;
+  int k = 0;
+  try {
+    for (int c : cands) {
+      ctx->opt.triples_chunk = c;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // the first evaluation builds the plans
+        RTCC3_CUDA(cudaEventRecord(e0, ctx->stream));
+        eval_stage<R>(ctx, b, ctx->y + size_t(b) * ctx->ny, nullptr, 0.0, ctx->tdev, 0.0, true,
+                      ctx->fdev + b, true, field_sweeps(ctx, b));
+        RTCC3_CUDA(cudaEventRecord(e1, ctx->stream));
+        RTCC3_CUDA(cudaEventSynchronize(e1));
+        RTCC3_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      check_device_timeout<R>(ctx);
+      if (k < max_out) {
+        if (cand_out) cand_out[k] = c;
+        if (ms_out) ms_out[k] = ms;
+      }
+      ++k;
+      if (best == 0 || ms < bms) {
+        best = c;
+        bms = ms;
+      }
+    }
+  } catch (...) {
+    ctx->opt.triples_chunk = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->opt.triples_chunk = best;
+  drop_graph(ctx);
+  if (best_chunk) *best_chunk = best;
+  if (best_ms) *best_ms = bms;
+  if (count) *count = k;
+  E.reset_launch_count();
+}
+
 uint64_t fnv1a(const unsigned char* p, size_t n) {
   uint64_t h = 1469598103934665603ULL;
   for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ULL; }
@@ -942,6 +1016,7 @@ void rtcc3_default_options(rtcc3_options* opt) {
   opt->triples_chunk = 0;
   opt->spin_budget = 0;
   opt->eig_sweep_cap = 0;
+  opt->storage = RTCC3_STORAGE_C128;
 }
 
 int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3_ctx** out) {
@@ -951,6 +1026,8 @@ int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3
   auto ctx = std::make_unique<rtcc3_ctx>();
   if (opt) ctx->opt = *opt; else rtcc3_default_options(&ctx->opt);
   if (ctx->opt.precision < RTCC3_PREC_FP64 || ctx->opt.precision > RTCC3_PREC_BF16)
+    return RTCC3_ERR_ARG;
+  if (ctx->opt.storage != RTCC3_STORAGE_C128 && ctx->opt.storage != RTCC3_STORAGE_C64)
     return RTCC3_ERR_ARG;
   ctx->o = nocc; ctx->v = nvir; ctx->n = nocc + nvir; ctx->nb = nbatch;
   ctx->n1 = size_t(nocc) * nvir;
@@ -1289,6 +1366,22 @@ int rtcc3_set_state(rtcc3_ctx* ctx, const void* buf, long long bytes) {
     ctx->time = hd.time;
     ctx->step_total = hd.step;
     RTCC3_CUDA(cudaMemcpy(ctx->tdev, &ctx->time, sizeof(double), cudaMemcpyHostToDevice));
+  });
+}
+
+int rtcc3_autotune_triples(rtcc3_ctx* ctx, int b, int* chunk, float* ms, int max_candidates,
+                           int* candidates, float* candidate_ms, int* count) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    require_ham(ctx);
+    check_slot(ctx, b);
+    RTCC3_CHECK(ctx->opt.triples && ctx->opt.field_solver == 0, RTCC3_ERR_STATE,
+                "autotuning needs the triples with the field-dressed eigenbasis solver");
+    RTCC3_CHECK(max_candidates >= 0, RTCC3_ERR_ARG, "max_candidates < 0");
+    if (ctx->fp64())
+      autotune_impl<double>(ctx, b, chunk, ms, max_candidates, candidates, candidate_ms, count);
+    else
+      autotune_impl<float>(ctx, b, chunk, ms, max_candidates, candidates, candidate_ms, count);
   });
 }
 

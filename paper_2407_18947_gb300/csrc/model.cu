@@ -260,13 +260,16 @@ __global__ void k_lincomb(const double2* __restrict__ X, const double2* __restri
   }
 }
 
+// y = acc (the RK4 result); with complex64 storage the state is rounded to
+// complex64 after every step (FP64 arithmetic inside the step).
 __global__ void k_step_finish(double2* __restrict__ y, const double2* __restrict__ acc, size_t ny,
-                              const int* step, int* bad_step) {
+                              const int* step, int* bad_step, int c64) {
   bool bad = false;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < ny;
        t += (size_t)gridDim.x * blockDim.x) {
-    const double2 a = acc[t];
+    double2 a = acc[t];
     if (!isfinite(a.x) || !isfinite(a.y)) bad = true;
+    if (c64) a = make_double2(double(float(a.x)), double(float(a.y)));
     y[t] = a;
   }
   if (bad) atomicCAS(bad_step, -1, *step);
@@ -385,8 +388,8 @@ void launch_lincomb(const double2* X, const double2* c, int m, size_t len, doubl
 }
 
 void launch_step_finish(double2* y, const double2* acc, size_t ny, const int* step, int* bad_step,
-                        cudaStream_t s) {
-  k_step_finish<<<grid_n(ny), 256, 0, s>>>(y, acc, ny, step, bad_step);
+                        bool c64, cudaStream_t s) {
+  k_step_finish<<<grid_n(ny), 256, 0, s>>>(y, acc, ny, step, bad_step, c64 ? 1 : 0);
   RTCC3_CUDA(cudaGetLastError());
 }
 

@@ -127,6 +127,7 @@ void launch_dots(const double2* E, const double2* e, int m, size_t len, double2*
 void launch_lincomb(const double2* X, const double2* c, int m, size_t len, double2* x, cudaStream_t s);
 // y = acc and flag non-finite entries (first bad step index kept in *bad_step).
 void launch_step_finish(double2* y, const double2* acc, size_t ny, const int* step, int* bad_step,
+                        bool c64,
                         cudaStream_t s);
 // *t += h; ++*step.
 void launch_step_advance(double* tdev, double h, int* step, cudaStream_t s);

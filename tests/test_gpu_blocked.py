@@ -112,3 +112,22 @@ def test_blocked_ground_state_and_propagation_match_stored():
     assert _rel(res[3][2], res[-1][2]) < 1e-10
     for a, b in zip(res[3][3], res[-1][3]):
         assert _rel(a, b) < 1e-10
+
+
+def test_autotuner_times_every_form_and_keeps_a_correct_one():
+    """The slab-size autotuner times the stored form and slabs of 5, 3, 2, 1
+    occupied indices on a water monomer (TF32), keeps the fastest, and the
+    residuals with its choice equal those of the stored form."""
+    s = water_system(1)
+    amps = random_amplitudes(s.nocc, s.nvir, seed=14)
+    eng = _engine(s, precision=2)
+    eng.set_field(0, 1, 0.002, direction=(0.0, 0.0, 1.0))
+    eng.set_amplitudes(0, *amps)
+    ref = eng.compute_residuals(0, 0.0)
+    choice, ms, table = eng.autotune_triples(0)
+    assert set(table) == {-1, 5, 3, 2, 1}
+    assert choice in table and ms == min(table.values()) and ms > 0
+    got = eng.compute_residuals(0, 0.0)
+    eng.close()
+    for k in ("r_t1", "r_t2", "r_l1", "r_l2"):
+        assert np.abs(got[k] - ref[k]).max() < 1e-6, k
