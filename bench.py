@@ -331,6 +331,8 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="time every triples storage form (whole / slabs of k occupied indices) "
                          "before the warm-up and keep the fastest (stated in config)")
+    ap.add_argument("--storage", default="c128", choices=["c128", "c64"],
+                    help="propagated state kept in complex128 or rounded to complex64 every step")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 and BF16 lines of the default workload")
     args = ap.parse_args()
@@ -361,7 +363,8 @@ def main():
     o, v = s.nocc, s.nvir
     prec = PRECISIONS[args.precision]
     F = max(1, args.fields)
-    eng = RTCC3(o, v, nbatch=F, precision=prec, device=local)
+    c64 = args.storage == "c64"
+    eng = RTCC3(o, v, nbatch=F, precision=prec, device=local, storage_c64=c64)
     eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
     # each rank propagates its own field strength (independent problems)
     amp = rank_field_amplitude(wl["amp"], rank)
@@ -371,7 +374,7 @@ def main():
         eng.set_field(b, wl["kind"], amp * (scale if F > 1 else 1.0), omega=wl["omega"],
                       direction=(0.0, 0.0, 1.0))
     def fresh_engine():
-        e = RTCC3(o, v, nbatch=F, precision=prec, device=local)
+        e = RTCC3(o, v, nbatch=F, precision=prec, device=local, storage_c64=c64)
         e.set_hamiltonian(s.eps, s.Lfac, s.dipole)
         for b in range(F):
             scale = 0.0 if b == 0 else (1 << ((b - 1) // 2)) * (1.0 if b % 2 else -1.0)
@@ -507,7 +510,8 @@ def main():
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": DTYPES[args.precision], "data": "synthetic",
                 "config": dict(workload_config(wl, args.precision, F), initial_state=init_state,
-                               triples_storage=storage_note(o, v, prec, tune)),
+                               triples_storage=storage_note(o, v, prec, tune),
+                               state_storage=args.storage),
                 "triples_tflops_nominal": round(flops * world * K * F / (ms_max / 1e3) / 1e12, 3),
                 "nominal_flops_per_step": flops,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

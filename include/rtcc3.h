@@ -203,6 +203,15 @@ int rtcc3_triples_forward_noalloc_dev(rtcc3_ctx* ctx, int b, double time, const 
 int rtcc3_autotune_triples(rtcc3_ctx* ctx, int b, int* chunk, float* ms, int max_candidates,
                            int* candidates, float* candidate_ms, int* count);
 
+/* Measured dense arithmetic rates of device `device` in TFLOP/s, the
+ * denominators of the roofline fractions the benchmark reports (no
+ * counterpart in the paper): tflops[0] TF32 and tflops[1] BF16 tcgen05 MMA
+ * issue rate (128 x 256 tiles from shared memory into tensor memory, one CTA
+ * per SM), tflops[2] FP32 and tflops[3] FP64 fused multiply-add on the CUDA
+ * cores.  Each probe runs once untimed and once timed with CUDA events
+ * (about 0.1 s in all).  No context needed. */
+int rtcc3_measure_peaks(int device, double* tflops);
+
 /* Change the wait budgets of an existing context (the rtcc3_options fields
  * spin_budget and eig_sweep_cap; 0 restores a default); later calls use them.
  * A wait that runs out of its budget does not hang or poison the context: the

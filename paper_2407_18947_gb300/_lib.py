@@ -65,6 +65,7 @@ SIGNATURES = {
     "rtcc3_set_state": (_I, [_P, _P, ctypes.c_longlong]),
     "rtcc3_stats": (_I, [_P, _LLP, _LLP]),
     "rtcc3_set_wait_budgets": (_I, [_P, ctypes.c_longlong, _I]),
+    "rtcc3_measure_peaks": (_I, [_I, _DP]),
     "rtcc3_autotune_triples": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float), _I,
                                     ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float),
                                     ctypes.POINTER(_I)]),

@@ -203,3 +203,14 @@ class RTCC3:
         return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms,
                                         "flops": arr[i].flops, "bytes": arr[i].bytes}
                 for i in range(cnt.value)}
+
+
+def measure_peaks(device: int = 0) -> dict:
+    """Measured dense rates (TFLOP/s) of the device's pipes: TF32 and BF16
+    tcgen05 MMA, FP32 and FP64 FMA (``rtcc3_measure_peaks``)."""
+    lib = _lib.load()
+    out = (ctypes.c_double * 4)()
+    rc = lib.rtcc3_measure_peaks(device, out)
+    if rc != 0:
+        raise RTCC3Error(rc, "rtcc3_measure_peaks failed")
+    return {"tf32_mma": out[0], "bf16_mma": out[1], "fp32_fma": out[2], "fp64_fma": out[3]}

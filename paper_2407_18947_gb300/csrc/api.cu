@@ -16,6 +16,7 @@
 #include "engine.h"
 #include "model.h"
 #include "stage_graph.h"
+#include "tc_gemm.h"
 
 using namespace rtcc3;
 
@@ -1382,6 +1383,31 @@ int rtcc3_autotune_triples(rtcc3_ctx* ctx, int b, int* chunk, float* ms, int max
       autotune_impl<double>(ctx, b, chunk, ms, max_candidates, candidates, candidate_ms, count);
     else
       autotune_impl<float>(ctx, b, chunk, ms, max_candidates, candidates, candidate_ms, count);
+  });
+}
+
+int rtcc3_measure_peaks(int device, double* tflops) {
+  if (!tflops) return RTCC3_ERR_ARG;
+  return guarded(nullptr, [&] {
+    RTCC3_CUDA(cudaSetDevice(device));
+    cudaStream_t s = nullptr;
+    int* flag = nullptr;
+    RTCC3_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    RTCC3_CUDA(cudaMalloc(&flag, sizeof(int)));
+    RTCC3_CUDA(cudaMemset(flag, 0, sizeof(int)));
+    try {
+      for (int w = 0; w < 4; ++w) tflops[w] = measure_pipe_tflops(w, flag, s);
+      int f = 0;
+      RTCC3_CUDA(cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost));
+      RTCC3_CHECK(f == 0, RTCC3_ERR_TIMEOUT, "a rate probe gave up waiting on its MMAs");
+    } catch (...) {
+      cudaStreamSynchronize(s);
+      cudaFree(flag);
+      cudaStreamDestroy(s);
+      throw;
+    }
+    cudaFree(flag);
+    cudaStreamDestroy(s);
   });
 }
 

@@ -1178,7 +1178,116 @@ bool launch_chains(const void* Atiled, const CUtensorMap& mb, const TcOperands& 
   return true;
 }
 
+// ---- pipe-rate probes (roofline denominators) -------------------------------
+// Tensor pipe: one CTA per SM issues `iters` K tiles of a 128 x 256 MMA (four
+// 32-byte K steps per tile: K = 32 TF32 or 64 BF16 elements) from zeroed
+// shared-memory tiles into one TMEM accumulator: no global traffic, the
+// issue rate of dense tcgen05 MMAs.  The kernel waits (drain budget) for its
+// MMAs before freeing tensor memory.
+template <bool BF16>
+__global__ void __launch_bounds__(128, 1) k_mma_rate(int iters, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int kA = 128 * 128, kB = 256 * 128;
+  uint64_t* fin = reinterpret_cast<uint64_t*>(smem + kA + kB);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  for (int t = threadIdx.x; t < (kA + kB) / 16; t += blockDim.x)
+    reinterpret_cast<uint4*>(smem)[t] = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(fin), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)), "r"(256) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = instr_desc<BF16>(128, 256);
+    const uint32_t sa = smem_u32(smem), sb = sa + kA;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma<BF16>(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (i | kk) ? 1u : 0u);
+    }
+    mma_commit(smem_u32(fin));
+    if (!mbar_wait(smem_u32(fin), 0, kDrainBudget) && err) atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
+                 : "memory");
+  }
+}
+
+// CUDA-core FMA pipes: eight independent multiply-add chains per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_rate(T* __restrict__ sink, int iters) {
+  T a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = T(threadIdx.x + j) * T(1e-3);
+  const T b = T(0.999999), c = T(1e-7);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+  }
+  T sum = T(0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) sum += a[j];
+  if (sum == T(-1)) sink[0] = sum;  // never true; keeps the chains alive
+}
+
 }  // namespace
+
+// Measured dense rate (TFLOP/s) of one pipe on the current device: 0 TF32
+// tcgen05 MMA, 1 BF16 tcgen05 MMA, 2 FP32 FMA, 3 FP64 FMA.  One untimed
+// launch, then one launch timed with CUDA events.
+double measure_pipe_tflops(int which, int* err_flag, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  RTCC3_CUDA(cudaGetDevice(&dev));
+  RTCC3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaEvent_t e0, e1;
+  RTCC3_CUDA(cudaEventCreate(&e0));
+  RTCC3_CUDA(cudaEventCreate(&e1));
+  double flops = 0.0;
+  float ms = 0.f;
+  for (int rep = 0; rep < 2; ++rep) {
+    RTCC3_CUDA(cudaEventRecord(e0, s));
+    if (which <= 1) {
+      const int iters = 4096;
+      const int smem = 128 * 128 + 256 * 128 + 64 + 1024;
+      if (which == 0) {
+        RTCC3_CUDA(cudaFuncSetAttribute(k_mma_rate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_mma_rate<false><<<sms, 128, smem, s>>>(iters, err_flag);
+      } else {
+        RTCC3_CUDA(cudaFuncSetAttribute(k_mma_rate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_mma_rate<true><<<sms, 128, smem, s>>>(iters, err_flag);
+      }
+      const double k = which == 0 ? 32.0 : 64.0;  // K elements per tile
+      flops = 2.0 * 128.0 * 256.0 * k * iters * sms;
+    } else {
+      const int iters = which == 2 ? 8192 : 1024;
+      const int blocks = sms * 8;
+      if (which == 2) k_fma_rate<float><<<blocks, 256, 0, s>>>(nullptr, iters);
+      else k_fma_rate<double><<<blocks, 256, 0, s>>>(nullptr, iters);
+      flops = 2.0 * 8.0 * iters * 256.0 * blocks;
+    }
+    RTCC3_CUDA(cudaGetLastError());
+    RTCC3_CUDA(cudaEventRecord(e1, s));
+    RTCC3_CUDA(cudaEventSynchronize(e1));
+    RTCC3_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return flops / (double(ms) * 1e-3) / 1e12;
+}
 
 void tc_pack_a(const float2* A, const long long* aM, const long long* aK, long long aoff, int M,
                int K, int Kp, int elem_bytes, bool kfast, bool tiled, void* out, cudaStream_t s) {

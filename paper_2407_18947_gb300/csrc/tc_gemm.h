@@ -102,6 +102,11 @@ void tc_split_finish(const float* partial, int nsplit, int M, int N, float2* C, 
                      cudaStream_t s);
 
 // Packed K for a complex K at the given element size (K tile = 128 bytes).
+// Measured dense rate (TFLOP/s) of one pipe on the current device: 0 TF32
+// tcgen05 MMA, 1 BF16 tcgen05 MMA, 2 FP32 FMA, 3 FP64 FMA (probe kernels, no
+// global memory traffic).
+double measure_pipe_tflops(int which, int* err_flag, cudaStream_t s);
+
 inline int tc_packed_k(int K, int elem_bytes) {
   const int tile = 128 / elem_bytes;
   return ((2 * K + tile - 1) / tile) * tile;

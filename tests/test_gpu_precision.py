@@ -5,7 +5,7 @@ From the FP64 GPU CC3 ground state, the cos field of the benchmark workload
 h = 0.01 au in FP64 (complex128), split TF32 and BF16 (triples on tcgen05,
 FP64 RK4, dipole and energy).  The dipole and energy of the reduced forms
 are compared with the FP64 form over all steps, and all three with the
-oracle over the first step.
+oracle at the start.
 """
 import numpy as np
 import pytest
@@ -59,15 +59,17 @@ def test_reduced_precision_trajectory_against_fp64(runs, precision, tol_dip, tol
     assert ed < tol_dip and ee < tol_en
 
 
-def test_first_step_against_oracle(runs):
+def test_initial_observables_against_oracle(runs):
+    """Dipole and energy of the ground state under the field at t = 0 (one
+    oracle evaluation at this size takes ~30 s on the host): FP64 to 1e-10,
+    the reduced forms within their stated bounds."""
     s, amps, out = runs
     ham = cc3.Hamiltonian.from_system(s)
-    field = cc3.FieldSpec(kind=cc3.FIELD_COS, amplitude=FIELD["amplitude"], omega=FIELD["omega"],
-                          direction=FIELD["direction"])
-    _, dips, ens = cc3.propagate_rk4(ham, field, amps, H, 1)
+    res = cc3.evaluate(ham, *amps, ham.field_operator([0.0, 0.0, FIELD["amplitude"]]))
     d64, e64 = out[0]
-    assert np.abs(d64[:2] - dips).max() < 1e-10 * np.abs(dips).max()
-    assert np.abs(e64[:2] - ens).max() < 1e-10 * max(1.0, np.abs(ens).max())
-    for prec, tol in ((2, 1e-6), (3, 2.5e-6)):
-        d, _ = out[prec]
-        assert np.abs(d[:2].real - dips.real).max() < tol
+    assert np.abs(d64[0] - res.dipole).max() < 1e-10 * np.abs(res.dipole).max()
+    assert abs(e64[0] - res.energy) < 1e-10 * max(1.0, abs(res.energy))
+    for prec, tol_d, tol_e in ((2, 1e-6, 4e-5), (3, 2.5e-6, 4e-5)):
+        d, e = out[prec]
+        assert np.abs(d[0].real - res.dipole.real).max() < tol_d
+        assert abs(e[0].real - res.energy.real) < tol_e
