@@ -95,9 +95,17 @@ typedef struct rtcc3_options {
   int eig_sweep_cap; /* QR sweeps the field eigensolver may take per matrix
                         before the call returns RTCC3_ERR_TIMEOUT; 0 =
                         default (60 n + 100)                                   */
+  int tc_all;        /* RTCC3_PREC_TF32 only: 1 = split-TF32 tensor cores also
+                        for the T1 dressing and CCSD contractions (default 0:
+                        only the triples; the others on FP32 CUDA cores)     */
   int storage;       /* propagated state: RTCC3_STORAGE_C128 (default) or
                         RTCC3_STORAGE_C64 (rounded to complex64 after every
                         RK4 step; the step itself is FP64)                    */
+  int checked;       /* 1: every device tensor of a stage gets a 256-byte
+                        canary, verified after the stage (RTCC3_ERR_STATE on
+                        an overrun); no CUDA graphs.  Independently of this,
+                        every operation's index ranges are checked on the
+                        host against its tensors before it is launched       */
 } rtcc3_options;
 
 /* Fill *opt with defaults (FP64, triples on, device 0, graphs on, automatic
@@ -202,6 +210,21 @@ int rtcc3_triples_forward_noalloc_dev(rtcc3_ctx* ctx, int b, double time, const 
  * changed.  RTCC3_ERR_STATE without triples or with field_solver = 1. */
 int rtcc3_autotune_triples(rtcc3_ctx* ctx, int b, int* chunk, float* ms, int max_candidates,
                            int* candidates, float* candidate_ms, int* count);
+
+/* Additional one-electron observables, recorded with the same density as
+ * the dipole (Section 2.2.3: the magnetic dipole moment is the density
+ * contracted with the magnetic dipole matrix elements; in a real orbital
+ * basis those are imaginary and antisymmetric): ops holds nops complex
+ * nmo x nmo matrices O_k (interleaved, row-major, [k][p][q]), and every
+ * compute or propagate call then also records sum_pq D_pq O_k,pq at each
+ * entry where it records the dipole.  nops = 0 (ops may be NULL) removes
+ * them; 0 <= nops <= 64.  The library copies ops. */
+int rtcc3_set_observables(rtcc3_ctx* ctx, int nops, const double* ops);
+/* Values recorded by the last compute (1 entry) or propagate call (nbatch x
+ * (nsteps + 1) entries, slot-major like the dipole): out[entry][k] complex.
+ * `entries` is the capacity of out in entries; RTCC3_ERR_ARG if it is smaller
+ * than what the last call recorded, RTCC3_ERR_STATE if nothing was recorded. */
+int rtcc3_get_observables(const rtcc3_ctx* ctx, double* out, long long entries);
 
 /* Measured dense arithmetic rates of device `device` in TFLOP/s, the
  * denominators of the roofline fractions the benchmark reports (no

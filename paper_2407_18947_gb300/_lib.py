@@ -28,7 +28,7 @@ class Options(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("field_tol", ctypes.c_double),
                 ("field_solver", ctypes.c_int), ("triples_chunk", ctypes.c_int),
                 ("spin_budget", ctypes.c_longlong), ("eig_sweep_cap", ctypes.c_int),
-                ("storage", ctypes.c_int)]
+                ("tc_all", ctypes.c_int), ("storage", ctypes.c_int), ("checked", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -66,6 +66,8 @@ SIGNATURES = {
     "rtcc3_stats": (_I, [_P, _LLP, _LLP]),
     "rtcc3_set_wait_budgets": (_I, [_P, ctypes.c_longlong, _I]),
     "rtcc3_measure_peaks": (_I, [_I, _DP]),
+    "rtcc3_set_observables": (_I, [_P, _I, _DP]),
+    "rtcc3_get_observables": (_I, [_P, _DP, ctypes.c_longlong]),
     "rtcc3_autotune_triples": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float), _I,
                                     ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float),
                                     ctypes.POINTER(_I)]),

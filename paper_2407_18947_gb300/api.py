@@ -31,7 +31,8 @@ class RTCC3:
     def __init__(self, nocc: int, nvir: int, nbatch: int = 1, precision: int = PREC_FP64,
                  triples: bool = True, device: int = 0, use_graphs: bool = True,
                  field_tol: float = 0.0, field_solver: int = 0, triples_chunk: int = 0,
-                 spin_budget: int = 0, eig_sweep_cap: int = 0, storage_c64: bool = False):
+                 spin_budget: int = 0, eig_sweep_cap: int = 0, storage_c64: bool = False,
+                 tc_all: bool = False, checked: bool = False):
         self.lib = _lib.load()
         self.nocc, self.nvir, self.nbatch = nocc, nvir, nbatch
         opt = _lib.Options()
@@ -46,11 +47,14 @@ class RTCC3:
         opt.spin_budget = spin_budget
         opt.eig_sweep_cap = eig_sweep_cap
         opt.storage = 1 if storage_c64 else 0
+        opt.tc_all = 1 if tc_all else 0
+        opt.checked = 1 if checked else 0
         h = ctypes.c_void_p()
         rc = self.lib.rtcc3_create(nocc, nvir, nbatch, ctypes.byref(opt), ctypes.byref(h))
         if rc != 0:
             raise RTCC3Error(rc, "rtcc3_create failed")
         self.h = h
+        self._nobs = 0
 
     # -- plumbing ---------------------------------------------------------
     def _check(self, rc):
@@ -173,6 +177,26 @@ class RTCC3:
         a, b = ctypes.c_longlong(), ctypes.c_longlong()
         self._check(self.lib.rtcc3_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return {"launches": a.value, "device_bytes": b.value}
+
+    def set_observables(self, ops):
+        """Additional one-electron operators (complex, (k, nmo, nmo)) whose
+        expectation values sum_pq D_pq O_pq are recorded beside the dipole."""
+        if ops is None or len(ops) == 0:
+            self._check(self.lib.rtcc3_set_observables(self.h, 0, None))
+            self._nobs = 0
+            return
+        a = np.ascontiguousarray(np.asarray(ops, dtype=np.complex128))
+        n = self.nocc + self.nvir
+        assert a.ndim == 3 and a.shape[1:] == (n, n)
+        self._check(self.lib.rtcc3_set_observables(self.h, a.shape[0], _dp(a.view(np.float64))))
+        self._nobs = a.shape[0]
+
+    def get_observables(self, entries: int):
+        """Values recorded by the last compute (entries = 1) or propagate call
+        (entries = nbatch * (nsteps + 1)): complex array (entries, nops)."""
+        out = np.zeros((entries, self._nobs), dtype=np.complex128)
+        self._check(self.lib.rtcc3_get_observables(self.h, _dp(out.view(np.float64)), entries))
+        return out
 
     def autotune_triples(self, b: int = 0):
         """Time every storage form of the triples for slot b and keep the

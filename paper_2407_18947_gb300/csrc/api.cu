@@ -106,12 +106,19 @@ struct rtcc3_ctx {
   double2* dip_traj = nullptr;
   double2* en_traj = nullptr;
   size_t traj_cap = 0;
+  // additional one-electron observables (rtcc3_set_observables)
+  int nobs = 0;
+  double2* obs_ops = nullptr;     // nobs x n x n
+  double2* obs_traj = nullptr;    // entries x nobs
+  size_t obs_cap = 0;             // entries
+  long long obs_last = 0;         // entries written by the last call
   size_t free_at_setup = 0;  // free device memory when the Hamiltonian was set
   double time = 0.0;
   long long step_total = 0;
   long long last_launches = 0;
   Profiler prof;
   TrajDesc* tdesc = nullptr;
+  int* checkflag = nullptr;  // raised by the canary check (checked mode)
   // cached CUDA graph of one RK4 step (all slots)
   cudaGraphExec_t gexec = nullptr;
   double gh = 0.0;
@@ -135,6 +142,8 @@ struct rtcc3_ctx {
     runner.reset();
     if (dip_traj) cudaFree(dip_traj);
     if (en_traj) cudaFree(en_traj);
+    if (obs_ops) cudaFree(obs_ops);
+    if (obs_traj) cudaFree(obs_traj);
     for (void* p : owned) cudaFree(p);
     if (stream) cudaStreamDestroy(stream);
   }
@@ -289,6 +298,7 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
   so.field_iters = sweeps;
   so.rotation = ctx->opt.field_solver == 0;
   so.triples_chunk = triples_chunk(ctx);
+  so.tc_all = ctx->opt.tc_all != 0;
   const bool basis_stage = so.triples && so.field_terms && so.rotation;
   if (basis_stage) so.basis = ahead.use;
   (void)ccsd_terms;
@@ -316,6 +326,16 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
     E.ensure_grad(S.t1);  // read outside the engine
     E.ensure_grad(S.t2);
     E.ensure_grad(S.w);
+  }
+  if (E.checked()) {
+    // checked mode: no tensor of the stage was written past its end
+    E.verify_canaries(ctx->checkflag);
+    int bad = 0;
+    RTCC3_CUDA(cudaMemcpy(&bad, ctx->checkflag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad) {
+      RTCC3_CUDA(cudaMemset(ctx->checkflag, 0, sizeof(int)));
+      throw Error(RTCC3_ERR_STATE, "checked mode: a device tensor was written past its end");
+    }
   }
   return S;
 }
@@ -416,10 +436,32 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
   RTCC3_CUDA(cudaMemcpy(H.ones, ones.data(), ones.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice));
   rn->E.set_profiler(&ctx->prof);
   rn->E.set_wait_budget(ctx->opt.spin_budget);
+  rn->E.set_checked(ctx->opt.checked != 0);
   rn->E.set_eig_sweep_cap(ctx->opt.eig_sweep_cap);
   if (ctx->opt.precision == RTCC3_PREC_TF32) rn->E.set_tensor_cores(4);
   if (ctx->opt.precision == RTCC3_PREC_BF16) rn->E.set_tensor_cores(2);
   ctx->runner = std::move(rn);
+}
+
+// Room for `entries` values of every additional observable.
+void ensure_obs(rtcc3_ctx* ctx, size_t entries) {
+  if (ctx->nobs == 0 || entries <= ctx->obs_cap) return;
+  if (ctx->obs_traj) cudaFree(ctx->obs_traj);
+  ctx->obs_traj = nullptr;
+  ctx->obs_cap = 0;
+  RTCC3_CUDA(cudaMalloc(&ctx->obs_traj, entries * ctx->nobs * sizeof(double2)));
+  ctx->obs_cap = entries;
+}
+
+// Trajectory descriptor with the context's additional observables.
+TrajDesc traj_desc(const rtcc3_ctx* ctx, double2* dip, double2* en, long long stride) {
+  TrajDesc td{dip, en, stride};
+  if (ctx->nobs > 0) {
+    td.obs = ctx->obs_traj;
+    td.ops = ctx->obs_ops;
+    td.nobs = ctx->nobs;
+  }
+  return td;
 }
 
 void ensure_traj(rtcc3_ctx* ctx, size_t entries) {
@@ -464,7 +506,8 @@ void rk4_step(rtcc3_ctx* ctx, double h, const std::vector<int>& sweeps) {
       if (s == 0) {
         PScope ps(ctx->prof, ctx->stream, "observables", 8.0 * ctx->n * ctx->n,
                   double(ctx->n) * ctx->n * (sizeof(Cx<R>) + 24.0));
-        launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->tdesc,
+        launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->nobs,
+                              ctx->tdesc,
                               b, ctx->stepdev, ctx->stream);
         E.add_launches(1);
       }
@@ -510,7 +553,8 @@ void final_observables(rtcc3_ctx* ctx, const std::vector<int>& sweeps) {
                                  true, sweeps[b]);
     PScope ps(ctx->prof, ctx->stream, "observables", 8.0 * ctx->n * ctx->n,
               double(ctx->n) * ctx->n * (sizeof(Cx<R>) + 24.0));
-    launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->tdesc, b,
+    launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->nobs,
+                              ctx->tdesc, b,
                           ctx->stepdev, ctx->stream);
   }
 }
@@ -546,7 +590,9 @@ void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2*
   Engine<R>& E = ctx->run<R>().E;
   std::vector<int> sweeps(ctx->nb);
   for (int b = 0; b < ctx->nb; ++b) sweeps[b] = field_sweeps(ctx, b);
-  const TrajDesc td{dip, en, (long long)stride};
+  ensure_obs(ctx, stride * ctx->nb);
+  ctx->obs_last = (long long)(stride * ctx->nb);
+  const TrajDesc td = traj_desc(ctx, dip, en, (long long)stride);
   RTCC3_CUDA(cudaMemcpyAsync(ctx->tdesc, &td, sizeof(td), cudaMemcpyHostToDevice, ctx->stream));
   RTCC3_CUDA(cudaMemsetAsync(ctx->stepdev, 0, sizeof(int), ctx->stream));
   const int minus1 = -1;
@@ -554,7 +600,7 @@ void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2*
   // stage-local buffers must not be overwritten before the copies above land
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   E.reset_launch_count();
-  const bool graphs = ctx->opt.use_graphs && !ctx->prof.enabled;
+  const bool graphs = ctx->opt.use_graphs && !ctx->prof.enabled && !ctx->opt.checked;
   // the captured step depends on h, the sweep counts and the engine's
   // persistent buffers; anything else is read from device memory
   if (ctx->gexec && (!graphs || ctx->gh != h || ctx->gsweeps != sweeps || ctx->ggen != E.generation()))
@@ -643,10 +689,12 @@ void residuals_impl(rtcc3_ctx* ctx, int b, double time, double* r_t1, double* r_
                             need_grad ? E.grad(S.t2) : nullptr, ctx->res, ctx->o, ctx->v, need_grad,
                             ctx->stream);
   ensure_traj(ctx, 1);
-  const TrajDesc td{ctx->dip_traj, ctx->en_traj, 0};
+  ensure_obs(ctx, 1);
+  ctx->obs_last = 1;
+  const TrajDesc td = traj_desc(ctx, ctx->dip_traj, ctx->en_traj, 0);
   RTCC3_CUDA(cudaMemcpyAsync(ctx->tdesc, &td, sizeof(td), cudaMemcpyHostToDevice, ctx->stream));
   launch_observables<R>(need_grad ? E.grad(S.w) : E.data(S.w), E.data(S.e), ctx->mu, ctx->e_ref,
-                        ctx->n, ctx->tdesc, 0, nullptr, ctx->stream);
+                        ctx->n, ctx->nobs, ctx->tdesc, 0, nullptr, ctx->stream);
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->last_launches = E.launches();
   check_device_timeout<R>(ctx);
@@ -802,6 +850,7 @@ void triples_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1, const d
   so.field_iters = field_sweeps(ctx, b);
   so.rotation = ctx->opt.field_solver == 0;
   so.triples_chunk = triples_chunk(ctx);
+  so.tc_all = ctx->opt.tc_all != 0;
   auto fill = [&](const StageNodes& s) {
     launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, ctx->stream);
     launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, ctx->teval, 0.0, ctx->n, ctx->stream);
@@ -1018,6 +1067,8 @@ void rtcc3_default_options(rtcc3_options* opt) {
   opt->spin_budget = 0;
   opt->eig_sweep_cap = 0;
   opt->storage = RTCC3_STORAGE_C128;
+  opt->tc_all = 0;
+  opt->checked = 0;
 }
 
 int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3_ctx** out) {
@@ -1050,6 +1101,8 @@ int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3
     raw->baddev = raw->dalloc<int>(1);
     raw->maxr = raw->dalloc<double>(1);
     raw->tdesc = raw->dalloc<TrajDesc>(1);
+    raw->checkflag = raw->dalloc<int>(1);
+    RTCC3_CUDA(cudaMemset(raw->checkflag, 0, sizeof(int)));
     raw->fhost.assign(nbatch, FieldDev{0, 0.0, 0.0, 0.0, 1.0, {0.0, 0.0, 1.0}});
     RTCC3_CUDA(cudaMemcpy(raw->fdev, raw->fhost.data(), nbatch * sizeof(FieldDev), cudaMemcpyHostToDevice));
     RTCC3_CUDA(cudaMemcpy(raw->fnone, raw->fhost.data(), sizeof(FieldDev), cudaMemcpyHostToDevice));
@@ -1383,6 +1436,45 @@ int rtcc3_autotune_triples(rtcc3_ctx* ctx, int b, int* chunk, float* ms, int max
       autotune_impl<double>(ctx, b, chunk, ms, max_candidates, candidates, candidate_ms, count);
     else
       autotune_impl<float>(ctx, b, chunk, ms, max_candidates, candidates, candidate_ms, count);
+  });
+}
+
+int rtcc3_set_observables(rtcc3_ctx* ctx, int nops, const double* ops) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  if (nops < 0 || nops > 64 || (nops > 0 && !ops))
+    return fail(ctx, RTCC3_ERR_ARG, "0 <= nops <= 64 with a non-null operator array");
+  return guarded(ctx, [&] {
+    RTCC3_CUDA(cudaSetDevice(ctx->opt.device));
+    const size_t nn = size_t(ctx->n) * ctx->n;
+    for (size_t t = 0; t < 2 * nn * size_t(nops); ++t)
+      RTCC3_CHECK(std::isfinite(ops[t]), RTCC3_ERR_ARG, "non-finite observable matrix element");
+    if (ctx->obs_ops) cudaFree(ctx->obs_ops);
+    if (ctx->obs_traj) cudaFree(ctx->obs_traj);
+    ctx->obs_ops = nullptr;
+    ctx->obs_traj = nullptr;
+    ctx->obs_cap = 0;
+    ctx->obs_last = 0;
+    ctx->nobs = 0;
+    if (nops > 0) {
+      RTCC3_CUDA(cudaMalloc(&ctx->obs_ops, nn * nops * sizeof(double2)));
+      RTCC3_CUDA(cudaMemcpy(ctx->obs_ops, ops, nn * nops * sizeof(double2), cudaMemcpyHostToDevice));
+      ctx->nobs = nops;
+    }
+    drop_graph(ctx);  // the observables kernel's grid depends on nops
+  });
+}
+
+int rtcc3_get_observables(const rtcc3_ctx* cctx, double* out, long long entries) {
+  rtcc3_ctx* ctx = const_cast<rtcc3_ctx*>(cctx);
+  if (!ctx || !out || entries < 0) return RTCC3_ERR_ARG;
+  return guarded(ctx, [&] {
+    RTCC3_CHECK(ctx->nobs > 0 && ctx->obs_last > 0, RTCC3_ERR_STATE,
+                "no observables recorded (rtcc3_set_observables, then a compute or propagate call)");
+    RTCC3_CHECK(entries >= ctx->obs_last, RTCC3_ERR_ARG,
+                "output holds fewer entries than the last call recorded (" +
+                    std::to_string(ctx->obs_last) + ")");
+    RTCC3_CUDA(cudaMemcpy(out, ctx->obs_traj, size_t(ctx->obs_last) * ctx->nobs * sizeof(double2),
+                          cudaMemcpyDeviceToHost));
   });
 }
 

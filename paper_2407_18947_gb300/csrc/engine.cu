@@ -569,6 +569,7 @@ void launch_fill(Cx<R>* p, size_t n, double re, double im, cudaStream_t s) {
 
 template <typename R>
 Engine<R>::~Engine() {
+  if (canary_list_) cudaFree(canary_list_);
   if (side_) cudaStreamDestroy(side_);
   if (fork_ev_) cudaEventDestroy(fork_ev_);
   if (join_ev_) cudaEventDestroy(join_ev_);
@@ -626,6 +627,59 @@ void Engine<R>::begin() {
   arena_.reset();
   nodes_.clear();
   tape_.clear();
+  canaries_.clear();
+}
+
+// Every element a view (moved by `shift` elements) addresses lies inside its
+// node: checked on the host for every operation before it is launched, so a
+// planning error is reported (kErrState) instead of reaching memory.
+template <typename R>
+void Engine<R>::check_view(const View& v, long long shift, const char* what) const {
+  RTCC3_CHECK(v.node >= 0 && v.node < int(nodes_.size()), kErrState,
+              std::string("view of an unknown tensor in ") + what);
+  if (v.numel() == 0) return;
+  long long lo = v.off + shift, hi = v.off + shift;
+  for (int d = 0; d < v.nd; ++d) {
+    const long long span = (long long)(v.shape[d] - 1) * v.stride[d];
+    if (span < 0) lo += span; else hi += span;
+  }
+  RTCC3_CHECK(lo >= 0 && hi < (long long)nodes_[v.node].numel, kErrState,
+              std::string("view outside its tensor in ") + what + " (elements " +
+                  std::to_string(lo) + ".." + std::to_string(hi) + " of " +
+                  std::to_string(nodes_[v.node].numel) + ")");
+}
+
+namespace {
+constexpr unsigned char kCanary = 0xA5;
+constexpr size_t kCanaryBytes = 256;
+
+// One block per guarded tensor: every byte of its canary must still hold the
+// pattern written when the tensor was created.
+__global__ void k_check_canaries(unsigned char* const* __restrict__ pads, int* __restrict__ flag) {
+  const unsigned char* p = pads[blockIdx.x];
+  bool bad = false;
+  for (size_t t = threadIdx.x; t < kCanaryBytes; t += blockDim.x) bad |= p[t] != kCanary;
+  if (bad) atomicOr(flag, 1);
+}
+}  // namespace
+
+template <typename R>
+void Engine<R>::verify_canaries(int* flag) {
+  if (canaries_.empty()) return;
+  const size_t bytes = canaries_.size() * sizeof(unsigned char*);
+  if (bytes > canary_list_bytes_) {
+    if (canary_list_) cudaFree(canary_list_);
+    canary_list_ = nullptr;
+    RTCC3_CUDA(cudaMalloc(&canary_list_, bytes));
+    canary_list_bytes_ = bytes;
+  }
+  RTCC3_CUDA(cudaMemcpyAsync(canary_list_, canaries_.data(), bytes, cudaMemcpyHostToDevice, stream_));
+  k_check_canaries<<<int(canaries_.size()), 128, 0, stream_>>>(
+      static_cast<unsigned char* const*>(canary_list_), flag);
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
+  // the host list must outlive the copy
+  RTCC3_CUDA(cudaStreamSynchronize(stream_));
 }
 
 template <typename R>
@@ -635,8 +689,14 @@ int Engine<R>::node(const std::vector<int>& shape, bool needs_grad, bool zero) {
   nd.numel = 1;
   for (int s : shape) nd.numel *= size_t(s);
   RTCC3_CHECK((int)shape.size() <= kMaxDim, kErrArg, "tensor rank too large");
-  nd.data = static_cast<C*>(arena_.alloc(nd.numel * sizeof(C)));
+  nd.data = static_cast<C*>(arena_.alloc(nd.numel * sizeof(C) + (checked_ ? kCanaryBytes : 0)));
   if (zero) RTCC3_CUDA(cudaMemsetAsync(nd.data, 0, nd.numel * sizeof(C), stream_));
+  if (checked_) {
+    // canary right after the tensor (checked mode): verified after the stage
+    unsigned char* pad = reinterpret_cast<unsigned char*>(nd.data + nd.numel);
+    RTCC3_CUDA(cudaMemsetAsync(pad, kCanary, kCanaryBytes, stream_));
+    canaries_.push_back(pad);
+  }
   nd.needs_grad = needs_grad;
   nodes_.push_back(nd);
   return int(nodes_.size()) - 1;
@@ -960,6 +1020,9 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
   const C* pb = (b_grad ? nodes_[B.node].grad : nodes_[B.node].data);
   C* pc = (c_grad ? nodes_[Cv.node].grad : nodes_[Cv.node].data);
   RTCC3_CHECK(pa && pb && pc, kErrState, "contraction on an unallocated buffer: " + spec);
+  check_view(A, sa, spec.c_str());
+  check_view(B, sb, spec.c_str());
+  check_view(Cv, sc, spec.c_str());
   pa += sa;
   pb += sb;
   pc += sc;
@@ -1154,6 +1217,8 @@ template <typename R>
 void Engine<R>::run_combine(const View* xs, const bool* xg, const double* alphas, int ns,
                             const View& Y, bool yg, bool overwrite, const char* name) {
   RTCC3_CHECK(ns >= 1 && ns <= kMaxSrc, kErrArg, "combine takes 1..6 sources");
+  for (int k = 0; k < ns; ++k) check_view(xs[k], 0, name);
+  check_view(Y, 0, name);
   {
     // sources on unset (zero) gradients drop out; none left: nothing to add
     View keep[kMaxSrc];
@@ -1320,6 +1385,8 @@ void Engine<R>::sym6_div(double alpha, const View& X, const EpsSpec& es, const V
 template <typename R>
 void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y,
                              bool yg, bool overwrite, int np) {
+  check_view(X, 0, "sym6_div");
+  check_view(Y, 0, "sym6_div");
   const bool cplx = es.osum_cr && es.vsum_cr;
   RTCC3_CHECK(cplx || (es.osum_r && es.vsum_r), kErrArg, "sym6_div needs denominator sum tables");
   auto dense6 = [&](const View& w) {
@@ -1431,6 +1498,8 @@ void Engine<R>::mulc(const View& X, const View& Cst, const View& Y) {
 template <typename R>
 void Engine<R>::run_div(const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
                         bool overwrite) {
+  check_view(X, 0, "div_eps");
+  check_view(Y, 0, "div_eps");
   RTCC3_CHECK(X.nd == Y.nd, kErrArg, "div_eps rank mismatch");
   if (xg && !nodes_[X.node].grad_ready) {
     if (!overwrite) return;  // zero cotangent
@@ -1593,6 +1662,8 @@ void Engine<R>::zero_grad_if_unset(int node) {
 template <typename R>
 void Engine<R>::exec_slab_div(double alpha, const View& X, int i0, const EpsSpec& es,
                               const View& Y) {
+  check_view(X, 0, "slab_div");
+  check_view(Y, 0, "slab_div");
   const bool cplx = es.osum_cr && es.vsum_cr;
   RTCC3_CHECK(cplx || (es.osum_r && es.vsum_r), kErrArg, "slab division needs sum tables");
   RTCC3_CHECK(X.nd == 6 && Y.nd == 6 && X.off == 0 && Y.off == 0, kErrArg,

@@ -250,6 +250,11 @@ class Engine {
   int* error_flag();
   // Clock cycles a tensor-core kernel's wait on another warp may spin before
   // it gives up and raises the error flag (0: the kernels' default).
+  // Checked mode: every tensor gets a canary after it, verified (raising
+  // *flag) by verify_canaries() after the stage.
+  void set_checked(bool c) { checked_ = c; }
+  bool checked() const { return checked_; }
+  void verify_canaries(int* flag);
   void set_wait_budget(long long cycles) { wait_budget_ = cycles; }
   long long wait_budget() const { return wait_budget_; }
   // QR sweeps the field eigensolver may take per matrix (0: its default).
@@ -325,6 +330,11 @@ class Engine {
   size_t scratch_bytes_[kScratchSlots] = {0, 0, 0, 0};
   int tc_eb_ = 0;
   long long wait_budget_ = 0;
+  bool checked_ = false;
+  std::vector<unsigned char*> canaries_;
+  void* canary_list_ = nullptr;
+  size_t canary_list_bytes_ = 0;
+  void check_view(const View& v, long long shift, const char* what) const;
   int eig_cap_ = 0;
   bool tc_region_ = false;
   int* err_ = nullptr;

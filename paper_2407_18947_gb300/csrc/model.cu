@@ -122,15 +122,26 @@ template <typename R>
 __global__ void k_observables(const Cx<R>* __restrict__ D, const Cx<R>* __restrict__ e,
                               const double* __restrict__ mu, double e_ref, int n,
                               const TrajDesc* __restrict__ td, int slot, const int* step) {
-  // one block per Cartesian component; FP64 reduction in fixed order
+  // one block per Cartesian component of the dipole, then one per additional
+  // observable; FP64 reduction in fixed order
   __shared__ double sr[256], si[256];
   const int x = blockIdx.x;
   const size_t nn = size_t(n) * n;
   double ar = 0.0, ai = 0.0;
-  for (size_t pq = threadIdx.x; pq < nn; pq += blockDim.x) {
-    const double m = mu[x * nn + pq];
-    ar += double(D[pq].x) * m;
-    ai += double(D[pq].y) * m;
+  if (x < 3) {
+    for (size_t pq = threadIdx.x; pq < nn; pq += blockDim.x) {
+      const double m = mu[x * nn + pq];
+      ar += double(D[pq].x) * m;
+      ai += double(D[pq].y) * m;
+    }
+  } else {
+    const double2* op = td->ops + size_t(x - 3) * nn;
+    for (size_t pq = threadIdx.x; pq < nn; pq += blockDim.x) {
+      const double2 m = op[pq];
+      const double dr = double(D[pq].x), di = double(D[pq].y);
+      ar += dr * m.x - di * m.y;
+      ai += dr * m.y + di * m.x;
+    }
   }
   sr[threadIdx.x] = ar;
   si[threadIdx.x] = ai;
@@ -141,6 +152,10 @@ __global__ void k_observables(const Cx<R>* __restrict__ D, const Cx<R>* __restri
   }
   if (threadIdx.x == 0) {
     const long long ent = (long long)slot * td->stride + (step ? *step : 0);
+    if (x >= 3) {
+      if (td->obs) td->obs[size_t(ent) * td->nobs + (x - 3)] = make_double2(sr[0], si[0]);
+      return;
+    }
     if (td->dip) td->dip[size_t(ent) * 3 + x] = make_double2(sr[0], si[0]);
     if (x == 0 && td->en) td->en[ent] = make_double2(double(e[0].x) - e_ref, double(e[0].y));
   }
@@ -348,8 +363,8 @@ void launch_stage_output(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, cons
 
 template <typename R>
 void launch_observables(const Cx<R>* D, const Cx<R>* e, const double* mu, double e_ref, int n,
-                        const TrajDesc* td, int slot, const int* step, cudaStream_t s) {
-  k_observables<R><<<3, 256, 0, s>>>(D, e, mu, e_ref, n, td, slot, step);
+                        int nobs, const TrajDesc* td, int slot, const int* step, cudaStream_t s) {
+  k_observables<R><<<3 + nobs, 256, 0, s>>>(D, e, mu, e_ref, n, td, slot, step);
   RTCC3_CUDA(cudaGetLastError());
 }
 
@@ -499,7 +514,7 @@ void launch_stage_prep_acc(double2* acc, const double2* y, size_t ny, cudaStream
   template void launch_stage_output<R>(const Cx<R>*, const Cx<R>*, const Cx<R>*, const Cx<R>*,    \
                                        double2*, double2*, double, int, int, cudaStream_t);       \
   template void launch_observables<R>(const Cx<R>*, const Cx<R>*, const double*, double, int,     \
-                                      const TrajDesc*, int, const int*, cudaStream_t);            \
+                                      int, const TrajDesc*, int, const int*, cudaStream_t);       \
   template void launch_residual_export<R>(const Cx<R>*, const Cx<R>*, const Cx<R>*, const Cx<R>*, \
                                           double2*, int, int, bool, cudaStream_t);                \
   template void launch_load_amplitudes<R>(const double2*, const double2*, Cx<R>*, Cx<R>*, int,  \

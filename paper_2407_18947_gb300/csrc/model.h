@@ -49,6 +49,9 @@ struct StageNodes {
 struct StageOptions {
   bool ccsd = true;  // false: R1, R2 hold only the triples terms X1, X2
   bool triples = true;
+  // tensor cores also for the dressing and CCSD contractions (split TF32
+  // only), not only inside the triples
+  bool tc_all = false;
   bool need_grad = true;
   bool field_terms = true;  // include the V-coupling of the triples equation
   bool rotation = true;     // field-dressed eigenbasis (else fixed-point sweeps)
@@ -103,11 +106,18 @@ struct TrajDesc {
   double2* dip;
   double2* en;
   long long stride;
+  // additional one-electron observables sum_pq D_pq O_pq (e.g. the magnetic
+  // dipole of Section 2.2.3): nobs complex n x n operators, values at
+  // obs[entry * nobs + k]
+  double2* obs = nullptr;
+  const double2* ops = nullptr;
+  int nobs = 0;
 };
 // dipole[3] = sum_pq D_pq mu^x_pq (FP64) and energy = e - e_ref, written at
 // entry (slot * td->stride + *step) (step may be NULL: entry slot * stride).
 template <typename R>
 void launch_observables(const Cx<R>* D, const Cx<R>* e, const double* mu, double e_ref, int n,
+                        int nobs,
                         const TrajDesc* td, int slot, const int* step, cudaStream_t s);
 // Host-readable FP64 copy of the residuals: out = [r1, r2, g1, g2 + g2^T].
 template <typename R>

@@ -504,6 +504,10 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   S.t2 = E.node({o, o, v, v}, opt.need_grad);
   S.w = E.node({n, n}, opt.need_grad);
   fill(S);
+  // contractions recorded while the region is open (and their adjoints) may
+  // take the tensor-core route
+  const bool all_tc = opt.tc_all && E.tensor_cores() == 4;
+  E.set_tc_region(all_tc);
 
   const int Lc = E.external(H.L, {na, n, n});
   const int hc = E.external(H.h, {n, n});
@@ -600,7 +604,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   if (opt.triples && opt.field_terms && opt.rotation) {
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores
     S.t3 = rotated_triples(E, H, T, wt, fb, g, ft, R1, SD, blk, opt.triples_chunk);
-    E.set_tc_region(false);
+    E.set_tc_region(all_tc);
   } else if (opt.triples) {
     E.set_tc_region(true);  // the dense triples contractions may use tensor cores
     const std::vector<int> s6 = {o, o, o, v, v, v};
@@ -676,7 +680,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
       E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), G("ooov"), E.v(S3), true);
       E.axpy(1.0, E.v(S3), SD);
     }
-    E.set_tc_region(false);
+    E.set_tc_region(all_tc);
   }
   // P_ij^ab on the symmetrised part
   E.combine({{1.0, SD}, {1.0, E.ev("jiba->ijab", SD)}}, R2, false);
@@ -690,6 +694,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   E.contract("ij,ij->", 2.0, E.ev("iijj->ij", G("oooo")), E.v(oo), Ev, true);
   E.contract("ij,ij->", -1.0, E.ev("ijji->ij", G("oooo")), E.v(oo), Ev, true);
   E.contract("ijab,iajb->", 1.0, T, E.v(Lov), Ev, true);
+  E.set_tc_region(false);
   return S;
 }
 

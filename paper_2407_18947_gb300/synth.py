@@ -112,3 +112,14 @@ def random_probe(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     """A seeded complex probe vector (for finite-difference checks)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return _crandn(rng, shape, scale)
+
+
+def magnetic_dipole(nmo: int, seed: int, scale: float = 0.1) -> np.ndarray:
+    """Synthetic magnetic-dipole matrices m^{x,y,z} (3, nmo, nmo), complex:
+    i times a real antisymmetric N(0, scale^2) matrix (the form of the
+    magnetic dipole operator's matrix elements in a real orbital basis),
+    from its own seeded stream (the system's draws are not affected)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = rng.normal(0.0, scale, size=(3, nmo, nmo))
+    a = a - a.transpose(0, 2, 1)
+    return 1j * a

@@ -62,3 +62,22 @@ def test_tensor_core_wait_budget_reports_timeout_and_context_recovers():
         got = _run(eng)
         assert np.abs(got - ref).max() <= 1e-6
     eng.close()
+
+
+def test_checked_mode_finds_no_overrun_and_gives_the_same_result():
+    """Checked mode (a canary after every device tensor of a stage, verified
+    after the stage; no CUDA graphs) on a propagation through the blocked
+    triples with split TF32: no overrun is reported and the trajectory
+    equals the unchecked one."""
+    from paper_2407_18947_gb300.api import RTCC3
+    s = water_system(1)
+    amps = random_amplitudes(s.nocc, s.nvir, seed=22)
+    out = []
+    for checked in (False, True):
+        eng = RTCC3(s.nocc, s.nvir, precision=2, triples_chunk=2, checked=checked)
+        eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+        eng.set_field(0, 2, 0.002, omega=0.1, direction=(0.0, 0.0, 1.0))
+        eng.set_amplitudes(0, *amps)
+        out.append(np.asarray(eng.propagate_rk4(0.01, 2)[0]))
+        eng.close()
+    assert np.abs(out[0] - out[1]).max() < 1e-9

@@ -93,3 +93,33 @@ def test_complex64_storage_rounds_the_state_every_step():
     assert not all(np.array_equal(x, x.astype(np.complex64).astype(np.complex128))
                    for x in out[False][1])
     assert np.abs(out[True][0] - out[False][0]).max() < 1e-6
+
+
+def test_magnetic_moment_observable_matches_oracle_density():
+    """Additional observables (the magnetic dipole of Section 2.2.3): the
+    density the GPU records them with is the oracle's dL/dw, so
+    sum_pq D_pq m_pq matches; and an observable equal to mu_z reproduces the
+    z dipole along a propagation."""
+    from paper_2407_18947_gb300.api import RTCC3
+    from paper_2407_18947_gb300.synth import magnetic_dipole
+    o, v = 4, 11
+    s = make_system(o, v, seed=97)
+    amps = random_amplitudes(o, v, seed=98)
+    m = magnetic_dipole(o + v, seed=99)
+    ham = cc3.Hamiltonian.from_system(s)
+    eng = RTCC3(o, v, precision=0, nbatch=2)
+    eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+    eng.set_observables(np.concatenate([m, s.dipole[2:3].astype(np.complex128)]))
+    for b in range(2):
+        eng.set_field(0 if b == 0 else 1, 2, 0.02 * (b + 1), omega=0.4, direction=(0.1, 0.0, 1.0))
+        eng.set_amplitudes(b, *amps)
+    eng.compute_residuals(0, 0.3)
+    got = eng.get_observables(1)[0]
+    w = ham.field_operator(np.asarray([0.1, 0.0, 1.0]) * 0.02 * np.cos(0.4 * 0.3))
+    ref = cc3.evaluate(ham, *amps, w)
+    want = np.einsum('pq,xpq->x', ref.density.numpy(), m)
+    assert _rel(got[:3], want) < 1e-10
+    dip, _ = eng.propagate_rk4(0.02, 3)
+    obs = eng.get_observables(2 * 4).reshape(2, 4, 4)
+    eng.close()
+    assert _rel(obs[:, :, 3], np.asarray(dip)[:, :, 2]) < 1e-12
