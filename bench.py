@@ -286,11 +286,14 @@ def first_order_state(s):
     return z1, t2, z1.copy(), l2
 
 
-def storage_note(o, v, prec, tune):
+def storage_note(o, v, prec, tune, chunk=0):
     """How the triples were held in this run (the library's automatic rule
-    unless the autotuner chose)."""
+    unless the autotuner or --triples-chunk chose)."""
     if tune:
         return dict(tune, rule="autotuned")
+    if chunk:
+        return {"rule": "given", "choice": "whole o^3 v^3 tensors" if chunk < 0 else
+                f"slabs of {chunk} occupied indices"}
     elem = 16 if prec == 0 else 8
     t3 = o ** 3 * v ** 3 * elem
     return {"rule": "automatic", "o3v3_tensor_GB": round(t3 / 1e9, 2)}
@@ -349,6 +352,9 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="time every triples storage form (whole / slabs of k occupied indices) "
                          "before the warm-up and keep the fastest (stated in config)")
+    ap.add_argument("--triples-chunk", type=int, default=0,
+                    help="triples storage: 0 automatic, -1 whole o^3 v^3 tensors, k > 0 slabs of k "
+                         "occupied indices")
     ap.add_argument("--storage", default="c128", choices=["c128", "c64"],
                     help="propagated state kept in complex128 or rounded to complex64 every step")
     ap.add_argument("--no-extras", action="store_true",
@@ -382,7 +388,8 @@ def main():
     prec = PRECISIONS[args.precision]
     F = max(1, args.fields)
     c64 = args.storage == "c64"
-    eng = RTCC3(o, v, nbatch=F, precision=prec, device=local, storage_c64=c64)
+    eng = RTCC3(o, v, nbatch=F, precision=prec, device=local, storage_c64=c64,
+                triples_chunk=args.triples_chunk)
     eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
     # each rank propagates its own field strength (independent problems)
     amp = rank_field_amplitude(wl["amp"], rank)
@@ -392,7 +399,8 @@ def main():
         eng.set_field(b, wl["kind"], amp * (scale if F > 1 else 1.0), omega=wl["omega"],
                       direction=(0.0, 0.0, 1.0))
     def fresh_engine():
-        e = RTCC3(o, v, nbatch=F, precision=prec, device=local, storage_c64=c64)
+        e = RTCC3(o, v, nbatch=F, precision=prec, device=local, storage_c64=c64,
+                  triples_chunk=args.triples_chunk)
         e.set_hamiltonian(s.eps, s.Lfac, s.dipole)
         for b in range(F):
             scale = 0.0 if b == 0 else (1 << ((b - 1) // 2)) * (1.0 if b % 2 else -1.0)
@@ -514,6 +522,18 @@ def main():
     peaks, peak_kind = load_peaks()
     roofline, dom = roofline_of(kstats, peaks, peak_kind, args.precision,
                                 wl.get("size", args.workload))
+    # pipe rates of this GPU from the library's probe kernels, beside the
+    # GEMM-based peaks the roofline fractions use
+    from paper_2407_18947_gb300.api import measure_peaks
+    probed = {k: round(v_, 2) for k, v_ in measure_peaks(local).items()}
+    for rl in (roofline, (roofline or {}).get("tensor_kernel")):
+        if not rl:
+            continue
+        key = {"alu": "fp64_fma" if args.precision == "fp64" else "fp32_fma",
+               "tensor": "bf16_mma" if args.precision == "bf16" else "tf32_mma"}.get(rl["bound"])
+        if key:
+            rl["frac_of_probed_pipe"] = round(rl["achieved"] / probed[key], 4)
+            rl["probed_pipe"] = key
     flops = nominal_flops(o, v)
 
     cpu = None
@@ -535,11 +555,12 @@ def main():
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": DTYPES[args.precision], "data": "synthetic",
                 "config": dict(workload_config(wl, args.precision, F), initial_state=init_state,
-                               triples_storage=storage_note(o, v, prec, tune),
+                               triples_storage=storage_note(o, v, prec, tune, args.triples_chunk),
                                state_storage=args.storage),
                 "triples_tflops_nominal": round(flops * world * K * F / (ms_max / 1e3) / 1e12, 3),
                 "nominal_flops_per_step": flops,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roofline, "peaks_probed_tflops": probed, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches),
                 "clocks": clk, "ground_state_s": round(t_gs, 2),
                 "kernels": {k: {"launches": v_["launches"], "ms": round(v_["ms"], 4)}
                             for k, v_ in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])}}

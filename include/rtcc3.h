@@ -202,7 +202,7 @@ int rtcc3_triples_forward_noalloc_dev(rtcc3_ctx* ctx, int b, double time, const 
  * after one untimed evaluation that builds the contraction plans) for every
  * storage form that fits in the device memory free at set-up: the whole
  * o^3 v^3 tensors (reported as -1) when about 24 of them fit in 70 % of it,
- * and slabs of o, o/2, o/4, ..., 1 occupied indices whose three slab buffers
+ * and slabs of o, o/2, o/4, ..., 1 occupied indices whose four slab buffers
  * fit in a quarter of it.  The fastest becomes the context's triples_chunk
  * option.  Outputs (any may be NULL): *chunk the choice, *ms its time,
  * candidates[] / candidate_ms[] the first max_candidates forms tried and

@@ -264,7 +264,7 @@ void launch_basis_ahead(rtcc3_ctx* ctx, const BasisBuffers& bb, const double2* b
 // Automatic: the stored form keeps about a dozen o^3 v^3 tensors and their
 // cotangents alive in a stage; when 24 of them do not fit in 70% of the
 // device memory free at set-up, the triples are blocked in slabs of k first
-// occupied indices with the three slab buffers within a quarter of that
+// occupied indices with the four slab buffers within a quarter of that
 // memory (at most 32 GB).
 int triples_chunk(const rtcc3_ctx* ctx) {
   if (!ctx->opt.triples || ctx->opt.field_solver != 0) return 0;
@@ -276,7 +276,7 @@ int triples_chunk(const rtcc3_ctx* ctx) {
   const double freeb = double(ctx->free_at_setup);
   if (24.0 * t3 <= 0.7 * freeb) return 0;
   const double budget = std::min(0.25 * freeb, 32.0 * (1ull << 30));
-  const double slab = 3.0 * double(o) * o * v * v * v * elem;
+  const double slab = 4.0 * double(o) * o * v * v * v * elem;
   return std::max(1, std::min(o, int(budget / slab)));
 }
 
@@ -967,7 +967,7 @@ void triples_noalloc_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1,
 // Candidate storage forms of the triples for this context, in the order
 // they are timed: whole tensors when 24 of them fit in 70% of the free
 // memory (-1), then slabs of o, o/2, o/4, ..., 1 first occupied indices
-// whose three slab buffers fit in a quarter of it.
+// whose four slab buffers fit in a quarter of it.
 std::vector<int> chunk_candidates(const rtcc3_ctx* ctx) {
   std::vector<int> c;
   const int o = ctx->o, v = ctx->v;
@@ -975,7 +975,7 @@ std::vector<int> chunk_candidates(const rtcc3_ctx* ctx) {
   const double freeb = double(ctx->free_at_setup);
   if (24.0 * double(o) * o * o * v * v * v * elem <= 0.7 * freeb) c.push_back(-1);
   for (int k = o; k >= 1; k = (k + 1) / 2) {
-    if (3.0 * double(k) * o * o * v * v * v * elem <= 0.25 * freeb &&
+    if (4.0 * double(k) * o * o * v * v * v * elem <= 0.25 * freeb &&
         std::find(c.begin(), c.end(), k) == c.end())
       c.push_back(k);
     if (k == 1) break;

@@ -100,8 +100,8 @@ struct FieldAdjoint {
   View wvv, woo, SO, SIO, SV, SIV;
 };
 
-// Forward: for each slab, W = P_ijk^abc Z from the six permuted Z products
-// (the slab's index i in each of the three occupied positions), t3 = -W / D,
+// Forward: for each slab, W = P_ijk^abc Z from the three Z slabs with the
+// slab's index i in each of the three occupied positions, t3 = -W / D,
 // and its contributions to X1 (rows of the slab) and S3.  Reverse (custom
 // adjoint, given grad X1 and grad S3): per slab, t3 is rebuilt; the
 // cotangents of Lp, Fp, Gb, Gc follow from t3; the t3 cotangent Q is
@@ -109,7 +109,7 @@ struct FieldAdjoint {
 // evaluated with the slab index in each of the three occupied positions
 // (Q is a sum of products of small tensors, so any arrangement is cheap to
 // form); Z's cotangent is -P(Q)/D, which gives those of Ac, Bc, T2, G2, and
-// with t3 the field-coupling slot densities.  Memory: three slabs of
+// with t3 the field-coupling slot densities.  Memory: four slabs of
 // chunk * o^2 v^3 elements instead of the dozen o^3 v^3 tensors of the stored
 // form.  X1o, S3o: output nodes (written here, zero-initialised).
 template <typename R>
@@ -122,9 +122,12 @@ void blocked_triples(Engine<R>& E, int o, int v, int chunk, const TriplesOperand
                  E.needs_grad(in.Lp.node) || E.needs_grad(in.Fp.node) ||
                  E.needs_grad(in.Gb.node) || E.needs_grad(in.Gc.node) ||
                  (fa.on && E.needs_grad(fa.wt));
+  // slab buffers: nb0 holds t3; nb1..nb3 hold the three Z slabs while W is
+  // built, then serve as scratch (nb1) and P(Q)/D (nb2) in the reverse pass
   const int nb0 = E.node({I0, o, o, v, v, v}, false, false);
   const int nb1 = E.node({I0, o, o, v, v, v}, false, false);
-  const int nb2 = g ? E.node({I0, o, o, v, v, v}, false, false) : -1;
+  const int nb2 = E.node({I0, o, o, v, v, v}, false, false);
+  const int nb3 = E.node({I0, o, o, v, v, v}, false, false);
   E.set_needs_grad(X1o, g);
   E.set_needs_grad(S3o, g);
 
@@ -151,23 +154,33 @@ void blocked_triples(Engine<R>& E, int o, int v, int chunk, const TriplesOperand
     }
     E.exec_contract_at(spec.c_str(), alpha, a.v, a.g, sh[0], b.v, b.g, sh[1], c.v, c.g, sh[2], acc);
   };
-  // t3 of the slab into T: the six permuted Z products, then -W / D
-  auto build_t3 = [&E, prod, in, es](const View& T, int i0, int I) {
-    static const char* kA[6] = {"ijaE,Ekbc->ijkabc", "jibE,Ekac->ijkabc", "ikaE,Ejcb->ijkabc",
-                                "kjcE,Eiba->ijkabc", "kicE,Ejab->ijkabc", "jkbE,Eica->ijkabc"};
-    static const char* kB[6] = {"imab,mjck->ijkabc", "jmba,mick->ijkabc", "imac,mkbj->ijkabc",
-                                "kmcb,mjai->ijkabc", "kmca,mibj->ijkabc", "jmbc,mkai->ijkabc"};
-    for (int p = 0; p < 6; ++p) {
-      prod(kA[p], 1.0, {in.Ac, false, false}, {in.Bc, false, false}, {T, false, true}, i0, I, p > 0);
-      prod(kB[p], -1.0, {in.T2, false, false}, {in.G2, false, false}, {T, false, true}, i0, I, true);
+  // t3 of the slab into T.  The three Z slabs with the slab index in each
+  // occupied position, Z1[i,j,k,..] = Z[i,j,k,..], Z2[i,j,k,..] = Z[j,i,k,..]
+  // and Z3[i,j,k,..] = Z[j,k,i,..] (two products each), then
+  // W = Z1 + Z1(ikjacb) + Z2(ijkbac) + Z2(ikjcab) + Z3(ikjcba) + Z3(ijkbca)
+  // (the six terms of P_ijk^abc) in one pass, and t3 = -W / D.
+  auto build_t3 = [&E, prod, in, es](const View& T, const View& Z1, const View& Z2, const View& Z3,
+                                     int i0, int I) {
+    const View* Zs[3] = {&Z1, &Z2, &Z3};
+    static const char* kA[3] = {"ijaE,Ekbc->ijkabc", "jiaE,Ekbc->ijkabc", "jkaE,Eibc->ijkabc"};
+    static const char* kB[3] = {"imab,mjck->ijkabc", "jmab,mick->ijkabc", "jmab,mkci->ijkabc"};
+    for (int p = 0; p < 3; ++p) {
+      prod(kA[p], 1.0, {in.Ac, false, false}, {in.Bc, false, false}, {*Zs[p], false, true}, i0, I,
+           false);
+      prod(kB[p], -1.0, {in.T2, false, false}, {in.G2, false, false}, {*Zs[p], false, true}, i0, I,
+           true);
     }
+    E.exec_combine({{1.0, Z1}, {1.0, E.ev("ikjacb->ijkabc", Z1)}, {1.0, E.ev("ijkbac->ijkabc", Z2)},
+                    {1.0, E.ev("ikjcab->ijkabc", Z2)}, {1.0, E.ev("ikjcba->ijkabc", Z3)},
+                    {1.0, E.ev("ijkbca->ijkabc", Z3)}},
+                   T, true);
     E.exec_slab_div(-1.0, T, i0, es, T);
   };
   const View X1v = E.v(X1o), S3v = E.v(S3o);
   for (int i0 = 0; i0 < o; i0 += I0) {
     const int I = std::min(I0, o - i0);
     const View T = slab(nb0, I), U = slab(nb1, I);
-    build_t3(T, i0, I);
+    build_t3(T, U, slab(nb2, I), slab(nb3, I), i0, I);
     E.exec_combine({{1.0, T}, {-1.0, E.ev("ijkcba->ijkabc", T)}}, U, true);
     prod("ijkabc,jkbc->ia", 1.0, {U, false, true}, {in.Lp, false, false}, {X1v, false, false}, i0, I, true);
     prod("ijkabc,kc->ijab", 1.0, {U, false, true}, {in.Fp, false, false}, {S3v, false, false}, i0, I, true);
@@ -183,7 +196,7 @@ void blocked_triples(Engine<R>& E, int o, int v, int chunk, const TriplesOperand
   const int Gb2 = E.node({v, v, o, v}, false, false);
   E.exec_combine({{2.0, in.Gb}, {-1.0, E.ev("dzrx->dxrz", in.Gb)}}, E.v(Gb2), true);
   const View GB2 = E.v(Gb2);
-  E.custom([&E, o, v, I0, in, es, fa, nb0, nb1, nb2, X1o, S3o, GB2, prod, build_t3, slab]() {
+  E.custom([&E, o, v, I0, in, es, fa, nb0, nb1, nb2, nb3, X1o, S3o, GB2, prod, build_t3, slab]() {
     const View X1v = E.v(X1o), S3v = E.v(S3o);
     const bool gl = E.needs_grad(in.Lp.node), gf = E.needs_grad(in.Fp.node),
                gb = E.needs_grad(in.Gb.node), gc = E.needs_grad(in.Gc.node);
@@ -217,7 +230,7 @@ void blocked_triples(Engine<R>& E, int o, int v, int chunk, const TriplesOperand
     for (int i0 = 0; i0 < o; i0 += I0) {
       const int I = std::min(I0, o - i0);
       const View T = slab(nb0, I), U = slab(nb1, I), W = slab(nb2, I);
-      build_t3(T, i0, I);
+      build_t3(T, U, W, slab(nb3, I), i0, I);
       // cotangents of the X-side operands
       if (gl || gf) {
         E.exec_combine({{1.0, T}, {-1.0, E.ev("ijkcba->ijkabc", T)}}, U, true);
