@@ -154,6 +154,13 @@ int rtcc3_compute_residuals(rtcc3_ctx* ctx, int b, double time, double* r_t1, do
  * until max|R| < tol; copies the result to every slot and sets time 0. */
 int rtcc3_solve_ground_state(rtcc3_ctx* ctx, double tol, int maxiter);
 
+/* Convergence record of the last rtcc3_solve_ground_state call (also when
+ * it failed): out[k] = max |R| of iteration k, the T iterations first
+ * (*t_iterations of them), then the lambda iterations; *count = iterations
+ * made (out receives at most max_entries of them). */
+int rtcc3_ground_state_history(const rtcc3_ctx* ctx, double* out, int max_entries, int* count,
+                               int* t_iterations);
+
 /* Advance every slot nsteps RK4 steps of size h (stage times t, t+h/2,
  * t+h/2, t+h).  dipole: nbatch x (nsteps+1) x 3 complex, energy: nbatch x
  * (nsteps+1) complex (either may be NULL); entry n is evaluated from the

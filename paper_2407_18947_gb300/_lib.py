@@ -66,6 +66,7 @@ SIGNATURES = {
     "rtcc3_stats": (_I, [_P, _LLP, _LLP]),
     "rtcc3_set_wait_budgets": (_I, [_P, ctypes.c_longlong, _I]),
     "rtcc3_measure_peaks": (_I, [_I, _DP]),
+    "rtcc3_ground_state_history": (_I, [_P, _DP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rtcc3_set_observables": (_I, [_P, _I, _DP]),
     "rtcc3_get_observables": (_I, [_P, _DP, ctypes.c_longlong]),
     "rtcc3_autotune_triples": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float), _I,

@@ -178,6 +178,18 @@ class RTCC3:
         self._check(self.lib.rtcc3_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return {"launches": a.value, "device_bytes": b.value}
 
+    def ground_state_history(self):
+        """(T max|R| per iteration, lambda max|R| per iteration) of the last
+        ground-state solve."""
+        cnt, nt = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.rtcc3_ground_state_history(self.h, None, 0, ctypes.byref(cnt),
+                                                        ctypes.byref(nt)))
+        out = np.zeros(max(cnt.value, 1))
+        self._check(self.lib.rtcc3_ground_state_history(self.h, _dp(out), cnt.value,
+                                                        ctypes.byref(cnt), ctypes.byref(nt)))
+        h = out[:cnt.value]
+        return h[:nt.value], h[nt.value:]
+
     def set_observables(self, ops):
         """Additional one-electron operators (complex, (k, nmo, nmo)) whose
         expectation values sum_pq D_pq O_pq are recorded beside the dipole."""

@@ -113,6 +113,9 @@ struct rtcc3_ctx {
   size_t obs_cap = 0;             // entries
   long long obs_last = 0;         // entries written by the last call
   size_t free_at_setup = 0;  // free device memory when the Hamiltonian was set
+  // max |R| per iteration of the last ground-state solve (T, then lambda)
+  std::vector<double> gs_history;
+  int gs_t_iters = 0;
   double time = 0.0;
   long long step_total = 0;
   long long last_launches = 0;
@@ -774,6 +777,8 @@ void ground_state_impl(rtcc3_ctx* ctx, double tol, int maxiter) {
   double2* Ev = ctx->dalloc<double2>(len * kDiis);
   double2* dots = ctx->dalloc<double2>(kDiis);
   double2* coef = ctx->dalloc<double2>(kDiis);
+  ctx->gs_history.clear();
+  ctx->gs_t_iters = 0;
   for (int pass = 0; pass < 2; ++pass) {
     const bool lam = pass == 1;
     const size_t off = lam ? len : 0;
@@ -796,6 +801,8 @@ void ground_state_impl(rtcc3_ctx* ctx, double tol, int maxiter) {
       RTCC3_CUDA(cudaMemcpyAsync(&mx, ctx->maxr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       RTCC3_CUDA(cudaMemcpyAsync(d.data(), dots, mm * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
       RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
+      ctx->gs_history.push_back(mx);
+      if (!lam) ctx->gs_t_iters = int(ctx->gs_history.size());
       if (!std::isfinite(mx)) {
         check_device_timeout<R>(ctx);  // a device-side cause is reported (and its flag cleared) first
         throw Error(RTCC3_ERR_NONFINITE, "non-finite residual in the ground-state solve");
@@ -1437,6 +1444,16 @@ int rtcc3_autotune_triples(rtcc3_ctx* ctx, int b, int* chunk, float* ms, int max
     else
       autotune_impl<float>(ctx, b, chunk, ms, max_candidates, candidates, candidate_ms, count);
   });
+}
+
+int rtcc3_ground_state_history(const rtcc3_ctx* ctx, double* out, int max_entries, int* count,
+                               int* t_iterations) {
+  if (!ctx || max_entries < 0 || (max_entries > 0 && !out)) return RTCC3_ERR_ARG;
+  const int n = int(ctx->gs_history.size());
+  for (int k = 0; k < std::min(n, max_entries); ++k) out[k] = ctx->gs_history[size_t(k)];
+  if (count) *count = n;
+  if (t_iterations) *t_iterations = ctx->gs_t_iters;
+  return RTCC3_OK;
 }
 
 int rtcc3_set_observables(rtcc3_ctx* ctx, int nops, const double* ops) {

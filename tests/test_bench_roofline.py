@@ -45,7 +45,8 @@ def test_dominant_hbm_kernel_reported_against_measured_bandwidth():
     assert abs(rl["frac"] - 2500.0 / 6762.3) < 1e-3
     assert rl["launches"] == 10 and abs(rl["avg_launch_us"] - 200.0) < 1e-6
     assert abs(rl["share_of_step"] - 2.0 / 4.5) < 1e-4
-    assert rl["traffic"] == bench.MEASURED_TRAFFIC[("k_tc_gemm_direct", "tf32", 2)]
+    # the traffic of a kernel is reported only while its counters are current
+    assert rl["traffic"] == bench.MEASURED_TRAFFIC.get(("k_tc_gemm_direct", "tf32", 2))
     # the tcgen05 short-sum kernel rides along against the TF32 tensor peak
     tk = rl["tensor_kernel"]
     assert tk["kernel"] == "k_tc_gemm" and tk["bound"] == "tensor"
