@@ -95,9 +95,11 @@ typedef struct rtcc3_options {
   int eig_sweep_cap; /* QR sweeps the field eigensolver may take per matrix
                         before the call returns RTCC3_ERR_TIMEOUT; 0 =
                         default (60 n + 100)                                   */
-  int tc_all;        /* RTCC3_PREC_TF32 only: 1 = split-TF32 tensor cores also
-                        for the T1 dressing and CCSD contractions (default 0:
-                        only the triples; the others on FP32 CUDA cores)     */
+  int tc_scope;      /* RTCC3_PREC_TF32 only, split-TF32 tensor cores for: 0 =
+                        the triples (default; the rest on FP32 CUDA cores),
+                        1 = also the dressed two-electron integrals
+                        g = L~^T L~ and their adjoints, 2 = every
+                        contraction of the stage                              */
   int storage;       /* propagated state: RTCC3_STORAGE_C128 (default) or
                         RTCC3_STORAGE_C64 (rounded to complex64 after every
                         RK4 step; the step itself is FP64)                    */

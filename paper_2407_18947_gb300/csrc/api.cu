@@ -301,7 +301,7 @@ StageNodes eval_stage(rtcc3_ctx* ctx, int b, const double2* ybase, const double2
   so.field_iters = sweeps;
   so.rotation = ctx->opt.field_solver == 0;
   so.triples_chunk = triples_chunk(ctx);
-  so.tc_all = ctx->opt.tc_all != 0;
+  so.tc_scope = ctx->opt.tc_scope;
   const bool basis_stage = so.triples && so.field_terms && so.rotation;
   if (basis_stage) so.basis = ahead.use;
   (void)ccsd_terms;
@@ -857,7 +857,7 @@ void triples_impl(rtcc3_ctx* ctx, int b, double time, const double2* t1, const d
   so.field_iters = field_sweeps(ctx, b);
   so.rotation = ctx->opt.field_solver == 0;
   so.triples_chunk = triples_chunk(ctx);
-  so.tc_all = ctx->opt.tc_all != 0;
+  so.tc_scope = ctx->opt.tc_scope;
   auto fill = [&](const StageNodes& s) {
     launch_load_amplitudes<R>(t1, t2, E.data(s.t1), E.data(s.t2), ctx->o, ctx->v, ctx->stream);
     launch_field_operator<R>(E.data(s.w), ctx->mu, ctx->fdev + b, ctx->teval, 0.0, ctx->n, ctx->stream);
@@ -1074,7 +1074,7 @@ void rtcc3_default_options(rtcc3_options* opt) {
   opt->spin_budget = 0;
   opt->eig_sweep_cap = 0;
   opt->storage = RTCC3_STORAGE_C128;
-  opt->tc_all = 0;
+  opt->tc_scope = 0;
   opt->checked = 0;
 }
 
@@ -1088,6 +1088,7 @@ int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3
     return RTCC3_ERR_ARG;
   if (ctx->opt.storage != RTCC3_STORAGE_C128 && ctx->opt.storage != RTCC3_STORAGE_C64)
     return RTCC3_ERR_ARG;
+  if (ctx->opt.tc_scope < 0 || ctx->opt.tc_scope > 2) return RTCC3_ERR_ARG;
   ctx->o = nocc; ctx->v = nvir; ctx->n = nocc + nvir; ctx->nb = nbatch;
   ctx->n1 = size_t(nocc) * nvir;
   ctx->n2 = ctx->n1 * ctx->n1;

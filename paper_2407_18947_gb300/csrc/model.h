@@ -49,9 +49,10 @@ struct StageNodes {
 struct StageOptions {
   bool ccsd = true;  // false: R1, R2 hold only the triples terms X1, X2
   bool triples = true;
-  // tensor cores also for the dressing and CCSD contractions (split TF32
-  // only), not only inside the triples
-  bool tc_all = false;
+  // split-TF32 tensor cores beyond the triples: 0 triples only, 1 also the
+  // dressed-integral product g = L~^T L~ (and its adjoints), 2 every
+  // contraction of the stage
+  int tc_scope = 0;
   bool need_grad = true;
   bool field_terms = true;  // include the V-coupling of the triples equation
   bool rotation = true;     // field-dressed eigenbasis (else fixed-point sweeps)

@@ -519,7 +519,7 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   fill(S);
   // contractions recorded while the region is open (and their adjoints) may
   // take the tensor-core route
-  const bool all_tc = opt.tc_all && E.tensor_cores() == 4;
+  const bool all_tc = opt.tc_scope >= 2 && E.tensor_cores() == 4;
   E.set_tc_region(all_tc);
 
   const int Lc = E.external(H.L, {na, n, n});
@@ -550,7 +550,9 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   FieldBasis<R> fb;
   if (opt.triples && opt.field_terms && opt.rotation) fb = start_field_basis(E, H, wt, opt.basis);
   const int g = E.node({n, n, n, n}, false, false);
+  E.set_tc_region(all_tc || (opt.tc_scope >= 1 && E.tensor_cores() == 4));
   E.contract("Ppq,Prs->pqrs", 1.0, E.v(Lt), E.v(Lt), E.v(g), false);
+  E.set_tc_region(all_tc);
   // f~ = h~ + sum_k 2 g~_pqkk - g~_pkkq
   const int ft = E.node({n, n});
   E.axpy(1.0, E.v(ht), E.v(ft));
