@@ -88,7 +88,6 @@ struct rtcc3_ctx {
   double* eps = nullptr;
   double* mu = nullptr;
   std::vector<double> eps_h, mu_h;
-  double e_ref = 0.0;
   // state: nb slots of [t1, t2, l1, l2] (complex128)
   size_t n1 = 0, n2 = 0, ny = 0;
   double2* y = nullptr;
@@ -351,7 +350,6 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
   H.o = ctx->o; H.v = ctx->v; H.n = n; H.naux = na;
   H.eps = ctx->eps;
   H.mu = ctx->mu;
-  H.e_ref = ctx->e_ref;
   // h = diag(eps) - (2J - K) with J, K from the DF factors (FP64 on host:
   // set-up only, O(naux n^2 o))
   std::vector<double> h(size_t(n) * n, 0.0);
@@ -370,10 +368,6 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
       }
       h[p * n + q] -= 2.0 * J - K;
     }
-  double eref = 0.0;
-  for (int i = 0; i < o; ++i) eref += h[i * n + i] + ctx->eps_h[i];
-  ctx->e_ref = eref;
-  H.e_ref = eref;
   std::vector<Cx<R>> hc(size_t(n) * n), Lc(size_t(na) * n * n), ones(n);
   for (size_t t = 0; t < hc.size(); ++t) hc[t] = cmake<R>(R(h[t]), R(0));
   for (size_t t = 0; t < Lc.size(); ++t) Lc[t] = cmake<R>(R(Lfac[t]), R(0));
@@ -509,16 +503,16 @@ void rk4_step(rtcc3_ctx* ctx, double h, const std::vector<int>& sweeps) {
       if (s == 0) {
         PScope ps(ctx->prof, ctx->stream, "observables", 8.0 * ctx->n * ctx->n,
                   double(ctx->n) * ctx->n * (sizeof(Cx<R>) + 24.0));
-        launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->nobs,
-                              ctx->tdesc,
-                              b, ctx->stepdev, ctx->stream);
+        launch_observables<R>(E.grad(S.w), E.data(S.e), yb, ctx->mu, ctx->fdev + b, ctx->tdev,
+                              0.0, ctx->o, ctx->v, ctx->nobs, ctx->tdesc, b, ctx->stepdev,
+                              ctx->stream);
         E.add_launches(1);
       }
       PScope ps(ctx->prof, ctx->stream, "rk4_update", 4.0 * ctx->ny,
                 double(ctx->ny) * sizeof(Cx<R>) + (s < 3 ? 3.0 : 2.0) * ybytes);
       launch_stage_output<R>(E.data(S.r1), E.data(S.r2), E.grad(S.t1), E.grad(S.t2),
-                             s < 3 ? ctx->kbuf : nullptr, ctx->acc, h * ws[s] / 6.0, ctx->o, ctx->v,
-                             ctx->stream);
+                             s < 3 ? ctx->kbuf : nullptr, ctx->acc, h * ws[s] / 6.0, ctx->mu,
+                             ctx->fdev + b, ctx->tdev, cs[s] * h, ctx->o, ctx->v, ctx->stream);
       E.add_launches(1);
     }
     PScope ps(ctx->prof, ctx->stream, "rk4_update", 0.0, 2.0 * ybytes);
@@ -556,9 +550,8 @@ void final_observables(rtcc3_ctx* ctx, const std::vector<int>& sweeps) {
                                  true, sweeps[b]);
     PScope ps(ctx->prof, ctx->stream, "observables", 8.0 * ctx->n * ctx->n,
               double(ctx->n) * ctx->n * (sizeof(Cx<R>) + 24.0));
-    launch_observables<R>(E.grad(S.w), E.data(S.e), ctx->mu, ctx->e_ref, ctx->n, ctx->nobs,
-                              ctx->tdesc, b,
-                          ctx->stepdev, ctx->stream);
+    launch_observables<R>(E.grad(S.w), E.data(S.e), yb, ctx->mu, ctx->fdev + b, ctx->tdev, 0.0,
+                          ctx->o, ctx->v, ctx->nobs, ctx->tdesc, b, ctx->stepdev, ctx->stream);
   }
 }
 
@@ -689,15 +682,16 @@ void residuals_impl(rtcc3_ctx* ctx, int b, double time, double* r_t1, double* r_
                                need_grad, ctx->fdev + b, need_grad || ctx->fhost[b].kind != 0,
                                field_sweeps(ctx, b));
   launch_residual_export<R>(E.data(S.r1), E.data(S.r2), need_grad ? E.grad(S.t1) : nullptr,
-                            need_grad ? E.grad(S.t2) : nullptr, ctx->res, ctx->o, ctx->v, need_grad,
-                            ctx->stream);
+                            need_grad ? E.grad(S.t2) : nullptr, ctx->mu, ctx->fdev + b, ctx->teval,
+                            ctx->res, ctx->o, ctx->v, need_grad, ctx->stream);
   ensure_traj(ctx, 1);
   ensure_obs(ctx, 1);
   ctx->obs_last = 1;
   const TrajDesc td = traj_desc(ctx, ctx->dip_traj, ctx->en_traj, 0);
   RTCC3_CUDA(cudaMemcpyAsync(ctx->tdesc, &td, sizeof(td), cudaMemcpyHostToDevice, ctx->stream));
-  launch_observables<R>(need_grad ? E.grad(S.w) : E.data(S.w), E.data(S.e), ctx->mu, ctx->e_ref,
-                        ctx->n, ctx->nobs, ctx->tdesc, 0, nullptr, ctx->stream);
+  launch_observables<R>(need_grad ? E.grad(S.w) : E.data(S.w), E.data(S.e),
+                        ctx->y + size_t(b) * ctx->ny, ctx->mu, ctx->fdev + b, ctx->teval, 0.0,
+                        ctx->o, ctx->v, ctx->nobs, ctx->tdesc, 0, nullptr, ctx->stream);
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->last_launches = E.launches();
   check_device_timeout<R>(ctx);
@@ -788,8 +782,8 @@ void ground_state_impl(rtcc3_ctx* ctx, double tol, int maxiter) {
     for (int it = 0; it < maxiter; ++it) {
       StageNodes S = eval_stage<R>(ctx, 0, y0, nullptr, 0.0, ctx->teval, 0.0, lam, ctx->fnone, false, 1);
       launch_residual_export<R>(E.data(S.r1), E.data(S.r2), lam ? E.grad(S.t1) : nullptr,
-                                lam ? E.grad(S.t2) : nullptr, ctx->res, ctx->o, ctx->v, lam,
-                                ctx->stream);
+                                lam ? E.grad(S.t2) : nullptr, ctx->mu, ctx->fnone, ctx->teval,
+                                ctx->res, ctx->o, ctx->v, lam, ctx->stream);
       RTCC3_CUDA(cudaMemsetAsync(ctx->maxr, 0, sizeof(double), ctx->stream));
       const int slot = head;
       launch_diis_step(y0 + off, ctx->res + off, ctx->eps, ctx->o, ctx->v, X + slot * len,

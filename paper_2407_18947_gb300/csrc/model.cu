@@ -90,21 +90,37 @@ __device__ __forceinline__ size_t pairT(size_t t, int o, int v) {
   return ((size_t(j) * o + i) * v + b) * v + a;
 }
 
+// w_ia = -E(t) dir . mu_ia (FP64) of the field at the time *tdev + dt.
+__device__ __forceinline__ double field_element(const FieldDev& f, const double* mu, double E,
+                                                size_t nn, size_t pq) {
+  return -E * (f.dir[0] * mu[pq] + f.dir[1] * mu[nn + pq] + f.dir[2] * mu[2 * nn + pq]);
+}
+
 template <typename R>
 __global__ void k_stage_output(const Cx<R>* __restrict__ r1, const Cx<R>* __restrict__ r2,
                                const Cx<R>* __restrict__ g1, const Cx<R>* __restrict__ g2,
                                double2* __restrict__ kout, double2* __restrict__ acc, double hw,
-                               int o, int v) {
+                               const double* __restrict__ mu, const FieldDev* __restrict__ f,
+                               const double* __restrict__ tdev, double dt, int o, int v) {
   const size_t n1 = size_t(o) * v, n2 = n1 * n1;
   const size_t total = 2 * (n1 + n2);
+  const int n = o + v;
+  const double E = field_strength(*f, *tdev + dt);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
     double re, im;  // residual value R; k = -i R (T part) or +i R (lambda part)
     double sgn;
     if (t < n1) { re = r1[t].x; im = r1[t].y; sgn = -1.0; }
     else if (t < n1 + n2) { re = r2[t - n1].x; im = r2[t - n1].y; sgn = -1.0; }
-    else if (t < 2 * n1 + n2) { re = g1[t - n1 - n2].x; im = g1[t - n1 - n2].y; sgn = 1.0; }
-    else {
+    else if (t < 2 * n1 + n2) {
+      const size_t q = t - n1 - n2;
+      // the energy's field term 2 sum_ia w_ia t_ia is kept out of the graph:
+      // its t1 derivative 2 w_ia joins the lambda residual here, in FP64
+      const size_t pq = (q / v) * size_t(n) + o + q % v;
+      re = double(g1[q].x) + 2.0 * field_element(*f, mu, E, size_t(n) * n, pq);
+      im = g1[q].y;
+      sgn = 1.0;
+    } else {
       const size_t q = t - 2 * n1 - n2;
       const size_t p = pairT(q, o, v);
       re = double(g2[q].x) + double(g2[p].x);
@@ -120,27 +136,65 @@ __global__ void k_stage_output(const Cx<R>* __restrict__ r1, const Cx<R>* __rest
 
 template <typename R>
 __global__ void k_observables(const Cx<R>* __restrict__ D, const Cx<R>* __restrict__ e,
-                              const double* __restrict__ mu, double e_ref, int n,
-                              const TrajDesc* __restrict__ td, int slot, const int* step) {
-  // one block per Cartesian component of the dipole, then one per additional
-  // observable; FP64 reduction in fixed order
+                              const double2* __restrict__ t1, const double* __restrict__ mu,
+                              const FieldDev* __restrict__ f, const double* __restrict__ tdev,
+                              double dt, int o, int v, const TrajDesc* __restrict__ td, int slot,
+                              const int* step) {
+  // one block per Cartesian component of the dipole, one per additional
+  // observable, and the last for the energy; FP64 reductions in fixed order.
+  // The graph's density and energy leave out the field-dressed reference
+  // terms, added here in FP64: the energy's 2 sum_i w_ii + 2 sum_ia w_ia t_ia
+  // and, for an operator O, its derivative part 2 sum_i O_ii + 2 sum_ia t_ia O_ia.
   __shared__ double sr[256], si[256];
-  const int x = blockIdx.x;
-  const size_t nn = size_t(n) * n;
+  const int x = blockIdx.x, nobs = td->nobs;
+  const int n = o + v;
+  const size_t nn = size_t(n) * n, n1 = size_t(o) * v;
   double ar = 0.0, ai = 0.0;
   if (x < 3) {
+    const double* m = mu + x * nn;
     for (size_t pq = threadIdx.x; pq < nn; pq += blockDim.x) {
-      const double m = mu[x * nn + pq];
-      ar += double(D[pq].x) * m;
-      ai += double(D[pq].y) * m;
+      ar += double(D[pq].x) * m[pq];
+      ai += double(D[pq].y) * m[pq];
     }
-  } else {
+    for (size_t q = threadIdx.x; q < n1 + o; q += blockDim.x) {
+      if (q < n1) {
+        const double mia = m[(q / v) * size_t(n) + o + q % v];
+        ar += 2.0 * t1[q].x * mia;
+        ai += 2.0 * t1[q].y * mia;
+      } else {
+        ar += 2.0 * m[(q - n1) * size_t(n + 1)];
+      }
+    }
+  } else if (x < int(gridDim.x) - 1) {
+    if (x - 3 >= nobs) return;  // block-uniform
     const double2* op = td->ops + size_t(x - 3) * nn;
     for (size_t pq = threadIdx.x; pq < nn; pq += blockDim.x) {
       const double2 m = op[pq];
       const double dr = double(D[pq].x), di = double(D[pq].y);
       ar += dr * m.x - di * m.y;
       ai += dr * m.y + di * m.x;
+    }
+    for (size_t q = threadIdx.x; q < n1 + o; q += blockDim.x) {
+      if (q < n1) {
+        const double2 m = op[(q / v) * size_t(n) + o + q % v], tq = t1[q];
+        ar += 2.0 * (tq.x * m.x - tq.y * m.y);
+        ai += 2.0 * (tq.x * m.y + tq.y * m.x);
+      } else {
+        const double2 m = op[(q - n1) * size_t(n + 1)];
+        ar += 2.0 * m.x;
+        ai += 2.0 * m.y;
+      }
+    }
+  } else {
+    const double E = field_strength(*f, *tdev + dt);
+    for (size_t q = threadIdx.x; q < n1 + o; q += blockDim.x) {
+      if (q < n1) {
+        const double wia = field_element(*f, mu, E, nn, (q / v) * size_t(n) + o + q % v);
+        ar += 2.0 * t1[q].x * wia;
+        ai += 2.0 * t1[q].y * wia;
+      } else {
+        ar += 2.0 * field_element(*f, mu, E, nn, (q - n1) * size_t(n + 1));
+      }
     }
   }
   sr[threadIdx.x] = ar;
@@ -152,27 +206,36 @@ __global__ void k_observables(const Cx<R>* __restrict__ D, const Cx<R>* __restri
   }
   if (threadIdx.x == 0) {
     const long long ent = (long long)slot * td->stride + (step ? *step : 0);
-    if (x >= 3) {
-      if (td->obs) td->obs[size_t(ent) * td->nobs + (x - 3)] = make_double2(sr[0], si[0]);
-      return;
+    if (x < 3) {
+      if (td->dip) td->dip[size_t(ent) * 3 + x] = make_double2(sr[0], si[0]);
+    } else if (x < int(gridDim.x) - 1) {
+      if (td->obs) td->obs[size_t(ent) * nobs + (x - 3)] = make_double2(sr[0], si[0]);
+    } else if (td->en) {
+      td->en[ent] = make_double2(double(e[0].x) + sr[0], double(e[0].y) + si[0]);
     }
-    if (td->dip) td->dip[size_t(ent) * 3 + x] = make_double2(sr[0], si[0]);
-    if (x == 0 && td->en) td->en[ent] = make_double2(double(e[0].x) - e_ref, double(e[0].y));
   }
 }
 
 template <typename R>
 __global__ void k_residual_export(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1,
-                                  const Cx<R>* g2, double2* out, int o, int v, int have_grad) {
+                                  const Cx<R>* g2, const double* __restrict__ mu,
+                                  const FieldDev* __restrict__ f, const double* __restrict__ tdev,
+                                  double2* out, int o, int v, int have_grad) {
   const size_t n1 = size_t(o) * v, n2 = n1 * n1;
   const size_t total = 2 * (n1 + n2);
+  const int n = o + v;
+  const double E = field_strength(*f, *tdev);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
     double2 r = make_double2(0.0, 0.0);
     if (t < n1) r = make_double2(r1[t].x, r1[t].y);
     else if (t < n1 + n2) r = make_double2(r2[t - n1].x, r2[t - n1].y);
-    else if (have_grad && t < 2 * n1 + n2) r = make_double2(g1[t - n1 - n2].x, g1[t - n1 - n2].y);
-    else if (have_grad) {
+    else if (have_grad && t < 2 * n1 + n2) {
+      // plus the t1 derivative 2 w_ia of the energy's field term (FP64)
+      const size_t q = t - n1 - n2, pq = (q / v) * size_t(n) + o + q % v;
+      r = make_double2(double(g1[q].x) + 2.0 * field_element(*f, mu, E, size_t(n) * n, pq),
+                       g1[q].y);
+    } else if (have_grad) {
       const size_t q = t - 2 * n1 - n2, p = pairT(q, o, v);
       r = make_double2(double(g2[q].x) + double(g2[p].x), double(g2[q].y) + double(g2[p].y));
     }
@@ -355,25 +418,30 @@ void launch_seeds(Cx<R>* ge, Cx<R>* gr1, Cx<R>* gr2, const Cx<R>* l1s, const Cx<
 
 template <typename R>
 void launch_stage_output(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, const Cx<R>* g2,
-                         double2* kout, double2* acc, double hw, int o, int v, cudaStream_t s) {
+                         double2* kout, double2* acc, double hw, const double* mu,
+                         const FieldDev* f, const double* tdev, double dt, int o, int v,
+                         cudaStream_t s) {
   const size_t n1 = size_t(o) * v;
-  k_stage_output<R><<<grid_n(2 * (n1 + n1 * n1)), 256, 0, s>>>(r1, r2, g1, g2, kout, acc, hw, o, v);
+  k_stage_output<R><<<grid_n(2 * (n1 + n1 * n1)), 256, 0, s>>>(r1, r2, g1, g2, kout, acc, hw, mu,
+                                                               f, tdev, dt, o, v);
   RTCC3_CUDA(cudaGetLastError());
 }
 
 template <typename R>
-void launch_observables(const Cx<R>* D, const Cx<R>* e, const double* mu, double e_ref, int n,
-                        int nobs, const TrajDesc* td, int slot, const int* step, cudaStream_t s) {
-  k_observables<R><<<3 + nobs, 256, 0, s>>>(D, e, mu, e_ref, n, td, slot, step);
+void launch_observables(const Cx<R>* D, const Cx<R>* e, const double2* t1, const double* mu,
+                        const FieldDev* f, const double* tdev, double dt, int o, int v, int nobs,
+                        const TrajDesc* td, int slot, const int* step, cudaStream_t s) {
+  k_observables<R><<<4 + nobs, 256, 0, s>>>(D, e, t1, mu, f, tdev, dt, o, v, td, slot, step);
   RTCC3_CUDA(cudaGetLastError());
 }
 
 template <typename R>
 void launch_residual_export(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, const Cx<R>* g2,
-                            double2* out, int o, int v, bool have_grad, cudaStream_t s) {
+                            const double* mu, const FieldDev* f, const double* tdev, double2* out,
+                            int o, int v, bool have_grad, cudaStream_t s) {
   const size_t n1 = size_t(o) * v;
-  k_residual_export<R><<<grid_n(2 * (n1 + n1 * n1)), 256, 0, s>>>(r1, r2, g1, g2, out, o, v,
-                                                                   have_grad ? 1 : 0);
+  k_residual_export<R><<<grid_n(2 * (n1 + n1 * n1)), 256, 0, s>>>(r1, r2, g1, g2, mu, f, tdev,
+                                                                   out, o, v, have_grad ? 1 : 0);
   RTCC3_CUDA(cudaGetLastError());
 }
 
@@ -512,11 +580,15 @@ void launch_stage_prep_acc(double2* acc, const double2* y, size_t ny, cudaStream
   template void launch_seeds<R>(Cx<R>*, Cx<R>*, Cx<R>*, const Cx<R>*, const Cx<R>*, int, int,     \
                                 cudaStream_t);                                                    \
   template void launch_stage_output<R>(const Cx<R>*, const Cx<R>*, const Cx<R>*, const Cx<R>*,    \
-                                       double2*, double2*, double, int, int, cudaStream_t);       \
-  template void launch_observables<R>(const Cx<R>*, const Cx<R>*, const double*, double, int,     \
-                                      int, const TrajDesc*, int, const int*, cudaStream_t);       \
+                                       double2*, double2*, double, const double*,                 \
+                                       const FieldDev*, const double*, double, int, int,          \
+                                       cudaStream_t);                                             \
+  template void launch_observables<R>(const Cx<R>*, const Cx<R>*, const double2*, const double*,  \
+                                      const FieldDev*, const double*, double, int, int, int,      \
+                                      const TrajDesc*, int, const int*, cudaStream_t);            \
   template void launch_residual_export<R>(const Cx<R>*, const Cx<R>*, const Cx<R>*, const Cx<R>*, \
-                                          double2*, int, int, bool, cudaStream_t);                \
+                                          const double*, const FieldDev*, const double*, double2*, \
+                                          int, int, bool, cudaStream_t);                          \
   template void launch_load_amplitudes<R>(const double2*, const double2*, Cx<R>*, Cx<R>*, int,  \
                                           int, cudaStream_t);                                     \
   template void launch_export<R>(const Cx<R>*, double2*, size_t, cudaStream_t);                   \

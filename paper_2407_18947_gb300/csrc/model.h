@@ -30,7 +30,6 @@ struct Hamil {
   R* osum_r = nullptr;     // the same sums rounded once to R
   R* vsum_r = nullptr;
   int* orbit_order = nullptr;  // o^3 occupied blocks, permutation orbits consecutive
-  double e_ref = 0.0;     // sum_i (h_ii + eps_i)
   // mid-gap energy c = (e_homo + e_lumo) / 2 subtracted from every orbital
   // energy (and every field-dressed eigenvalue) entering a sum table: the
   // denominators D = vsum - osum are unchanged (three terms on each side),
@@ -42,7 +41,7 @@ struct Hamil {
 // Node ids of one recorded stage.
 struct StageNodes {
   int t1 = -1, t2 = -1, w = -1;  // leaves
-  int r1 = -1, r2 = -1, e = -1;  // T residuals and the (reference-less) energy
+  int r1 = -1, r2 = -1, e = -1;  // T residuals and the correlation part of the energy
   int t3 = -1;                   // final triples amplitudes (for diagnostics)
 };
 
@@ -96,10 +95,15 @@ void launch_next_field_matrices(const double2* y, const Cx<R>* r1, double ch, co
 template <typename R>
 void launch_seeds(Cx<R>* ge, Cx<R>* gr1, Cx<R>* gr2, const Cx<R>* l1s, const Cx<R>* l2s, int o,
                   int v, cudaStream_t s);
-// k = (-i R1, -i R2, +i g1, +i (g2 + g2^T)); acc += hw * k; optional k copy.
+// k = (-i R1, -i R2, +i (g1 + 2 w_ov), +i (g2 + g2^T)); acc += hw * k; optional
+// k copy. w_ov is the FP64 field operator's occupied-virtual block at time
+// *tdev + dt (the t1 derivative of the energy's field term, kept out of the
+// graph).
 template <typename R>
 void launch_stage_output(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, const Cx<R>* g2,
-                         double2* kout, double2* acc, double hw, int o, int v, cudaStream_t s);
+                         double2* kout, double2* acc, double hw, const double* mu,
+                         const FieldDev* f, const double* tdev, double dt, int o, int v,
+                         cudaStream_t s);
 // Where a propagation writes its observables (device struct, so a captured
 // step graph does not depend on the output buffers of one call): entry
 // (slot * stride + step) of dip (x3) and en.
@@ -114,16 +118,23 @@ struct TrajDesc {
   const double2* ops = nullptr;
   int nobs = 0;
 };
-// dipole[3] = sum_pq D_pq mu^x_pq (FP64) and energy = e - e_ref, written at
-// entry (slot * td->stride + *step) (step may be NULL: entry slot * stride).
+// dipole[3] = sum_pq D_pq mu^x_pq + 2 sum_i mu^x_ii + 2 sum_ia t1_ia mu^x_ia,
+// each additional observable the same with its operator, and energy =
+// e + 2 sum_i w_ii + 2 sum_ia t1_ia w_ia (w at time *tdev + dt), all in FP64:
+// the graph's density D and energy e leave out the field-dressed reference
+// terms. t1 is the FP64 state the stage was evaluated at (its first o*v
+// entries). Written at entry (slot * td->stride + *step) (step may be NULL:
+// entry slot * stride).
 template <typename R>
-void launch_observables(const Cx<R>* D, const Cx<R>* e, const double* mu, double e_ref, int n,
-                        int nobs,
+void launch_observables(const Cx<R>* D, const Cx<R>* e, const double2* t1, const double* mu,
+                        const FieldDev* f, const double* tdev, double dt, int o, int v, int nobs,
                         const TrajDesc* td, int slot, const int* step, cudaStream_t s);
-// Host-readable FP64 copy of the residuals: out = [r1, r2, g1, g2 + g2^T].
+// Host-readable FP64 copy of the residuals: out = [r1, r2, g1 + 2 w_ov, g2 + g2^T]
+// (w at time *tdev).
 template <typename R>
 void launch_residual_export(const Cx<R>* r1, const Cx<R>* r2, const Cx<R>* g1, const Cx<R>* g2,
-                            double2* out, int o, int v, bool have_grad, cudaStream_t s);
+                            const double* mu, const FieldDev* f, const double* tdev, double2* out,
+                            int o, int v, bool have_grad, cudaStream_t s);
 // Jacobi update of one amplitude pair: x1 -= r1 / D1, x2 -= r2 / D2 (orbital-
 // energy denominators, FP64) and max |r| into *maxr.
 void launch_jacobi(double2* x1, double2* x2, const double2* r1, const double2* r2,

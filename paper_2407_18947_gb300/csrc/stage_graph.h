@@ -700,14 +700,18 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   // P_ij^ab on the symmetrised part
   E.combine({{1.0, SD}, {1.0, E.ev("jiba->ijab", SD)}}, R2, false);
 
-  // ---- energy <0|H + [H,T2]|0> - E_ref (Eq. A8); E_ref is subtracted in FP64 ----
+  // ---- energy <0|H + [H,T2]|0> - E_ref (Eq. A8) --------------------------------
+  // With canonical orbitals (F_ia = 0) the dressed expression equals
+  //   2 sum_i w_ii + 2 sum_ia w_ia t_i^a + sum_iajb L_iajb (t_ij^ab + t_i^a t_j^b),
+  // L_iajb = 2 g_iajb - g_ibja (the ov|ov block is not changed by the
+  // dressing). The graph holds the last sum only, so no reference-sized term
+  // is summed in the compute precision; the field terms (and their t1 and w
+  // derivatives) are added in FP64 by the integrator kernels.
   S.e = E.node({});
   const View Ev = E.v(S.e);
-  const int oo = E.node({o, o});
-  E.fill_ones(oo);
-  E.contract("i,i->", 2.0, E.ev("ii->i", blk(ht, "oo")), ones_o, Ev, true);
-  E.contract("ij,ij->", 2.0, E.ev("iijj->ij", G("oooo")), E.v(oo), Ev, true);
-  E.contract("ij,ij->", -1.0, E.ev("ijji->ij", G("oooo")), E.v(oo), Ev, true);
+  const int tL = E.node({o, v}, false, false);
+  E.contract("ia,iajb->jb", 1.0, E.v(S.t1), E.v(Lov), E.v(tL), false);
+  E.contract("jb,jb->", 1.0, E.v(tL), E.v(S.t1), Ev, true);
   E.contract("ijab,iajb->", 1.0, T, E.v(Lov), Ev, true);
   E.set_tc_region(false);
   return S;

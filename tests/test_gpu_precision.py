@@ -41,10 +41,11 @@ def runs():
     return s, amps, out
 
 
-# measured on GB300 (20 steps): split TF32 dipole 3.8e-7 au, energy 1.3e-5 Ha;
-# BF16 8.7e-7 au, 8.4e-6 Ha.  The energy's error comes from its
-# reference-sized one- and two-electron sums, formed in the complex64 graph
-# (only the reference energy is subtracted in FP64).
+# measured on GB300 (20 steps): split TF32 dipole 2.3e-7 au, energy 1.1e-5 Ha;
+# BF16 8.9e-7 au, 8.8e-6 Ha.  At t = 0 both errors are below 1e-7 (the
+# field-dressed reference part of the energy and of the density is added in
+# FP64, outside the complex64 graph); the energy's error then grows about
+# linearly with time: it is the drift of the reduced-precision trajectory.
 @pytest.mark.parametrize("precision,tol_dip,tol_en", [(2, 1e-6, 4e-5), (3, 2.5e-6, 4e-5)])
 def test_reduced_precision_trajectory_against_fp64(runs, precision, tol_dip, tol_en):
     _, _, out = runs
@@ -69,7 +70,8 @@ def test_initial_observables_against_oracle(runs):
     d64, e64 = out[0]
     assert np.abs(d64[0] - res.dipole).max() < 1e-10 * np.abs(res.dipole).max()
     assert abs(e64[0] - res.energy) < 1e-10 * max(1.0, abs(res.energy))
-    for prec, tol_d, tol_e in ((2, 1e-6, 4e-5), (3, 2.5e-6, 4e-5)):
+    # measured: split TF32 dipole 7.7e-8 au, energy 6.0e-8 Ha; BF16 6.2e-8, 6.0e-8
+    for prec, tol_d, tol_e in ((2, 4e-7, 4e-7), (3, 4e-7, 4e-7)):
         d, e = out[prec]
         assert np.abs(d[0].real - res.dipole.real).max() < tol_d
         assert abs(e[0].real - res.energy.real) < tol_e
