@@ -232,26 +232,60 @@ k_contract(const Cx<R>* __restrict__ A, const Cx<R>* __restrict__ B, Cx<R>* __re
 #pragma unroll
     for (int j = 0; j < TN; ++j) { accr[i][j] = R(0); acci[i][j] = R(0); }
   const Cx<R> zero = cmake<R>(R(0), R(0));
+  // each thread stages the same (row, k-offset) slots of every K slice: the
+  // row offsets are looked up once, and the next slice is loaded into
+  // registers while the current one is multiplied
+  constexpr int LA = (BM * BK + kThreads - 1) / kThreads;
+  constexpr int LB = (BN * BK + kThreads - 1) / kThreads;
+  long long arow[LA], brow[LB];
+  bool aok[LA], bok[LB];
+  Cx<R> ra[LA], rb[LB];
+#pragma unroll
+  for (int l = 0; l < LA; ++l) {
+    const int e = l * kThreads + tid;
+    const int mm = A_KC ? e / BK : e % BM;
+    aok[l] = e < BM * BK && m0 + mm < M;
+    arow[l] = aok[l] ? aM[m0 + mm] : 0;
+  }
+#pragma unroll
+  for (int l = 0; l < LB; ++l) {
+    const int e = l * kThreads + tid;
+    const int nn = B_KC ? e / BK : e % BN;
+    bok[l] = e < BN * BK && n0 + nn < N;
+    brow[l] = bok[l] ? bN[n0 + nn] : 0;
+  }
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int l = 0; l < LA; ++l) {
+      const int e = l * kThreads + tid;
+      const int k = k0 + (A_KC ? e % BK : e / BM);
+      ra[l] = (aok[l] && k < kend) ? Ab[arow[l] + aK[k]] : zero;
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int e = l * kThreads + tid;
+      const int k = k0 + (B_KC ? e % BK : e / BN);
+      rb[l] = (bok[l] && k < kend) ? Bb[brow[l] + bK[k]] : zero;
+    }
+  };
+  if (kbeg < kend) load(kbeg);
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-    for (int e0 = 0; e0 < BM * BK; e0 += kThreads) {
-      const int e = e0 + tid;
+    for (int l = 0; l < LA; ++l) {
+      const int e = l * kThreads + tid;
       if ((BM * BK) % kThreads != 0 && e >= BM * BK) break;
-      int mm, kk;
-      if (A_KC) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
-      const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < kend) ? Ab[aM[m] + aK[k]] : zero;
+      if (A_KC) As[e % BK][e / BK] = ra[l];
+      else As[e / BM][e % BM] = ra[l];
     }
 #pragma unroll
-    for (int e0 = 0; e0 < BN * BK; e0 += kThreads) {
-      const int e = e0 + tid;
+    for (int l = 0; l < LB; ++l) {
+      const int e = l * kThreads + tid;
       if ((BN * BK) % kThreads != 0 && e >= BN * BK) break;
-      int nn, kk;
-      if (B_KC) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
-      const int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < kend) ? Bb[bN[n] + bK[k]] : zero;
+      if (B_KC) Bs[e % BK][e / BK] = rb[l];
+      else Bs[e / BN][e % BN] = rb[l];
     }
     __syncthreads();
+    if (k0 + BK < kend) load(k0 + BK);
 #pragma unroll 8
     for (int kk = 0; kk < BK; ++kk) {
       Cx<R> a[TM], bv[TN];
