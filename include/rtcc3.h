@@ -176,6 +176,18 @@ int rtcc3_propagate_rk4(rtcc3_ctx* ctx, double h, int nsteps, double* dipole, do
 int rtcc3_propagate_rk4_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_dev,
                             void* energy_dev, void* stream);
 
+/* Trajectory in chunks: as rtcc3_propagate_rk4 / rtcc3_propagate_rk4_dev
+ * but without the evaluation of the final state, so dipole holds nbatch x
+ * nsteps x 3 and energy nbatch x nsteps complex entries, entry n from the
+ * state at t0 + n h (n < nsteps).  The state the chunk ends in is entry 0 of
+ * the next chunk: consecutive chunks give the rtcc3_propagate_rk4 trajectory
+ * with every RK4 step evaluated once (Section 2.1: four stage evaluations
+ * per step, the observables of the step's start state from its first stage). */
+int rtcc3_propagate_rk4_chunk(rtcc3_ctx* ctx, double h, int nsteps, double* dipole,
+                              double* energy);
+int rtcc3_propagate_rk4_chunk_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_dev,
+                                  void* energy_dev, void* stream);
+
 /* Triples map of slot b's Hamiltonian at `time` (device buffers, interleaved
  * complex double): (t1, t2) -> (X1, X2), the triples contributions to the T
  * residuals (Eqs. A21-A22), and its holomorphic vector-Jacobian product

@@ -57,6 +57,8 @@ SIGNATURES = {
     "rtcc3_solve_ground_state": (_I, [_P, _D, _I]),
     "rtcc3_propagate_rk4": (_I, [_P, _D, _I, _DP, _DP]),
     "rtcc3_propagate_rk4_dev": (_I, [_P, _D, _I, _P, _P, _P]),
+    "rtcc3_propagate_rk4_chunk": (_I, [_P, _D, _I, _DP, _DP]),
+    "rtcc3_propagate_rk4_chunk_dev": (_I, [_P, _D, _I, _P, _P, _P]),
     "rtcc3_triples_forward_dev": (_I, [_P, _I, _D, _P, _P, _P, _P, _P]),
     "rtcc3_triples_vjp_dev": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, _P, _P]),
     "rtcc3_triples_forward_noalloc_dev": (_I, [_P, _I, _D, _P, _P, _P, _P, _P]),

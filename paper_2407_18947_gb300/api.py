@@ -145,6 +145,20 @@ class RTCC3:
                                                      ctypes.c_void_p(en_ptr),
                                                      ctypes.c_void_p(stream_ptr or 0)))
 
+    def propagate_rk4_chunk(self, h, nsteps):
+        """nsteps RK4 steps recording the state at the start of each step only
+        (entries 0..nsteps-1); the final state is entry 0 of the next chunk."""
+        dip = np.zeros((self.nbatch, nsteps, 3), np.complex128)
+        en = np.zeros((self.nbatch, nsteps), np.complex128)
+        self._check(self.lib.rtcc3_propagate_rk4_chunk(self.h, h, nsteps, _dp(dip), _dp(en)))
+        return dip, en
+
+    def propagate_rk4_chunk_dev(self, h, nsteps, dip_ptr, en_ptr, stream_ptr=None):
+        self._check(self.lib.rtcc3_propagate_rk4_chunk_dev(self.h, h, nsteps,
+                                                           ctypes.c_void_p(dip_ptr),
+                                                           ctypes.c_void_p(en_ptr),
+                                                           ctypes.c_void_p(stream_ptr or 0)))
+
     def triples_forward_dev(self, b, time, t1_ptr, t2_ptr, x1_ptr, x2_ptr, stream_ptr=None):
         P = ctypes.c_void_p
         self._check(self.lib.rtcc3_triples_forward_dev(self.h, b, time, P(t1_ptr), P(t2_ptr), P(x1_ptr),

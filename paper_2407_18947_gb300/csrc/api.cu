@@ -582,7 +582,8 @@ void drop_graph(rtcc3_ctx* ctx) {
 }
 
 template <typename R>
-void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2* en, size_t stride) {
+void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2* en, size_t stride,
+                    bool final) {
   Engine<R>& E = ctx->run<R>().E;
   std::vector<int> sweeps(ctx->nb);
   for (int b = 0; b < ctx->nb; ++b) sweeps[b] = field_sweeps(ctx, b);
@@ -651,7 +652,7 @@ void propagate_impl(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2*
     launches += E.launches();
   }
   E.reset_launch_count();
-  final_observables<R>(ctx, sweeps);
+  if (final) final_observables<R>(ctx, sweeps);
   ctx->last_launches = launches + E.launches();
   RTCC3_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->time += h * nsteps;
@@ -1251,11 +1252,14 @@ int rtcc3_solve_ground_state(rtcc3_ctx* ctx, double tol, int maxiter) {
 }
 
 static int propagate_common(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, double2* en,
-                            bool host, double* dip_h, double* en_h) {
+                            bool host, double* dip_h, double* en_h, bool final) {
   return guarded(ctx, [&] {
     require_ham(ctx);
     RTCC3_CHECK(nsteps >= 0 && std::isfinite(h) && h != 0.0, RTCC3_ERR_ARG, "bad step size or count");
-    const size_t entries = size_t(nsteps) + 1;
+    // a chunk records the state at the start of each step only; the state it
+    // ends in is entry 0 of the next chunk
+    const size_t entries = size_t(nsteps) + (final ? 1 : 0);
+    if (entries == 0) return;
     double2* d = dip;
     double2* e = en;
     if (host) {
@@ -1263,8 +1267,8 @@ static int propagate_common(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, 
       d = ctx->dip_traj;
       e = ctx->en_traj;
     }
-    if (ctx->fp64()) propagate_impl<double>(ctx, h, nsteps, d, e, entries);
-    else propagate_impl<float>(ctx, h, nsteps, d, e, entries);
+    if (ctx->fp64()) propagate_impl<double>(ctx, h, nsteps, d, e, entries, final);
+    else propagate_impl<float>(ctx, h, nsteps, d, e, entries, final);
     if (host) {
       if (dip_h)
         RTCC3_CUDA(cudaMemcpy(dip_h, d, entries * ctx->nb * 3 * sizeof(double2), cudaMemcpyDeviceToHost));
@@ -1274,14 +1278,8 @@ static int propagate_common(rtcc3_ctx* ctx, double h, int nsteps, double2* dip, 
   });
 }
 
-int rtcc3_propagate_rk4(rtcc3_ctx* ctx, double h, int nsteps, double* dipole, double* energy) {
-  if (!ctx) return RTCC3_ERR_ARG;
-  return propagate_common(ctx, h, nsteps, nullptr, nullptr, true, dipole, energy);
-}
-
-int rtcc3_propagate_rk4_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_dev,
-                            void* energy_dev, void* stream) {
-  if (!ctx) return RTCC3_ERR_ARG;
+static int propagate_dev_common(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_dev,
+                                void* energy_dev, void* stream, bool final) {
   // the work runs on the context stream; an external stream is ordered
   // before and after it with events
   cudaStream_t ext = static_cast<cudaStream_t>(stream);
@@ -1294,7 +1292,8 @@ int rtcc3_propagate_rk4_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_d
       cudaEventDestroy(ev);
     }
     const int rc = propagate_common(ctx, h, nsteps, static_cast<double2*>(dipole_dev),
-                                    static_cast<double2*>(energy_dev), false, nullptr, nullptr);
+                                    static_cast<double2*>(energy_dev), false, nullptr, nullptr,
+                                    final);
     if (rc != RTCC3_OK) throw Error(rc, ctx->err);
     if (ext) {
       cudaEvent_t ev;
@@ -1304,6 +1303,29 @@ int rtcc3_propagate_rk4_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_d
       cudaEventDestroy(ev);
     }
   });
+}
+
+int rtcc3_propagate_rk4(rtcc3_ctx* ctx, double h, int nsteps, double* dipole, double* energy) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return propagate_common(ctx, h, nsteps, nullptr, nullptr, true, dipole, energy, true);
+}
+
+int rtcc3_propagate_rk4_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_dev,
+                            void* energy_dev, void* stream) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return propagate_dev_common(ctx, h, nsteps, dipole_dev, energy_dev, stream, true);
+}
+
+int rtcc3_propagate_rk4_chunk(rtcc3_ctx* ctx, double h, int nsteps, double* dipole,
+                              double* energy) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return propagate_common(ctx, h, nsteps, nullptr, nullptr, true, dipole, energy, false);
+}
+
+int rtcc3_propagate_rk4_chunk_dev(rtcc3_ctx* ctx, double h, int nsteps, void* dipole_dev,
+                                  void* energy_dev, void* stream) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  return propagate_dev_common(ctx, h, nsteps, dipole_dev, energy_dev, stream, false);
 }
 
 int rtcc3_triples_forward_dev(rtcc3_ctx* ctx, int b, double time, const void* t1, const void* t2,

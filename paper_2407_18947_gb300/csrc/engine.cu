@@ -959,8 +959,9 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
     return ref;
   }
   // tile shape: 64 x 64; 16 x 256 (256 x 16) when one side is at most 16;
-  // 16 x 16 with 64-deep K slices for skinny outputs with long sums
-  P->small_tile = std::max(M, N) <= 48 && K >= 1024;
+  // 16 x 16 with 64-deep K slices for small outputs with long sums, and for
+  // small products whose whole sum is one such slice (more CTAs, one pass)
+  P->small_tile = std::max(M, N) <= 48 && (K >= 1024 || K <= kSBK);
   if (!P->small_tile && M <= 16 && N > 64) P->tile = 1;
   else if (!P->small_tile && N <= 16 && M > 64) P->tile = 2;
   int bmm = kBM, bnn = kBN, bk = kBK;

@@ -159,6 +159,33 @@ def test_batched_slots_match_single(water1):
         assert np.array_equal(dip[b], d1[0]) and np.array_equal(en[b], n1[0])
 
 
+@pytest.mark.parametrize("graphs", [True, False])
+def test_chunked_trajectory_equals_one_call(water1, graphs):
+    """Chunks of 2 + 3 + 1 steps give the 6-step trajectory of one call
+    (entries 0..5) and end in the same state, to rounding: a chunk starts by
+    decomposing its first stage's field eigenbasis from the state, where one
+    call reuses the basis its previous step looked ahead to (the same matrix
+    up to rounding)."""
+    s, ham, y0 = water1
+    amps = [x.numpy() for x in y0]
+    eng = _engine(s, use_graphs=graphs)
+    eng.set_field(0, 2, 0.002, omega=0.0656, direction=(0, 0, 1))
+    eng.set_amplitudes(0, *amps)
+    dip, en = eng.propagate_rk4(0.01, 6)
+    end = eng.get_amplitudes(0)
+    eng.set_amplitudes(0, *amps)
+    eng.set_time(0.0)
+    parts = [eng.propagate_rk4_chunk(0.01, n) for n in (2, 3, 1)]
+    end_c = eng.get_amplitudes(0)
+    eng.close()
+    dc = np.concatenate([p[0] for p in parts], axis=1)
+    ec = np.concatenate([p[1] for p in parts], axis=1)
+    assert dc.shape == (1, 6, 3) and ec.shape == (1, 6)
+    assert _rel(dc, dip[:, :6]) < 1e-12 and _rel(ec, en[:, :6]) < 1e-12
+    for a, b in zip(end_c, end):
+        assert _rel(a, b) < 1e-12
+
+
 def test_nonfinite_state_is_reported(water1):
     s, ham, y0 = water1
     eng = _engine(s)
