@@ -129,6 +129,30 @@ const char* rtcc3_last_error(const rtcc3_ctx* ctx);
 int rtcc3_set_hamiltonian(rtcc3_ctx* ctx, const double* eps, int naux, const double* Lfac,
                           const double* dipole);
 
+/* Hamiltonian from dense chemists' integrals eri[nmo][nmo][nmo][nmo] = (pq|rs)
+ * (real, with the symmetries (pq|rs) = (qp|rs) = (rs|pq), positive
+ * semidefinite as a matrix over the pairs (pq)), otherwise as
+ * rtcc3_set_hamiltonian.  The integrals enter through their pivoted Cholesky
+ * factors (rtcc3_eri_cholesky with tol 1e-12: every integral reproduced to
+ * 1e-12), which the T1 transformation of Eq. A4 then dresses as DF factors.
+ * RTCC3_ERR_ARG if eri is non-finite, not symmetric or not positive
+ * semidefinite. */
+int rtcc3_set_hamiltonian_eri(rtcc3_ctx* ctx, const double* eps, const double* eri,
+                              const double* dipole);
+
+/* Pivoted (incomplete) Cholesky factorisation of the integral matrix
+ * V[(pq)][(rs)] = (pq|rs) on the host, no context or GPU needed: L[k][p][q],
+ * k < *rank, with V - sum_k L_k L_k^T positive semidefinite and its largest
+ * diagonal element <= tol (so every integral is reproduced to within tol).
+ * Each step takes the largest remaining diagonal element as the pivot.
+ * Lfac holds max_rank x nmo x nmo doubles (caller-owned).  Returns
+ * RTCC3_ERR_ARG for bad sizes, non-finite, asymmetric or indefinite input
+ * (a remaining diagonal element below -tol), RTCC3_ERR_NOT_CONVERGED if
+ * max_rank factors do not reach tol (*rank = max_rank, the factors so far
+ * in Lfac). */
+int rtcc3_eri_cholesky(int nmo, const double* eri, double tol, int max_rank, double* Lfac,
+                       int* rank);
+
 /* Field of slot b (0 <= b < nbatch): kind RTCC3_FIELD_*, amplitude A (au),
  * omega, center, width (au; the ramp duration t_r for LRCW / QRCW) and a
  * Cartesian direction dir[3]; the perturbation is V = -E(t) dir . mu. */

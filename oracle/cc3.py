@@ -56,20 +56,27 @@ def _ct(x):
 class Hamiltonian:
     """Closed-shell Hamiltonian of Eqs. A1-A3 from orbital energies and DF factors.
 
-    ``(pq|rs) = sum_P L[P,p,q] L[P,r,s]``.  The core operator is
+    ``(pq|rs) = sum_P L[P,p,q] L[P,r,s]``, or the dense chemists' integrals
+    themselves (``eri``, then ``Lfac`` is None and the T1 transformation
+    acts on the four-index tensor directly).  The core operator is
     ``h = f - G[D_ref]`` with ``G_pq = sum_k 2(pq|kk) - (pk|kq)`` so that the
     reference Fock operator is exactly ``F = sum_p eps_p E_pp`` (Eq. A2).
     """
 
-    def __init__(self, eps, Lfac, dipole, nocc: int):
+    def __init__(self, eps, Lfac, dipole, nocc: int, eri=None):
         self.o = int(nocc)
         self.eps = torch.as_tensor(np.asarray(eps), dtype=RD)
         self.n = self.eps.numel()
         self.v = self.n - self.o
-        self.L = torch.as_tensor(np.asarray(Lfac), dtype=RD)
         self.mu = torch.as_tensor(np.asarray(dipole), dtype=RD)
         o = self.o
-        g = torch.einsum('Ppq,Prs->pqrs', self.L, self.L)
+        if eri is not None:
+            self.L = None
+            g = torch.as_tensor(np.asarray(eri), dtype=RD).reshape(self.n, self.n, self.n, self.n)
+            self.g = g
+        else:
+            self.L = torch.as_tensor(np.asarray(Lfac), dtype=RD)
+            g = torch.einsum('Ppq,Prs->pqrs', self.L, self.L)
         J = torch.einsum('pqkk->pq', g[:, :, :o, :o])
         K = torch.einsum('pkkq->pq', g[:, :o, :o, :])
         self.h = torch.diag(self.eps) - (2.0 * J - K)
@@ -159,10 +166,18 @@ def dress(ham: Hamiltonian, t1: torch.Tensor, w: torch.Tensor):
     eye = torch.eye(n, dtype=CD)
     X = eye - tau
     Y = eye + tau
-    Lt = torch.einsum('pr,Prs,sq->Ppq', X, ham.L.to(CD), Y)
     ht = X @ (ham.h.to(CD) + w) @ Y
     wt = X @ w @ Y
-    gt = torch.einsum('Ppq,Prs->pqrs', Lt, Lt)
+    if ham.L is not None:
+        Lt = torch.einsum('pr,Prs,sq->Ppq', X, ham.L.to(CD), Y)
+        gt = torch.einsum('Ppq,Prs->pqrs', Lt, Lt)
+    else:
+        # (pq|rs)~ = sum X_pt Y_uq X_rv Y_ws (tu|vw), one index at a time
+        g = ham.g.to(CD)
+        g = torch.einsum('pt,tuvw->puvw', X, g)
+        g = torch.einsum('puvw,uq->pqvw', g, Y)
+        g = torch.einsum('rv,pqvw->pqrw', X, g)
+        gt = torch.einsum('pqrw,ws->pqrs', g, Y)
     J = torch.einsum('pqkk->pq', gt[:, :, :o, :o])
     K = torch.einsum('pkkq->pq', gt[:, :o, :o, :])
     ft = ht + 2.0 * J - K

@@ -48,6 +48,8 @@ SIGNATURES = {
     "rtcc3_destroy": (_I, [_P]),
     "rtcc3_last_error": (ctypes.c_char_p, [_P]),
     "rtcc3_set_hamiltonian": (_I, [_P, _DP, _I, _DP, _DP]),
+    "rtcc3_set_hamiltonian_eri": (_I, [_P, _DP, _DP, _DP]),
+    "rtcc3_eri_cholesky": (_I, [_I, _DP, _D, _I, _DP, ctypes.POINTER(ctypes.c_int)]),
     "rtcc3_set_field": (_I, [_P, _I, _I, _D, _D, _D, _D, _DP]),
     "rtcc3_set_amplitudes": (_I, [_P, _I, _DP, _DP, _DP, _DP]),
     "rtcc3_get_amplitudes": (_I, [_P, _I, _DP, _DP, _DP, _DP]),

@@ -95,6 +95,17 @@ class RTCC3:
         self._check(self.lib.rtcc3_set_hamiltonian(self.h, _dp(eps), Lfac.shape[0], _dp(Lfac),
                                                    _dp(dipole)))
 
+    def set_hamiltonian_eri(self, eps, eri, dipole):
+        """Hamiltonian from dense chemists' integrals (pq|rs), factored by the
+        library (pivoted Cholesky, ``rtcc3_set_hamiltonian_eri``)."""
+        n = self.nocc + self.nvir
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        eri = np.ascontiguousarray(eri, dtype=np.float64)
+        dipole = np.ascontiguousarray(dipole, dtype=np.float64)
+        if eps.shape != (n,) or eri.shape != (n, n, n, n) or dipole.shape != (3, n, n):
+            raise ValueError("Hamiltonian arrays have the wrong shape")
+        self._check(self.lib.rtcc3_set_hamiltonian_eri(self.h, _dp(eps), _dp(eri), _dp(dipole)))
+
     def set_field(self, b, kind, amplitude=0.0, omega=0.0, center=0.0, width=1.0,
                   direction=(0.0, 0.0, 1.0)):
         d = np.ascontiguousarray(direction, dtype=np.float64)
@@ -253,6 +264,24 @@ class RTCC3:
         return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms,
                                         "flops": arr[i].flops, "bytes": arr[i].bytes}
                 for i in range(cnt.value)}
+
+
+def eri_cholesky(eri, tol=1e-12, max_rank=None):
+    """Pivoted Cholesky factors L[k, p, q] of dense integrals eri[p, q, r, s]
+    (``rtcc3_eri_cholesky``, host only): sum_k L[k,p,q] L[k,r,s] reproduces
+    every integral to within tol."""
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    n = eri.shape[0]
+    if eri.shape != (n, n, n, n):
+        raise ValueError("eri must have shape (n, n, n, n)")
+    max_rank = n * n if max_rank is None else int(max_rank)
+    L = np.zeros((max_rank, n, n), np.float64)
+    rank = ctypes.c_int(0)
+    lib = _lib.load()
+    rc = lib.rtcc3_eri_cholesky(n, _dp(eri), float(tol), max_rank, _dp(L), ctypes.byref(rank))
+    if rc != 0:
+        raise RTCC3Error(rc, "rtcc3_eri_cholesky failed")
+    return L[:rank.value].copy()
 
 
 def measure_peaks(device: int = 0) -> dict:

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <deque>
 #include <memory>
+#include <new>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1157,6 +1158,106 @@ int rtcc3_set_hamiltonian(rtcc3_ctx* ctx, const double* eps, int naux, const dou
     ctx->free_at_setup = fr;
     ctx->have_ham = true;
   });
+}
+
+namespace {
+
+// Pivoted Cholesky factors of V[(pq)][(rs)] = (pq|rs): the pivot is the
+// largest remaining diagonal element, the new factor the pivot's residual
+// column over its square root, until every remaining diagonal element is
+// <= tol (the residual is positive semidefinite, so no integral then differs
+// by more than tol).  Row p of V is read for column p (V symmetric).
+int eri_cholesky_impl(int n, const double* eri, double tol, int max_rank,
+                      std::vector<double>& L, int& rank) {
+  rank = 0;
+  if (n < 1 || !eri || !(tol > 0.0) || max_rank < 1) return RTCC3_ERR_ARG;
+  const size_t N = size_t(n) * n;
+  double vmax = 0.0;
+  for (size_t i = 0; i < N * N; ++i) {
+    if (!std::isfinite(eri[i])) return RTCC3_ERR_ARG;
+    vmax = std::max(vmax, std::fabs(eri[i]));
+  }
+  const double symtol = 1e-12 * std::max(1.0, vmax);
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < n; ++r)
+        for (int s = 0; s < n; ++s) {
+          const double x = eri[((size_t(p) * n + q) * n + r) * n + s];
+          if (std::fabs(x - eri[((size_t(q) * n + p) * n + r) * n + s]) > symtol ||
+              std::fabs(x - eri[((size_t(r) * n + s) * n + p) * n + q]) > symtol)
+            return RTCC3_ERR_ARG;
+        }
+  std::vector<double> d(N);
+  for (size_t i = 0; i < N; ++i) d[i] = eri[i * N + i];
+  L.clear();
+  while (true) {
+    size_t piv = 0;
+    for (size_t i = 1; i < N; ++i)
+      if (d[i] > d[piv]) piv = i;
+    const double dp = d[piv];
+    if (dp <= tol) break;
+    if (rank >= max_rank) return RTCC3_ERR_NOT_CONVERGED;
+    L.resize(size_t(rank + 1) * N);
+    double* Lr = L.data() + size_t(rank) * N;
+    const double* row = eri + piv * N;
+    for (size_t i = 0; i < N; ++i) Lr[i] = row[i];
+    for (int k = 0; k < rank; ++k) {
+      const double* Lk = L.data() + size_t(k) * N;
+      const double lk = Lk[piv];
+      if (lk != 0.0)
+        for (size_t i = 0; i < N; ++i) Lr[i] -= lk * Lk[i];
+    }
+    const double sc = 1.0 / std::sqrt(dp);
+    for (size_t i = 0; i < N; ++i) {
+      Lr[i] *= sc;
+      d[i] -= Lr[i] * Lr[i];
+    }
+    d[piv] = 0.0;
+    ++rank;
+  }
+  for (size_t i = 0; i < N; ++i)
+    if (d[i] < -tol) return RTCC3_ERR_ARG;  // not positive semidefinite
+  return RTCC3_OK;
+}
+
+}  // namespace
+
+int rtcc3_eri_cholesky(int nmo, const double* eri, double tol, int max_rank, double* Lfac,
+                       int* rank) {
+  if (!Lfac || !rank) return RTCC3_ERR_ARG;
+  try {
+    std::vector<double> L;
+    int r = 0;
+    const int rc = eri_cholesky_impl(nmo, eri, tol, max_rank, L, r);
+    *rank = r;
+    if (r > 0) std::copy(L.begin(), L.begin() + size_t(r) * nmo * nmo, Lfac);
+    return rc;
+  } catch (const std::bad_alloc&) {
+    return RTCC3_ERR_OOM;
+  } catch (...) {
+    return RTCC3_ERR_ARG;
+  }
+}
+
+int rtcc3_set_hamiltonian_eri(rtcc3_ctx* ctx, const double* eps, const double* eri,
+                              const double* dipole) {
+  if (!ctx) return RTCC3_ERR_ARG;
+  if (!eps || !eri || !dipole) return fail(ctx, RTCC3_ERR_ARG, "null input");
+  std::vector<double> L;
+  int rank = 0;
+  int rc;
+  try {
+    rc = eri_cholesky_impl(ctx->n, eri, 1e-12, ctx->n * ctx->n, L, rank);
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, RTCC3_ERR_OOM, "host allocation failed in the Cholesky factorisation");
+  }
+  if (rc != RTCC3_OK)
+    return fail(ctx, rc, "two-electron integrals not finite, not symmetric or not positive semidefinite");
+  if (rank == 0) {  // all integrals below the tolerance: one zero factor
+    rank = 1;
+    L.assign(size_t(ctx->n) * ctx->n, 0.0);
+  }
+  return rtcc3_set_hamiltonian(ctx, eps, rank, L.data(), dipole);
 }
 
 int rtcc3_set_field(rtcc3_ctx* ctx, int b, int kind, double amplitude, double omega, double center,

@@ -812,6 +812,35 @@ void* Engine<R>::scratch(int slot, size_t bytes) {
   return scratch_[slot];
 }
 
+// Resident CTAs per SM of the k_contract instantiation a plan launches
+// (registers decide it; cached per tile shape and operand layout).
+template <typename R>
+int simt_ctas_per_sm(bool small_tile, int tile, bool akc, bool bkc) {
+  static int cache[4][2][2] = {};
+  int& c = cache[small_tile ? 3 : tile][akc ? 1 : 0][bkc ? 1 : 0];
+  if (c > 0) return c;
+  auto q = [&](auto kern) {
+    RTCC3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kern, kThreads, 0));
+  };
+#define RTCC3_OCC(TBM, TBN, TBK, TTM, TTN)                                       \
+  if (akc && bkc) q(k_contract<R, true, true, TBM, TBN, TBK, TTM, TTN>);        \
+  else if (akc) q(k_contract<R, true, false, TBM, TBN, TBK, TTM, TTN>);         \
+  else if (bkc) q(k_contract<R, false, true, TBM, TBN, TBK, TTM, TTN>);         \
+  else q(k_contract<R, false, false, TBM, TBN, TBK, TTM, TTN>)
+  if (small_tile) {
+    RTCC3_OCC(kSBM, kSBM, kSBK, 1, 1);
+  } else if (tile == 1) {
+    RTCC3_OCC(16, 256, kTBK, 4, 4);
+  } else if (tile == 2) {
+    RTCC3_OCC(256, 16, kTBK, 4, 4);
+  } else {
+    RTCC3_OCC(kBM, kBN, kBK, 4, 4);
+  }
+#undef RTCC3_OCC
+  c = std::max(c, 1);
+  return c;
+}
+
 template <typename R>
 ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View& B, const View& Cv) {
   // tensor cores only inside the tensor-core region (the triples): the
@@ -968,13 +997,34 @@ ContractPlan& Engine<R>::plan(const std::string& spec, const View& A, const View
   if (P->small_tile) { bmm = bnn = kSBM; bk = kSBK; }
   else if (P->tile == 1) { bmm = 16; bnn = 256; bk = kTBK; }
   else if (P->tile == 2) { bmm = 256; bnn = 16; bk = kTBK; }
-  // split-K when the output tiles alone do not fill the GPU
+  // split-K when the output tiles alone do not fill the GPU: from about four
+  // CTAs per SM up, the fewest splits (each at least four K slices) whose
+  // CTAs fill their last wave of resident CTAs to 90 %, else the best-filled
+  // count
   const long long tiles = ((M + bmm - 1) / bmm) * ((N + bnn - 1) / bnn) * NB;
   int nsplit = 1;
   if (tiles < 2 * 152 && K > 4 * bk) {
-    const long long want = (4 * 152 + tiles - 1) / tiles;
     const long long maxs = (K + 4 * bk - 1) / (4 * bk);
-    nsplit = int(std::max<long long>(1, std::min(want, maxs)));
+    const long long slots = 152LL * simt_ctas_per_sm<R>(P->small_tile, P->tile, P->a_kcontig,
+                                                         P->b_kcontig);
+    // at least enough splits for four CTAs per SM (more CTAs hide latency)
+    const long long want = std::min(maxs, (4 * 152 + tiles - 1) / tiles);
+    double best_eff = -1.0;
+    for (long long ns = std::max<long long>(1, want); ns <= maxs; ++ns) {
+      long long kc = (K + ns - 1) / ns;
+      kc = ((kc + bk - 1) / bk) * bk;
+      const long long used = (K + kc - 1) / kc;
+      const long long ctas = tiles * used, waves = (ctas + slots - 1) / slots;
+      const double eff = double(ctas) / double(waves * slots);
+      if (eff >= 0.9 && ctas >= slots) {
+        nsplit = int(used);
+        break;
+      }
+      if (eff > best_eff + 1e-9) {
+        best_eff = eff;
+        nsplit = int(used);
+      }
+    }
   }
   int kchunk = int((K + nsplit - 1) / nsplit);
   kchunk = ((kchunk + bk - 1) / bk) * bk;

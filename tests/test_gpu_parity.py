@@ -56,6 +56,35 @@ def test_residuals_fp64_match_oracle(ov, direction, amp):
     eng.close()
 
 
+def test_dense_integrals_match_oracle():
+    """rtcc3_set_hamiltonian_eri (dense (pq|rs), factored by the library)
+    against the oracle's four-index dressing of the same integrals, and
+    against the DF-factor entry point of the same system, FP64, with a field."""
+    o, v = 4, 11
+    s = make_system(o, v, seed=77)
+    eri = np.einsum('Ppq,Prs->pqrs', s.Lfac, s.Lfac)
+    ham = cc3.Hamiltonian(s.eps, None, s.dipole, s.nocc, eri=eri)
+    t1, t2, l1, l2 = random_amplitudes(o, v, seed=6, t1_scale=0.05)
+    from paper_2407_18947_gb300.api import RTCC3
+    got = {}
+    for form in ("eri", "df"):
+        eng = RTCC3(o, v, precision=0)
+        if form == "eri":
+            eng.set_hamiltonian_eri(s.eps, eri, s.dipole)
+        else:
+            eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+        eng.set_field(0, 1, 0.01, direction=(0.3, 0.2, 1.0))
+        eng.set_amplitudes(0, t1, t2, l1, l2)
+        got[form] = eng.compute_residuals(0, 0.0)
+        eng.close()
+    ref = cc3.evaluate(ham, t1, t2, l1, l2, ham.field_operator(np.array([0.3, 0.2, 1.0]) * 0.01))
+    for k in ("r_t1", "r_t2", "r_l1", "r_l2"):
+        assert _rel(got["eri"][k], getattr(ref, k).numpy()) < 1e-10, k
+        assert _rel(got["eri"][k], got["df"][k]) < 1e-10, k
+    assert abs(got["eri"]["energy"] - ref.energy) < 1e-10 * max(1.0, abs(ref.energy))
+    assert _rel(got["eri"]["dipole"], ref.dipole) < 1e-10
+
+
 def test_residuals_fp32_within_tolerance():
     o, v = 5, 19
     s = make_system(o, v, seed=40)
