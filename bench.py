@@ -138,15 +138,15 @@ KERNEL_FAMILIES = {
 # dram__bytes_write.sum, one pass, full-size workload):
 # (kernel, precision, workload) -> bytes.  An entry is removed when its kernel
 # changes after the counters were taken.
-# (the tcgen05 kernels changed since their counters were taken: exit drains and
-# a runtime wait budget; their entries are dropped until they are re-measured)
 MEASURED_TRAFFIC = {
-    ("k_contract", "tf32", 2): 2.79e6,
-    ("k_combine_nd", "tf32", 2): 124.21e6,
-    ("k_sym6_div", "tf32", 2): 842.05e6,
-    ("k_reduce_small", "tf32", 2): 176.91e6,
-    ("k_outer", "tf32", 2): 241.71e6,
-    ("k_gemv", "tf32", 2): 221.84e6,
+    ("k_contract", "tf32", 2): 2.87e6,
+    ("k_combine_nd", "tf32", 2): 124.25e6,
+    ("k_sym6_div", "tf32", 2): 841.15e6,
+    ("k_reduce_small", "tf32", 2): 149.09e6,
+    ("k_tc_gemm", "tf32", 2): 517.98e6,
+    ("k_tc_gemm_direct", "tf32", 2): 485.49e6,
+    ("k_outer", "tf32", 2): 201.64e6,
+    ("k_gemv", "tf32", 2): 221.79e6,
     ("k_pack", "tf32", 2): 2.01e6,
 }
 
