@@ -607,6 +607,9 @@ Engine<R>::~Engine() {
   if (side_) cudaStreamDestroy(side_);
   if (fork_ev_) cudaEventDestroy(fork_ev_);
   if (join_ev_) cudaEventDestroy(join_ev_);
+  if (branch_) cudaStreamDestroy(branch_);
+  if (branch_fork_) cudaEventDestroy(branch_fork_);
+  if (branch_join_) cudaEventDestroy(branch_join_);
   if (pool_) return;  // everything lives in the caller's pool
   for (auto& kv : plans_)
     if (kv.second->dev) cudaFree(kv.second->dev);
@@ -1121,7 +1124,7 @@ void Engine<R>::run_contract(const std::string& spec, double alpha, const View& 
   }
   C* part = nullptr;
   if (P.nsplit > 1)
-    part = static_cast<C*>(scratch(0, size_t(P.nb) * P.nsplit * P.M * P.N * sizeof(C)));
+    part = static_cast<C*>(scratch(split_slot_, size_t(P.nb) * P.nsplit * P.M * P.N * sizeof(C)));
   int bmm = kBM, bnn = kBN;
   if (P.small_tile) bmm = bnn = kSBM;
   else if (P.tile == 1) { bmm = 16; bnn = 256; }
@@ -1199,7 +1202,8 @@ void Engine<R>::run_contract_small(ContractPlan& P, double alpha, const C* pa, c
     return;
   }
   C* part = nullptr;
-  if (P.nsplit > 1) part = static_cast<C*>(scratch(0, size_t(P.nsplit) * P.M * P.N * sizeof(C)));
+  if (P.nsplit > 1)
+    part = static_cast<C*>(scratch(split_slot_, size_t(P.nsplit) * P.M * P.N * sizeof(C)));
   const int pk = pbegin();
   launch_reduce_small<R>(P.small_cfg, sw ? P.b_kcontig : P.a_kcontig, sw ? P.a_kcontig : P.b_kcontig,
                          sw ? pb : pa, sw ? P.b_off0 : P.a_off0, sw ? P.bN : P.aM, sw ? P.bK : P.aK,
@@ -1773,6 +1777,45 @@ void Engine<R>::exec_slab_div(double alpha, const View& X, int i0, const EpsSpec
   pend(pk, "slab_div", 8.0 * double(n), 2.0 * double(n) * sizeof(C));
 }
 
+// The adjoints dA = dC . B and dB = A . dC of one product read the same
+// inputs and write different cotangents: when both run on CUDA cores they
+// are launched as two branches (dB on the branch stream with its own split-K
+// scratch, dA on the engine's stream) that join before the next operation.
+// Not while profiling (per-operation timings stay serial), with a caller's
+// pool (one stream) or when A and B are one node (both adjoints add into it).
+template <typename R>
+bool Engine<R>::run_adjoints_branched(const Op& op) {
+  if (!branches_ || pool_ || (prof_ && prof_->enabled)) return false;
+  if (op.a.node == op.b.node || !nodes_[op.a.node].needs_grad || !nodes_[op.b.node].needs_grad)
+    return false;
+  const Spec s = parse(op.spec);
+  const std::string sa = s.c + "," + s.b + "->" + s.a, sb = s.a + "," + s.c + "->" + s.b;
+  if (plan(sa, op.c, op.b, op.a).use_tc || plan(sb, op.a, op.c, op.b).use_tc) return false;
+  if (!branch_) {
+    RTCC3_CUDA(cudaStreamCreateWithFlags(&branch_, cudaStreamNonBlocking));
+    RTCC3_CUDA(cudaEventCreateWithFlags(&branch_fork_, cudaEventDisableTiming));
+    RTCC3_CUDA(cudaEventCreateWithFlags(&branch_join_, cudaEventDisableTiming));
+  }
+  RTCC3_CUDA(cudaEventRecord(branch_fork_, stream_));
+  RTCC3_CUDA(cudaStreamWaitEvent(branch_, branch_fork_, 0));
+  cudaStream_t main = stream_;
+  stream_ = branch_;
+  split_slot_ = 4;
+  try {
+    run_contract(sb, op.alpha, op.a, false, op.c, true, op.b, true, true);
+  } catch (...) {
+    stream_ = main;
+    split_slot_ = 0;
+    throw;
+  }
+  stream_ = main;
+  split_slot_ = 0;
+  run_contract(sa, op.alpha, op.c, true, op.b, false, op.a, true, true);
+  RTCC3_CUDA(cudaEventRecord(branch_join_, branch_));
+  RTCC3_CUDA(cudaStreamWaitEvent(stream_, branch_join_, 0));
+  return true;
+}
+
 template <typename R>
 void Engine<R>::backward() {
   for (auto it = tape_.rbegin(); it != tape_.rend(); ++it) {
@@ -1781,6 +1824,7 @@ void Engine<R>::backward() {
       if (!nodes_[op.c.node].needs_grad) continue;
       const Spec s = parse(op.spec);
       cur_tc_ = op.tc;
+      if (run_adjoints_branched(op)) continue;
       if (nodes_[op.a.node].needs_grad)
         run_contract(s.c + "," + s.b + "->" + s.a, op.alpha, op.c, true, op.b, false, op.a, true, true);
       if (nodes_[op.b.node].needs_grad)

@@ -237,7 +237,8 @@ class Engine {
   // graph is being captured: plans upload tables synchronously).
   void freeze_plans(bool f) { frozen_ = f; }
   // Persistent scratch buffers by slot: 0 split-K partials, 1/2 packed
-  // tensor-core operands, 3 tensor-core split-K partials.
+  // tensor-core operands, 3 tensor-core split-K partials, 4 split-K partials
+  // of the reverse pass's branch stream.
   void* scratch(int slot, size_t bytes);
   // Route large contractions of a complex64 graph to the tcgen05 GEMM with
   // TF32 (elem_bytes 4) or BF16 (2) operands; 0 keeps the CUDA-core kernel.
@@ -270,6 +271,9 @@ class Engine {
   // a captured CUDA graph recorded under an older generation is stale.
   int generation() const { return generation_; }
   void set_profiler(Profiler* p) { prof_ = p; }
+  // Reverse pass: the A and B adjoints of a CUDA-core product as parallel
+  // branches (default on; off runs them one after the other).
+  void set_branches(bool on) { branches_ = on; }
   // A second stream for independent work (created on first use; with a
   // caller-owned pool the engine's own stream is used instead), and the
   // points where it forks from and joins back into the engine's stream (also
@@ -325,9 +329,19 @@ class Engine {
   std::vector<Node> nodes_;
   std::vector<Op> tape_;
   std::map<std::string, std::unique_ptr<ContractPlan>> plans_;
-  static constexpr int kScratchSlots = 4;
-  void* scratch_[kScratchSlots] = {nullptr, nullptr, nullptr, nullptr};
-  size_t scratch_bytes_[kScratchSlots] = {0, 0, 0, 0};
+  static constexpr int kScratchSlots = 5;
+  void* scratch_[kScratchSlots] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t scratch_bytes_[kScratchSlots] = {0, 0, 0, 0, 0};
+  // split-K partials of CUDA-core contractions: slot 0 on the engine's
+  // stream, slot 4 on the branch stream of the reverse pass
+  int split_slot_ = 0;
+  // reverse pass: the two adjoints of one product (different outputs, same
+  // inputs) run as parallel branches (a stream of their own, forked from and
+  // joined into the engine's stream, also under graph capture)
+  cudaStream_t branch_ = nullptr;
+  cudaEvent_t branch_fork_ = nullptr, branch_join_ = nullptr;
+  bool branches_ = true;
+  bool run_adjoints_branched(const Op& op);
   int tc_eb_ = 0;
   long long wait_budget_ = 0;
   bool checked_ = false;
