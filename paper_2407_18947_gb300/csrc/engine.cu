@@ -610,6 +610,9 @@ Engine<R>::~Engine() {
   if (branch_) cudaStreamDestroy(branch_);
   if (branch_fork_) cudaEventDestroy(branch_fork_);
   if (branch_join_) cudaEventDestroy(branch_join_);
+  if (region_) cudaStreamDestroy(region_);
+  if (region_fork_) cudaEventDestroy(region_fork_);
+  if (region_join_) cudaEventDestroy(region_join_);
   if (pool_) return;  // everything lives in the caller's pool
   for (auto& kv : plans_)
     if (kv.second->dev) cudaFree(kv.second->dev);
@@ -661,6 +664,9 @@ int* Engine<R>::error_flag() {
 template <typename R>
 void Engine<R>::begin() {
   tc_region_ = false;
+  // a stage abandoned inside a concurrent region (an error) leaves it here
+  if (in_region_) region_leave();
+  region_pending_ = false;
   arena_.reset();
   nodes_.clear();
   tape_.clear();
@@ -1784,8 +1790,54 @@ void Engine<R>::exec_slab_div(double alpha, const View& X, int i0, const EpsSpec
 // Not while profiling (per-operation timings stay serial), with a caller's
 // pool (one stream) or when A and B are one node (both adjoints add into it).
 template <typename R>
+void Engine<R>::region_enter() {
+  if (!region_) {
+    RTCC3_CUDA(cudaStreamCreateWithFlags(&region_, cudaStreamNonBlocking));
+    RTCC3_CUDA(cudaEventCreateWithFlags(&region_fork_, cudaEventDisableTiming));
+    RTCC3_CUDA(cudaEventCreateWithFlags(&region_join_, cudaEventDisableTiming));
+  }
+  RTCC3_CUDA(cudaEventRecord(region_fork_, stream_));
+  RTCC3_CUDA(cudaStreamWaitEvent(region_, region_fork_, 0));
+  region_main_ = stream_;
+  stream_ = region_;
+  split_slot_ = 5;
+  in_region_ = true;
+}
+
+template <typename R>
+void Engine<R>::region_leave() {
+  stream_ = region_main_;
+  split_slot_ = 0;
+  in_region_ = false;
+}
+
+template <typename R>
+void Engine<R>::region_begin() {
+  if (!regions() || in_region_ || region_pending_) return;
+  region_enter();
+  region_pending_ = true;
+  tape_.push_back(Op{kRegionBegin, "", 0.0, View(), View(), View(), EpsSpec()});
+}
+
+template <typename R>
+void Engine<R>::region_end() {
+  if (!in_region_) return;
+  region_leave();
+  tape_.push_back(Op{kRegionEnd, "", 0.0, View(), View(), View(), EpsSpec()});
+}
+
+template <typename R>
+void Engine<R>::region_join() {
+  if (!region_pending_ || in_region_) return;
+  RTCC3_CUDA(cudaEventRecord(region_join_, region_));
+  RTCC3_CUDA(cudaStreamWaitEvent(stream_, region_join_, 0));
+  region_pending_ = false;
+  tape_.push_back(Op{kRegionJoin, "", 0.0, View(), View(), View(), EpsSpec()});
+}
+
+template <typename R>
 bool Engine<R>::run_adjoints_branched(const Op& op) {
-  if (!branches_ || pool_ || (prof_ && prof_->enabled)) return false;
+  if (!branches_ || pool_ || (prof_ && prof_->enabled) || in_region_) return false;
   if (op.a.node == op.b.node || !nodes_[op.a.node].needs_grad || !nodes_[op.b.node].needs_grad)
     return false;
   const Spec s = parse(op.spec);
@@ -1877,6 +1929,19 @@ void Engine<R>::backward() {
     } else if (op.kind == kSym6Div) {
       if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
       run_sym6_div(op.alpha, op.c, true, op.es, op.a, true, false, 6);
+    } else if (op.kind == kRegionJoin) {
+      // the region's adjoints may start once everything after it is done
+      RTCC3_CUDA(cudaEventRecord(region_fork_, stream_));
+      RTCC3_CUDA(cudaStreamWaitEvent(region_, region_fork_, 0));
+    } else if (op.kind == kRegionEnd) {
+      region_main_ = stream_;
+      stream_ = region_;
+      split_slot_ = 5;
+      in_region_ = true;
+    } else if (op.kind == kRegionBegin) {
+      region_leave();
+      RTCC3_CUDA(cudaEventRecord(region_join_, region_));
+      RTCC3_CUDA(cudaStreamWaitEvent(stream_, region_join_, 0));
     } else {
       const bool saved = tc_region_;
       tc_region_ = op.tc;

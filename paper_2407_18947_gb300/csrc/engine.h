@@ -272,8 +272,24 @@ class Engine {
   int generation() const { return generation_; }
   void set_profiler(Profiler* p) { prof_ = p; }
   // Reverse pass: the A and B adjoints of a CUDA-core product as parallel
-  // branches (default on; off runs them one after the other).
+  // branches, and concurrent regions (default on; off runs everything on
+  // the engine's stream in recording order).
   void set_branches(bool on) { branches_ = on; }
+  // Concurrent region: operations recorded between region_begin() and
+  // region_end() run on a stream of their own, forked from the engine's
+  // stream at region_begin(), concurrently with the operations recorded
+  // after region_end() up to region_join(), which joins it back.  The
+  // reverse pass mirrors it: the region's adjoints run on its stream,
+  // forked where the reverse pass meets region_join() and joined where it
+  // meets region_begin().  Every node the region writes, values or
+  // cotangents, must be private to it (inputs shared with the rest of the
+  // stage are copied before region_begin()).  regions() is false, and the
+  // three calls do nothing, while profiling, with a caller's pool or with
+  // branches off.
+  bool regions() const { return branches_ && !pool_ && !(prof_ && prof_->enabled); }
+  void region_begin();
+  void region_end();
+  void region_join();
   // A second stream for independent work (created on first use; with a
   // caller-owned pool the engine's own stream is used instead), and the
   // points where it forks from and joins back into the engine's stream (also
@@ -299,7 +315,8 @@ class Engine {
   // to use (false = overwrite when the write covers a gradient not yet set).
   bool begin_grad_write(const View& dst, bool accumulate);
   void zero_grad_if_unset(int node);
-  enum OpKind { kContract, kAxpy, kMulc, kDiv, kCustom, kSym6, kSym6Div };
+  enum OpKind { kContract, kAxpy, kMulc, kDiv, kCustom, kSym6, kSym6Div, kRegionBegin, kRegionEnd,
+                kRegionJoin };
   struct Op {
     OpKind kind;
     std::string spec;
@@ -329,12 +346,19 @@ class Engine {
   std::vector<Node> nodes_;
   std::vector<Op> tape_;
   std::map<std::string, std::unique_ptr<ContractPlan>> plans_;
-  static constexpr int kScratchSlots = 5;
-  void* scratch_[kScratchSlots] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t scratch_bytes_[kScratchSlots] = {0, 0, 0, 0, 0};
+  static constexpr int kScratchSlots = 6;
+  void* scratch_[kScratchSlots] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t scratch_bytes_[kScratchSlots] = {0, 0, 0, 0, 0, 0};
   // split-K partials of CUDA-core contractions: slot 0 on the engine's
-  // stream, slot 4 on the branch stream of the reverse pass
+  // stream, slot 4 on the branch stream of the reverse pass, slot 5 in a
+  // concurrent region
   int split_slot_ = 0;
+  // concurrent region (region_begin / region_end / region_join)
+  cudaStream_t region_ = nullptr, region_main_ = nullptr;
+  cudaEvent_t region_fork_ = nullptr, region_join_ = nullptr;
+  bool in_region_ = false, region_pending_ = false;
+  void region_enter();
+  void region_leave();
   // reverse pass: the two adjoints of one product (different outputs, same
   // inputs) run as parallel branches (a stream of their own, forked from and
   // joined into the engine's stream, also under graph capture)

@@ -571,9 +571,6 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   auto F = [&](const char* b) { return blk(ft, b); };
 
   // ---- CCSD residual (T1-transformed, spin adapted) ---------------------------
-  const int u = E.node({o, o, v, v}, false, false);
-  E.combine({{2.0, T}, {-1.0, E.ev("ijba->ijab", T)}}, E.v(u), true);
-  const View U = E.v(u);
   S.r1 = E.node({o, v});
   const View R1 = E.v(S.r1);
   S.r2 = E.node({o, o, v, v});
@@ -582,38 +579,69 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
   const View SD = E.v(Sd);
   const int Lov = E.node({o, v, o, v}, false, false);
   E.combine({{2.0, G("ovov")}, {-1.0, E.ev("lckd->ldkc", G("ovov"))}}, E.v(Lov), true);
+  // With the triples beside it, the CCSD part runs as a concurrent region of
+  // the stage (and of its reverse pass): it reads private copies of the
+  // dressed integrals, f~ and t2 and writes R1c, SDc, added to R1, SD after
+  // the join, so no value or cotangent is written from both sides.
+  const bool region = opt.ccsd && opt.triples && !all_tc && E.regions();
+  int gq = g, fq = ft, R1n = S.r1, SDn = Sd;
+  View Tq = T;
+  if (region) {
+    gq = E.node({n, n, n, n}, false, false);
+    E.combine({{1.0, E.v(g)}}, E.v(gq), true);
+    fq = E.node({n, n}, false, false);
+    E.combine({{1.0, E.v(ft)}}, E.v(fq), true);
+    const int tq = E.node({o, o, v, v}, false, false);
+    E.combine({{1.0, T}}, E.v(tq), true);
+    Tq = E.v(tq);
+    E.region_begin();
+    R1n = E.node({o, v});
+    SDn = E.node({o, o, v, v});
+  }
   if (opt.ccsd) {
-  E.contract("kicd,adkc->ia", 1.0, U, G("vvov"), R1, true);
-  E.contract("klac,kilc->ia", -1.0, U, G("ooov"), R1, true);
-  E.contract("ikac,kc->ia", 1.0, U, F("ov"), R1, true);
-  E.axpy(1.0, E.ev("ai->ia", F("vo")), R1);
+  auto Gq = [&](const char* b) { return blk(gq, b); };
+  auto Fq = [&](const char* b) { return blk(fq, b); };
+  const View R1q = E.v(R1n), SDq = E.v(SDn);
+  const int u = E.node({o, o, v, v}, false, false);
+  E.combine({{2.0, Tq}, {-1.0, E.ev("ijba->ijab", Tq)}}, E.v(u), true);
+  const View U = E.v(u);
+  int Lq = Lov;
+  if (region) {
+    Lq = E.node({o, v, o, v}, false, false);
+    E.combine({{2.0, Gq("ovov")}, {-1.0, E.ev("lckd->ldkc", Gq("ovov"))}}, E.v(Lq), true);
+  }
+  E.contract("kicd,adkc->ia", 1.0, U, Gq("vvov"), R1q, true);
+  E.contract("klac,kilc->ia", -1.0, U, Gq("ooov"), R1q, true);
+  E.contract("ikac,kc->ia", 1.0, U, Fq("ov"), R1q, true);
+  E.axpy(1.0, E.ev("ai->ia", Fq("vo")), R1q);
 
-  E.axpy(1.0, E.ev("aibj->ijab", G("vovo")), R2);
-  E.contract("ijcd,acbd->ijab", 1.0, T, G("vvvv"), R2, true);
+  E.axpy(1.0, E.ev("aibj->ijab", Gq("vovo")), R2);
+  E.contract("ijcd,acbd->ijab", 1.0, Tq, Gq("vvvv"), R2, true);
   const int Wk = E.node({o, o, o, o});
-  E.axpy(1.0, G("oooo"), E.v(Wk));
-  E.contract("ijcd,kcld->kilj", 1.0, T, G("ovov"), E.v(Wk), true);
-  E.contract("klab,kilj->ijab", 1.0, T, E.v(Wk), R2, true);
+  E.axpy(1.0, Gq("oooo"), E.v(Wk));
+  E.contract("ijcd,kcld->kilj", 1.0, Tq, Gq("ovov"), E.v(Wk), true);
+  E.contract("klab,kilj->ijab", 1.0, Tq, E.v(Wk), R2, true);
   const int Xc = E.node({o, o, v, v});
-  E.axpy(1.0, G("oovv"), E.v(Xc));
-  E.contract("liad,kdlc->kiac", -0.5, T, G("ovov"), E.v(Xc), true);
-  E.contract("kjbc,kiac->ijab", -0.5, T, E.v(Xc), SD, true);
-  E.contract("kibc,kjac->ijab", -1.0, T, E.v(Xc), SD, true);
+  E.axpy(1.0, Gq("oovv"), E.v(Xc));
+  E.contract("liad,kdlc->kiac", -0.5, Tq, Gq("ovov"), E.v(Xc), true);
+  E.contract("kjbc,kiac->ijab", -0.5, Tq, E.v(Xc), SDq, true);
+  E.contract("kibc,kjac->ijab", -1.0, Tq, E.v(Xc), SDq, true);
   const int Ltv = E.node({v, o, o, v});
-  E.axpy(2.0, G("voov"), E.v(Ltv));
-  E.axpy(-1.0, E.ev("acki->aikc", G("vvoo")), E.v(Ltv));
+  E.axpy(2.0, Gq("voov"), E.v(Ltv));
+  E.axpy(-1.0, E.ev("acki->aikc", Gq("vvoo")), E.v(Ltv));
   const int Xd = E.node({o, v, o, v});
   E.axpy(1.0, E.ev("aikc->iakc", E.v(Ltv)), E.v(Xd));
-  E.contract("ilad,ldkc->iakc", 0.5, U, E.v(Lov), E.v(Xd), true);
-  E.contract("jkbc,iakc->ijab", 0.5, U, E.v(Xd), SD, true);
+  E.contract("ilad,ldkc->iakc", 0.5, U, E.v(Lq), E.v(Xd), true);
+  E.contract("jkbc,iakc->ijab", 0.5, U, E.v(Xd), SDq, true);
   const int Fvv = E.node({v, v}), Foo = E.node({o, o});
-  E.axpy(1.0, F("vv"), E.v(Fvv));
-  E.contract("klbd,ldkc->bc", -1.0, U, G("ovov"), E.v(Fvv), true);
-  E.axpy(1.0, F("oo"), E.v(Foo));
-  E.contract("ljcd,kdlc->kj", 1.0, U, G("ovov"), E.v(Foo), true);
-  E.contract("ijac,bc->ijab", 1.0, T, E.v(Fvv), SD, true);
-  E.contract("ikab,kj->ijab", -1.0, T, E.v(Foo), SD, true);
+  E.axpy(1.0, Fq("vv"), E.v(Fvv));
+  E.contract("klbd,ldkc->bc", -1.0, U, Gq("ovov"), E.v(Fvv), true);
+  E.axpy(1.0, Fq("oo"), E.v(Foo));
+  E.contract("ljcd,kdlc->kj", 1.0, U, Gq("ovov"), E.v(Foo), true);
+  E.contract("ijac,bc->ijab", 1.0, Tq, E.v(Fvv), SDq, true);
+  E.contract("ikab,kj->ijab", -1.0, Tq, E.v(Foo), SDq, true);
   }  // opt.ccsd
+  E.region_end();
 
   // ---- triples ---------------------------------------------------------------
   if (opt.triples && opt.field_terms && opt.rotation) {
@@ -696,6 +724,11 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
       E.axpy(1.0, E.v(S3), SD);
     }
     E.set_tc_region(all_tc);
+  }
+  if (region) {
+    E.region_join();
+    E.axpy(1.0, E.v(R1n), R1);
+    E.axpy(1.0, E.v(SDn), SD);
   }
   // P_ij^ab on the symmetrised part
   E.combine({{1.0, SD}, {1.0, E.ev("jiba->ijab", SD)}}, R2, false);
