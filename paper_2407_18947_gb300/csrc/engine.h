@@ -331,6 +331,11 @@ class Engine {
                bool overwrite = false);
   void run_combine(const View* xs, const bool* xg, const double* alphas, int ns, const View& Y,
                    bool yg, bool overwrite, const char* name);
+  // run_combine (overwriting) for dense (..., v, v, v) operands whose
+  // sources permute the last three indices, when the brick thread layout
+  // touches fewer sectors; false: not that form, nothing launched
+  bool run_combine_brick(const View* xs, const bool* xg, const double* alphas, int ns,
+                         const View& Y, bool yg, bool overwrite, const char* name);
   void run_sym6(double alpha, const View& X, bool xg, const View& Y, bool yg, bool overwrite);
   void run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
                     bool overwrite, int np);
