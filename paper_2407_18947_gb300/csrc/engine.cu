@@ -114,6 +114,25 @@ __global__ void k_slab_div(const Cx<R>* X, Cx<R>* Y, const R* __restrict__ osum,
   }
 }
 
+// Thread layout of a 4 (a) x 8 (b) x 8 (c) brick, 256 threads (LAYOUT 0: a
+// warp on 4 x 4 x 2 elements, a fastest; 1: on 2 x 4 x 4, c fastest), first
+// c of the thread (stepping by 8).
+template <int LAYOUT>
+__device__ __forceinline__ void brick_coords(int v, unsigned& a, unsigned& b, unsigned& c0) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nbb = (v + 7) / 8;
+  const unsigned ta = unsigned(blockIdx.x / nbb) * 4, tb = unsigned(blockIdx.x % nbb) * 8;
+  if (LAYOUT == 0) {
+    a = ta + (lane & 3);
+    b = tb + (w & 1) * 4 + ((lane >> 2) & 3);
+    c0 = unsigned((w >> 1) * 2 + (lane >> 4));
+  } else {
+    a = ta + (w & 1) * 2 + (lane >> 4);
+    b = tb + ((w >> 1) & 1) * 4 + ((lane >> 2) & 3);
+    c0 = unsigned((w >> 2) * 4 + (lane & 3));
+  }
+}
+
 // Y (+)= alpha P(X) / D for X, Y dense (o,o,o,v,v,v): P sums the six
 // simultaneous permutations of (ijk, abc) (NP = 6) or the identity and the
 // exchanges of slot 1 with slots 2 and 3 (NP = 3), then divides by the
@@ -174,16 +193,13 @@ k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx, l
   };
   if (NP == 6) {
     // a CTA covers a 4 (a) x 8 (b) x 8 (c) brick, stepping over c; a warp
-    // covers 4 x 4 x 2 of it, so every source is read in runs of 2 to 4
+    // covers 2 x 4 x 4 of it, so every source is read in runs of 2 to 4
     // consecutive elements along its own fastest index (the sources permute
     // a, b, c)
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nbb = (v + 7) / 8;
-    const unsigned a = unsigned((blockIdx.x / nbb) * 4 + (lane & 3));
-    const unsigned b = unsigned((blockIdx.x % nbb) * 8 + (w & 1) * 4 + ((lane >> 2) & 3));
+    unsigned a, b, c0;
+    brick_coords<1>(v, a, b, c0);
     if (a >= unsigned(v) || b >= unsigned(v)) return;
-    for (unsigned c = unsigned((w >> 1) * 2 + (lane >> 4)); c < unsigned(v); c += 8)
-      element(a, b, c, (a * v + b) * v + c);
+    for (unsigned c = c0; c < unsigned(v); c += 8) element(a, b, c, (a * v + b) * v + c);
   } else {
     // two of the three sources keep c fastest: consecutive threads on
     // consecutive abc
@@ -523,11 +539,11 @@ __global__ void __launch_bounds__(256) k_combine_nd(Cx<R>* __restrict__ Y, const
 }
 
 // Y[blk][abc] (+)= sum_s alpha_s X_s[blk][sigma_s(abc)] over dense
-// (nblk, v, v, v) tensors whose sources permute the last three indices: the
-// thread layout of k_sym6_div's six-term path (a CTA per 4 x 8 (a, b) brick
-// of a block, stepping over c; a warp on 4 x 4 x 2 elements), so sources
-// whose fastest index is a or b are read in runs of 4 instead of one
-// element per lane.  Source s has stride 1, v or v^2 for a, b, c as encoded
+// (nblk, v, v, v) tensors whose sources permute the last three indices, in
+// brick thread layouts (a CTA per 4 x 8 (a, b) brick of a block, stepping
+// over c; a warp on 4 x 4 x 2 or 2 x 4 x 4 elements), so sources whose
+// fastest index is a or b are read in runs of 2 to 4 instead of one element
+// per lane.  Source s has stride 1, v or v^2 for a, b, c as encoded
 // in lv (bits 0-1, 2-3, 4-5: 0 stride 1, 1 stride v, 2 stride v^2).
 template <typename R>
 struct BrickDesc {
@@ -540,15 +556,13 @@ struct BrickDesc {
   int v;
 };
 
-template <typename R, int NS>
+template <typename R, int NS, int LAYOUT>
 __global__ void __launch_bounds__(256) k_combine_brick(const BrickDesc<R> d) {
   const int v = d.v;
   const unsigned v2 = unsigned(v) * unsigned(v);
   const size_t v3 = size_t(v2) * v;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int nbb = (v + 7) / 8;
-  const unsigned a = unsigned((blockIdx.x / nbb) * 4 + (lane & 3));
-  const unsigned b = unsigned((blockIdx.x % nbb) * 8 + (w & 1) * 4 + ((lane >> 2) & 3));
+  unsigned a, b, c0;
+  brick_coords<LAYOUT>(v, a, b, c0);
   if (a >= unsigned(v) || b >= unsigned(v)) return;
   const size_t blk = size_t(blockIdx.y) * v3;
   unsigned sa[NS], sb[NS], sc[NS];
@@ -560,7 +574,7 @@ __global__ void __launch_bounds__(256) k_combine_brick(const BrickDesc<R> d) {
     sb[s] = lb == 0 ? 1u : (lb == 1 ? unsigned(v) : v2);
     sc[s] = lc == 0 ? 1u : (lc == 1 ? unsigned(v) : v2);
   }
-  for (unsigned c = unsigned((w >> 1) * 2 + (lane >> 4)); c < unsigned(v); c += 8) {
+  for (unsigned c = c0; c < unsigned(v); c += 8) {
     R re = R(0), im = R(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -1511,8 +1525,9 @@ bool Engine<R>::run_combine_brick(const View* xs, const bool* xg, const double* 
                                   const View& Y, bool yg, bool overwrite, const char* name) {
   // dense (..., v, v, v) operands that share the leading indices and permute
   // the last three
-  // (overwriting sums only: accumulating into the output measured slower in
-  // this layout, 1.0 against 0.4 ms per (H2O)2 o^3 v^3 gather)
+  // (overwriting sums only: accumulating into the output measured no faster
+  // (three sources) or twice as slow (two) in both brick layouts at (H2O)2
+  // size, against the flat layout)
   const int nd = Y.nd;
   const size_t n = Y.numel();
   if (!overwrite || nd < 3 || n < (size_t(1) << 16)) return false;
@@ -1528,10 +1543,11 @@ bool Engine<R>::run_combine_brick(const View* xs, const bool* xg, const double* 
   const long long vl = v, v2 = vl * vl;
   BrickDesc<R> d{};
   d.nsrc = ns;
-  // 32-byte sectors a warp touches per element group: the flat layout reads
-  // a source whose fastest index is c in 8 sectors and any other in 32; the
-  // brick layout in 16 and 8, and writes the output in 16 instead of 8
-  int flat = 8, brick = 16;
+  // 32-byte sectors a warp touches per 32 elements: flat layout 8 for a
+  // source whose fastest index is c, 32 otherwise, output 8; 4x4x2 warps 16
+  // (c fastest), 8 (a or b), output 16; 2x4x4 warps 8 (c or b), 16 (a),
+  // output 8
+  int flat = 8, brick0 = 16, brick1 = 8;
   for (int s = 0; s < ns; ++s) {
     const View& x = xs[s];
     if (x.nd != nd) return false;
@@ -1545,12 +1561,14 @@ bool Engine<R>::run_combine_brick(const View* xs, const bool* xg, const double* 
     }
     if (lev[0] == lev[1] || lev[0] == lev[2] || lev[1] == lev[2]) return false;
     flat += lev[2] == 0 ? 8 : 32;
-    brick += lev[2] == 0 ? 16 : 8;
+    brick0 += lev[2] == 0 ? 16 : 8;
+    brick1 += lev[0] == 0 ? 16 : 8;
     d.src[s] = (xg[s] ? nodes_[x.node].grad : nodes_[x.node].data) + x.off;
     d.alpha[s] = R(alphas[s]);
     d.lv[s] = lev[0] | (lev[1] << 2) | (lev[2] << 4);
   }
-  if (brick >= flat) return false;
+  if (std::min(brick0, brick1) >= flat) return false;
+  const int layout = brick1 <= brick0 ? 1 : 0;
   const size_t nblk = n / size_t(v2 * vl);
   if (nblk >= 65536) return false;
   d.y = (yg ? nodes_[Y.node].grad : nodes_[Y.node].data) + Y.off;
@@ -1558,14 +1576,18 @@ bool Engine<R>::run_combine_brick(const View* xs, const bool* xg, const double* 
   d.v = v;
   const dim3 grid(unsigned((v + 3) / 4) * unsigned((v + 7) / 8), unsigned(nblk));
   const int pk = pbegin();
+#define RTCC3_BRK(NSV)                                                     \
+  if (layout == 1) k_combine_brick<R, NSV, 1><<<grid, 256, 0, stream_>>>(d); \
+  else k_combine_brick<R, NSV, 0><<<grid, 256, 0, stream_>>>(d)
   switch (ns) {
-    case 1: k_combine_brick<R, 1><<<grid, 256, 0, stream_>>>(d); break;
-    case 2: k_combine_brick<R, 2><<<grid, 256, 0, stream_>>>(d); break;
-    case 3: k_combine_brick<R, 3><<<grid, 256, 0, stream_>>>(d); break;
-    case 4: k_combine_brick<R, 4><<<grid, 256, 0, stream_>>>(d); break;
-    case 5: k_combine_brick<R, 5><<<grid, 256, 0, stream_>>>(d); break;
-    default: k_combine_brick<R, 6><<<grid, 256, 0, stream_>>>(d); break;
+    case 1: RTCC3_BRK(1); break;
+    case 2: RTCC3_BRK(2); break;
+    case 3: RTCC3_BRK(3); break;
+    case 4: RTCC3_BRK(4); break;
+    case 5: RTCC3_BRK(5); break;
+    default: RTCC3_BRK(6); break;
   }
+#undef RTCC3_BRK
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
   pend(pk, name, 2.0 * ns * n, double(n) * sizeof(C) * (ns + (overwrite ? 1 : 2)),
