@@ -448,7 +448,7 @@ __global__ void k_div_eps(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, St
 
 // Y[.] (+)= sum_s alpha_s X_s[.] over Y's shape: up to kMaxSrc strided
 // sources, one pass, coalesced on Y (threads walk Y's last index fastest).
-constexpr int kMaxSrc = 6;
+constexpr int kMaxSrc = 8;
 template <typename R>
 struct CombDesc {
   int nd, nsrc, overwrite;
@@ -1395,7 +1395,7 @@ void Engine<R>::run_axpy(double alpha, const View& X, bool xg, const View& Y, bo
 template <typename R>
 void Engine<R>::run_combine(const View* xs, const bool* xg, const double* alphas, int ns,
                             const View& Y, bool yg, bool overwrite, const char* name) {
-  RTCC3_CHECK(ns >= 1 && ns <= kMaxSrc, kErrArg, "combine takes 1..6 sources");
+  RTCC3_CHECK(ns >= 1 && ns <= kMaxSrc, kErrArg, "combine takes 1..8 sources");
   for (int k = 0; k < ns; ++k) check_view(xs[k], 0, name);
   check_view(Y, 0, name);
   {
@@ -1585,7 +1585,9 @@ bool Engine<R>::run_combine_brick(const View* xs, const bool* xg, const double* 
     case 3: RTCC3_BRK(3); break;
     case 4: RTCC3_BRK(4); break;
     case 5: RTCC3_BRK(5); break;
-    default: RTCC3_BRK(6); break;
+    case 6: RTCC3_BRK(6); break;
+    case 7: RTCC3_BRK(7); break;
+    default: RTCC3_BRK(8); break;
   }
 #undef RTCC3_BRK
   ++launches_;
@@ -1601,12 +1603,12 @@ template <typename R>
 void Engine<R>::combine(std::initializer_list<std::pair<double, View>> srcs, const View& Y,
                         bool overwrite) {
   View xs[kMaxSrc];
-  bool xg[kMaxSrc] = {false, false, false, false, false, false};
+  bool xg[kMaxSrc] = {};
   double al[kMaxSrc];
   int ns = 0;
   bool g = false;
   for (auto& s : srcs) {
-    RTCC3_CHECK(ns < kMaxSrc, kErrArg, "combine takes at most 6 sources");
+    RTCC3_CHECK(ns < kMaxSrc, kErrArg, "combine takes at most 8 sources");
     RTCC3_CHECK(s.second.node != Y.node, kErrArg, "combine output aliases an input");
     xs[ns] = s.second;
     al[ns] = s.first;
@@ -2035,9 +2037,59 @@ bool Engine<R>::run_adjoints_branched(const Op& op) {
 }
 
 template <typename R>
+void Engine<R>::defer_gather(const View* xs, const double* al, int ns, const View& dst) {
+  static_assert(kMaxSrc == 8, "pending gather capacity");
+  for (size_t k = 0; k < gathers_.size(); ++k) {
+    PendingGather& p = gathers_[k];
+    if (!same_view(p.dst, dst)) continue;
+    if (p.ns + ns <= kMaxSrc) {
+      for (int s = 0; s < ns; ++s) {
+        p.xs[p.ns] = xs[s];
+        p.al[p.ns] = al[s];
+        ++p.ns;
+      }
+      return;
+    }
+    flush_gathers(dst.node);
+    break;
+  }
+  PendingGather p;
+  p.dst = dst;
+  p.ns = ns;
+  for (int s = 0; s < ns; ++s) {
+    p.xs[s] = xs[s];
+    p.al[s] = al[s];
+  }
+  gathers_.push_back(p);
+}
+
+template <typename R>
+void Engine<R>::flush_gathers(int node) {
+  std::vector<PendingGather> keep;
+  std::vector<PendingGather> run;
+  for (auto& p : gathers_) (node < 0 || p.dst.node == node ? run : keep).push_back(p);
+  gathers_.swap(keep);
+  for (auto& p : run) {
+    bool xg[kMaxSrc];
+    for (int s = 0; s < kMaxSrc; ++s) xg[s] = true;
+    run_combine(p.xs, xg, p.al, p.ns, p.dst, true, false, "axpy_gather");
+  }
+}
+
+template <typename R>
 void Engine<R>::backward() {
+  gathers_.clear();
   for (auto it = tape_.rbegin(); it != tape_.rend(); ++it) {
     const Op& op = *it;
+    // a held-back gather completes a cotangent before anything reads it: the
+    // adjoint of the operation that produced its node, any custom adjoint,
+    // and a change of stream
+    if (op.kind == kContract || op.kind == kAxpy || op.kind == kMulc || op.kind == kDiv ||
+        op.kind == kSym6 || op.kind == kSym6Div) {
+      if (!gathers_.empty()) flush_gathers(op.c.node);
+    } else if (!gathers_.empty()) {
+      flush_gathers(-1);
+    }
     if (op.kind == kContract) {
       if (!nodes_[op.c.node].needs_grad) continue;
       const Spec s = parse(op.spec);
@@ -2081,7 +2133,7 @@ void Engine<R>::backward() {
           ++ns;
           done[j] = true;
         }
-        run_combine(xs, xg, al, ns, dense, true, false, "axpy_gather");
+        defer_gather(xs, al, ns, dense);
       }
     } else if (op.kind == kMulc) {
       if (!nodes_[op.c.node].needs_grad || !nodes_[op.a.node].needs_grad) continue;
@@ -2115,6 +2167,7 @@ void Engine<R>::backward() {
       tc_region_ = saved;
     }
   }
+  flush_gathers(-1);
 }
 
 template class Engine<double>;

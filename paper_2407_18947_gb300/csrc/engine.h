@@ -103,7 +103,7 @@ class Engine {
   void contract(const char* spec, double alpha, const View& A, const View& B, const View& Cv,
                 bool accumulate);
   void axpy(double alpha, const View& X, const View& Y);
-  // Y (+)= sum_s alpha_s X_s in one pass (up to six strided sources).
+  // Y (+)= sum_s alpha_s X_s in one pass (up to eight strided sources).
   void combine(std::initializer_list<std::pair<double, View>> srcs, const View& Y, bool overwrite);
   // Y (+)= alpha P_ijk^abc X for 6-index tensors (o,o,o,v,v,v); self-adjoint.
   void sym6(double alpha, const View& X, const View& Y, bool overwrite);
@@ -371,6 +371,18 @@ class Engine {
   cudaEvent_t branch_fork_ = nullptr, branch_join_ = nullptr;
   bool branches_ = true;
   bool run_adjoints_branched(const Op& op);
+  // reverse pass: gathers (adjoints of permuted sums) into one destination
+  // view are held back and merged, up to kMaxSrc sources per pass, until the
+  // destination's cotangent is read or the pass ends
+  struct PendingGather {
+    View dst;
+    int ns = 0;
+    View xs[8];
+    double al[8];
+  };
+  std::vector<PendingGather> gathers_;
+  void defer_gather(const View* xs, const double* al, int ns, const View& dst);
+  void flush_gathers(int node);  // node < 0: all
   int tc_eb_ = 0;
   long long wait_budget_ = 0;
   bool checked_ = false;
