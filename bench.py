@@ -119,6 +119,8 @@ class ClockSampler:
 # that runs them, with the roofline that bounds that kernel.
 KERNEL_FAMILIES = {
     "k_combine_nd": (("combine", "axpy_gather", "axpy_strided", "copy", "sym6"), "hbm"),
+    # the o^3 v^3 permuted sums in the brick thread layout
+    "k_combine_brick": (("combine_brick",), "hbm"),
     "k_tc_gemm": (("contract_tc_tf32", "contract_tc_bf16"), "tensor"),
     # long sums reading the o^3 v^3 operand from its source (tcgen05, TF32
     # split): N = 10 or 38 complex columns, ~N flop per byte, HBM-bound
@@ -139,12 +141,13 @@ KERNEL_FAMILIES = {
 # (kernel, precision, workload) -> bytes.  An entry is removed when its kernel
 # changes after the counters were taken.
 MEASURED_TRAFFIC = {
-    ("k_contract", "tf32", 2): 2.87e6,
-    ("k_combine_nd", "tf32", 2): 124.25e6,
-    ("k_sym6_div", "tf32", 2): 841.15e6,
+    ("k_contract", "tf32", 2): 2.86e6,
+    ("k_combine_nd", "tf32", 2): 3.61e6,
+    ("k_combine_brick", "tf32", 2): 1061.54e6,
+    ("k_sym6_div", "tf32", 2): 844.50e6,
     ("k_reduce_small", "tf32", 2): 149.09e6,
-    ("k_tc_gemm", "tf32", 2): 517.98e6,
-    ("k_tc_gemm_direct", "tf32", 2): 485.49e6,
+    ("k_tc_gemm", "tf32", 2): 518.05e6,
+    ("k_tc_gemm_direct", "tf32", 2): 485.19e6,
     ("k_outer", "tf32", 2): 201.64e6,
     ("k_gemv", "tf32", 2): 221.79e6,
     ("k_pack", "tf32", 2): 2.01e6,

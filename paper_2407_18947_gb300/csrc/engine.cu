@@ -1592,9 +1592,9 @@ bool Engine<R>::run_combine_brick(const View* xs, const bool* xg, const double* 
 #undef RTCC3_BRK
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
-  pend(pk, name, 2.0 * ns * n, double(n) * sizeof(C) * (ns + (overwrite ? 1 : 2)),
-       prof_ && prof_->detail() ? "n=" + std::to_string(n) + " nsrc=" + std::to_string(ns) +
-                                      " brick"
+  pend(pk, "combine_brick", 2.0 * ns * n, double(n) * sizeof(C) * (ns + (overwrite ? 1 : 2)),
+       prof_ && prof_->detail() ? std::string(name) + " n=" + std::to_string(n) +
+                                      " nsrc=" + std::to_string(ns)
                                 : std::string());
   return true;
 }
