@@ -751,6 +751,11 @@ void Engine<R>::begin() {
   // a stage abandoned inside a concurrent region (an error) leaves it here
   if (in_region_) region_leave();
   region_pending_ = false;
+  if (branch_state_ != 0) {
+    stream_ = branch_main_;
+    split_slot_ = 0;
+    branch_state_ = 0;
+  }
   arena_.reset();
   nodes_.clear();
   tape_.clear();
@@ -2004,18 +2009,52 @@ void Engine<R>::region_join() {
 }
 
 template <typename R>
+void Engine<R>::ensure_branch_stream() {
+  if (branch_) return;
+  RTCC3_CUDA(cudaStreamCreateWithFlags(&branch_, cudaStreamNonBlocking));
+  RTCC3_CUDA(cudaEventCreateWithFlags(&branch_fork_, cudaEventDisableTiming));
+  RTCC3_CUDA(cudaEventCreateWithFlags(&branch_join_, cudaEventDisableTiming));
+}
+
+template <typename R>
+void Engine<R>::branch_begin() {
+  if (!regions() || in_region_ || branch_state_ != 0) return;
+  ensure_branch_stream();
+  RTCC3_CUDA(cudaEventRecord(branch_fork_, stream_));
+  RTCC3_CUDA(cudaStreamWaitEvent(branch_, branch_fork_, 0));
+  branch_main_ = stream_;
+  stream_ = branch_;
+  split_slot_ = 4;
+  branch_state_ = 1;
+}
+
+template <typename R>
+void Engine<R>::branch_switch() {
+  if (branch_state_ != 1) return;
+  stream_ = branch_main_;
+  split_slot_ = 0;
+  branch_state_ = 2;
+}
+
+template <typename R>
+void Engine<R>::branch_join() {
+  if (branch_state_ == 0) return;
+  if (branch_state_ == 1) branch_switch();
+  RTCC3_CUDA(cudaEventRecord(branch_join_, branch_));
+  RTCC3_CUDA(cudaStreamWaitEvent(stream_, branch_join_, 0));
+  branch_state_ = 0;
+}
+
+template <typename R>
 bool Engine<R>::run_adjoints_branched(const Op& op) {
-  if (!branches_ || pool_ || (prof_ && prof_->enabled) || in_region_) return false;
+  if (!branches_ || pool_ || (prof_ && prof_->enabled) || in_region_ || branch_state_ != 0)
+    return false;
   if (op.a.node == op.b.node || !nodes_[op.a.node].needs_grad || !nodes_[op.b.node].needs_grad)
     return false;
   const Spec s = parse(op.spec);
   const std::string sa = s.c + "," + s.b + "->" + s.a, sb = s.a + "," + s.c + "->" + s.b;
   if (plan(sa, op.c, op.b, op.a).use_tc || plan(sb, op.a, op.c, op.b).use_tc) return false;
-  if (!branch_) {
-    RTCC3_CUDA(cudaStreamCreateWithFlags(&branch_, cudaStreamNonBlocking));
-    RTCC3_CUDA(cudaEventCreateWithFlags(&branch_fork_, cudaEventDisableTiming));
-    RTCC3_CUDA(cudaEventCreateWithFlags(&branch_join_, cudaEventDisableTiming));
-  }
+  ensure_branch_stream();
   RTCC3_CUDA(cudaEventRecord(branch_fork_, stream_));
   RTCC3_CUDA(cudaStreamWaitEvent(branch_, branch_fork_, 0));
   cudaStream_t main = stream_;

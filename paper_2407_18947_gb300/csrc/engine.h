@@ -287,6 +287,16 @@ class Engine {
   // three calls do nothing, while profiling, with a caller's pool or with
   // branches off.
   bool regions() const { return branches_ && !pool_ && !(prof_ && prof_->enabled); }
+  // Two-sided branch inside a stage or a custom adjoint: work issued between
+  // branch_begin() and branch_switch() runs on the branch stream (forked from
+  // the engine's stream, with its own split-K scratch), work issued between
+  // branch_switch() and branch_join() on the engine's stream concurrently,
+  // and branch_join() joins the two.  The two sides must not write the same
+  // tensor (nor the same cotangent).  Everything stays on the engine's
+  // stream when regions() is false or inside a concurrent region.
+  void branch_begin();
+  void branch_switch();
+  void branch_join();
   void region_begin();
   void region_end();
   void region_join();
@@ -367,8 +377,10 @@ class Engine {
   // reverse pass: the two adjoints of one product (different outputs, same
   // inputs) run as parallel branches (a stream of their own, forked from and
   // joined into the engine's stream, also under graph capture)
-  cudaStream_t branch_ = nullptr;
+  cudaStream_t branch_ = nullptr, branch_main_ = nullptr;
   cudaEvent_t branch_fork_ = nullptr, branch_join_ = nullptr;
+  int branch_state_ = 0;  // 1: on the branch stream, 2: back on the engine's stream
+  void ensure_branch_stream();
   bool branches_ = true;
   bool run_adjoints_branched(const Op& op);
   // reverse pass: gathers (adjoints of permuted sums) into one destination

@@ -261,10 +261,13 @@ void blocked_triples(Engine<R>& E, int o, int v, int chunk, const TriplesOperand
       if (gfield) {
         // slot densities of the symmetrised y' = P(Q) / (6 D) with t3,
         // summed over the three slots: 1/2 of one slot of P(Q) / D
-        E.exec_contract_at("ijkabc,ijkdbc->ad", 0.5, W, false, 0, T, false, 0, E.v(Dv), false, 0,
-                           true);
+        E.branch_begin();
         E.exec_contract_at("jkiabc,jklabc->li", 0.5, W, false, 0, T, false, 0, E.v(Do), false, 0,
                            true);
+        E.branch_switch();
+        E.exec_contract_at("ijkabc,ijkdbc->ad", 0.5, W, false, 0, T, false, 0, E.v(Dv), false, 0,
+                           true);
+        E.branch_join();
       }
       if (E.needs_grad(in.Ac.node))
         prod("ijkabc,Ekbc->ijaE", -1.0, {W, false, true}, {in.Bc, false, false}, {in.Ac, true, false}, i0, I, true);
@@ -404,8 +407,13 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
       const int ys = E.node(s6, false, false);
       E.exec_sym3_div(T3, true, es, E.v(ys));
       const int Dv = E.node({v, v}), Do = E.node({o, o});
-      E.exec_contract("ijkabc,ijkdbc->ad", 1.0, E.v(ys), false, T3, false, E.v(Dv), false);
+      // the two slot densities read the same tensors and write their own:
+      // as parallel branches (the vv one FP32-bound, the oo one HBM-bound)
+      E.branch_begin();
       E.exec_contract("ijkabc,ljkabc->li", 1.0, E.v(ys), false, T3, false, E.v(Do), false);
+      E.branch_switch();
+      E.exec_contract("ijkabc,ijkdbc->ad", 1.0, E.v(ys), false, T3, false, E.v(Dv), false);
+      E.branch_join();
       const int tv = E.node({v, v}), to = E.node({o, o});
       E.exec_contract("Aa,AD->aD", 1.0, SIV, false, E.v(Dv), false, E.v(tv), false);
       E.exec_contract("aD,dD->ad", -1.0, E.v(tv), false, SV, false, wvv, true);
