@@ -592,6 +592,55 @@ __global__ void __launch_bounds__(256) k_combine_brick(const BrickDesc<R> d) {
   }
 }
 
+// Several outputs of one pass over shared permuted sources (layout as
+// k_combine_brick): Y_o[blk][abc] = sum_u coef[o][u] X_u[blk][sigma_u(abc)],
+// each source element loaded once for all outputs.
+constexpr int kMultiOut = 3;
+template <typename R>
+struct BrickMultiDesc {
+  const Cx<R>* src[6];
+  int lv[6];
+  R coef[kMultiOut][6];
+  Cx<R>* y[kMultiOut];
+  int v;
+};
+
+template <typename R, int NU, int NO, int LAYOUT>
+__global__ void __launch_bounds__(256) k_combine_brick_multi(const BrickMultiDesc<R> d) {
+  const int v = d.v;
+  const unsigned v2 = unsigned(v) * unsigned(v);
+  const size_t v3 = size_t(v2) * v;
+  unsigned a, b, c0;
+  brick_coords<LAYOUT>(v, a, b, c0);
+  if (a >= unsigned(v) || b >= unsigned(v)) return;
+  const size_t blk = size_t(blockIdx.y) * v3;
+  unsigned sa[NU], sb[NU], sc[NU];
+#pragma unroll
+  for (int u = 0; u < NU; ++u) {
+    const int lv = d.lv[u];
+    const int la = lv & 3, lb = (lv >> 2) & 3, lc = (lv >> 4) & 3;
+    sa[u] = la == 0 ? 1u : (la == 1 ? unsigned(v) : v2);
+    sb[u] = lb == 0 ? 1u : (lb == 1 ? unsigned(v) : v2);
+    sc[u] = lc == 0 ? 1u : (lc == 1 ? unsigned(v) : v2);
+  }
+  for (unsigned c = c0; c < unsigned(v); c += 8) {
+    Cx<R> x[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) x[u] = d.src[u][blk + a * sa[u] + b * sb[u] + c * sc[u]];
+    const size_t out = blk + (a * v + b) * v + c;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      R re = R(0), im = R(0);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        re += d.coef[o][u] * x[u].x;
+        im += d.coef[o][u] * x[u].y;
+      }
+      d.y[o][out] = cmake<R>(re, im);
+    }
+  }
+}
+
 template <typename R>
 __global__ void k_fill(Cx<R>* p, size_t n, R re, R im) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
@@ -1625,6 +1674,125 @@ void Engine<R>::combine(std::initializer_list<std::pair<double, View>> srcs, con
   for (int s = 0; s < ns; ++s) {
     Op op{kAxpy, "", al[s], xs[s], View(), Y, EpsSpec()};
     tape_.push_back(op);  // adjoint: grad(X_s) += alpha_s grad(Y)
+  }
+}
+
+template <typename R>
+void Engine<R>::combine_multi(const std::vector<std::vector<std::pair<double, View>>>& srcs,
+                              const std::vector<View>& ys) {
+  RTCC3_CHECK(srcs.size() == ys.size() && !ys.empty(), kErrArg, "combine_multi: one source list per output");
+  // the fused pass: overwriting outputs of one dense (..., v, v, v) shape,
+  // at most six distinct sources (views of data, not cotangents) that share
+  // the leading indices and permute the last three
+  bool fused = ys.size() <= size_t(kMultiOut);
+  const View& Y0 = ys[0];
+  const int nd = Y0.nd;
+  int v = nd >= 3 ? Y0.shape[nd - 1] : 0;
+  fused = fused && nd >= 3 && v >= 4 && Y0.shape[nd - 2] == v && Y0.shape[nd - 3] == v &&
+          Y0.numel() >= (size_t(1) << 16);
+  std::vector<View> uniq;
+  BrickMultiDesc<R> d{};
+  const long long vl = v, v2 = vl * vl;
+  for (size_t o = 0; fused && o < ys.size(); ++o) {
+    const View& Y = ys[o];
+    if (Y.nd != nd) { fused = false; break; }
+    long long st = 1;
+    for (int k = nd - 1; k >= 0; --k) {
+      if (Y.shape[k] != Y0.shape[k] || Y.stride[k] != st) { fused = false; break; }
+      st *= Y.shape[k];
+    }
+    for (auto& sv : srcs[o]) {
+      if (!fused) break;
+      const View& x = sv.second;
+      if (x.nd != nd || x.node == Y.node) { fused = false; break; }
+      size_t u = 0;
+      while (u < uniq.size() && !same_view(uniq[u], x)) ++u;
+      if (u == uniq.size()) {
+        if (uniq.size() == 6) { fused = false; break; }
+        int lev[3];
+        for (int k = 0; k < nd; ++k)
+          if (x.shape[k] != Y0.shape[k] || (k < nd - 3 && x.stride[k] != Y0.stride[k])) fused = false;
+        for (int q = 0; q < 3 && fused; ++q) {
+          const long long sq = x.stride[nd - 3 + q];
+          lev[q] = sq == 1 ? 0 : (sq == vl ? 1 : (sq == v2 ? 2 : -1));
+          if (lev[q] < 0) fused = false;
+        }
+        if (!fused || lev[0] == lev[1] || lev[0] == lev[2] || lev[1] == lev[2]) { fused = false; break; }
+        d.src[u] = nodes_[x.node].data + x.off;
+        d.lv[u] = lev[0] | (lev[1] << 2) | (lev[2] << 4);
+        uniq.push_back(x);
+      }
+      d.coef[o][u] += R(sv.first);
+    }
+  }
+  const size_t nblk = fused ? Y0.numel() / size_t(v2 * vl) : 0;
+  fused = fused && nblk < 65536;
+  if (!fused) {
+    for (size_t o = 0; o < ys.size(); ++o) {
+      View xs[kMaxSrc];
+      bool xg[kMaxSrc] = {};
+      double al[kMaxSrc];
+      int ns = 0;
+      for (auto& sv : srcs[o]) {
+        RTCC3_CHECK(ns < kMaxSrc, kErrArg, "combine takes at most 8 sources");
+        xs[ns] = sv.second;
+        al[ns] = sv.first;
+        ++ns;
+      }
+      run_combine(xs, xg, al, ns, ys[o], false, true, "combine");
+    }
+  } else {
+    for (auto& x : uniq) check_view(x, 0, "combine_multi");
+    for (size_t o = 0; o < ys.size(); ++o) {
+      check_view(ys[o], 0, "combine_multi");
+      d.y[o] = nodes_[ys[o].node].data + ys[o].off;
+    }
+    d.v = v;
+    // layout by 32-byte sectors per warp and 32 elements (see run_combine_brick)
+    int b0 = 16 * int(ys.size()), b1 = 8 * int(ys.size());
+    for (auto& x : uniq) {
+      const long long sa = x.stride[nd - 3], sc = x.stride[nd - 1];
+      b0 += sc == 1 ? 16 : 8;
+      b1 += sa == 1 ? 16 : 8;
+    }
+    const int layout = b1 <= b0 ? 1 : 0;
+    const dim3 grid(unsigned((v + 3) / 4) * unsigned((v + 7) / 8), unsigned(nblk));
+    const int pk = pbegin();
+    const int nu = int(uniq.size()), no = int(ys.size());
+#define RTCC3_BM(NUV, NOV)                                                                   \
+  if (layout == 1) k_combine_brick_multi<R, NUV, NOV, 1><<<grid, 256, 0, stream_>>>(d);      \
+  else k_combine_brick_multi<R, NUV, NOV, 0><<<grid, 256, 0, stream_>>>(d)
+#define RTCC3_BMO(NUV)                                \
+  if (no == 1) { RTCC3_BM(NUV, 1); }                 \
+  else if (no == 2) { RTCC3_BM(NUV, 2); }            \
+  else { RTCC3_BM(NUV, 3); }
+    switch (nu) {
+      case 1: RTCC3_BMO(1); break;
+      case 2: RTCC3_BMO(2); break;
+      case 3: RTCC3_BMO(3); break;
+      case 4: RTCC3_BMO(4); break;
+      case 5: RTCC3_BMO(5); break;
+      default: RTCC3_BMO(6); break;
+    }
+#undef RTCC3_BMO
+#undef RTCC3_BM
+    ++launches_;
+    RTCC3_CUDA(cudaGetLastError());
+    const size_t n = Y0.numel();
+    pend(pk, "combine_brick", 2.0 * n * nu * no, double(n) * sizeof(C) * (nu + no),
+         prof_ && prof_->detail() ? "multi n=" + std::to_string(n) + " nsrc=" + std::to_string(nu) +
+                                        " nout=" + std::to_string(no)
+                                  : std::string());
+  }
+  // the tape holds one combine per output, as if each had run alone
+  for (size_t o = 0; o < ys.size(); ++o) {
+    bool g = false;
+    for (auto& sv : srcs[o]) g = g || nodes_[sv.second.node].needs_grad;
+    if (g) nodes_[ys[o].node].needs_grad = true;
+    for (auto& sv : srcs[o]) {
+      Op op{kAxpy, "", sv.first, sv.second, View(), ys[o], EpsSpec()};
+      tape_.push_back(op);
+    }
   }
 }
 

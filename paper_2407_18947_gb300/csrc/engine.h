@@ -105,6 +105,12 @@ class Engine {
   void axpy(double alpha, const View& X, const View& Y);
   // Y (+)= sum_s alpha_s X_s in one pass (up to eight strided sources).
   void combine(std::initializer_list<std::pair<double, View>> srcs, const View& Y, bool overwrite);
+  // Several overwriting combines at once (Y_o = sum_s alpha_os X_os): one
+  // pass reading each distinct source once when the outputs are dense
+  // (..., v, v, v) tensors and the sources permute their last three indices,
+  // else one combine after another; the tape records one combine per output.
+  void combine_multi(const std::vector<std::vector<std::pair<double, View>>>& srcs,
+                     const std::vector<View>& ys);
   // Y (+)= alpha P_ijk^abc X for 6-index tensors (o,o,o,v,v,v); self-adjoint.
   void sym6(double alpha, const View& X, const View& Y, bool overwrite);
   void mulc(const View& X, const View& Cst, const View& Y);

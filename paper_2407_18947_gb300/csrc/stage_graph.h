@@ -423,17 +423,18 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   }
   // ---- X1, X2 in the rotated basis ------------------------------------------------
   const View T3 = E.v(t3p);
+  // t - t(cba), 2 t^cbe - t^ceb - t^ebc and 2 t^cba - t^bca - t^abc from one
+  // pass over t3' (four distinct permuted views)
   const int dd = E.node(s6, false, false);
-  E.combine({{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}}, E.v(dd), true);
+  const int Ub = E.node(s6, false, false);
+  const int Uc = E.node(s6, false, false);
+  E.combine_multi({{{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}},
+                   {{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
+                   {{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}}},
+                  {E.v(dd), E.v(Ub), E.v(Uc)});
   E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), Lp, E.v(X1p), false);
   E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), Fp, E.v(S3p), false);
-  const int Ub = E.node(s6, false, false);
-  E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
-            E.v(Ub), true);
   E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), Gb, E.v(S3p), true);
-  const int Uc = E.node(s6, false, false);
-  E.combine({{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}},
-            E.v(Uc), true);
   E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), Gc, E.v(S3p), true);
   }
   // ---- rotate the results back: X = (S_o x S_v) X' -----------------------------
@@ -714,20 +715,19 @@ StageNodes record_stage(Engine<R>& E, const Hamil<R>& H, const StageOptions& opt
       const View T3 = E.v(t3);
       // X1 (Eq. A21) and X2 (Eq. A22)
       const int dd = E.node(s6, false, false);  // t_ijk^abc - t_ijk^cba
-      E.combine({{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}}, E.v(dd), true);
+      const int Ub = E.node(s6, false, false);  // 2 t^cbe - t^ceb - t^ebc  as [ijk cbe]
+      const int Uc = E.node(s6, false, false);  // 2 t_mjk^cba - t_mjk^bca - t_mjk^abc
+      E.combine_multi({{{1.0, T3}, {-1.0, E.ev("ijkcba->ijkabc", T3)}},
+                       {{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
+                       {{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}}},
+                      {E.v(dd), E.v(Ub), E.v(Uc)});
       const int Ljk = E.node({o, o, v, v}, false, false);
       E.combine({{2.0, E.ev("jbkc->jkbc", G("ovov"))}, {-1.0, E.ev("jckb->jkbc", G("ovov"))}},
                 E.v(Ljk), true);
       E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), E.v(Ljk), R1, true);
       const int S3 = E.node({o, o, v, v}, false, false);
       E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), F("ov"), E.v(S3), false);
-      const int Ub = E.node(s6, false, false);  // 2 t^cbe - t^ceb - t^ebc  as [ijk cbe]
-      E.combine({{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
-                E.v(Ub), true);
       E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), G("vvov"), E.v(S3), true);
-      const int Uc = E.node(s6, false, false);  // 2 t_mjk^cba - t_mjk^bca - t_mjk^abc
-      E.combine({{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}},
-                E.v(Uc), true);
       E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), G("ooov"), E.v(S3), true);
       E.axpy(1.0, E.v(S3), SD);
     }
