@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256)
 k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx, long long offy,
            const R* __restrict__ osum, const R* __restrict__ vsum, const Cx<R>* __restrict__ osum_c,
            const Cx<R>* __restrict__ vsum_c, const int* __restrict__ order, int o, int v, R alpha,
-           int overwrite, const FastDiv fv2, const FastDiv fv) {
+           int overwrite, const FastDiv fv2, const FastDiv fv, Cx<R>* __restrict__ Y3) {
   const int ijk = order ? order[blockIdx.y] : int(blockIdx.y);
   const int i = ijk / (o * o), j = (ijk / o) % o, k = ijk % o;
   const unsigned v2 = unsigned(v) * v, v3 = v2 * v;
@@ -159,6 +159,9 @@ k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx, l
   const Cx<R>* b4 = X + offx + O(k, i, j);
   const Cx<R>* b5 = X + offx + O(j, k, i);
   Cx<R>* yb = Y + offy + O(i, j, k);
+  // NP = 6 with Y3: also Y3 = (x0 + x1 + x3) / D, the NP = 3 sum of the same
+  // sources (overwritten; dense, no offset)
+  Cx<R>* y3b = Y3 ? Y3 + O(i, j, k) : nullptr;
   auto V = [&](unsigned x, unsigned y, unsigned z) { return (x * v + y) * v + z; };
   auto element = [&](unsigned a, unsigned b, unsigned c, unsigned abc) {
     const Cx<R> x0 = b0[abc];
@@ -171,6 +174,23 @@ k_sym6_div(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, long long offx, l
       const Cx<R> x5 = b5[V(b, c, a)];
       sr = alpha * (((x0.x + x1.x) + (x2.x + x3.x)) + (x4.x + x5.x));
       si = alpha * (((x0.y + x1.y) + (x2.y + x3.y)) + (x4.y + x5.y));
+      if (y3b) {
+        const R tr = (x0.x + x1.x) + x3.x, ti = (x0.y + x1.y) + x3.y;
+        Cx<R> z;
+        if (CPLX) {
+          const Cx<R> vs = vsum_c[abc], os = osum_c[ijk];
+          const R dr = vs.x - os.x, di = vs.y - os.y;
+          const R m = R(1) / (dr * dr + di * di);
+          const R ir = dr * m, ii = -di * m;
+          z.x = tr * ir - ti * ii;
+          z.y = tr * ii + ti * ir;
+        } else {
+          const R inv = R(1) / (vsum[abc] - osum[ijk]);
+          z.x = tr * inv;
+          z.y = ti * inv;
+        }
+        y3b[abc] = z;
+      }
     } else {
       // identity, (ij)(ab) and (ik)(ac): the three slot exchanges with slot 1
       sr = alpha * ((x0.x + x1.x) + x3.x);
@@ -1816,9 +1836,10 @@ void Engine<R>::sym6_div(double alpha, const View& X, const EpsSpec& es, const V
 
 template <typename R>
 void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y,
-                             bool yg, bool overwrite, int np) {
+                             bool yg, bool overwrite, int np, const View* Y3) {
   check_view(X, 0, "sym6_div");
   check_view(Y, 0, "sym6_div");
+  if (Y3) check_view(*Y3, 0, "sym6_div");
   const bool cplx = es.osum_cr && es.vsum_cr;
   RTCC3_CHECK(cplx || (es.osum_r && es.vsum_r), kErrArg, "sym6_div needs denominator sum tables");
   auto dense6 = [&](const View& w) {
@@ -1832,8 +1853,10 @@ void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec
     return true;
   };
   RTCC3_CHECK(dense6(X) && dense6(Y), kErrArg, "sym6_div needs dense triples views");
+  RTCC3_CHECK(!Y3 || (np == 6 && dense6(*Y3) && Y3->off == 0), kErrArg,
+              "sym6_div: the three-term output needs NP = 6 and a dense tensor");
   if (xg && !nodes_[X.node].grad_ready) {
-    if (!overwrite) return;  // zero cotangent
+    if (!overwrite && !Y3) return;  // zero cotangent
     zero_grad_if_unset(X.node);
   }
   if (yg) overwrite = !begin_grad_write(Y, !overwrite);
@@ -1854,7 +1877,8 @@ void Engine<R>::run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec
 #define RTCC3_S6D(CP, NPV)                                                                         \
   k_sym6_div<R, CP, NPV><<<grid, 256, 0, stream_>>>(px, py, X.off, Y.off, es.osum_r, es.vsum_r,     \
                                                     es.osum_cr, es.vsum_cr, es.order, es.o, es.v,  \
-                                                    R(alpha), overwrite ? 1 : 0, fv2, fv)
+                                                    R(alpha), overwrite ? 1 : 0, fv2, fv,    \
+                                                    Y3 ? nodes_[Y3->node].data : nullptr)
   if (cplx) {
     if (np == 6) RTCC3_S6D(true, 6);
     else RTCC3_S6D(true, 3);

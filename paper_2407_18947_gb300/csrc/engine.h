@@ -194,6 +194,17 @@ class Engine {
   }
   // Y = (X + X(jik,bac) + X(kji,cba)) / D over dense triples (X on its data
   // or gradient buffer; untaped; es with FP64 sum tables).
+  // The forward of sym6_div without recording it (the caller's custom
+  // adjoint then owns its reverse), and that reverse fused with the
+  // three-term sum of the same cotangent: grad(X) (+)= alpha P6(grad(Y)) / D
+  // and Y3 = P3(grad(Y)) / D (data of a dense node) in one pass.
+  void exec_sym6_div(double alpha, const View& X, const EpsSpec& es, const View& Y) {
+    run_sym6_div(alpha, X, false, es, Y, false, true, 6);
+  }
+  void exec_sym6_div_adjoint_pair(double alpha, const View& Yg, const EpsSpec& es, const View& Xg,
+                                  const View& Y3) {
+    run_sym6_div(alpha, Yg, true, es, Xg, true, false, 6, &Y3);
+  }
   void exec_sym3_div(const View& X, bool xg, const EpsSpec& es, const View& Y) {
     run_sym6_div(1.0, X, xg, es, Y, false, true, 3);
   }
@@ -354,7 +365,7 @@ class Engine {
                          const View& Y, bool yg, bool overwrite, const char* name);
   void run_sym6(double alpha, const View& X, bool xg, const View& Y, bool yg, bool overwrite);
   void run_sym6_div(double alpha, const View& X, bool xg, const EpsSpec& es, const View& Y, bool yg,
-                    bool overwrite, int np);
+                    bool overwrite, int np, const View* Y3 = nullptr);
   void run_contract(const std::string& spec, double alpha, const View& A, bool a_grad, const View& B,
                     bool b_grad, const View& Cv, bool c_grad, bool accumulate, long long sa = 0,
                     long long sb = 0, long long sc = 0);

@@ -393,11 +393,20 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
   E.contract("imab,mjck->ijkabc", -1.0, T2p, G2p, E.v(Z), true);
   // ---- t3' = -P(Z) / D' with the complex denominators ---------------------------
   t3p = E.node(s6, false, false);
-  E.sym6_div(-1.0, E.v(Z), es, E.v(t3p));
   const int wtn = wt;
+  // with the field adjoint below, it also takes over the reverse of the
+  // symmetrised division: both read the six permutations of grad(t3'), so
+  // grad(Z) and ys come from one pass
+  const bool pair = E.needs_grad(Z) && E.needs_grad(wtn);
+  if (pair) {
+    E.exec_sym6_div(-1.0, E.v(Z), es, E.v(t3p));
+    E.set_needs_grad(t3p, true);
+  } else {
+    E.sym6_div(-1.0, E.v(Z), es, E.v(t3p));
+  }
   if (E.needs_grad(t3p) && E.needs_grad(wtn)) {
     const View wvv = blk(wt, "vv"), woo = blk(wt, "oo");
-    E.custom([&E, t3p, wtn, es, s6, SO, SIO, SV, SIV, wvv, woo, o, v]() {
+    E.custom([&E, t3p, wtn, Z, pair, es, s6, SO, SIO, SV, SIV, wvv, woo, o, v]() {
       if (!E.needs_grad(t3p) || !E.needs_grad(wtn)) return;
       const View T3 = E.v(t3p);
       // y' = grad(t3') / D'; t3' is invariant under the simultaneous
@@ -405,7 +414,8 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
       // slot-1 densities of the permuted y': ys = y' + y'(jik,bac) + y'(kji,cba)
       // (D' is invariant too, so ys is formed from grad(t3') in one pass)
       const int ys = E.node(s6, false, false);
-      E.exec_sym3_div(T3, true, es, E.v(ys));
+      if (pair) E.exec_sym6_div_adjoint_pair(-1.0, T3, es, E.v(Z), E.v(ys));
+      else E.exec_sym3_div(T3, true, es, E.v(ys));
       const int Dv = E.node({v, v}), Do = E.node({o, o});
       // the two slot densities read the same tensors and write their own:
       // as parallel branches (the vv one FP32-bound, the oo one HBM-bound)
