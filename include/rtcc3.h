@@ -108,6 +108,11 @@ typedef struct rtcc3_options {
                         an overrun); no CUDA graphs.  Independently of this,
                         every operation's index ranges are checked on the
                         host against its tensors before it is launched       */
+  int serial;        /* 1: every operation of a stage on the context's one
+                        stream in recording order; 0 (default): independent
+                        work (the two adjoints of a CUDA-core product, the
+                        CCSD part beside the triples) on streams of its own,
+                        joined before its results are read                    */
 } rtcc3_options;
 
 /* Fill *opt with defaults (FP64, triples on, device 0, graphs on, automatic

@@ -28,7 +28,8 @@ class Options(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("field_tol", ctypes.c_double),
                 ("field_solver", ctypes.c_int), ("triples_chunk", ctypes.c_int),
                 ("spin_budget", ctypes.c_longlong), ("eig_sweep_cap", ctypes.c_int),
-                ("tc_scope", ctypes.c_int), ("storage", ctypes.c_int), ("checked", ctypes.c_int)]
+                ("tc_scope", ctypes.c_int), ("storage", ctypes.c_int), ("checked", ctypes.c_int),
+                ("serial", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):

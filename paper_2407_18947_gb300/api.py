@@ -32,7 +32,7 @@ class RTCC3:
                  triples: bool = True, device: int = 0, use_graphs: bool = True,
                  field_tol: float = 0.0, field_solver: int = 0, triples_chunk: int = 0,
                  spin_budget: int = 0, eig_sweep_cap: int = 0, storage_c64: bool = False,
-                 tc_scope: int = 0, checked: bool = False):
+                 tc_scope: int = 0, checked: bool = False, serial: bool = False):
         self.lib = _lib.load()
         self.nocc, self.nvir, self.nbatch = nocc, nvir, nbatch
         opt = _lib.Options()
@@ -49,6 +49,7 @@ class RTCC3:
         opt.storage = 1 if storage_c64 else 0
         opt.tc_scope = int(tc_scope)
         opt.checked = 1 if checked else 0
+        opt.serial = 1 if serial else 0
         h = ctypes.c_void_p()
         rc = self.lib.rtcc3_create(nocc, nvir, nbatch, ctypes.byref(opt), ctypes.byref(h))
         if rc != 0:

@@ -435,6 +435,7 @@ void setup_runner(rtcc3_ctx* ctx, const double* Lfac) {
   rn->E.set_profiler(&ctx->prof);
   rn->E.set_wait_budget(ctx->opt.spin_budget);
   rn->E.set_checked(ctx->opt.checked != 0);
+  rn->E.set_branches(ctx->opt.serial == 0);
   rn->E.set_eig_sweep_cap(ctx->opt.eig_sweep_cap);
   if (ctx->opt.precision == RTCC3_PREC_TF32) rn->E.set_tensor_cores(4);
   if (ctx->opt.precision == RTCC3_PREC_BF16) rn->E.set_tensor_cores(2);
@@ -1072,6 +1073,7 @@ void rtcc3_default_options(rtcc3_options* opt) {
   opt->storage = RTCC3_STORAGE_C128;
   opt->tc_scope = 0;
   opt->checked = 0;
+  opt->serial = 0;
 }
 
 int rtcc3_create(int nocc, int nvir, int nbatch, const rtcc3_options* opt, rtcc3_ctx** out) {

@@ -215,6 +215,35 @@ def test_chunked_trajectory_equals_one_call(water1, graphs):
         assert _rel(a, b) < 1e-12
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (2, 1e-6)])
+def test_concurrent_streams_equal_serial(water1, precision, tol):
+    """The concurrent branches (the two adjoints of each CUDA-core product,
+    the CCSD part beside the triples, the field-density pair) give the serial
+    results: residuals of one stage and a three-step captured propagation
+    (FP64 to rounding, TF32 within its stage tolerance)."""
+    s, ham, y0 = water1
+    amps = [x.numpy() for x in y0]
+    out = {}
+    for serial in (False, True):
+        from paper_2407_18947_gb300.api import RTCC3
+        eng = RTCC3(s.nocc, s.nvir, precision=precision, serial=serial)
+        eng.set_hamiltonian(s.eps, s.Lfac, s.dipole)
+        eng.set_field(0, 2, 0.002, omega=0.0656, direction=(0.2, 0.0, 1.0))
+        eng.set_amplitudes(0, *amps)
+        res = eng.compute_residuals(0, 0.1)
+        dip, en = eng.propagate_rk4(0.01, 3)
+        out[serial] = (res, dip, en)
+        eng.close()
+    (r0, d0, e0), (r1, d1, e1) = out[False], out[True]
+    for k in ("r_t1", "r_t2", "r_l1", "r_l2"):
+        if precision == 0:
+            assert _rel(r0[k], r1[k]) < tol, k
+        else:
+            assert np.abs(r0[k] - r1[k]).max() < tol, k
+    assert np.abs(d0 - d1).max() < (1e-12 if precision == 0 else 1e-7)
+    assert np.abs(e0 - e1).max() < (1e-11 if precision == 0 else 1e-6)
+
+
 def test_nonfinite_state_is_reported(water1):
     s, ham, y0 = water1
     eng = _engine(s)
