@@ -661,6 +661,46 @@ __global__ void __launch_bounds__(256) k_combine_brick_multi(const BrickMultiDes
   }
 }
 
+// Y[ijk][abc] (+)= a1 x1[i,a] y1[j,k,b,c] + a2 x2[i,j,a,b] y2[k,c] over
+// dense (o,o,o,v,v,v): the two outer products of the adjoints of X1 and of
+// the first X2 term (Eqs. A21-A22) in one pass (a term with a zero
+// coefficient is not read).  One block row per (i,j,k), consecutive threads
+// on consecutive abc.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_outer_pair(Cx<R>* __restrict__ Y, const Cx<R>* __restrict__ x1, const Cx<R>* __restrict__ y1,
+             const Cx<R>* __restrict__ x2, const Cx<R>* __restrict__ y2, R a1, R a2, int o, int v,
+             int accumulate, const FastDiv fv2, const FastDiv fv) {
+  const int ijk = blockIdx.y;
+  const int i = ijk / (o * o), j = (ijk / o) % o, k = ijk % o;
+  const unsigned v2 = unsigned(v) * v, v3 = v2 * v;
+  Cx<R>* yb = Y + size_t(ijk) * v3;
+  const Cx<R>* x1i = x1 + size_t(i) * v;
+  const Cx<R>* y1jk = y1 + (size_t(j) * o + k) * v2;
+  const Cx<R>* x2ij = x2 + (size_t(i) * o + j) * v2;
+  const Cx<R>* y2k = y2 + size_t(k) * v;
+  for (unsigned abc = blockIdx.x * blockDim.x + threadIdx.x; abc < v3; abc += gridDim.x * blockDim.x) {
+    const unsigned a = fv2.div(abc), bc = abc - a * v2, b = fv.div(bc), c = bc - b * v;
+    R re = R(0), im = R(0);
+    if (a1 != R(0)) {
+      const Cx<R> p = x1i[a], q = y1jk[bc];
+      re += a1 * (p.x * q.x - p.y * q.y);
+      im += a1 * (p.x * q.y + p.y * q.x);
+    }
+    if (a2 != R(0)) {
+      const Cx<R> p = x2ij[a * v + b], q = y2k[c];
+      re += a2 * (p.x * q.x - p.y * q.y);
+      im += a2 * (p.x * q.y + p.y * q.x);
+    }
+    if (accumulate) {
+      const Cx<R> y = yb[abc];
+      re += y.x;
+      im += y.y;
+    }
+    yb[abc] = cmake<R>(re, im);
+  }
+}
+
 template <typename R>
 __global__ void k_fill(Cx<R>* p, size_t n, R re, R im) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
@@ -1814,6 +1854,47 @@ void Engine<R>::combine_multi(const std::vector<std::vector<std::pair<double, Vi
       tape_.push_back(op);
     }
   }
+}
+
+template <typename R>
+void Engine<R>::exec_outer_pair(double a1, const View& x1g, const View& y1, double a2,
+                                const View& x2g, const View& y2, const View& dstg) {
+  auto dense = [](const View& w, std::initializer_list<int> dims) {
+    if (w.nd != int(dims.size())) return false;
+    long long st = 1;
+    int k = w.nd - 1;
+    std::vector<int> d(dims);
+    for (; k >= 0; --k) {
+      if (w.shape[k] != d[k] || w.stride[k] != st) return false;
+      st *= d[k];
+    }
+    return true;
+  };
+  const int o = dstg.shape[0], v = dstg.shape[3];
+  RTCC3_CHECK(dense(dstg, {o, o, o, v, v, v}) && dense(x1g, {o, v}) && dense(y1, {o, o, v, v}) &&
+                  dense(x2g, {o, o, v, v}) && dense(y2, {o, v}) && dstg.off == 0,
+              kErrArg, "outer_pair needs dense operands");
+  check_view(x1g, 0, "outer_pair");
+  check_view(y1, 0, "outer_pair");
+  check_view(x2g, 0, "outer_pair");
+  check_view(y2, 0, "outer_pair");
+  check_view(dstg, 0, "outer_pair");
+  if (a1 == 0.0 && a2 == 0.0) return;
+  const bool acc = begin_grad_write(dstg, true);
+  const unsigned v2 = unsigned(v) * unsigned(v), v3 = v2 * unsigned(v);
+  RTCC3_CHECK(size_t(o) * o * o < 65536u, kErrArg, "outer_pair: too many occupied blocks");
+  const dim3 grid(std::max(1u, (v3 + 1023u) / 1024u), unsigned(o) * o * o);
+  const int pk = pbegin();
+  k_outer_pair<R><<<grid, 256, 0, stream_>>>(
+      nodes_[dstg.node].grad, a1 != 0.0 ? nodes_[x1g.node].grad + x1g.off : nullptr,
+      nodes_[y1.node].data + y1.off, a2 != 0.0 ? nodes_[x2g.node].grad + x2g.off : nullptr,
+      nodes_[y2.node].data + y2.off, R(a1), R(a2), o, v, acc ? 1 : 0, FastDiv(v2),
+      FastDiv(unsigned(v)));
+  ++launches_;
+  RTCC3_CUDA(cudaGetLastError());
+  const double n = double(dstg.numel());
+  pend(pk, sizeof(R) == 8 ? "contract_outer_c128" : "contract_outer_c64", 16.0 * n,
+       n * sizeof(C) * (acc ? 2.0 : 1.0));
 }
 
 template <typename R>

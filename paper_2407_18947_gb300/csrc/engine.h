@@ -205,6 +205,11 @@ class Engine {
                                   const View& Y3) {
     run_sym6_div(alpha, Yg, true, es, Xg, true, false, 6, &Y3);
   }
+  // grad(dst) (+)= a1 grad(x1)[i,a] y1[j,k,b,c] + a2 grad(x2)[i,j,a,b] y2[k,c]
+  // over dense (o,o,o,v,v,v) in one pass (untaped; a zero coefficient drops
+  // its term unread).
+  void exec_outer_pair(double a1, const View& x1g, const View& y1, double a2, const View& x2g,
+                       const View& y2, const View& dstg);
   void exec_sym3_div(const View& X, bool xg, const EpsSpec& es, const View& Y) {
     run_sym6_div(1.0, X, xg, es, Y, false, true, 3);
   }

@@ -442,8 +442,27 @@ int rotated_triples(Engine<R>& E, const Hamil<R>& H, const View& T, int wt, cons
                    {{2.0, T3}, {-1.0, E.ev("ijkxzy->ijkxyz", T3)}, {-1.0, E.ev("ijkzyx->ijkxyz", T3)}},
                    {{2.0, T3}, {-1.0, E.ev("mjkyxz->mjkxyz", T3)}, {-1.0, E.ev("mjkzyx->mjkxyz", T3)}}},
                   {E.v(dd), E.v(Ub), E.v(Uc)});
-  E.contract("ijkabc,jkbc->ia", 1.0, E.v(dd), Lp, E.v(X1p), false);
-  E.contract("ijkabc,kc->ijab", 1.0, E.v(dd), Fp, E.v(S3p), false);
+  // X1 = sum dd Lp (Eq. A21) and the first term of X2, S3 = sum dd Fp
+  // (Eq. A22), as one operation whose reverse writes grad(dd) =
+  // gX1 x Lp + gS3 x Fp in one pass (as two products, the second outer
+  // product re-reads the first one's output)
+  E.exec_contract_at("ijkabc,jkbc->ia", 1.0, E.v(dd), false, 0, Lp, false, 0, E.v(X1p), false, 0,
+                     false);
+  E.exec_contract_at("ijkabc,kc->ijab", 1.0, E.v(dd), false, 0, Fp, false, 0, E.v(S3p), false, 0,
+                     false);
+  {
+    const bool gd = E.needs_grad(dd), gl = E.needs_grad(Lp.node), gf = E.needs_grad(Fp.node);
+    if (gd || gl) E.set_needs_grad(X1p, true);
+    if (gd || gf) E.set_needs_grad(S3p, true);
+    if (gd || gl || gf)
+      E.custom([&E, dd, Lp, Fp, X1p, S3p, gd, gl, gf]() {
+        const bool hx = E.grad_ready(X1p), hs = E.grad_ready(S3p);
+        if (gd)
+          E.exec_outer_pair(hx ? 1.0 : 0.0, E.v(X1p), Lp, hs ? 1.0 : 0.0, E.v(S3p), Fp, E.v(dd));
+        if (gl) E.exec_contract("ijkabc,ia->jkbc", 1.0, E.v(dd), false, E.v(X1p), true, Lp, true);
+        if (gf) E.exec_contract("ijkabc,ijab->kc", 1.0, E.v(dd), false, E.v(S3p), true, Fp, true);
+      }, true);
+  }
   E.contract("ijkcbe,acke->ijab", 1.0, E.v(Ub), Gb, E.v(S3p), true);
   E.contract("mjkcba,kimc->ijab", -1.0, E.v(Uc), Gc, E.v(S3p), true);
   }
