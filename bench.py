@@ -119,13 +119,16 @@ class ClockSampler:
 # that runs them, with the roofline that bounds that kernel.
 KERNEL_FAMILIES = {
     "k_combine_nd": (("combine", "axpy_gather", "axpy_strided", "copy", "sym6"), "hbm"),
-    # the o^3 v^3 permuted sums in the brick thread layout
+    # the o^3 v^3 permuted sums in the brick thread layouts (k_combine_brick
+    # and its several-output form k_combine_brick_multi)
     "k_combine_brick": (("combine_brick",), "hbm"),
     "k_tc_gemm": (("contract_tc_tf32", "contract_tc_bf16"), "tensor"),
     # long sums reading the o^3 v^3 operand from its source (tcgen05, TF32
     # split): N = 10 or 38 complex columns, ~N flop per byte, HBM-bound
     "k_tc_gemm_direct": (("contract_tc_direct_tf32",), "hbm"),
     "k_outer": (("contract_outer_c64", "contract_outer_c128"), "hbm"),
+    # the two outer products of the X1 / X2 adjoints in one pass
+    "k_outer_pair": (("outer_pair",), "hbm"),
     "k_contract": (("contract_simt_c64", "contract_simt_c128"), "alu"),
     "k_sym6_div": (("sym6_div", "sym3_div"), "hbm"),
     "k_pack": (("tc_pack",), "hbm"),
@@ -143,13 +146,13 @@ KERNEL_FAMILIES = {
 MEASURED_TRAFFIC = {
     ("k_contract", "tf32", 2): 2.86e6,
     ("k_combine_nd", "tf32", 2): 3.61e6,
-    ("k_combine_brick", "tf32", 2): 1061.54e6,
-    ("k_sym6_div", "tf32", 2): 844.50e6,
+    ("k_combine_brick", "tf32", 2): 1755.6e6,
+    ("k_sym6_div", "tf32", 2): 1070.54e6,
     ("k_reduce_small", "tf32", 2): 149.09e6,
-    ("k_tc_gemm", "tf32", 2): 518.05e6,
-    ("k_tc_gemm_direct", "tf32", 2): 485.19e6,
-    ("k_outer", "tf32", 2): 201.64e6,
-    ("k_gemv", "tf32", 2): 221.79e6,
+    ("k_tc_gemm", "tf32", 2): 517.74e6,
+    ("k_tc_gemm_direct", "tf32", 2): 485.34e6,
+    ("k_outer_pair", "tf32", 2): 377.12e6,
+    ("k_gemv", "tf32", 2): 221.78e6,
     ("k_pack", "tf32", 2): 2.01e6,
 }
 

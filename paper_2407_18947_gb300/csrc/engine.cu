@@ -1893,8 +1893,7 @@ void Engine<R>::exec_outer_pair(double a1, const View& x1g, const View& y1, doub
   ++launches_;
   RTCC3_CUDA(cudaGetLastError());
   const double n = double(dstg.numel());
-  pend(pk, sizeof(R) == 8 ? "contract_outer_c128" : "contract_outer_c64", 16.0 * n,
-       n * sizeof(C) * (acc ? 2.0 : 1.0));
+  pend(pk, "outer_pair", 16.0 * n, n * sizeof(C) * (acc ? 2.0 : 1.0));
 }
 
 template <typename R>
