@@ -468,7 +468,7 @@ __global__ void k_div_eps(const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y, St
 
 // Y[.] (+)= sum_s alpha_s X_s[.] over Y's shape: up to kMaxSrc strided
 // sources, one pass, coalesced on Y (threads walk Y's last index fastest).
-constexpr int kMaxSrc = 8;
+constexpr int kMaxSrc = kCombineSources;
 template <typename R>
 struct CombDesc {
   int nd, nsrc, overwrite;
@@ -2349,7 +2349,6 @@ bool Engine<R>::run_adjoints_branched(const Op& op) {
 
 template <typename R>
 void Engine<R>::defer_gather(const View* xs, const double* al, int ns, const View& dst) {
-  static_assert(kMaxSrc == 8, "pending gather capacity");
   for (size_t k = 0; k < gathers_.size(); ++k) {
     PendingGather& p = gathers_[k];
     if (!same_view(p.dst, dst)) continue;

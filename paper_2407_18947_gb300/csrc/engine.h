@@ -23,6 +23,10 @@
 
 namespace rtcc3 {
 
+// Most sources one pass of a combine (and one merged reverse-pass gather)
+// sums.
+constexpr int kCombineSources = 8;
+
 constexpr int kMaxDim = 8;
 
 struct View {
@@ -221,11 +225,12 @@ class Engine {
   // Y (+)= sum_s alpha_s X_s over data buffers (untaped).
   void exec_combine(std::initializer_list<std::pair<double, View>> srcs, const View& Y,
                     bool overwrite) {
-    View xs[6];
-    bool xg[6] = {false, false, false, false, false, false};
-    double al[6];
+    View xs[kCombineSources];
+    bool xg[kCombineSources] = {};
+    double al[kCombineSources];
     int ns = 0;
     for (auto& s : srcs) {
+      RTCC3_CHECK(ns < kCombineSources, kErrArg, "combine takes at most 8 sources");
       xs[ns] = s.second;
       al[ns] = s.first;
       ++ns;
@@ -411,8 +416,8 @@ class Engine {
   struct PendingGather {
     View dst;
     int ns = 0;
-    View xs[8];
-    double al[8];
+    View xs[kCombineSources];
+    double al[kCombineSources];
   };
   std::vector<PendingGather> gathers_;
   void defer_gather(const View* xs, const double* al, int ns, const View& dst);
