@@ -1548,11 +1548,16 @@ void Engine<R>::run_combine(const View* xs, const bool* xg, const double* alphas
   int nd = Y.nd;
   int shape[kMaxDim];
   long long sy[kMaxDim], sx[kMaxSrc][kMaxDim];
+  // stable insertion sort of the (at most kMaxDim) dims by decreasing |stride|
   int ord[kMaxDim];
-  for (int k = 0; k < nd; ++k) ord[k] = k;
-  std::stable_sort(ord, ord + nd, [&](int p, int q) {
-    return std::llabs(Y.stride[p]) > std::llabs(Y.stride[q]);
-  });
+  for (int k = 0; k < nd; ++k) {
+    int m = k;
+    while (m > 0 && std::llabs(Y.stride[ord[m - 1]]) < std::llabs(Y.stride[k])) {
+      ord[m] = ord[m - 1];
+      --m;
+    }
+    ord[m] = k;
+  }
   for (int k = 0; k < nd; ++k) {
     shape[k] = Y.shape[ord[k]];
     sy[k] = Y.stride[ord[k]];
@@ -1718,7 +1723,7 @@ void Engine<R>::combine(std::initializer_list<std::pair<double, View>> srcs, con
                         bool overwrite) {
   View xs[kMaxSrc];
   bool xg[kMaxSrc] = {};
-  double al[kMaxSrc];
+  double al[kMaxSrc] = {};
   int ns = 0;
   bool g = false;
   for (auto& s : srcs) {
@@ -2430,7 +2435,6 @@ void Engine<R>::backward() {
           continue;
         }
         View xs[kMaxSrc];
-        bool xg[kMaxSrc];
         double al[kMaxSrc];
         int ns = 0;
         for (size_t j = i; j < run.size() && ns < kMaxSrc; ++j) {
@@ -2438,7 +2442,6 @@ void Engine<R>::backward() {
           View dj, sj;
           if (!invert_view(run[j]->a, run[j]->c, dj, sj) || !same_view(dj, dense)) continue;
           xs[ns] = sj;
-          xg[ns] = true;
           al[ns] = run[j]->alpha;
           ++ns;
           done[j] = true;
