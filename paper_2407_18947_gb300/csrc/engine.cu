@@ -863,6 +863,7 @@ void Engine<R>::begin() {
   if (branch_state_ != 0) {
     stream_ = branch_main_;
     split_slot_ = 0;
+    tc_slot_ = 1;
     branch_state_ = 0;
   }
   arena_.reset();
@@ -1447,11 +1448,12 @@ void Engine<R>::run_contract_tc(ContractPlan& P, double alpha, const C* pa, cons
     const bool direct = tc_direct(op, P.tc_nsplit);
     op.a_tiled = !direct && tc_chained(op, P.tc_nsplit);
     const size_t a_rows = op.a_tiled ? size_t((op.M + 127) / 128) * 128 : size_t(op.M);
-    void* apk = direct ? nullptr : scratch(1, a_rows * op.Kp * tc_eb_);
-    void* bpk = scratch(2, size_t(2 * op.N) * op.Kp * tc_eb_ * (op.split ? 2 : 1));
+    void* apk = direct ? nullptr : scratch(tc_slot_, a_rows * op.Kp * tc_eb_);
+    void* bpk = scratch(tc_slot_ + 1, size_t(2 * op.N) * op.Kp * tc_eb_ * (op.split ? 2 : 1));
     float* part = nullptr;
     if (P.tc_nsplit > 1)
-      part = static_cast<float*>(scratch(3, size_t(P.tc_nsplit) * op.M * 2 * op.N * sizeof(float)));
+      part = static_cast<float*>(
+          scratch(tc_slot_ + 2, size_t(P.tc_nsplit) * op.M * 2 * op.N * sizeof(float)));
     int* err = error_flag();
     const bool a_kc = sw ? P.b_kcontig : P.a_kcontig;
     const double rows_packed = direct ? 2.0 * op.N : op.M + 2.0 * op.N;
@@ -2234,9 +2236,9 @@ void Engine<R>::exec_slab_div(double alpha, const View& X, int i0, const EpsSpec
 }
 
 // The adjoints dA = dC . B and dB = A . dC of one product read the same
-// inputs and write different cotangents: when both run on CUDA cores they
-// are launched as two branches (dB on the branch stream with its own split-K
-// scratch, dA on the engine's stream) that join before the next operation.
+// inputs and write different cotangents: they are launched as two branches
+// (dB on the branch stream with its own split-K and tensor-core scratch, dA
+// on the engine's stream) that join before the next operation.
 // Not while profiling (per-operation timings stay serial), with a caller's
 // pool (one stream) or when A and B are one node (both adjoints add into it).
 template <typename R>
@@ -2302,6 +2304,7 @@ void Engine<R>::branch_begin() {
   branch_main_ = stream_;
   stream_ = branch_;
   split_slot_ = 4;
+  tc_slot_ = 6;
   branch_state_ = 1;
 }
 
@@ -2310,6 +2313,7 @@ void Engine<R>::branch_switch() {
   if (branch_state_ != 1) return;
   stream_ = branch_main_;
   split_slot_ = 0;
+  tc_slot_ = 1;
   branch_state_ = 2;
 }
 
@@ -2330,22 +2334,24 @@ bool Engine<R>::run_adjoints_branched(const Op& op) {
     return false;
   const Spec s = parse(op.spec);
   const std::string sa = s.c + "," + s.b + "->" + s.a, sb = s.a + "," + s.c + "->" + s.b;
-  if (plan(sa, op.c, op.b, op.a).use_tc || plan(sb, op.a, op.c, op.b).use_tc) return false;
   ensure_branch_stream();
   RTCC3_CUDA(cudaEventRecord(branch_fork_, stream_));
   RTCC3_CUDA(cudaStreamWaitEvent(branch_, branch_fork_, 0));
   cudaStream_t main = stream_;
   stream_ = branch_;
   split_slot_ = 4;
+  tc_slot_ = 6;
   try {
     run_contract(sb, op.alpha, op.a, false, op.c, true, op.b, true, true);
   } catch (...) {
     stream_ = main;
     split_slot_ = 0;
+    tc_slot_ = 1;
     throw;
   }
   stream_ = main;
   split_slot_ = 0;
+  tc_slot_ = 1;
   run_contract(sa, op.alpha, op.c, true, op.b, false, op.a, true, true);
   RTCC3_CUDA(cudaEventRecord(branch_join_, branch_));
   RTCC3_CUDA(cudaStreamWaitEvent(stream_, branch_join_, 0));

@@ -265,7 +265,8 @@ class Engine {
   void freeze_plans(bool f) { frozen_ = f; }
   // Persistent scratch buffers by slot: 0 split-K partials, 1/2 packed
   // tensor-core operands, 3 tensor-core split-K partials, 4 split-K partials
-  // of the reverse pass's branch stream.
+  // of the branch stream, 5 those of a concurrent region, 6-8 the branch
+  // stream's tensor-core buffers.
   void* scratch(int slot, size_t bytes);
   // Route large contractions of a complex64 graph to the tcgen05 GEMM with
   // TF32 (elem_bytes 4) or BF16 (2) operands; 0 keeps the CUDA-core kernel.
@@ -388,9 +389,12 @@ class Engine {
   std::vector<Node> nodes_;
   std::vector<Op> tape_;
   std::map<std::string, std::unique_ptr<ContractPlan>> plans_;
-  static constexpr int kScratchSlots = 6;
-  void* scratch_[kScratchSlots] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t scratch_bytes_[kScratchSlots] = {0, 0, 0, 0, 0, 0};
+  static constexpr int kScratchSlots = 9;
+  void* scratch_[kScratchSlots] = {};
+  size_t scratch_bytes_[kScratchSlots] = {};
+  // tensor-core scratch (packed A, packed B, split partials): slots 1-3 on
+  // the engine's stream, 6-8 on the branch stream
+  int tc_slot_ = 1;
   // split-K partials of CUDA-core contractions: slot 0 on the engine's
   // stream, slot 4 on the branch stream of the reverse pass, slot 5 in a
   // concurrent region
